@@ -1,0 +1,32 @@
+"""Compile the CPU oracle (test infrastructure) into oracle/_crisp_oracle.so.
+
+gcc, plain C11, -O2, no FMA contraction (the oracle's FP32 orders use explicit
+fmaf calls only), OpenMP across queries.  No architecture-specific flags: the
+same source builds on x86-64 and aarch64 and gives the same results.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "crisp_oracle.c")
+LIB = os.path.join(HERE, "_crisp_oracle.so")
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas", SRC, "-o", tmp, "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))
