@@ -1,0 +1,285 @@
+/*
+ * crisp.h -- C ABI of the GB300 (sm_103a) CRISP engine.
+ *
+ * CRISP (Correlation-Resilient Indexing via Subspace Partitioning, arXiv
+ * 2603.05180) is an approximate-nearest-neighbour index for very high
+ * dimensional vectors under squared L2.  This library builds the index on the
+ * GPU (§4.1 correlation test and rotation, §4.2 IMI k-means cells and CSR lists)
+ * and answers batches of k-NN queries with the dual-mode engine of Algorithm 1
+ * (§4.3): per-subspace partial distances, multi-sequence cell traversal,
+ * collision counting, threshold cut, and exact re-rank (Guaranteed Mode) or
+ * Hamming-ordered ADSampling with patience (Optimized Mode).
+ *
+ * Conventions for every entry point below:
+ *  - Pointers are DEVICE pointers unless the argument says "host".  The caller
+ *    owns every buffer it passes; the library owns what it allocates inside a
+ *    crisp_index and frees it in crisp_free.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated; argument errors are reported
+ *    before anything is enqueued, and then nothing is written.  Errors raised by
+ *    the device surface as CRISP_ECUDA from this or a later call.
+ *  - Row-major layouts.  Ids are 0-based row numbers of the indexed matrix X.
+ *    Distances are squared L2 (monotone in L2, §3 "Exact and Approximate
+ *    Similarity Search").
+ *  - On error, crisp_last_error() returns a message for the calling thread.
+ *
+ * Fixed readings of the paper (the library and its tests agree on them):
+ *  - tau = ceil(alpha*M - 1e-9) collisions (Theorem 1, tau = alpha M);
+ *    budget = max(1, ceil(rho*N - 1e-9)) ids per subspace (Algorithm 1).
+ *  - Subspace m covers dims [floor(mD/M), floor((m+1)D/M)); its left half is
+ *    the first floor(d_m/2) of them (§3, IMI halves).
+ *  - cell = cL*K + cR with cL, cR the nearest left/right centroid (§3 u(x)).
+ *  - Stored rows are padded with zeros to Dp = 32*ceil(D/32) dims.
+ *  - FP32 orders.  SEQ: acc = fmaf(a_i - b_i, a_i - b_i, acc) over i in order
+ *    (half distances, k-means).  GEMV: y_j = fmaf chain over d of x_d R[d][j]
+ *    (rotation).  CR32: per 32-dim block eight fmaf chains over 4 dims each,
+ *    block sum ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)), blocks summed in order
+ *    (re-rank and ADSampling distances; every ADSampling partial d_t is a
+ *    prefix of the same sum).
+ */
+#ifndef CRISP_H
+#define CRISP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crisp_index crisp_index; /* opaque; owns its device memory */
+
+typedef enum {
+    CRISP_OK = 0,
+    CRISP_EINVAL = -1,        /* invalid argument; nothing was enqueued */
+    CRISP_ENOMEM = -2,        /* device or host allocation failed */
+    CRISP_ECUDA = -3,         /* a CUDA runtime error (message in crisp_last_error) */
+    CRISP_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    CRISP_EUNSUPPORTED = -5   /* a size the kernels do not handle (e.g. K > 64) */
+} crisp_status;
+
+/* Index-build parameters (§4.1, §4.2).  The random draws of the build may be
+ * given explicitly (host arrays, copied before return); NULL means "draw from
+ * `seed`" with the library's own generator. */
+typedef struct {
+    int32_t M;                 /* subspaces, 1 <= M <= D/2 */
+    int32_t K;                 /* centroids per half, 2 <= K <= 64 (paper: 50) */
+    double tau_cev;            /* CEV threshold (paper: 0.85); rotate iff CEV > tau_cev */
+    int32_t rotate;            /* -1 decide by the CEV test, 0 never, 1 always */
+    int32_t kmeans_iters;      /* Lloyd iterations (20) */
+    int64_t kmeans_train;      /* training rows when kmeans_sample is NULL (1e5) */
+    uint64_t seed;
+    const int64_t *cev_sample;    /* host [cev_sample_n] row numbers, or NULL */
+    int64_t cev_sample_n;         /* NULL sample: min(floor(0.1N), 1e5), at least 2 */
+    const double *gaussian;       /* host [D][D] G_ij ~ N(0,1) (§3 rotation), or NULL */
+    const int64_t *kmeans_sample; /* host [kmeans_sample_n] row numbers, or NULL */
+    int64_t kmeans_sample_n;
+    const int32_t *kmeans_init;   /* host [M][2][K] positions in the k-means sample, or NULL */
+} crisp_build_params;
+
+/* Search parameters (Algorithm 1, §4.3, Table 1). */
+typedef struct {
+    int32_t k;                 /* neighbours returned (k_size), 1 <= k <= 256 */
+    int32_t mode;              /* 0 Guaranteed (phi = 0), 1 Optimized (phi = 1) */
+    double rho;                /* coverage: ids retrieved per subspace / N, in (0, 1] */
+    double alpha;              /* minimum collision fraction, in [0, 1]; tau = ceil(alpha M) */
+    int32_t patience_factor;   /* Optimized: stop after P = patience_factor*k unchanged; <= 0 off */
+    float eps0;                /* Optimized: ADSampling margin of Eq. 2 (2.1); may be +inf */
+    int64_t max_candidates;    /* 0 = no cap; else keep the cap best (V desc, id asc), cap >= k */
+} crisp_search_params;
+
+/* Per-query counters written by crisp_search (device array, may be NULL). */
+typedef struct {
+    int64_t n_candidates;      /* |C| after the cut */
+    int64_t n_verified;        /* candidates visited by the verification stage */
+    int64_t n_full;            /* full-dimension distances computed */
+    int64_t n_retrieved;       /* ids retrieved over all subspaces */
+    int32_t fallback;          /* 1 if |C| < k triggered the fallback of Stage 1 */
+    int32_t capped;            /* 1 if max_candidates cut C */
+    int32_t tau;
+    int32_t _pad;
+} crisp_query_stats;
+
+typedef struct {
+    int64_t N;
+    int32_t D, Dp, M, K, H;    /* H = widest subspace half */
+    int32_t rotated;
+    double cev;                /* CEV of the sample covariance (§4.1) */
+    int32_t max_cell;          /* largest cell population over all subspaces */
+    int32_t id_tile_log2;      /* ids per counting tile = 2^id_tile_log2 */
+    int64_t device_bytes;      /* device memory held by the index */
+    /* device arrays owned by the index (read-only for callers) */
+    const float *R32;          /* [D][D] or NULL */
+    const float *cent;         /* [M][2][K][H] */
+    const int32_t *offsets;    /* [M][K*K+1] */
+    const int32_t *ids;        /* [M][N] */
+    const float *Xr;           /* [N][Dp] */
+    const uint32_t *codes;     /* [N][Dp/32] */
+} crisp_index_info;
+
+/* ================================================================ index */
+
+/* Build the index of §4.1-§4.2 from X (device [N][D] float32, caller-owned,
+ * copied): spectral check, rotation when CEV > tau_cev (the library keeps the
+ * rotated copy and R), k-means per subspace half, cells, CSR, sign codes.
+ * Synchronises `stream` before returning.  *out receives a new index.
+ * EINVAL: N < 2, D < 2, M outside [1, D/2], K outside [2, 64], K > N. */
+crisp_status crisp_build(const float *X, int64_t N, int32_t D, const crisp_build_params *params,
+                         void *stream, crisp_index **out);
+
+/* Release an index (NULL is a no-op).  Synchronises the device first. */
+void crisp_free(crisp_index *index);
+
+/* Serialise an index into a host buffer.  With host_buf == NULL only the size
+ * is written to *bytes.  Format: a 256-byte header (magic "CRISPIX1", then
+ * int64 version=1, N, D, Dp, M, K, H, rotated, float64 CEV at byte 72), then
+ * the arrays R32 (only if rotated), cent, offsets, ids, Xr, codes of
+ * crisp_index_info, each starting at a multiple of 256 bytes.  Synchronous. */
+crisp_status crisp_index_export(const crisp_index *index, void *host_buf, size_t *bytes);
+
+/* Create an index from a blob in the export format (host memory), e.g. one
+ * written by another implementation of the method.  Synchronous. */
+crisp_status crisp_index_import(const void *host_buf, size_t bytes, void *stream, crisp_index **out);
+
+crisp_status crisp_index_get_info(const crisp_index *index, crisp_index_info *out);
+
+const char *crisp_last_error(void);
+
+/* Number of kernels this library has launched in the process so far (search
+ * path and step entry points; the index build is not counted).  For launch
+ * accounting by benchmarks; thread-safe, never resets. */
+uint64_t crisp_kernel_launches(void);
+
+/* ================================================================ search */
+
+/* Answer nq queries (Algorithm 1).  Q: device [nq][D] float32 in the original
+ * space (rotated inside when the index is rotated).  ids: device [nq][k] int64,
+ * sqdist: device [nq][k] float32, both ascending by (distance, id) and padded
+ * with -1 / +inf when fewer than k points qualify.  stats: device [nq] or NULL.
+ * Scratch comes from the stream-ordered allocator of the current device.
+ * EINVAL: k outside [1, 256] or > N, rho outside (0, 1], alpha outside [0, 1],
+ * mode outside {0, 1}, 0 < max_candidates < k, nq < 0. */
+crisp_status crisp_search(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *params,
+                          int64_t *ids, float *sqdist, crisp_query_stats *stats, void *stream);
+
+/* As crisp_search, with HOST buffers (Q [nq][D], ids [nq][k], sqdist [nq][k],
+ * stats [nq] or NULL): copies in, searches, copies out, and synchronises. */
+crisp_status crisp_search_host(const crisp_index *index, const float *Q, int32_t nq,
+                               const crisp_search_params *params, int64_t *ids, float *sqdist,
+                               crisp_query_stats *stats, void *stream);
+
+/* Device bytes of scratch crisp_search needs for nq queries (for admission). */
+crisp_status crisp_search_scratch_bytes(const crisp_index *index, int32_t nq, const crisp_search_params *params,
+                                        size_t *bytes);
+
+/* ====================================== steps of the path (one per stage) */
+
+/* B1 (§4.1): sample covariance, FP64, mean-centred, divided by S-1, of the
+ * rows X[rows[s]] (X device [N][ldx] float32, rows device [S] int64 < N).
+ * cov: device [D][D] float64.  EINVAL: S < 2, D < 1. */
+crisp_status crisp_covariance(const float *X, int64_t N, int32_t D, int32_t ldx, const int64_t *rows, int64_t S,
+                              double *cov, void *stream);
+
+/* B1 (§4.1 "Eigenvalue Decomposition"): all eigenvalues of the symmetric
+ * matrix A (device [D][D] float64, overwritten), descending, into eig (device
+ * [D] float64): Householder tridiagonalisation, then Sturm-sequence bisection. */
+crisp_status crisp_eigvalsh(double *A, int32_t D, double *eig, void *stream);
+
+/* B1: CEV = (sum of the top floor(0.2 D) eigenvalues) / (sum of all) of the
+ * sample covariance of X[rows] (§4.1).  *cev is a host double; synchronous. */
+crisp_status crisp_cev(const float *X, int64_t N, int32_t D, int32_t ldx, const int64_t *rows, int64_t S,
+                       double *cev, void *stream);
+
+/* B2 (§3 Randomized Orthogonal Rotation): R = Q diag(sign(diag R')) where
+ * G = Q R' is the Householder QR of G (device [D][D] float64, row-major,
+ * not modified).  R: device [D][D] float64. */
+crisp_status crisp_rotation_from_gaussian(const double *G, int32_t D, double *R, void *stream);
+
+/* B2 / Q1: Y = X R in the GEMV order (FP32), X device [N][ldx], R device
+ * [D][D] float32, Y device [N][ldy] with ldy >= D; columns D..ldy-1 of Y are
+ * zeroed.  Y must not overlap X. */
+crisp_status crisp_rotate_rows(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                               int32_t ldy, void *stream);
+
+/* B3 (§4.2, IMI codebooks): Lloyd's k-means over dims [off, off+h) of the S
+ * training rows T (device [S][ldt] float32): centroids start at the rows
+ * init (device [K] int32 < S) and are updated `iters` times (assignment by
+ * the SEQ distance, ties to the lowest index; means in FP64 rounded to FP32;
+ * an empty cluster keeps its centroid).  C: device [K][H] float32, columns
+ * h..H-1 zeroed. */
+crisp_status crisp_kmeans(const float *T, int64_t S, int32_t ldt, int32_t off, int32_t h, int32_t K, int32_t H,
+                          const int32_t *init, int32_t iters, float *C, void *stream);
+
+/* B3 (§3 u(x)): cells[m][n] = argmin_left*K + argmin_right of row n of Xr
+ * (device [N][Dp]) in subspace m, SEQ distances, ties to the lowest index.
+ * cent: device [M][2][K][H]; cells: device [M][N] uint16. */
+crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
+                                int32_t H, const float *cent, uint16_t *cells, void *stream);
+
+/* B4 (§4.2 CSR): for one subspace, Offsets (device [K2+1] int32) and ids
+ * (device [N] int32): ids grouped by ascending cell, ascending inside a cell.
+ * cells: device [N] uint16 < K2.  EINVAL: K2 > 4096 or N >= 2^31. */
+crisp_status crisp_csr_build(const uint16_t *cells, int64_t N, int32_t K2, int32_t *offsets, int32_t *ids,
+                             void *stream);
+
+/* B5 (§3 Binary Quantization): codes[n][w] bit b = (Xr[n][32w+b] > 0).
+ * Xr device [N][Dp] (Dp multiple of 32), codes device [N][Dp/32] uint32. */
+crisp_status crisp_sign_codes(const float *Xr, int64_t N, int32_t Dp, uint32_t *codes, void *stream);
+
+/* Q2 (Algorithm 1 "Dist1, Dist2"): for every query row of Qr (device [nq][Dp],
+ * already rotated) and subspace m, the K partial squared distances to each
+ * half's centroids (SEQ order), sorted ascending with ties by centroid index.
+ * sorted, perm: device [nq][M][2][K] (float32, int32 centroid index). */
+crisp_status crisp_half_dists(const crisp_index *index, const float *Qr, int32_t nq, float *sorted, int32_t *perm,
+                              void *stream);
+
+/* Q2+Q3 (Algorithm 1 lines 3-17, §4.3.1 multi-sequence): per query and
+ * subspace, the cells visited in ascending (cost, i, j), cost = fl(Dist1s[i] +
+ * Dist2s[j]), until the ids retrieved reach `budget` (a visited cell is
+ * consumed whole).  act: device [nq][M][K*K] int32 entries (w << 16) | cell in
+ * visit order, w = 2 if phi == 1 and rank <= k else 1; nact: device [nq][M]
+ * int32; retrieved: device [nq][M] int64 (may be NULL). */
+crisp_status crisp_activate(const crisp_index *index, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                            int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, void *stream);
+
+/* Q4+Q5 (Eq. 1 collision counting, Algorithm 1 line 20, §4.3.2 Stage 1):
+ * V[x] = sum over subspaces of the weight of the activated cell holding x;
+ * C = {x : V[x] >= tau} in ascending id; if tau >= 1 and |C| < k, C is the
+ * min(k, #{V >= 1}) points of highest (V, -id) (fallback); if cap > 0 and
+ * |C| > cap, C keeps its cap points of highest (V, -id).  act/nact as written
+ * by crisp_activate.  cand: device [nq][cand_stride] int32, ncand: device
+ * [nq] int64, score: device [nq][cand_stride] uint8 (V of each candidate) or
+ * NULL, how: device [nq] int32 (0 plain, 1 fallback, 2 capped) or NULL.
+ * cand_stride must bound |C|: EINVAL if cap > cand_stride; when cap == 0 a
+ * query whose |C| exceeds cand_stride reports CRISP_EINVAL at the next sync
+ * through how = -1 and ncand = the true |C| (nothing past the stride is written).
+ * EUNSUPPORTED: weighted scores above 255 (M > 127). */
+crisp_status crisp_count_cut(const crisp_index *index, const int32_t *act, const int32_t *nact, int32_t nq,
+                             int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t cand_stride,
+                             int64_t *ncand, uint8_t *score, int32_t *how, void *stream);
+
+/* Q6 (§4.3.2 Stage 3, phi = 0): exact CR32 distance from each query row of Qr
+ * (device [nq][Dp]) to each of its candidates, then the k smallest by
+ * (distance, id).  cand/ncand as written by crisp_count_cut (ascending ids).
+ * ids: device [nq][k] int64, sqdist: device [nq][k] float32, padded -1/+inf. */
+crisp_status crisp_rerank(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
+                          int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
+                          void *stream);
+
+/* Q7 (§4.3.2 Stages 2-3, phi = 1; Eq. 2): candidates ordered by (Hamming
+ * distance of sign codes, id); each is pruned by ADSampling checks at t = 32,
+ * 64, ... < D when the running top-k is full (d_t > fl(r_k^2 * f_t), f_t =
+ * fl32((t/D)(1 + eps0/sqrt t)^2) evaluated in FP64), else measured exactly and
+ * offered to the top-k; the walk stops once P = patience consecutive
+ * candidates left the top-k unchanged (patience <= 0: never).  Results equal
+ * the sequential walk exactly.  n_verified, n_full: device [nq] int64 or NULL.
+ * EUNSUPPORTED: a query with more than 32768 candidates (cap them). */
+crisp_status crisp_verify_opt(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
+                              int64_t cand_stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
+                              int64_t *ids, float *sqdist, int64_t *n_verified, int64_t *n_full, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRISP_H */

@@ -149,7 +149,17 @@ def cr32(x, q) -> np.float32:
 
 # ------------------------------------------------------- B1 covariance + CEV
 def covariance(X, rows) -> np.ndarray:
-    """Sample covariance of X[rows] in FP64, mean-centred, 1/(S-1) (§4.1)."""
+    """Sample covariance of X[rows] in FP64, mean-centred, 1/(S-1) (§4.1).
+
+    The centred product Xc^T Xc is a library matmul (numpy/BLAS)."""
+    Xs = np.asarray(X)[np.asarray(rows, np.int64)].astype(np.float64)
+    Xs -= Xs.mean(axis=0, keepdims=True)
+    cov = (Xs.T @ Xs) / float(Xs.shape[0] - 1)
+    return 0.5 * (cov + cov.T)
+
+
+def covariance_loops(X, rows) -> np.ndarray:
+    """The same covariance written as plain loops in C (a second form, for small inputs)."""
     X = _c(X, np.float32)
     rows = _c(rows, np.int64)
     D = X.shape[1]

@@ -110,14 +110,16 @@ float or_cr32(const float *x, const float *q, int Dp) {
     return acc;
 }
 
-/* y = x R in the GEMV order (Q1 / B2). x has D entries, y gets Dp (zero pad). */
+/* y = x R in the GEMV order (Q1 / B2): y_j is an fmaf chain over d = 0..D-1
+ * of x_d R[d][j], from 0.  The d loop is outermost so R streams by rows; every
+ * y_j still sees its terms in ascending d.  x has D entries, y gets Dp. */
 void or_rotate_row(const float *x, const float *R, int D, int Dp, float *y) {
-    for (int j = 0; j < D; ++j) {
-        float acc = 0.0f;
-        for (int d = 0; d < D; ++d) acc = fmaf(x[d], R[(int64_t)d * D + j], acc);
-        y[j] = acc;
+    for (int j = 0; j < Dp; ++j) y[j] = 0.0f;
+    for (int d = 0; d < D; ++d) {
+        const float xd = x[d];
+        const float *r = R + (int64_t)d * D;
+        for (int j = 0; j < D; ++j) y[j] = fmaf(xd, r[j], y[j]);
     }
-    for (int j = D; j < Dp; ++j) y[j] = 0.0f;
 }
 
 void or_rotate_rows(const float *X, int64_t N, int D, int ldx, const float *R, int Dp, float *Y) {

@@ -1,0 +1,315 @@
+"""Python binding of the CRISP GB300 engine (arXiv 2603.05180).
+
+A thin ctypes layer over ``libcrisp_gb300.so`` (built in-tree by
+``_build.build()``): the functions below carry the C ABI's names
+(include/crisp.h) and only marshal arguments.  Every step of the method runs in
+the library's CUDA kernels; there is no CPU fallback, and every call fails
+loudly when the library is missing.
+
+Device buffers may be passed as torch CUDA tensors or as raw integer device
+addresses; ``stream`` is a torch.cuda.Stream, a raw cudaStream_t integer, or
+None (the current torch stream when torch is loaded, else the default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcrisp_gb300.so")
+_lib = None
+
+CRISP_OK, CRISP_EINVAL, CRISP_ENOMEM, CRISP_ECUDA, CRISP_ETIMEOUT, CRISP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+_STATUS = {0: "CRISP_OK", -1: "CRISP_EINVAL", -2: "CRISP_ENOMEM", -3: "CRISP_ECUDA", -4: "CRISP_ETIMEOUT",
+           -5: "CRISP_EUNSUPPORTED"}
+
+
+class CrispError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("M", C.c_int32), ("K", C.c_int32), ("tau_cev", C.c_double), ("rotate", C.c_int32),
+                ("kmeans_iters", C.c_int32), ("kmeans_train", C.c_int64), ("seed", C.c_uint64),
+                ("cev_sample", C.c_void_p), ("cev_sample_n", C.c_int64), ("gaussian", C.c_void_p),
+                ("kmeans_sample", C.c_void_p), ("kmeans_sample_n", C.c_int64), ("kmeans_init", C.c_void_p)]
+
+
+class SearchParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
+                ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64)]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_verified", C.c_int64), ("n_full", C.c_int64),
+                ("n_retrieved", C.c_int64), ("fallback", C.c_int32), ("capped", C.c_int32), ("tau", C.c_int32),
+                ("_pad", C.c_int32)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("N", C.c_int64), ("D", C.c_int32), ("Dp", C.c_int32), ("M", C.c_int32), ("K", C.c_int32),
+                ("H", C.c_int32), ("rotated", C.c_int32), ("cev", C.c_double), ("max_cell", C.c_int32),
+                ("id_tile_log2", C.c_int32), ("device_bytes", C.c_int64), ("R32", C.c_void_p),
+                ("cent", C.c_void_p), ("offsets", C.c_void_p), ("ids", C.c_void_p), ("Xr", C.c_void_p),
+                ("codes", C.c_void_p)]
+
+
+_P, _I32, _I64, _F, _D, _S = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
+_SIGS = {
+    "crisp_build": [_P, _I64, _I32, C.POINTER(BuildParams), _P, C.POINTER(_P)],
+    "crisp_index_export": [_P, _P, C.POINTER(_S)],
+    "crisp_index_import": [_P, _S, _P, C.POINTER(_P)],
+    "crisp_index_get_info": [_P, C.POINTER(IndexInfo)],
+    "crisp_search": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
+    "crisp_search_host": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
+    "crisp_search_scratch_bytes": [_P, _I32, C.POINTER(SearchParams), C.POINTER(_S)],
+    "crisp_covariance": [_P, _I64, _I32, _I32, _P, _I64, _P, _P],
+    "crisp_eigvalsh": [_P, _I32, _P, _P],
+    "crisp_cev": [_P, _I64, _I32, _I32, _P, _I64, C.POINTER(_D), _P],
+    "crisp_rotation_from_gaussian": [_P, _I32, _P, _P],
+    "crisp_rotate_rows": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
+    "crisp_kmeans": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P, _P],
+    "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
+    "crisp_csr_build": [_P, _I64, _I32, _P, _P, _P],
+    "crisp_sign_codes": [_P, _I64, _I32, _P, _P],
+    "crisp_half_dists": [_P, _P, _I32, _P, _P, _P],
+    "crisp_activate": [_P, _P, _I32, _I32, _I32, _I64, _P, _P, _P, _P],
+    "crisp_count_cut": [_P, _P, _P, _I32, _I32, _I32, _I64, _P, _I64, _P, _P, _P, _P],
+    "crisp_rerank": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
+    "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P],
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CRISP CUDA library missing ({LIB_PATH}); build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.crisp_free.argtypes = [_P]
+        L.crisp_free.restype = None
+        L.crisp_last_error.argtypes = []
+        L.crisp_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array (host)
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        import sys
+
+        if "torch" in sys.modules:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st):
+    if st != 0:
+        raise CrispError(st, lib().crisp_last_error().decode(errors="replace"))
+
+
+def _call(name, *args):
+    _check(getattr(lib(), name)(*args))
+
+
+# ------------------------------------------------------------------ index
+class Index:
+    """Owner of a crisp_index handle (freed with crisp_free)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def info(self) -> IndexInfo:
+        return crisp_index_get_info(self)
+
+    def free(self):
+        if self.handle:
+            lib().crisp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+
+def crisp_build(X, N, D, params: BuildParams, stream=None) -> Index:
+    out = C.c_void_p()
+    _call("crisp_build", _ptr(X), N, D, C.byref(params), _stream(stream), C.byref(out))
+    return Index(out.value)
+
+
+def crisp_free(index: Index):
+    index.free()
+
+
+def crisp_index_export(index: Index) -> bytes:
+    n = C.c_size_t(0)
+    _call("crisp_index_export", index, None, C.byref(n))
+    buf = C.create_string_buffer(n.value)
+    _call("crisp_index_export", index, buf, C.byref(n))
+    return buf.raw[: n.value]
+
+
+def crisp_index_import(blob: bytes, stream=None) -> Index:
+    out = C.c_void_p()
+    buf = C.create_string_buffer(blob, len(blob))
+    _call("crisp_index_import", buf, len(blob), _stream(stream), C.byref(out))
+    return Index(out.value)
+
+
+def crisp_index_get_info(index: Index) -> IndexInfo:
+    info = IndexInfo()
+    _call("crisp_index_get_info", index, C.byref(info))
+    return info
+
+
+def crisp_search(index, Q, nq, params: SearchParams, ids, sqdist, stats=None, stream=None):
+    _call("crisp_search", index, _ptr(Q), nq, C.byref(params), _ptr(ids), _ptr(sqdist), _ptr(stats), _stream(stream))
+
+
+def crisp_search_host(index, Q, nq, params: SearchParams, ids, sqdist, stats=None, stream=None):
+    _call("crisp_search_host", index, _ptr(Q), nq, C.byref(params), _ptr(ids), _ptr(sqdist), _ptr(stats),
+          _stream(stream))
+
+
+def crisp_search_scratch_bytes(index, nq, params: SearchParams) -> int:
+    n = C.c_size_t(0)
+    _call("crisp_search_scratch_bytes", index, nq, C.byref(params), C.byref(n))
+    return n.value
+
+
+def crisp_covariance(X, N, D, ldx, rows, S, cov, stream=None):
+    _call("crisp_covariance", _ptr(X), N, D, ldx, _ptr(rows), S, _ptr(cov), _stream(stream))
+
+
+def crisp_eigvalsh(A, D, eig, stream=None):
+    _call("crisp_eigvalsh", _ptr(A), D, _ptr(eig), _stream(stream))
+
+
+def crisp_cev(X, N, D, ldx, rows, S, stream=None) -> float:
+    out = C.c_double(0.0)
+    _call("crisp_cev", _ptr(X), N, D, ldx, _ptr(rows), S, C.byref(out), _stream(stream))
+    return out.value
+
+
+def crisp_rotation_from_gaussian(G, D, R, stream=None):
+    _call("crisp_rotation_from_gaussian", _ptr(G), D, _ptr(R), _stream(stream))
+
+
+def crisp_rotate_rows(X, N, D, ldx, R, Y, ldy, stream=None):
+    _call("crisp_rotate_rows", _ptr(X), N, D, ldx, _ptr(R), _ptr(Y), ldy, _stream(stream))
+
+
+def crisp_kmeans(T, S, ldt, off, h, K, H, init, iters, Cout, stream=None):
+    _call("crisp_kmeans", _ptr(T), S, ldt, off, h, K, H, _ptr(init), iters, _ptr(Cout), _stream(stream))
+
+
+def crisp_assign_cells(Xr, N, D, Dp, M, K, H, cent, cells, stream=None):
+    _call("crisp_assign_cells", _ptr(Xr), N, D, Dp, M, K, H, _ptr(cent), _ptr(cells), _stream(stream))
+
+
+def crisp_csr_build(cells, N, K2, offsets, ids, stream=None):
+    _call("crisp_csr_build", _ptr(cells), N, K2, _ptr(offsets), _ptr(ids), _stream(stream))
+
+
+def crisp_sign_codes(Xr, N, Dp, codes, stream=None):
+    _call("crisp_sign_codes", _ptr(Xr), N, Dp, _ptr(codes), _stream(stream))
+
+
+def crisp_half_dists(index, Qr, nq, sorted_out, perm, stream=None):
+    _call("crisp_half_dists", index, _ptr(Qr), nq, _ptr(sorted_out), _ptr(perm), _stream(stream))
+
+
+def crisp_activate(index, Qr, nq, phi, k, budget, act, nact, retrieved=None, stream=None):
+    _call("crisp_activate", index, _ptr(Qr), nq, phi, k, budget, _ptr(act), _ptr(nact), _ptr(retrieved),
+          _stream(stream))
+
+
+def crisp_count_cut(index, act, nact, nq, tau, k, cap, cand, cand_stride, ncand, score=None, how=None, stream=None):
+    _call("crisp_count_cut", index, _ptr(act), _ptr(nact), nq, tau, k, cap, _ptr(cand), cand_stride, _ptr(ncand),
+          _ptr(score), _ptr(how), _stream(stream))
+
+
+def crisp_rerank(index, Qr, nq, cand, cand_stride, ncand, k, ids, sqdist, stream=None):
+    _call("crisp_rerank", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, _ptr(ids), _ptr(sqdist),
+          _stream(stream))
+
+
+def crisp_verify_opt(index, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified=None,
+                     n_full=None, stream=None):
+    _call("crisp_verify_opt", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, float(eps0), patience,
+          _ptr(ids), _ptr(sqdist), _ptr(n_verified), _ptr(n_full), _stream(stream))
+
+
+# ------------------------------------------------------------ conveniences
+def tau(alpha: float, M: int) -> int:
+    """tau = ceil(alpha M - 1e-9) (the library's reading of Theorem 1's tau = alpha M)."""
+    import math
+
+    return int(math.ceil(alpha * M - 1e-9))
+
+
+def budget(rho: float, N: int) -> int:
+    """max(1, ceil(rho N - 1e-9)) ids per subspace (Algorithm 1's budget)."""
+    import math
+
+    return max(1, int(math.ceil(rho * N - 1e-9)))
+
+
+def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0) -> SearchParams:
+    return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates)
+
+
+def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None):
+    """BuildParams; ``draws`` (host numpy arrays: cev_sample, gaussian,
+    kmeans_sample, kmeans_init) are referenced, so keep them alive for the call."""
+    p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None)
+    if draws is not None:
+        p.cev_sample = draws.cev_sample.ctypes.data
+        p.cev_sample_n = draws.cev_sample.size
+        p.gaussian = draws.gaussian.ctypes.data
+        p.kmeans_sample = draws.kmeans_sample.ctypes.data
+        p.kmeans_sample_n = draws.kmeans_sample.size
+        p.kmeans_init = draws.kmeans_init.ctypes.data
+    return p
+
+
+def crisp_kernel_launches() -> int:
+    f = lib().crisp_kernel_launches
+    f.restype = C.c_uint64
+    return int(f())
+
+
+def crisp_last_error() -> str:
+    return lib().crisp_last_error().decode(errors="replace")

@@ -1,0 +1,91 @@
+// Internal declarations of the CRISP GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "crisp.h"
+
+// Ids per counting tile: the per-query collision counters of one tile live in
+// shared memory as bytes, so a tile of 2^16 ids takes 64 KB.
+#define CRISP_TILE_LOG2 16
+#define CRISP_TILE (1 << CRISP_TILE_LOG2)
+#define CRISP_KMAX 64
+#define CRISP_KOUT_MAX 256
+#define CRISP_OPT_MAX_CAND 32768
+
+struct crisp_index {
+    int64_t N = 0;
+    int32_t D = 0, Dp = 0, M = 0, K = 0, H = 0, rotated = 0;
+    double cev = 0.0;
+    int32_t max_cell = 0;
+    int32_t T = 0;                 // number of id tiles
+    float *R32 = nullptr;          // [D][D]
+    float *cent = nullptr;         // [M][2][K][H]
+    int32_t *offsets = nullptr;    // [M][K*K+1]
+    int32_t *ids = nullptr;        // [M][N]
+    int32_t *tile_off = nullptr;   // [M][K*K][T+1]
+    float *Xr = nullptr;           // [N][Dp]
+    uint32_t *codes = nullptr;     // [N][Dp/32]
+    int device = 0;
+    int64_t bytes = 0;
+};
+
+// Plain-old-data view of an index handed to kernels by value.
+struct IxView {
+    int64_t N;
+    int32_t D, Dp, M, K, H, T;
+    const float *cent;
+    const int32_t *offsets;
+    const int32_t *ids;
+    const int32_t *tile_off;
+    const float *Xr;
+    const uint32_t *codes;
+};
+
+static inline IxView ix_view(const crisp_index *ix) {
+    IxView v;
+    v.N = ix->N; v.D = ix->D; v.Dp = ix->Dp; v.M = ix->M; v.K = ix->K; v.H = ix->H; v.T = ix->T;
+    v.cent = ix->cent; v.offsets = ix->offsets; v.ids = ix->ids; v.tile_off = ix->tile_off;
+    v.Xr = ix->Xr; v.codes = ix->codes;
+    return v;
+}
+
+// ------------------------------------------------------- launch accounting
+extern std::atomic<unsigned long long> g_crisp_launches;
+#define CRISP_COUNT_LAUNCH() g_crisp_launches.fetch_add(1, std::memory_order_relaxed)
+
+// ---------------------------------------------------------------- errors
+void crisp_set_error(const char *fmt, ...);
+crisp_status crisp_cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define CRISP_CK(call)                                                          \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) return crisp_cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define CRISP_CK_LAUNCH() CRISP_CK(cudaGetLastError())
+
+#define CRISP_REQUIRE(cond, ...)                                                \
+    do {                                                                        \
+        if (!(cond)) { crisp_set_error(__VA_ARGS__); return CRISP_EINVAL; }     \
+    } while (0)
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------- host-side readings
+int32_t crisp_tau(double alpha, int32_t M);
+int64_t crisp_budget(double rho, int64_t N);
+void crisp_subspace(int32_t D, int32_t M, int32_t m, int32_t *lo, int32_t *hl, int32_t *hr);
+
+// ------------------------------------------------ internal launchers
+crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
+                             cudaStream_t st);
+crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);
+crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
+                                int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
+                                crisp_query_stats *stats, cudaStream_t st);

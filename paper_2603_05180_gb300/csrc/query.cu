@@ -1,0 +1,864 @@
+// Query-side kernels of the CRISP engine (Algorithm 1, §4.3) for sm_103a.
+//
+//   k_rotate      Q1 / B2  y = x R, FP32, each output an fmaf chain over d in order
+//   k_activate    Q2 + Q3  half distances, sorted lists, multi-sequence cell walk
+//   k_count_cut   Q4 + Q5  collision counting in shared-memory id tiles + threshold cut
+//   k_rerank      Q6       exact CR32 distances of the candidates, radix select + bitonic top-k
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void subspace_dev(int D, int M, int m, int *lo, int *hl, int *hr) {
+    int a = (int)(((long long)m * D) / M), b = (int)(((long long)(m + 1) * D) / M);
+    int d = b - a;
+    *lo = a;
+    *hl = d / 2;
+    *hr = d - d / 2;
+}
+
+// ------------------------------------------------------------------ block scans
+// Exclusive scan of one int per thread over a block of NT threads; returns the
+// prefix and writes the block total to *total.  `ws` holds NT/32 + 1 ints.
+template <int NT>
+__device__ __forceinline__ long long block_excl_scan(long long v, long long *ws, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < NT / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < NT / 32) ws[lane] = t;       // inclusive warp prefix
+        if (lane == NT / 32 - 1) ws[NT / 32] = t;
+    }
+    __syncthreads();
+    long long excl = x - v + (warp > 0 ? ws[warp - 1] : 0);
+    *total = ws[NT / 32];
+    __syncthreads();
+    return excl;
+}
+
+// ======================================================= Q1 / B2 rotation
+constexpr int RB_M = 128, RB_N = 128, RB_K = 16, RT = 8;
+
+__global__ void __launch_bounds__(256) k_rotate(const float *__restrict__ X, long long N, int D, int ldx,
+                                                const float *__restrict__ R, float *__restrict__ Y, int ldy) {
+    __shared__ float As[RB_K][RB_M];
+    __shared__ __align__(16) float Bs[RB_K][RB_N];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long row0 = (long long)blockIdx.y * RB_M;
+    const int col0 = blockIdx.x * RB_N;
+    float acc[RT][RT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < D; k0 += RB_K) {
+        for (int e = tid; e < RB_M * RB_K; e += 256) {
+            int r = e / RB_K, kk = e % RB_K;
+            long long n = row0 + r;
+            int d = k0 + kk;
+            As[kk][r] = (n < N && d < D) ? X[n * ldx + d] : 0.0f;
+        }
+        for (int e = tid; e < RB_K * RB_N; e += 256) {
+            int kk = e / RB_N, c = e % RB_N;
+            int d = k0 + kk, j = col0 + c;
+            Bs[kk][c] = (d < D && j < D) ? R[(long long)d * D + j] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < RB_K; ++kk) {
+            float a[RT], b[RT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) a[i] = As[kk][ty * RT + i];
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * RT]);
+            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * RT + 4]);
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+            b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+#pragma unroll
+                for (int j = 0; j < RT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+        long long n = row0 + ty * RT + i;
+        if (n >= N) continue;
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            int c = col0 + tx * RT + j;
+            if (c < ldy) Y[n * ldy + c] = c < D ? acc[i][j] : 0.0f;
+        }
+    }
+}
+
+__global__ void k_pad_rows(const float *__restrict__ X, long long N, int D, int ldx, float *__restrict__ Y, int ldy) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = N * (long long)ldy;
+    for (; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        long long n = i / ldy;
+        int j = (int)(i % ldy);
+        Y[i] = j < D ? X[n * ldx + j] : 0.0f;
+    }
+}
+
+// ================================================ Q2 + Q3 activation
+constexpr int ACT_WARPS = 8;
+constexpr int ACT_WARP_WORDS_FIXED = 7 * 64;
+
+__global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const float *__restrict__ Qr, int nq, int phi,
+                                                             int kk, long long budget, int *__restrict__ act,
+                                                             int *__restrict__ nact, long long *__restrict__ retrieved,
+                                                             float *__restrict__ sorted_out, int *__restrict__ perm_out) {
+    extern __shared__ float sm[];
+    const int K = ix.K, H = ix.H, K2 = K * K, m = blockIdx.y, M = ix.M;
+    float *CtL = sm;
+    float *CtR = CtL + H * K;
+    int *offs = reinterpret_cast<int *>(CtR + H * K);
+    float *wbase = reinterpret_cast<float *>(offs + K2 + 1);
+    int lo, hl, hr;
+    subspace_dev(ix.D, M, m, &lo, &hl, &hr);
+    const float *cL = ix.cent + ((long long)m * 2 + 0) * K * H;
+    const float *cR = ix.cent + ((long long)m * 2 + 1) * K * H;
+    for (int e = threadIdx.x; e < K * H; e += blockDim.x) {
+        int c = e / H, d = e % H;
+        CtL[d * K + c] = cL[e];
+        CtR[d * K + c] = cR[e];
+    }
+    for (int e = threadIdx.x; e <= K2; e += blockDim.x) offs[e] = ix.offsets[(long long)m * (K2 + 1) + e];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * ACT_WARPS + warp;
+    if (q >= nq) return;
+    float *qs = wbase + warp * (2 * H + ACT_WARP_WORDS_FIXED);
+    float *dl = qs + 2 * H, *dr = dl + 64, *s1 = dr + 64, *s2 = s1 + 64;
+    int *p1 = reinterpret_cast<int *>(s2 + 64), *p2 = p1 + 64, *rowlen = p2 + 64;
+
+    const float *qrow = Qr + (long long)q * ix.Dp + lo;
+    for (int d = lane; d < hl + hr; d += 32) qs[d] = qrow[d];
+    __syncwarp();
+    // Dist1 / Dist2 (SEQ order) for centroids lane and lane + 32
+    for (int c = lane; c < 64; c += 32) {
+        float a = FLT_MAX, b = FLT_MAX;
+        if (c < K) {
+            a = 0.0f;
+            for (int d = 0; d < hl; ++d) {
+                float diff = qs[d] - CtL[d * K + c];
+                a = fmaf(diff, diff, a);
+            }
+            b = 0.0f;
+            for (int d = 0; d < hr; ++d) {
+                float diff = qs[hl + d] - CtR[d * K + c];
+                b = fmaf(diff, diff, b);
+            }
+        }
+        dl[c] = a;
+        dr[c] = b;
+    }
+    __syncwarp();
+    // sort by (distance, index): rank = number of smaller keys
+    for (int c = lane; c < K; c += 32) {
+        float a = dl[c], b = dr[c];
+        int ra = 0, rb = 0;
+        for (int c2 = 0; c2 < K; ++c2) {
+            float x = dl[c2], y = dr[c2];
+            ra += (x < a) || (x == a && c2 < c);
+            rb += (y < b) || (y == b && c2 < c);
+        }
+        s1[ra] = a; p1[ra] = c;
+        s2[rb] = b; p2[rb] = c;
+    }
+    __syncwarp();
+    if (sorted_out) {
+        long long base = ((long long)q * M + m) * 2 * K;
+        for (int c = lane; c < K; c += 32) {
+            sorted_out[base + c] = s1[c]; perm_out[base + c] = p1[c];
+            sorted_out[base + K + c] = s2[c]; perm_out[base + K + c] = p2[c];
+        }
+    }
+    if (!act) return;
+
+    // multi-sequence walk: row i's next cell is (i, rowlen[i]); it is on the
+    // frontier once (i-1, rowlen[i]) has been visited.  Pop the frontier's
+    // smallest (cost, i) until the ids retrieved reach the budget.
+    for (int i = lane; i < 64; i += 32) rowlen[i] = 0;
+    __syncwarp();
+    long long got = 0;
+    int count = 0;
+    int *out = act + ((long long)q * M + m) * K2;
+    while (got < budget) {
+        float bc = FLT_MAX;
+        int bi = INT_MAX;
+        bool have = false;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int i = lane + 32 * r;
+            if (i < K) {
+                int j = rowlen[i];
+                if (j < K && (i == 0 || rowlen[i - 1] > j)) {
+                    float c = s1[i] + s2[j];
+                    if (!have || c < bc || (c == bc && i < bi)) { bc = c; bi = i; have = true; }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            bool oh = __shfl_xor_sync(0xffffffffu, (int)have, o) != 0;
+            if (oh && (!have || oc < bc || (oc == bc && oi < bi))) { bc = oc; bi = oi; have = true; }
+        }
+        if (!have) break;
+        int j = rowlen[bi];
+        int cell = p1[bi] * K + p2[j];
+        ++count;
+        int w = (phi == 1 && count <= kk) ? 2 : 1;
+        got += offs[cell + 1] - offs[cell];
+        __syncwarp();
+        if (lane == 0) {
+            out[count - 1] = (w << 16) | cell;
+            rowlen[bi] = j + 1;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        nact[(long long)q * M + m] = count;
+        if (retrieved) retrieved[(long long)q * M + m] = got;
+    }
+}
+
+// ==================================================== tile offsets
+__global__ void k_tile_off(IxView ix, int *__restrict__ tile_off) {
+    const int K2 = ix.K * ix.K, T = ix.T;
+    long long total = (long long)ix.M * K2 * (T + 1);
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    int t = (int)(gid % (T + 1));
+    long long mc = gid / (T + 1);
+    int cell = (int)(mc % K2);
+    int m = (int)(mc / K2);
+    const int *off = ix.offsets + (long long)m * (K2 + 1);
+    const int *ids = ix.ids + (long long)m * ix.N;
+    int lo = off[cell], hi = off[cell + 1];
+    long long target = (long long)t << CRISP_TILE_LOG2;
+    while (lo < hi) {
+        int mid = lo + (hi - lo) / 2;
+        if ((long long)ids[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    tile_off[gid] = lo;
+}
+
+// ================================================== Q4 + Q5 count and cut
+constexpr int CNT_NT = 512;
+constexpr int CNT_SEG = CRISP_TILE / CNT_NT;   // bytes of counters per thread (128)
+
+struct CountShared {
+    int base[129];
+    unsigned hist[256];
+    int w_gt[CNT_NT / 32], w_eq[CNT_NT / 32];
+    long long w_eqbase[CNT_NT / 32], w_outbase[CNT_NT / 32];
+    long long tile_sel, tile_eq;
+    int sel_s, sel_need;
+};
+
+// Count tile t of query q into the byte counters `cnt` (zeroed here): every id
+// of every activated cell that falls in the tile adds its cell's weight.
+__device__ void count_tile(const IxView &ix, const int *__restrict__ actq, const CountShared &S, int E, int t,
+                           uint32_t *cnt) {
+    const int K2 = ix.K * ix.K, T = ix.T, M = ix.M;
+    uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+    for (int i = threadIdx.x; i < CRISP_TILE / 16; i += CNT_NT) c4[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long tbase = (long long)t << CRISP_TILE_LOG2;
+    const int nbatch = (E + 31) / 32;
+    for (int b = warp; b < nbatch; b += CNT_NT / 32) {
+        int e = b * 32 + lane;
+        int beg = 0, end = 0, w = 0, m = 0;
+        if (e < E) {
+            int lo = 0, hi = M - 1;            // m with base[m] <= e < base[m+1]
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (S.base[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            m = lo;
+            int ent = actq[(long long)m * K2 + (e - S.base[m])];
+            int cell = ent & 0xFFFF;
+            w = ent >> 16;
+            const int *to = ix.tile_off + ((long long)m * K2 + cell) * (T + 1) + t;
+            beg = to[0];
+            end = to[1];
+        }
+        for (int j = 0; j < 32; ++j) {
+            int bj = __shfl_sync(0xffffffffu, beg, j);
+            int ej = __shfl_sync(0xffffffffu, end, j);
+            int wj = __shfl_sync(0xffffffffu, w, j);
+            int mj = __shfl_sync(0xffffffffu, m, j);
+            const int *idsm = ix.ids + (long long)mj * ix.N;
+            for (int p = bj + lane; p < ej; p += 32) {
+                int local = (int)((long long)__ldg(idsm + p) - tbase);
+                atomicAdd(&cnt[local >> 2], (uint32_t)wj << ((local & 3) * 8));
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Byte masks (0xFF per byte) of v > s and v == s for the four bytes of w.
+__device__ __forceinline__ unsigned gt_mask(unsigned w, int s) {
+    if (s < 0) return 0xFFFFFFFFu;
+    if (s > 254) return 0u;
+    return __vcmpgtu4(w, (unsigned)s * 0x01010101u);
+}
+__device__ __forceinline__ unsigned eq_mask(unsigned w, int s) {
+    if (s < 0 || s > 255) return 0u;
+    return __vcmpeq4(w, (unsigned)s * 0x01010101u);
+}
+// 0xFF for bytes b < nvalid of a word whose first byte is number `first`.
+__device__ __forceinline__ unsigned valid_mask(int first, int nvalid) {
+    int k = nvalid - first;
+    if (k >= 4) return 0xFFFFFFFFu;
+    if (k <= 0) return 0u;
+    return (1u << (8 * k)) - 1u;
+}
+
+constexpr int CNT_WARP_BYTES = CRISP_TILE / (CNT_NT / 32);  // 4096 bytes of counters per warp
+constexpr int CNT_ROUNDS = CNT_WARP_BYTES / 512;             // 16 bytes per lane per round
+
+// Emit, in ascending id, the ids of tile t whose counter v satisfies v > s_hi,
+// or v == s_hi and the id is among the first need_eq such ids counted from the
+// start of the query (*eq_seen holds how many came before this tile).  Each
+// warp owns a contiguous 4 KB of counters, read 512 B per round without bank
+// conflicts.  Returns the number emitted (block-uniform).
+__device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t *cnt, int t, int s_hi, long long need_eq,
+                               long long *eq_seen, long long out_base, int *candq, uint8_t *scoreq, long long stride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long id0 = ((long long)t << CRISP_TILE_LOG2) + (long long)warp * CNT_WARP_BYTES;
+    long long lim = ix.N - id0;
+    const int vlim = lim <= 0 ? 0 : (lim >= CNT_WARP_BYTES ? CNT_WARP_BYTES : (int)lim);
+    const uint4 *wc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(cnt) + warp * CNT_WARP_BYTES);
+    int c_gt = 0, c_eq = 0;
+#pragma unroll 4
+    for (int r = 0; r < CNT_ROUNDS; ++r) {
+        int b0 = r * 512 + lane * 16;
+        uint4 v = wc[r * 32 + lane];
+        unsigned ws[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            unsigned vm = valid_mask(b0 + 4 * u, vlim);
+            c_gt += __popc(gt_mask(ws[u], s_hi) & vm) >> 3;
+            c_eq += __popc(eq_mask(ws[u], s_hi) & vm) >> 3;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        c_gt += __shfl_xor_sync(0xffffffffu, c_gt, o);
+        c_eq += __shfl_xor_sync(0xffffffffu, c_eq, o);
+    }
+    if (lane == 0) { S.w_gt[warp] = c_gt; S.w_eq[warp] = c_eq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long eqb = *eq_seen, outb = out_base;
+        for (int w = 0; w < CNT_NT / 32; ++w) {
+            S.w_eqbase[w] = eqb;
+            S.w_outbase[w] = outb;
+            long long take = need_eq - eqb;
+            take = take < 0 ? 0 : (take > S.w_eq[w] ? S.w_eq[w] : take);
+            outb += S.w_gt[w] + take;
+            eqb += S.w_eq[w];
+        }
+        S.tile_sel = outb - out_base;
+        S.tile_eq = eqb - *eq_seen;
+    }
+    __syncthreads();
+    long long eq_run = S.w_eqbase[warp], pos_run = S.w_outbase[warp];
+    const long long tot_sel = S.tile_sel, tot_eq = S.tile_eq;
+    if (S.w_gt[warp] + S.w_eq[warp] > 0) {
+        for (int r = 0; r < CNT_ROUNDS; ++r) {
+            int b0 = r * 512 + lane * 16;
+            uint4 v = wc[r * 32 + lane];
+            unsigned ws[4] = {v.x, v.y, v.z, v.w};
+            unsigned gm[4], em[4];
+            int e_l = 0, g_l = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                unsigned vm = valid_mask(b0 + 4 * u, vlim);
+                gm[u] = gt_mask(ws[u], s_hi) & vm;
+                em[u] = eq_mask(ws[u], s_hi) & vm;
+                g_l += __popc(gm[u]) >> 3;
+                e_l += __popc(em[u]) >> 3;
+            }
+            int e_in = e_l, e_tot = e_l;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, e_in, o);
+                if (lane >= o) e_in += y;
+            }
+            e_tot = __shfl_sync(0xffffffffu, e_in, 31);
+            long long eq_start = eq_run + (e_in - e_l);
+            long long tk = need_eq - eq_start;
+            int take = tk <= 0 ? 0 : (tk >= e_l ? e_l : (int)tk);
+            int s_l = g_l + take, s_in = s_l;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s_in, o);
+                if (lane >= o) s_in += y;
+            }
+            int s_tot = __shfl_sync(0xffffffffu, s_in, 31);
+            if (s_l > 0) {
+                long long pos = pos_run + (s_in - s_l);
+                int taken = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        bool g = (gm[u] >> (8 * bb)) & 1u;
+                        bool e = (em[u] >> (8 * bb)) & 1u;
+                        bool sel = g || (e && taken < take);
+                        taken += (e && !g && taken < take) ? 1 : 0;
+                        if (sel) {
+                            if (pos < stride) {
+                                candq[pos] = (int)(id0 + b0 + 4 * u + bb);
+                                if (scoreq) scoreq[pos] = (uint8_t)((ws[u] >> (8 * bb)) & 0xFFu);
+                            }
+                            ++pos;
+                        }
+                    }
+                }
+            }
+            eq_run += e_tot;
+            pos_run += s_tot;
+        }
+    }
+    *eq_seen += tot_eq;
+    __syncthreads();
+    return tot_sel;
+}
+
+__global__ void __launch_bounds__(CNT_NT) k_count_cut(IxView ix, const int *__restrict__ act,
+                                                      const int *__restrict__ nact, int nq, int tau, int kk,
+                                                      long long cap, int *__restrict__ cand, long long stride,
+                                                      long long *__restrict__ ncand, uint8_t *__restrict__ score,
+                                                      int *__restrict__ how) {
+    extern __shared__ __align__(16) uint32_t cnt[];
+    __shared__ CountShared S;
+    const int q = blockIdx.x, M = ix.M, K2 = ix.K * ix.K;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int m = 0; m < M; ++m) {
+            S.base[m] = acc;
+            acc += nact[(long long)q * M + m];
+        }
+        S.base[M] = acc;
+    }
+    __syncthreads();
+    const int E = S.base[M];
+    const int *actq = act + (long long)q * M * K2;
+    int *candq = cand + (long long)q * stride;
+    uint8_t *scoreq = score ? score + (long long)q * stride : nullptr;
+    const int T = ix.T;
+
+    // pass 1: C = {x : V[x] >= tau}
+    long long total = 0, eq_seen = 0;
+    for (int t = 0; t < T; ++t) {
+        count_tile(ix, actq, S, E, t, cnt);
+        total += emit_tile(ix, S, cnt, t, tau - 1, 0, &eq_seen, total, candq, scoreq, stride);
+    }
+    int mode = 0;
+    long long want = 0;
+    int lo = 0;
+    if (tau >= 1 && total < kk) { mode = 1; want = kk; lo = 1; }
+    else if (cap > 0 && total > cap) { mode = 2; want = cap; lo = tau < 0 ? 0 : tau; }
+    if (mode == 0) {
+        if (threadIdx.x == 0) {
+            ncand[q] = total;
+            if (how) how[q] = total > stride ? -1 : 0;
+        }
+        return;
+    }
+    // pass A: histogram of V over v >= lo (rare path: fallback or cap)
+    for (int i = threadIdx.x; i < 256; i += CNT_NT) S.hist[i] = 0;
+    __syncthreads();
+    for (int t = 0; t < T; ++t) {
+        count_tile(ix, actq, S, E, t, cnt);
+        const long long id0 = ((long long)t << CRISP_TILE_LOG2);
+        const uint8_t *cb = reinterpret_cast<const uint8_t *>(cnt);
+        for (int i = threadIdx.x; i < CRISP_TILE; i += CNT_NT) {
+            if (id0 + i >= ix.N) break;
+            int v = cb[i];
+            if (v >= lo) atomicAdd(&S.hist[v], 1u);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // largest s >= lo with #{V >= s} >= want, taking only the first `need`
+        // ids at V == s; if no such s, every v >= lo
+        long long above = 0;
+        int s_star = -1;
+        long long need = 0;
+        for (int s = 255; s >= lo; --s) {
+            long long h = S.hist[s];
+            if (above + h >= want) { s_star = s; need = want - above; break; }
+            above += h;
+        }
+        if (s_star < 0) { s_star = lo; need = INT_MAX; }
+        S.sel_s = s_star;
+        S.sel_need = (int)need;
+    }
+    __syncthreads();
+    const int s_star = S.sel_s;
+    const long long need = S.sel_need;
+    long long out = 0;
+    eq_seen = 0;
+    for (int t = 0; t < T; ++t) {
+        count_tile(ix, actq, S, E, t, cnt);
+        out += emit_tile(ix, S, cnt, t, s_star, need, &eq_seen, out, candq, scoreq, stride);
+    }
+    if (threadIdx.x == 0) {
+        ncand[q] = out;
+        if (how) how[q] = out > stride ? -1 : mode;
+    }
+}
+
+// ==================================================== Q6 re-rank + top-k
+constexpr int RR_NT = 256;
+constexpr int RR_U = 8;   // 32-dim blocks in flight per lane
+
+// CR32 block sum of one 32-dim block for the 8-lane group holding x4/q4 in lane
+// (lane & 7): four fmaf into a lane partial, then the xor 4, 2, 1 tree.
+__device__ __forceinline__ float cr32_block(float4 x, float4 qv, unsigned gmask) {
+    float d0 = x.x - qv.x, d1 = x.y - qv.y, d2 = x.z - qv.z, d3 = x.w - qv.w;
+    float a = 0.0f;
+    a = fmaf(d0, d0, a);
+    a = fmaf(d1, d1, a);
+    a = fmaf(d2, d2, a);
+    a = fmaf(d3, d3, a);
+    a = a + __shfl_xor_sync(gmask, a, 4);
+    a = a + __shfl_xor_sync(gmask, a, 2);
+    a = a + __shfl_xor_sync(gmask, a, 1);
+    return a;
+}
+
+struct TopkShared {
+    unsigned hist[256];
+    long long scan_ws[RR_NT / 32 + 1];
+    unsigned skey[CRISP_KOUT_MAX];
+    int sid[CRISP_KOUT_MAX];
+    unsigned prefix;
+    int need;
+};
+
+// Block-wide: the kk smallest (key, id) of n entries (keys from dist[], ids
+// from candq[], ids ascending in list order), sorted, into S.skey / S.sid.
+// Returns the number selected (min(n, kk)).
+__device__ int select_topk(const float *distq, const int *candq, long long n, int kk, TopkShared &S) {
+    const int tid = threadIdx.x;
+    int nsel;
+    if (n <= kk) {
+        for (int i = tid; i < n; i += RR_NT) { S.skey[i] = __float_as_uint(distq[i]); S.sid[i] = candq[i]; }
+        nsel = (int)n;
+    } else {
+        unsigned prefix = 0, mask = 0;
+        int need = kk;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
+            __syncthreads();
+            for (long long i = tid; i < n; i += RR_NT) {
+                unsigned key = __float_as_uint(distq[i]);
+                if ((key & mask) == prefix) atomicAdd(&S.hist[(key >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned cum = 0;
+                int b = 0;
+                for (; b < 256; ++b) {
+                    if (cum + S.hist[b] >= (unsigned)need) break;
+                    cum += S.hist[b];
+                }
+                S.prefix = prefix | ((unsigned)b << shift);
+                S.need = need - (int)cum;
+            }
+            __syncthreads();
+            prefix = S.prefix;
+            need = S.need;
+            mask |= 255u << shift;
+            __syncthreads();
+        }
+        // prefix = key of the kk-th smallest; take every key < prefix and the
+        // first `need` (lowest ids, list order) with key == prefix
+        long long eq_seen = 0, sel_seen = 0;
+        for (long long c0 = 0; c0 < n; c0 += RR_NT) {
+            long long i = c0 + tid;
+            unsigned key = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
+            int is_eq = (i < n && key == prefix);
+            long long eq_tot;
+            long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
+            int sel = (i < n) && (key < prefix || (is_eq && eq_seen + eq_off < need));
+            long long sel_tot;
+            long long sel_off = block_excl_scan<RR_NT>(sel, S.scan_ws, &sel_tot);
+            if (sel) { S.skey[sel_seen + sel_off] = key; S.sid[sel_seen + sel_off] = candq[i]; }
+            eq_seen += eq_tot;
+            sel_seen += sel_tot;
+        }
+        nsel = kk;
+    }
+    __syncthreads();
+    // bitonic sort of CRISP_KOUT_MAX entries by (key, id); padding sorts last
+    for (int i = nsel + tid; i < CRISP_KOUT_MAX; i += RR_NT) { S.skey[i] = 0xFFFFFFFFu; S.sid[i] = INT_MAX; }
+    __syncthreads();
+    for (int size = 2; size <= CRISP_KOUT_MAX; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < CRISP_KOUT_MAX; i += RR_NT) {
+                int j = i ^ stride;
+                if (j > i) {
+                    bool up = (i & size) == 0;
+                    unsigned ki = S.skey[i], kj = S.skey[j];
+                    int ii = S.sid[i], ij = S.sid[j];
+                    bool gt = ki > kj || (ki == kj && ii > ij);
+                    if (gt == up) { S.skey[i] = kj; S.skey[j] = ki; S.sid[i] = ij; S.sid[j] = ii; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return nsel;
+}
+
+__global__ void __launch_bounds__(RR_NT) k_rerank(IxView ix, const float *__restrict__ Qr, int nq,
+                                                  const int *__restrict__ cand, long long stride,
+                                                  const long long *__restrict__ ncand, int kk, float *__restrict__ dbuf,
+                                                  long long *__restrict__ out_ids, float *__restrict__ out_d) {
+    extern __shared__ __align__(16) float qs[];
+    __shared__ TopkShared S;
+    const int q = blockIdx.x;
+    const int Dp = ix.Dp, nb = Dp / 32;
+    long long n = ncand[q];
+    if (n > stride) n = stride;
+    for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, l = threadIdx.x & 7;
+    const unsigned gmask = 0xFFu << (lane & 24);
+    const int *candq = cand + (long long)q * stride;
+    float *distq = dbuf + (long long)q * stride;
+    for (long long i = g; i < n; i += RR_NT / 8) {
+        const float4 *row = reinterpret_cast<const float4 *>(ix.Xr + (long long)candq[i] * Dp) + l;
+        float acc = 0.0f;
+        for (int b0 = 0; b0 < nb; b0 += RR_U) {
+            float4 v[RR_U];
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u)
+                if (b0 + u < nb) v[u] = __ldcs(row + 8 * (b0 + u));
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u) {
+                if (b0 + u < nb) {
+                    float4 qv = *reinterpret_cast<const float4 *>(qs + 32 * (b0 + u) + 4 * l);
+                    acc = acc + cr32_block(v[u], qv, gmask);
+                }
+            }
+        }
+        if (l == 0) distq[i] = acc;
+    }
+    __syncthreads();
+    int nsel = select_topk(distq, candq, n, kk, S);
+    for (int r = threadIdx.x; r < kk; r += RR_NT) {
+        bool ok = r < nsel;
+        out_ids[(long long)q * kk + r] = ok ? (long long)S.sid[r] : -1LL;
+        out_d[(long long)q * kk + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
+    }
+}
+
+__global__ void k_stats(int nq, const long long *ncand, const int *how, const long long *retrieved, int M,
+                        const long long *nver, const long long *nfull, int tau, crisp_query_stats *st) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    crisp_query_stats s;
+    s.n_candidates = ncand[q];
+    long long r = 0;
+    if (retrieved)
+        for (int m = 0; m < M; ++m) r += retrieved[(long long)q * M + m];
+    s.n_retrieved = r;
+    s.n_verified = nver ? nver[q] : ncand[q];
+    s.n_full = nfull ? nfull[q] : ncand[q];
+    int h = how ? how[q] : 0;
+    s.fallback = h == 1;
+    s.capped = h == 2;
+    s.tau = tau;
+    s._pad = h < 0 ? 1 : 0;
+    st[q] = s;
+}
+
+}  // namespace
+
+// ============================================================ launchers
+crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
+                             cudaStream_t st) {
+    if (N <= 0) return CRISP_OK;
+    long long tot = (long long)N * ldy;
+    int blocks = (int)((tot + 255) / 256 < 152 * 64 ? (tot + 255) / 256 : 152 * 64);
+    k_pad_rows<<<blocks, 256, 0, st>>>(X, N, D, ldx, Y, ldy);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st) {
+    long long total = (long long)ix->M * ix->K * ix->K * (ix->T + 1);
+    k_tile_off<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ix_view(ix), ix->tile_off);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
+                                int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
+                                crisp_query_stats *stats, cudaStream_t st) {
+    if (nq <= 0 || !stats) return CRISP_OK;
+    k_stats<<<(nq + 255) / 256, 256, 0, st>>>(nq, (const long long *)ncand, how, (const long long *)retrieved, M,
+                                              (const long long *)nver, (const long long *)nfull, tau, stats);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+static size_t activate_smem(const crisp_index *ix) {
+    return sizeof(float) * (2 * (size_t)ix->H * ix->K) + sizeof(int) * ((size_t)ix->K * ix->K + 1) +
+           sizeof(float) * ACT_WARPS * (2 * (size_t)ix->H + ACT_WARP_WORDS_FIXED);
+}
+
+static crisp_status run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                                 int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, float *sorted,
+                                 int32_t *perm, cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    size_t smem = activate_smem(ix);
+    CRISP_CK(cudaFuncSetAttribute(k_activate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((nq + ACT_WARPS - 1) / ACT_WARPS, ix->M);
+    k_activate<<<grid, ACT_WARPS * 32, smem, st>>>(ix_view(ix), Qr, nq, phi, k, (long long)budget, act, nact,
+                                                   (long long *)retrieved, sorted, perm);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status crisp_run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                                int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st) {
+    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, st);
+}
+
+crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
+                                 int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t stride, int64_t *ncand,
+                                 uint8_t *score, int32_t *how, cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    size_t smem = CRISP_TILE;
+    CRISP_CK(cudaFuncSetAttribute(k_count_cut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_count_cut<<<nq, CNT_NT, smem, st>>>(ix_view(ix), act, nact, nq, tau, k, (long long)cap, cand,
+                                         (long long)stride, (long long *)ncand, score, how);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                              int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
+                              cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    size_t smem = sizeof(float) * (size_t)ix->Dp;
+    if (smem > 48 * 1024)
+        CRISP_CK(cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rerank<<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
+                                      dbuf, (long long *)ids, d2);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+// ============================================================ C ABI steps
+extern "C" crisp_status crisp_rotate_rows(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                                          int32_t ldy, void *stream) {
+    CRISP_REQUIRE(N >= 0 && D >= 1 && ldx >= D && ldy >= D, "crisp_rotate_rows: bad sizes");
+    CRISP_REQUIRE(N == 0 || (X && R && Y), "crisp_rotate_rows: null pointer");
+    CRISP_REQUIRE((const void *)X != (const void *)Y, "crisp_rotate_rows: Y overlaps X");
+    if (N == 0) return CRISP_OK;
+    dim3 grid((ldy + RB_N - 1) / RB_N, (unsigned)((N + RB_M - 1) / RB_M));
+    CRISP_REQUIRE(grid.y <= 65535u * 1024u, "crisp_rotate_rows: N too large");
+    for (long long r0 = 0; r0 < N; r0 += 65535LL * RB_M) {
+        long long nr = N - r0 < 65535LL * RB_M ? N - r0 : 65535LL * RB_M;
+        dim3 g((ldy + RB_N - 1) / RB_N, (unsigned)((nr + RB_M - 1) / RB_M));
+        k_rotate<<<g, 256, 0, as_stream(stream)>>>(X + r0 * ldx, nr, D, ldx, R, Y + r0 * ldy, ldy);
+        CRISP_COUNT_LAUNCH();
+        CRISP_CK_LAUNCH();
+    }
+    return CRISP_OK;
+}
+
+static crisp_status check_query_step(const crisp_index *ix, const void *Qr, int32_t nq) {
+    CRISP_REQUIRE(ix != nullptr, "null index");
+    CRISP_REQUIRE(nq >= 0, "nq < 0");
+    CRISP_REQUIRE(nq == 0 || Qr != nullptr, "null query pointer");
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_half_dists(const crisp_index *ix, const float *Qr, int32_t nq, float *sorted,
+                                         int32_t *perm, void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(nq == 0 || (sorted && perm), "crisp_half_dists: null output");
+    return run_activate(ix, Qr, nq, 0, 0, 0, nullptr, nullptr, nullptr, sorted, perm, as_stream(stream));
+}
+
+extern "C" crisp_status crisp_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                                       int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(phi == 0 || phi == 1, "crisp_activate: phi must be 0 or 1");
+    CRISP_REQUIRE(budget >= 1, "crisp_activate: budget < 1");
+    CRISP_REQUIRE(nq == 0 || (act && nact), "crisp_activate: null output");
+    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, as_stream(stream));
+}
+
+extern "C" crisp_status crisp_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
+                                        int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t cand_stride,
+                                        int64_t *ncand, uint8_t *score, int32_t *how, void *stream) {
+    crisp_status s = check_query_step(ix, act, nq);
+    if (s) return s;
+    CRISP_REQUIRE(ix->M <= 127, "crisp_count_cut: M > 127 overflows the byte counters");
+    CRISP_REQUIRE(k >= 1 && cap >= 0 && (cap == 0 || cap >= k), "crisp_count_cut: need k >= 1, cap 0 or >= k");
+    CRISP_REQUIRE(cap <= cand_stride, "crisp_count_cut: cap > cand_stride");
+    CRISP_REQUIRE(cand_stride >= 1, "crisp_count_cut: cand_stride < 1");
+    CRISP_REQUIRE(nq == 0 || (nact && cand && ncand), "crisp_count_cut: null pointer");
+    return crisp_run_count_cut(ix, act, nact, nq, tau, k, cap, cand, cand_stride, ncand, score, how,
+                               as_stream(stream));
+}
+
+extern "C" crisp_status crisp_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                     int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
+                                     void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(k >= 1 && k <= CRISP_KOUT_MAX, "crisp_rerank: k outside [1, 256]");
+    CRISP_REQUIRE(nq == 0 || (cand && ncand && ids && sqdist), "crisp_rerank: null pointer");
+    if (nq == 0) return CRISP_OK;
+    cudaStream_t st = as_stream(stream);
+    float *dbuf = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
+    crisp_status r = crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, st);
+    cudaFreeAsync(dbuf, st);
+    return r;
+}

@@ -246,6 +246,7 @@ def test_covariance_brute_force_small():
     X = rng.standard_normal((40, 6)).astype(np.float32)
     rows = np.array([0, 3, 5, 9, 17, 22, 39])
     cov = oracle.covariance(X, rows)
+    assert np.allclose(cov, oracle.covariance_loops(X, rows), rtol=1e-12, atol=1e-14)
     S = X[rows].astype(np.float64)
     mu = S.mean(0)
     ref = sum(np.outer(s - mu, s - mu) for s in S) / (len(rows) - 1)
