@@ -1,0 +1,502 @@
+#!/usr/bin/env python3
+"""Benchmark of the CRISP GB300 engine (arXiv 2603.05180): QPS at recall@10 >= 0.95.
+
+Workload (the paper's datasets are not available; synthetic rows of the Gist
+shape stand in for them): N = 1,000,000 rows, D = 960, x = U diag(sqrt(l)) z
+with l_i = i^-1.2 and U Haar-orthogonal (the CEV test triggers the rotation);
+10,000 held-out queries from the same law; k = 10; M = 20 subspaces, K = 50.
+
+A step is one crisp_search over the whole 10,000-query batch (Q1-Q7 of the
+engine), inputs already resident in HBM; L2 (129 MB) is flushed by a 512 MB
+write before every timed step, outside the timed events.  `value` is the
+throughput of the plain FP32 engine at the operating point (mode, rho, alpha)
+whose recall@10 on all 10,000 queries is reported beside it.  `e2e` is the
+same metric through crisp_search_host (host buffers in, host buffers out,
+copies inside the timed region).
+
+Also printed: a roofline entry for the dominant kernel (algorithmic bytes per
+launch over its CUDA-event duration, against the measured HBM copy bandwidth),
+the CPU oracle timed on a bounded query sample on this machine's cores, SM
+clocks sampled during the timed region, and the number of library kernels
+launched inside it.
+
+--impl reference times the CPU oracle itself on the same workload and
+operating point (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10≥0.95 on 1 GB300 (plain FP32 vs learned+BF16), % HBM peak, p99 ms"
+WORKLOAD = ("powerlaw N=1,000,000 D=960 (lambda_i = i^-1.2, Haar mix), 10,000 held-out queries, k=10, "
+            "M=20 subspaces, K=50 centroids per half")
+# operating point of the plain FP32 engine on this workload (recall@10 >= 0.95)
+DEFAULT_POINT = dict(mode=0, rho=0.03, alpha=0.3)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.tmp.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- ground truth
+def ground_truth(torch, X, Q, k, extra=32):
+    """Exact k-NN: FP32 expansion picks k+32 candidates, FP64 distances order them."""
+    xn = (X * X).sum(1)
+    nq = Q.shape[0]
+    gd = torch.empty((nq, k), dtype=torch.float64, device=X.device)
+    gi = torch.empty((nq, k), dtype=torch.int64, device=X.device)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for s in range(0, nq, 1000):
+        q = Q[s:s + 1000]
+        d = xn[None, :] - 2.0 * (q @ X.T)
+        _, ci = torch.topk(d, k + extra, dim=1, largest=False)
+        dd = ((X[ci].double() - q.double()[:, None, :]) ** 2).sum(-1)
+        o = torch.argsort(dd, dim=1)[:, :k]
+        gd[s:s + 1000] = torch.gather(dd, 1, o)
+        gi[s:s + 1000] = torch.gather(ci, 1, o)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return gi, gd
+
+
+def recall_at_k(torch, X, Q, ids, gdk, rel=1e-5):
+    """Tie-aware recall@k: a returned id counts if its FP64 distance is within (1 + rel) of the true k-th."""
+    ids = ids.clone()
+    valid = ids >= 0
+    ids[~valid] = 0
+    hits = 0
+    for s in range(0, ids.shape[0], 2000):
+        d = ((X[ids[s:s + 2000]].double() - Q[s:s + 2000].double()[:, None, :]) ** 2).sum(-1)
+        hits += int(((d <= gdk[s:s + 2000, None] * (1 + rel)) & valid[s:s + 2000]).sum().item())
+    return hits / (ids.shape[0] * ids.shape[1])
+
+
+def make_workload(args, device):
+    import synthetic
+
+    return synthetic.powerlaw(args.n, args.dim, args.nq, seed=args.seed, device=device)
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_index(Xh, args):
+    import oracle
+    import synthetic
+
+    draws = synthetic.method_draws(args.n, args.dim, args.M, 50, seed=args.seed)
+    t = time.perf_counter()
+    ix = oracle.build_index(Xh, M=args.M, draws=draws)
+    return ix, time.perf_counter() - t
+
+
+def oracle_time(ix, Qh, point, k, seconds):
+    """Time the oracle's batched search on a bounded prefix of the queries."""
+    import oracle
+
+    p = oracle.SearchParams(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"])
+    t = time.perf_counter()
+    _, _, _, used = oracle.search(ix, Qh[:16], p)
+    per_q = (time.perf_counter() - t) / 16
+    n = int(max(16, min(Qh.shape[0], seconds / max(per_q, 1e-6))))
+    t = time.perf_counter()
+    _, _, _, used = oracle.search(ix, Qh[:n], p)
+    dt = time.perf_counter() - t
+    return n / dt, n, used, dt
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+
+    point = dict(DEFAULT_POINT)
+    if args.mode is not None:
+        point["mode"] = args.mode
+    if args.rho is not None:
+        point["rho"] = args.rho
+    if args.alpha is not None:
+        point["alpha"] = args.alpha
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    X, Q = make_workload(args, device)
+    Xh = X.cpu().numpy() if device == "cuda" else X
+    Qh = Q.cpu().numpy() if device == "cuda" else Q
+    ix, build_s = oracle_index(Xh, args)
+    import oracle
+
+    p = oracle.SearchParams(k=args.k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"])
+    t = time.perf_counter()
+    oracle.search(ix, Qh[:8], p)
+    per_q = (time.perf_counter() - t) / 8
+    nper = int(max(8, min(Qh.shape[0], args.ref_step_seconds / max(per_q, 1e-6))))
+    times, used = [], 1
+    for s in range(args.warmup + args.steps):
+        lo = (s * nper) % max(1, Qh.shape[0] - nper + 1)
+        t = time.perf_counter()
+        _, _, _, used = oracle.search(ix, Qh[lo:lo + nper], p)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    tot = sum(times)
+    qps = nper * len(times) / tot
+    sample = f"{nper} queries per step of the 10,000, on the oracle's own index (built in {build_s:.0f} s, not timed)"
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, **point, "k": args.k},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_crisp(args):
+    import torch
+
+    import paper_2603_05180_gb300 as crisp
+    import synthetic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = load_peaks()
+
+    X, Q = make_workload(args, "cuda")
+    N, D, nq, k = args.n, args.dim, args.nq, args.k
+    draws = synthetic.method_draws(N, D, args.M, 50, seed=args.seed)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ix = crisp.crisp_build(X, N, D, crisp.build_params(args.M, draws=draws))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t
+    info = ix.info()
+    gi, gd = ground_truth(torch, X, Q, k)
+    gdk = gd[:, k - 1].contiguous()
+
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    st = torch.empty((nq, 6), dtype=torch.int64, device=dev)
+
+    def search(point, nqq=nq, Qx=Q, out=(ids, d2, st)):
+        sp = crisp.search_params(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"])
+        crisp.crisp_search(ix, Qx, nqq, sp, out[0][:nqq], out[1][:nqq], out[2][:nqq], stream)
+
+    # ---- operating point
+    point = dict(DEFAULT_POINT)
+    sweep_log = []
+    if args.sweep:
+        ns = 2000
+        best = None
+        for mode in (0, 1):
+            for alpha in (0.1, 0.2, 0.3, 0.4, 0.5):
+                for rho in (0.001, 0.002, 0.004, 0.007, 0.01, 0.015, 0.02, 0.03, 0.05):
+                    pt = dict(mode=mode, rho=rho, alpha=alpha)
+                    search(pt, ns)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    search(pt, ns)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    r = recall_at_k(torch, X, Q[:ns], ids[:ns], gdk[:ns])
+                    q = ns / (e0.elapsed_time(e1) / 1e3)
+                    sweep_log.append(dict(pt, recall=r, qps=q))
+                    if r >= 0.955 and (best is None or q > best[1]):
+                        best = (pt, q)
+                    if r >= 0.995:
+                        break
+        if best:
+            point = best[0]
+    for key in ("mode", "rho", "alpha"):
+        v = getattr(args, key)
+        if v is not None:
+            point[key] = v
+
+    # ---- timed region: W warm-up steps, K timed steps, L2 flushed before each
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        search(point)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = crisp.crisp_kernel_launches()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        search(point)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    launches = crisp.crisp_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    rec = recall_at_k(torch, X, Q, ids, gdk)
+    stats = st.cpu().numpy()
+    qps = world * nq * args.steps / (total_ms / 1e3)
+
+    # ---- stage-timed pass through the step entry points (same kernels, same launch shapes)
+    stage = stage_pass(torch, crisp, ix, info, Q, point, k, args.steps, stream, flush)
+    shares = {n: v["ms"] for n, v in stage.items()}
+    dom = max((n for n in stage if stage[n]["bytes"]), key=lambda n: stage[n]["ms"])
+    dbytes, dms = stage[dom]["bytes"], stage[dom]["ms"]
+    achieved = dbytes / (dms / 1e3) / 1e9
+    traffic = _ncu_traffic(dom)
+    roofline = {"kernel": stage[dom]["kernel"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "stage_ms": {n: round(v, 4) for n, v in shares.items()},
+                "algorithmic_bytes_per_launch": dbytes}
+    step_bytes = sum(v["bytes"] for v in stage.values())
+
+    # ---- end to end through the host-buffer entry point
+    Qh = torch.empty((nq, D), dtype=torch.float32, pin_memory=True)
+    Qh.copy_(Q.cpu())
+    ih = torch.empty((nq, k), dtype=torch.int64, pin_memory=True)
+    dh = torch.empty((nq, k), dtype=torch.float32, pin_memory=True)
+    sp = crisp.search_params(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"])
+    crisp.crisp_search_host(ix, Qh, nq, sp, ih, dh, None, stream)
+    e2e_t = []
+    for s in range(max(3, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        crisp.crisp_search_host(ix, Qh, nq, sp, ih, dh, None, stream)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_qps = world * nq * len(e2e_t) / sum(e2e_t)
+
+    # ---- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Xh, Qhn = X.cpu().numpy(), Q.cpu().numpy()
+        ixo, obuild = oracle_index(Xh, args)
+        v, n, used, dt = oracle_time(ixo, Qhn, point, k, args.cpu_seconds)
+        cpu = {"value": v, "unit": "queries/s", "cores": used, "kind": "oracle",
+               "sample": f"first {n} of the 10,000 queries ({dt:.1f} s), on the oracle's own index of the same rows "
+                         f"and draws (built in {obuild:.0f} s, not timed)"}
+
+    if rank == 0:
+        mode_name = "guaranteed" if point["mode"] == 0 else "optimized"
+        line = {"metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "D": D, "nq": nq, "k": k, "M": args.M, "K": 50,
+                           "mode": mode_name, "rho": point["rho"], "alpha": point["alpha"],
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed before every timed step (512 MB write, outside the timed events)",
+                           "index_rotated": bool(info.rotated), "cev": info.cev, "build_s": round(build_s, 3)},
+                "recall_at_10": rec,
+                "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+                "latency_note": "per-step (whole 10,000-query batch) latency; per-request p99 comes with the serving loop",
+                "hbm_frac_step": step_bytes / (total_ms / args.steps / 1e3) / 1e9 / peak,
+                "candidates_mean": float(stats[:, 0].mean()), "full_distances_mean": float(stats[:, 2].mean()),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
+                        "d2h_bytes_per_step": nq * k * 12},
+                "gpu_launches": launches, "clocks": clk}
+        if sweep_log:
+            line["sweep"] = sweep_log
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
+    """Time each kernel of the search path with CUDA events on the launching stream,
+    and count the algorithmic bytes each launch must move (DESIGN: per-stage units)."""
+    nq, Dp, M, K = Q.shape[0], info.Dp, info.M, info.K
+    dev = Q.device
+    tau = crisp.tau(point["alpha"], M)
+    bud = crisp.budget(point["rho"], info.N)
+    w = 2 if point["mode"] == 1 else 1
+    stride = min(info.N, max(-(-w * M * (bud + info.max_cell) // tau), k)) if tau > 0 else info.N
+    Qr = torch.empty((nq, Dp), dtype=torch.float32, device=dev)
+    act = torch.empty((nq, M, K * K), dtype=torch.int32, device=dev)
+    nact = torch.empty((nq, M), dtype=torch.int32, device=dev)
+    got = torch.empty((nq, M), dtype=torch.int64, device=dev)
+    cand = torch.empty((nq, stride), dtype=torch.int32, device=dev)
+    ncand = torch.empty((nq,), dtype=torch.int64, device=dev)
+    how = torch.empty((nq,), dtype=torch.int32, device=dev)
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    nv = torch.empty((nq,), dtype=torch.int64, device=dev)
+    nf = torch.empty((nq,), dtype=torch.int64, device=dev)
+    nb = torch.empty((nq,), dtype=torch.int64, device=dev)
+    names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
+    kernels = ["k_rotate", "k_activate", "k_count_cut", "k_rerank" if point["mode"] == 0 else "k_verify_opt"]
+    acc = {n: 0.0 for n in names}
+
+    def one():
+        if info.rotated:
+            crisp.crisp_rotate_rows(Q, nq, info.D, info.D, info.R32, Qr, Dp, stream)
+        else:
+            Qr.zero_()
+            Qr[:, :info.D] = Q
+        yield
+        crisp.crisp_activate(ix, Qr, nq, point["mode"], k, bud, act, nact, got, stream)
+        yield
+        crisp.crisp_count_cut(ix, act, nact, nq, tau, k, 0, cand, stride, ncand, None, how, stream)
+        yield
+        if point["mode"] == 0:
+            crisp.crisp_rerank(ix, Qr, nq, cand, stride, ncand, k, ids, d2, stream)
+        else:
+            crisp.crisp_verify_opt(ix, Qr, nq, cand, stride, ncand, k, 2.1, 40 * k, ids, d2, nv, nf, nb, stream)
+        yield
+
+    for s in range(steps + 1):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        evs[0].record(stream)
+        for i, _ in enumerate(one()):
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if s == 0:
+            continue            # warm-up
+        for i, n in enumerate(names):
+            acc[n] += evs[i].elapsed_time(evs[i + 1]) / steps
+    C = float(ncand.sum().item())
+    retr = float(got.sum().item())
+    cells = float(nact.sum().item())
+    W = Dp // 32
+    out = {
+        "rotate": {"ms": acc["rotate"], "bytes": 0, "kernel": "k_rotate"},
+        "activate": {"ms": acc["activate"], "bytes": 0, "kernel": "k_activate"},
+        # ids streamed from the CSR lists + 8 B per activated cell + candidate ids written
+        "count_cut": {"ms": acc["count_cut"], "bytes": 4 * retr + 8 * cells + 4 * C, "kernel": "k_count_cut"},
+    }
+    if point["mode"] == 0:
+        # every candidate row (Dp floats) + its id
+        out["rerank"] = {"ms": acc["rerank"], "bytes": C * (4 * Dp + 4), "kernel": "k_rerank"}
+    else:
+        blocks = float(nb.sum().item())
+        out["verify_opt"] = {"ms": acc["verify_opt"], "bytes": C * (4 * W + 4) + 128 * blocks,
+                             "kernel": "k_verify_opt"}
+    for n, kn in zip(names, kernels):
+        out[n]["kernel"] = kn
+    return out
+
+
+def _ncu_traffic(stage):
+    """DRAM bytes per launch from the committed ncu summary, when one exists for this kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        v = d.get(stage)
+        return v
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["crisp", "reference"], default="crisp")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--dim", type=int, default=960)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--M", type=int, default=20)
+    ap.add_argument("--mode", type=int, default=None)
+    ap.add_argument("--rho", type=float, default=None)
+    ap.add_argument("--alpha", type=float, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--sweep", action="store_true", help="pick the operating point by a recall/QPS sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_crisp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -156,7 +156,8 @@ uint64_t crisp_kernel_launches(void);
  * space (rotated inside when the index is rotated).  ids: device [nq][k] int64,
  * sqdist: device [nq][k] float32, both ascending by (distance, id) and padded
  * with -1 / +inf when fewer than k points qualify.  stats: device [nq] or NULL.
- * Scratch comes from the stream-ordered allocator of the current device.
+ * Scratch comes from a stream-ordered memory pool the library keeps per device
+ * (it holds its memory between calls; crisp_search_scratch_bytes tells how much).
  * EINVAL: k outside [1, 256] or > N, rho outside (0, 1], alpha outside [0, 1],
  * mode outside {0, 1}, 0 < max_candidates < k, nq < 0. */
 crisp_status crisp_search(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *params,
@@ -272,11 +273,14 @@ crisp_status crisp_rerank(const crisp_index *index, const float *Qr, int32_t nq,
  * fl32((t/D)(1 + eps0/sqrt t)^2) evaluated in FP64), else measured exactly and
  * offered to the top-k; the walk stops once P = patience consecutive
  * candidates left the top-k unchanged (patience <= 0: never).  Results equal
- * the sequential walk exactly.  n_verified, n_full: device [nq] int64 or NULL.
+ * the sequential walk exactly.  n_verified, n_full: device [nq] int64 or NULL;
+ * n_blocks: device [nq] int64 or NULL, the 32-dim row blocks the kernel read
+ * (its row traffic is 128 bytes per block).
  * EUNSUPPORTED: a query with more than 32768 candidates (cap them). */
 crisp_status crisp_verify_opt(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t cand_stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
-                              int64_t *ids, float *sqdist, int64_t *n_verified, int64_t *n_full, void *stream);
+                              int64_t *ids, float *sqdist, int64_t *n_verified, int64_t *n_full,
+                              int64_t *n_blocks, void *stream);
 
 #ifdef __cplusplus
 }

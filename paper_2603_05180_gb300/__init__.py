@@ -78,7 +78,7 @@ _SIGS = {
     "crisp_activate": [_P, _P, _I32, _I32, _I32, _I64, _P, _P, _P, _P],
     "crisp_count_cut": [_P, _P, _P, _I32, _I32, _I32, _I64, _P, _I64, _P, _P, _P, _P],
     "crisp_rerank": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
-    "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P],
+    "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P, _P],
 }
 
 
@@ -267,9 +267,9 @@ def crisp_rerank(index, Qr, nq, cand, cand_stride, ncand, k, ids, sqdist, stream
 
 
 def crisp_verify_opt(index, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified=None,
-                     n_full=None, stream=None):
+                     n_full=None, n_blocks=None, stream=None):
     _call("crisp_verify_opt", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, float(eps0), patience,
-          _ptr(ids), _ptr(sqdist), _ptr(n_verified), _ptr(n_full), _stream(stream))
+          _ptr(ids), _ptr(sqdist), _ptr(n_verified), _ptr(n_full), _ptr(n_blocks), _stream(stream))
 
 
 # ------------------------------------------------------------ conveniences
@@ -293,8 +293,9 @@ def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.
 
 def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None):
     """BuildParams; ``draws`` (host numpy arrays: cev_sample, gaussian,
-    kmeans_sample, kmeans_init) are referenced, so keep them alive for the call."""
+    kmeans_sample, kmeans_init) are referenced by the returned struct."""
     p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None)
+    p._draws = draws          # the struct holds raw pointers into these arrays: keep them alive with it
     if draws is not None:
         p.cev_sample = draws.cev_sample.ctypes.data
         p.cev_sample_n = draws.cev_sample.size

@@ -22,9 +22,43 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
                               cudaStream_t st);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
-                                  int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, void *scratch,
+                                  int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
                                   cudaStream_t st);
-size_t crisp_verify_opt_scratch(const crisp_index *ix, int32_t nq, int64_t stride);
+
+// ------------------------------------------------------------ scratch pool
+#include <mutex>
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+static bool g_pool_ok[64];
+
+static cudaMemPool_t scratch_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_pool_ok[dev]) {
+        cudaMemPoolProps pp = {};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = dev;
+        if (cudaMemPoolCreate(&g_pool[dev], &pp) != cudaSuccess) return nullptr;
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool_ok[dev] = true;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t crisp_scratch_alloc(void **p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = scratch_pool(dev);
+    if (!pool) return cudaMallocAsync(p, bytes, st);
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void crisp_scratch_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
 
 // ------------------------------------------------------------------ errors
 static thread_local char g_err[512] = "";
@@ -249,18 +283,25 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     pl->phi = p->mode;
     pl->k = p->k;
     pl->cap = p->max_candidates;
-    int64_t bound = pl->tau <= 0 ? ix->N
-                                 : std::min<int64_t>(ix->N, (int64_t)ix->M * (pl->budget + ix->max_cell));
+    // Every candidate needs V >= tau and the scores sum to at most w * (ids
+    // retrieved), each subspace retrieving fewer than budget + largest cell:
+    // |C| <= w M (budget + max_cell) / tau; the fallback returns at most k.
+    int64_t bound = ix->N;
+    if (pl->tau > 0) {
+        int64_t w = p->mode == 1 ? 2 : 1;
+        int64_t votes = w * (int64_t)ix->M * (pl->budget + ix->max_cell);
+        bound = std::min<int64_t>(ix->N, std::max<int64_t>((votes + pl->tau - 1) / pl->tau, p->k));
+    }
     pl->stride = p->max_candidates > 0 ? std::min<int64_t>(p->max_candidates, bound) : bound;
     if (pl->cap > pl->stride) pl->cap = 0;   // the cap can never bind
     pl->stride = std::max<int64_t>(pl->stride, 1);
     const int64_t K2 = (int64_t)ix->K * ix->K;
     pl->per_query = sizeof(float) * ix->Dp + sizeof(int32_t) * ix->M * K2 + sizeof(int32_t) * ix->M +
                     sizeof(int64_t) * ix->M + sizeof(int32_t) * pl->stride * 2 + 64;
-    size_t budget_bytes = (size_t)4 << 30;
+    size_t budget_bytes = (size_t)16 << 30;
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
-    chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, 8192));
+    chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, 32768));
     pl->chunk = (int32_t)std::min<int64_t>(chunk, std::max<int32_t>(nq, 1));
     return CRISP_OK;
 }
@@ -271,7 +312,7 @@ extern "C" crisp_status crisp_search_scratch_bytes(const crisp_index *ix, int32_
     crisp_status s = plan_search(ix, nq, p, &pl);
     if (s) return s;
     CRISP_REQUIRE(bytes, "crisp_search_scratch_bytes: null output");
-    *bytes = pl.per_query * (size_t)pl.chunk + (p->mode == 1 ? crisp_verify_opt_scratch(ix, pl.chunk, pl.stride) : 0);
+    *bytes = pl.per_query * (size_t)pl.chunk;
     return CRISP_OK;
 }
 
@@ -291,18 +332,17 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
     CRISP_REQUIRE(Q && ids && d2, "crisp_search: null pointer");
     const int64_t K2 = (int64_t)ix->K * ix->K;
     const int32_t C = pl.chunk, M = ix->M;
-    size_t vbytes = p->mode == 1 ? crisp_verify_opt_scratch(ix, C, pl.stride) : 0;
     size_t total = 0;
     {
         size_t parts[] = {sizeof(float) * (size_t)C * ix->Dp, sizeof(int32_t) * (size_t)C * M * K2,
                           sizeof(int32_t) * (size_t)C * M, sizeof(int64_t) * (size_t)C * M,
                           sizeof(int32_t) * (size_t)C * pl.stride, sizeof(float) * (size_t)C * pl.stride,
                           sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C, sizeof(int64_t) * (size_t)C,
-                          sizeof(int64_t) * (size_t)C, vbytes};
+                          sizeof(int64_t) * (size_t)C};
         for (size_t x : parts) total += (x + 255) / 256 * 256;
     }
     uint8_t *base = nullptr;
-    CRISP_CK(cudaMallocAsync((void **)&base, total, st));
+    CRISP_CK(crisp_scratch_alloc((void **)&base, total, st));
     uint8_t *cur = base;
     float *Qr = carve<float>(cur, (size_t)C * ix->Dp);
     int32_t *act = carve<int32_t>(cur, (size_t)C * M * K2);
@@ -314,7 +354,6 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
     int32_t *how = carve<int32_t>(cur, C);
     int64_t *nver = carve<int64_t>(cur, C);
     int64_t *nfull = carve<int64_t>(cur, C);
-    void *vscr = vbytes ? (void *)carve<uint8_t>(cur, vbytes) : nullptr;
     for (int32_t c0 = 0; c0 < nq && s == CRISP_OK; c0 += C) {
         int32_t nc = std::min(C, nq - c0);
         const float *Qc = Q + (int64_t)c0 * ix->D;
@@ -331,11 +370,11 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
         } else if (!s) {
             int64_t P = p->patience_factor > 0 ? (int64_t)p->patience_factor * pl.k : 0;
             s = crisp_run_verify_opt(ix, Qr, nc, cand, pl.stride, ncand, pl.k, p->eps0, P, ids_c, d2_c, nver, nfull,
-                                     vscr, st);
+                                     nullptr, st);
             if (!s && stats) s = launch_write_stats(nc, ncand, how, retr, M, nver, nfull, pl.tau, stats + c0, st);
         }
     }
-    cudaFreeAsync(base, st);
+    crisp_scratch_free(base, st);
     return s;
 }
 
@@ -357,7 +396,7 @@ extern "C" crisp_status crisp_search_host(const crisp_index *ix, const float *Q,
            db = sizeof(float) * (size_t)nq * p->k, sb = stats ? sizeof(crisp_query_stats) * (size_t)nq : 0;
     uint8_t *buf = nullptr;
     size_t tot = (qb + 255) / 256 * 256 + (ib + 255) / 256 * 256 + (db + 255) / 256 * 256 + (sb + 255) / 256 * 256;
-    CRISP_CK(cudaMallocAsync((void **)&buf, tot, st));
+    CRISP_CK(crisp_scratch_alloc((void **)&buf, tot, st));
     uint8_t *cur = buf;
     float *dQ = carve<float>(cur, (size_t)nq * ix->D);
     int64_t *dI = carve<int64_t>(cur, (size_t)nq * p->k);
@@ -372,7 +411,7 @@ extern "C" crisp_status crisp_search_host(const crisp_index *ix, const float *Q,
         if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, dS, sb, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) s = crisp_cuda_fail(e, "cudaMemcpyAsync(out)", __FILE__, __LINE__);
     }
-    cudaFreeAsync(buf, st);
+    crisp_scratch_free(buf, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (!s && e2 != cudaSuccess) s = crisp_cuda_fail(e2, "cudaStreamSynchronize", __FILE__, __LINE__);
     return s;

@@ -82,6 +82,11 @@ int32_t crisp_tau(double alpha, int32_t M);
 int64_t crisp_budget(double rho, int64_t N);
 void crisp_subspace(int32_t D, int32_t M, int32_t m, int32_t *lo, int32_t *hl, int32_t *hr);
 
+// ------------------------------------------ stream-ordered scratch memory
+// A memory pool per device that keeps its memory between calls.
+cudaError_t crisp_scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+void crisp_scratch_free(void *p, cudaStream_t st);
+
 // ------------------------------------------------ internal launchers
 crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
                              cudaStream_t st);

@@ -857,8 +857,8 @@ extern "C" crisp_status crisp_rerank(const crisp_index *ix, const float *Qr, int
     if (nq == 0) return CRISP_OK;
     cudaStream_t st = as_stream(stream);
     float *dbuf = nullptr;
-    CRISP_CK(cudaMallocAsync((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
+    CRISP_CK(crisp_scratch_alloc((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
     crisp_status r = crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, st);
-    cudaFreeAsync(dbuf, st);
+    crisp_scratch_free(dbuf, st);
     return r;
 }

@@ -45,6 +45,7 @@ struct VoShared {
     long long counter, processed, nfull;
     int done;
     int stop_b[VO_CHUNK];      // blocks computed by the group (nb = full row)
+    unsigned long long nblk;
     float full[VO_CHUNK];
     int cid[VO_CHUNK];
     float r2_start;
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
                                                       const long long *__restrict__ ncand, int kk, float eps0,
                                                       long long patience, int cap_keys,
                                                       long long *__restrict__ out_ids, float *__restrict__ out_d,
-                                                      long long *__restrict__ out_nver, long long *__restrict__ out_nfull) {
+                                                      long long *__restrict__ out_nver, long long *__restrict__ out_nfull,
+                                                      long long *__restrict__ out_nblk) {
     extern __shared__ __align__(16) float smv[];
     __shared__ VoShared S;
     const int q = blockIdx.x, tid = threadIdx.x;
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
         qc[w] = v;
     }
     if (tid == 0) {
-        S.tk_n = 0; S.counter = 0; S.processed = 0; S.nfull = 0; S.done = 0;
+        S.tk_n = 0; S.counter = 0; S.processed = 0; S.nfull = 0; S.done = 0; S.nblk = 0;
     }
     __syncthreads();
 
@@ -143,7 +145,9 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
             float acc = 0.0f;
             int stop = nb;
             constexpr int U = 4;
+            int b_read = 0;
             for (int b0 = 0; b0 < nb && stop == nb; b0 += U) {
+                b_read = b0 + U;
                 float4 v[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -160,6 +164,8 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
                 }
             }
             if (l == 0) {
+                int rd = b_read < nb ? b_read : nb;
+                atomicAdd(&S.nblk, (unsigned long long)rd);
                 S.stop_b[g] = stop;
                 S.full[g] = acc;
                 S.cid[g] = id;
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
     if (tid == 0) {
         if (out_nver) out_nver[q] = S.processed;
         if (out_nfull) out_nfull[q] = S.nfull;
+        if (out_nblk) out_nblk[q] = (long long)S.nblk;
     }
 }
 
@@ -259,13 +266,10 @@ size_t vo_smem(const crisp_index *ix, int cap_keys) {
 
 }  // namespace
 
-size_t crisp_verify_opt_scratch(const crisp_index *, int32_t nq, int64_t) { return sizeof(int64_t) * (size_t)nq; }
-
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
-                                  int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, void *scratch,
+                                  int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
                                   cudaStream_t st) {
-    (void)scratch;
     if (nq <= 0) return CRISP_OK;
     int64_t cap = stride;
     if (cap > CRISP_OPT_MAX_CAND) {
@@ -289,7 +293,7 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
     CRISP_CK(cudaFuncSetAttribute(k_verify_opt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_verify_opt<<<nq, VO_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
                                           eps0, (long long)patience, cap_keys, (long long *)ids, d2,
-                                          (long long *)nver, (long long *)nfull);
+                                          (long long *)nver, (long long *)nfull, (long long *)nblk);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -298,11 +302,11 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
 extern "C" crisp_status crisp_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                          int64_t cand_stride, const int64_t *ncand, int32_t k, float eps0,
                                          int64_t patience, int64_t *ids, float *sqdist, int64_t *n_verified,
-                                         int64_t *n_full, void *stream) {
+                                         int64_t *n_full, int64_t *n_blocks, void *stream) {
     CRISP_REQUIRE(ix != nullptr, "null index");
     CRISP_REQUIRE(nq >= 0 && k >= 1 && k <= CRISP_KOUT_MAX, "crisp_verify_opt: bad nq or k");
     CRISP_REQUIRE(nq == 0 || (Qr && cand && ncand && ids && sqdist), "crisp_verify_opt: null pointer");
     CRISP_REQUIRE(cand_stride >= 1, "crisp_verify_opt: cand_stride < 1");
     return crisp_run_verify_opt(ix, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified,
-                                n_full, nullptr, as_stream(stream));
+                                n_full, n_blocks, as_stream(stream));
 }
