@@ -267,6 +267,27 @@ crisp_status crisp_rerank(const crisp_index *index, const float *Qr, int32_t nq,
                           int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
                           void *stream);
 
+/* crisp_rerank for callers that cannot allocate device memory while they
+ * search -- for instance when another allocator owns all of the GPU's memory,
+ * or when the query path must not call cudaMalloc/cudaFree (both can block and
+ * synchronise the device).  Same arguments, same results as crisp_rerank, but
+ * nothing is allocated: the per-candidate distance scratch is a fixed array of
+ * CRISP_RERANK_NOALLOC_MAX floats (16 MiB) that every GPU loading this library
+ * holds until the process exits.  The paper has no counterpart to this entry
+ * point; it exists for such callers only.
+ *  - EINVAL if nq * cand_stride > CRISP_RERANK_NOALLOC_MAX (nothing is run).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array and it keeps the previous call's contents;
+ *    every value is written before it is read, so nothing needs clearing.
+ *    Calls that overlap on the GPU (e.g. on two streams) race on the array:
+ *    order them on one stream or synchronise between them. */
+#define CRISP_RERANK_NOALLOC_MAX (4 * 1024 * 1024)
+crisp_status crisp_rerank_noalloc(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
+                                  int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
+                                  void *stream);
+
 /* Q7 (§4.3.2 Stages 2-3, phi = 1; Eq. 2): candidates ordered by (Hamming
  * distance of sign codes, id); each is pruned by ADSampling checks at t = 32,
  * 64, ... < D when the running top-k is full (d_t > fl(r_k^2 * f_t), f_t =

@@ -78,6 +78,7 @@ _SIGS = {
     "crisp_activate": [_P, _P, _I32, _I32, _I32, _I64, _P, _P, _P, _P],
     "crisp_count_cut": [_P, _P, _P, _I32, _I32, _I32, _I64, _P, _I64, _P, _P, _P, _P],
     "crisp_rerank": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
+    "crisp_rerank_noalloc": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
     "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P, _P],
 }
 
@@ -264,6 +265,15 @@ def crisp_count_cut(index, act, nact, nq, tau, k, cap, cand, cand_stride, ncand,
 def crisp_rerank(index, Qr, nq, cand, cand_stride, ncand, k, ids, sqdist, stream=None):
     _call("crisp_rerank", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, _ptr(ids), _ptr(sqdist),
           _stream(stream))
+
+
+def crisp_rerank_noalloc(index, Qr, nq, cand, cand_stride, ncand, k, ids, sqdist, stream=None):
+    """crisp_rerank without any device allocation (fixed 16 MiB scratch; see include/crisp.h)."""
+    _call("crisp_rerank_noalloc", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, _ptr(ids),
+          _ptr(sqdist), _stream(stream))
+
+
+CRISP_RERANK_NOALLOC_MAX = 4 * 1024 * 1024
 
 
 def crisp_verify_opt(index, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified=None,

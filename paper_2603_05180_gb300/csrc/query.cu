@@ -862,3 +862,47 @@ extern "C" crisp_status crisp_rerank(const crisp_index *ix, const float *Qr, int
     crisp_scratch_free(dbuf, st);
     return r;
 }
+
+// ==================================================== no-allocation re-rank
+// Distance scratch of crisp_rerank_noalloc: a fixed device array instead of an
+// allocation, for callers that cannot allocate device memory while searching.
+// In host code the name below is only a host-side stand-in; its device address
+// is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) float g_rerank_noalloc_dist[CRISP_RERANK_NOALLOC_MAX];
+
+#include <mutex>
+static std::mutex g_noalloc_mu;
+static float *g_noalloc_ptr[64];
+
+// Device address of the array on the current device (set up on first use).
+static crisp_status noalloc_scratch(float **out) {
+    int dev = 0;
+    CRISP_CK(cudaGetDevice(&dev));
+    CRISP_REQUIRE(dev >= 0 && dev < 64, "crisp_rerank_noalloc: device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        CRISP_CK(cudaGetSymbolAddress(&p, g_rerank_noalloc_dist));
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_rerank_noalloc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                             int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids,
+                                             float *sqdist, void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(k >= 1 && k <= CRISP_KOUT_MAX, "crisp_rerank_noalloc: k outside [1, 256]");
+    CRISP_REQUIRE(cand_stride >= 1, "crisp_rerank_noalloc: cand_stride < 1");
+    CRISP_REQUIRE(nq == 0 || (cand && ncand && ids && sqdist), "crisp_rerank_noalloc: null pointer");
+    CRISP_REQUIRE((int64_t)nq * cand_stride <= (int64_t)CRISP_RERANK_NOALLOC_MAX,
+                  "crisp_rerank_noalloc: nq * cand_stride = %lld exceeds the fixed scratch of %d floats",
+                  (long long)nq * cand_stride, CRISP_RERANK_NOALLOC_MAX);
+    if (nq == 0) return CRISP_OK;
+    float *dbuf = nullptr;
+    s = noalloc_scratch(&dbuf);
+    if (s) return s;
+    return crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, as_stream(stream));
+}
