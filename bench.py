@@ -240,7 +240,7 @@ def run_crisp(args):
     draws = synthetic.method_draws(N, D, args.M, 50, seed=args.seed)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    ix = crisp.crisp_build(X, N, D, crisp.build_params(args.M, draws=draws))
+    ix = crisp.crisp_build(X, N, D, crisp.build_params(args.M, draws=draws, copies=3))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t
     info = ix.info()
@@ -252,8 +252,23 @@ def run_crisp(args):
     st = torch.empty((nq, 6), dtype=torch.int64, device=dev)
 
     def search(point, nqq=nq, Qx=Q, out=(ids, d2, st)):
-        sp = crisp.search_params(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"])
+        sp = crisp.search_params(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"],
+                                 precision=point.get("precision", 0), shortlist=point.get("shortlist", 0))
         crisp.crisp_search(ix, Qx, nqq, sp, out[0][:nqq], out[1][:nqq], out[2][:nqq], stream)
+
+    def timed(point, steps):
+        for _ in range(3):
+            search(point)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            search(point)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return nq * steps / (tot / 1e3), recall_at_k(torch, X, Q, ids, gdk), tot / steps
 
     # ---- operating point
     point = dict(DEFAULT_POINT)
@@ -315,6 +330,7 @@ def run_crisp(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     rec = recall_at_k(torch, X, Q, ids, gdk)
+    rec_sub = recall_at_k(torch, X, Q[:2000], ids[:2000], gdk[:2000])
     stats = st.cpu().numpy()
     qps = world * nq * args.steps / (total_ms / 1e3)
 
@@ -331,6 +347,24 @@ def run_crisp(args):
                 "stage_ms": {n: round(v, 4) for n, v in shares.items()},
                 "algorithmic_bytes_per_launch": dbytes}
     step_bytes = sum(v["bytes"] for v in stage.values())
+
+    # ---- coarse-scoring variants (BF16 / FP8 rows, FP32 re-rank of a shortlist)
+    variants = {}
+    if not args.no_variants:
+        ns = 2000
+        for name, prec in (("bf16", 1), ("fp8", 2)):
+            chosen = None
+            for S in (50, 100, 200, 400, 800, 1600):
+                pt = dict(point, precision=prec, shortlist=S)
+                search(pt, ns)
+                torch.cuda.synchronize()
+                r = recall_at_k(torch, X, Q[:ns], ids[:ns], gdk[:ns])
+                chosen = pt
+                if r >= rec_sub - 0.002:
+                    break
+            q_v, r_v, ms_v = timed(chosen, args.steps)
+            variants[name] = {"precision": name, "shortlist": chosen["shortlist"], "value": q_v, "recall_at_10": r_v,
+                              "ms_per_step": ms_v, "speedup_vs_fp32": q_v / qps * world}
 
     # ---- end to end through the host-buffer entry point
     Qh = torch.empty((nq, D), dtype=torch.float32, pin_memory=True)
@@ -376,7 +410,8 @@ def run_crisp(args):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
                         "d2h_bytes_per_step": nq * k * 12},
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk,
+                "coarse_scoring": variants}
         if sweep_log:
             line["sweep"] = sweep_log
         print(json.dumps(line), flush=True)
@@ -487,6 +522,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--sweep", action="store_true", help="pick the operating point by a recall/QPS sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the BF16 / FP8 coarse-scoring measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = ap.parse_args()

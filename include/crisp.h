@@ -75,6 +75,7 @@ typedef struct {
     const int64_t *kmeans_sample; /* host [kmeans_sample_n] row numbers, or NULL */
     int64_t kmeans_sample_n;
     const int32_t *kmeans_init;   /* host [M][2][K] positions in the k-means sample, or NULL */
+    uint32_t copies;              /* low-precision row copies to keep: bit 0 BF16, bit 1 FP8 E4M3 */
 } crisp_build_params;
 
 /* Search parameters (Algorithm 1, §4.3, Table 1). */
@@ -86,6 +87,10 @@ typedef struct {
     int32_t patience_factor;   /* Optimized: stop after P = patience_factor*k unchanged; <= 0 off */
     float eps0;                /* Optimized: ADSampling margin of Eq. 2 (2.1); may be +inf */
     int64_t max_candidates;    /* 0 = no cap; else keep the cap best (V desc, id asc), cap >= k */
+    int32_t precision;         /* Guaranteed mode coarse scoring: 0 none (FP32 re-rank of every
+                                  candidate), 1 BF16 rows, 2 FP8 E4M3 rows with per-row scales */
+    int32_t shortlist;         /* precision > 0: candidates kept by the coarse score for the FP32
+                                  re-rank (>= k) */
 } crisp_search_params;
 
 /* Per-query counters written by crisp_search (device array, may be NULL). */
@@ -115,6 +120,9 @@ typedef struct {
     const int32_t *ids;        /* [M][N] */
     const float *Xr;           /* [N][Dp] */
     const uint32_t *codes;     /* [N][Dp/32] */
+    const uint16_t *Xb;        /* [N][Dp] BF16 bits, or NULL */
+    const uint8_t *X8;         /* [N][Dp] FP8 E4M3 codes, or NULL */
+    const float *S8;           /* [N] FP8 row scales, or NULL */
 } crisp_index_info;
 
 /* ================================================================ index */
@@ -143,6 +151,11 @@ crisp_status crisp_index_import(const void *host_buf, size_t bytes, void *stream
 
 crisp_status crisp_index_get_info(const crisp_index *index, crisp_index_info *out);
 
+/* Add low-precision copies of the stored rows to an index (bit 0: BF16, bit 1:
+ * FP8 E4M3), as crisp_quantize_bf16 / crisp_quantize_e4m3 define them.  Copies
+ * already present are kept.  Synchronous. */
+crisp_status crisp_index_add_copies(crisp_index *index, uint32_t copies, void *stream);
+
 const char *crisp_last_error(void);
 
 /* Number of kernels this library has launched in the process so far (search
@@ -159,7 +172,9 @@ uint64_t crisp_kernel_launches(void);
  * Scratch comes from a stream-ordered memory pool the library keeps per device
  * (it holds its memory between calls; crisp_search_scratch_bytes tells how much).
  * EINVAL: k outside [1, 256] or > N, rho outside (0, 1], alpha outside [0, 1],
- * mode outside {0, 1}, 0 < max_candidates < k, nq < 0. */
+ * mode outside {0, 1}, 0 < max_candidates < k, nq < 0, precision outside
+ * {0, 1, 2} or used outside Guaranteed mode, shortlist < k, or a precision
+ * whose row copy the index lacks. */
 crisp_status crisp_search(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *params,
                           int64_t *ids, float *sqdist, crisp_query_stats *stats, void *stream);
 
@@ -226,6 +241,26 @@ crisp_status crisp_csr_build(const uint16_t *cells, int64_t N, int32_t K2, int32
 /* B5 (§3 Binary Quantization): codes[n][w] bit b = (Xr[n][32w+b] > 0).
  * Xr device [N][Dp] (Dp multiple of 32), codes device [N][Dp/32] uint32. */
 crisp_status crisp_sign_codes(const float *Xr, int64_t N, int32_t Dp, uint32_t *codes, void *stream);
+
+/* F2 (coarse scoring): BF16 copy of Xr (device [N][Dp] float32) with round to
+ * nearest even; Xb: device [N][Dp] uint16 (the BF16 bit patterns). */
+crisp_status crisp_quantize_bf16(const float *Xr, int64_t N, int32_t Dp, uint16_t *Xb, void *stream);
+
+/* F2: FP8 E4M3 copy with one scale per row: s = fl(max_d |x_d| / 448) (1 for a
+ * zero row), code = e4m3(fl(x_d / s)), round to nearest even, saturating to
+ * +-448 (OCP E4M3, no infinities).  X8: device [N][Dp] uint8; scale: device [N]. */
+crisp_status crisp_quantize_e4m3(const float *Xr, int64_t N, int32_t Dp, uint8_t *X8, float *scale, void *stream);
+
+/* F2: coarse scoring of the candidates.  For each query row of Qr (device
+ * [nq][Dp]) the CR32 distance to every candidate's dequantised row (BF16 widened
+ * exactly, or the E4M3 value times the row scale, precision 1 or 2), then the S
+ * smallest by (distance, id), written in ascending id to out (device
+ * [nq][out_stride] int32) with their number in nout (device [nq] int64).
+ * cand/ncand as written by crisp_count_cut.  EINVAL: the index lacks the copy,
+ * S < 1, out_stride < S. */
+crisp_status crisp_shortlist(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
+                             int64_t cand_stride, const int64_t *ncand, int32_t precision, int32_t S, int32_t *out,
+                             int64_t out_stride, int64_t *nout, void *stream);
 
 /* Q2 (Algorithm 1 "Dist1, Dist2"): for every query row of Qr (device [nq][Dp],
  * already rotated) and subspace m, the K partial squared distances to each

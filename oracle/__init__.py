@@ -46,12 +46,15 @@ class _OrIndex(C.Structure):
     _fields_ = [("N", C.c_int64), ("D", C.c_int32), ("Dp", C.c_int32), ("M", C.c_int32), ("K", C.c_int32),
                 ("H", C.c_int32), ("rotated", C.c_int32), ("_pad", C.c_int32),
                 ("R32", C.c_void_p), ("cent", C.c_void_p), ("offsets", C.c_void_p), ("ids", C.c_void_p),
-                ("Xr", C.c_void_p), ("codes", C.c_void_p)]
+                ("Xr", C.c_void_p), ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p),
+                ("S8", C.c_void_p), ("mlp", C.c_void_p), ("mlp_H", C.c_int32), ("_pad2", C.c_int32)]
 
 
 class _OrParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
-                ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64)]
+                ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64),
+                ("precision", C.c_int32), ("shortlist", C.c_int32), ("depth_margin", C.c_float),
+                ("short_margin", C.c_float)]
 
 
 STATS_DTYPE = np.dtype([("n_candidates", np.int64), ("n_verified", np.int64), ("n_full", np.int64),
@@ -88,6 +91,21 @@ def _declare(L):
         "or_verify_opt": (_I32, [_P, _P, _P, _P, _I64, _I32, _F, _I64, _P, _P, _P, _P]),
         "or_search_batch": (_I32, [_P, _P, _I64, _I32, _P, _P, _P, _P, _I32]),
         "or_knn_f64": (None, [_P, _I64, _I32, _I32, _P, _I64, _I32, _I32, _P, _P]),
+        "or_bf16_rne": (C.c_uint16, [_F]),
+        "or_bf16_to_f32": (_F, [C.c_uint16]),
+        "or_e4m3_rne": (C.c_uint8, [_F]),
+        "or_e4m3_to_f32": (_F, [C.c_uint8]),
+        "or_quantize_bf16": (None, [_P, _I64, _I32, _P]),
+        "or_quantize_e4m3": (None, [_P, _I64, _I32, _P, _P]),
+        "or_prescore": (_F, [_P, _P, _F, _P, _I32]),
+        "or_shortlist": (_I64, [_P, _P, _P, _I32, _P, _P, _I64, _I64, _P]),
+        "or_erf_as": (_F, [_F]),
+        "or_gelu": (_F, [_F]),
+        "or_mlp_infer": (None, [_P, _I32, _I32, _I32, _P, _P]),
+        "or_features": (None, [_P, _P, _I64, _I64, _P, _P, _I32, _I32, _I32, _P]),
+        "or_depth": (_I64, [_F, _F, _I64, _I64]),
+        "or_select_by_score": (_I64, [_P, _P, _I64, _I64, _P]),
+        "or_activate_heap_costs": (_I32, [_P, _P, _I32, _I32, _I32, _I64, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -273,14 +291,33 @@ class Index:
     cells: np.ndarray         # [M][N] uint16 (u_m(x), kept for the Eq. 1 check)
     R64: np.ndarray | None = None
     eig: np.ndarray | None = None
+    Xb: np.ndarray | None = None          # [N][Dp] BF16 bits (F2)
+    X8: np.ndarray | None = None          # [N][Dp] FP8 E4M3 codes (F2)
+    S8: np.ndarray | None = None          # [N] FP8 row scales
+    mlp: np.ndarray | None = None         # learned depth model, packed FP32 parameters
+    mlp_H: int = 0
     _st: _OrIndex | None = field(default=None, repr=False)
+
+    def set_model(self, params, H):
+        self.mlp = np.ascontiguousarray(params, np.float32)
+        self.mlp_H = int(H)
+        self._st = None
+        return self
+
+    def add_copies(self, bf16=True, fp8=True):
+        if bf16 and self.Xb is None:
+            self.Xb = quantize_bf16(self.Xr)
+        if fp8 and self.X8 is None:
+            self.X8, self.S8 = quantize_e4m3(self.Xr)
+        self._st = None
+        return self
 
     def st(self) -> _OrIndex:
         if self._st is None:
+            pv = lambda a: _p(a).value if a is not None else None
             self._st = _OrIndex(self.N, self.D, self.Dp, self.M, self.K, self.H, self.rotated, 0,
-                                _p(self.R32).value if self.R32 is not None else None,
-                                _p(self.cent).value, _p(self.offsets).value, _p(self.ids).value,
-                                _p(self.Xr).value, _p(self.codes).value)
+                                pv(self.R32), pv(self.cent), pv(self.offsets), pv(self.ids), pv(self.Xr),
+                                pv(self.codes), pv(self.Xb), pv(self.X8), pv(self.S8), pv(self.mlp), self.mlp_H, 0)
         return self._st
 
 
@@ -359,10 +396,14 @@ class SearchParams:
     patience_factor: int = 40
     eps0: float = 2.1
     max_candidates: int = 0
+    precision: int = 0            # Guaranteed mode coarse scoring: 0 none, 1 BF16, 2 FP8 E4M3
+    shortlist: int = 0            # candidates kept for the FP32 re-rank when precision > 0
+    depth_margin: float = 0.0     # learned mode (2): margins on the predicted log2 depths
+    short_margin: float = 0.0
 
     def st(self) -> _OrParams:
         return _OrParams(self.k, self.mode, self.rho, self.alpha, self.patience_factor, self.eps0,
-                         self.max_candidates)
+                         self.max_candidates, self.precision, self.shortlist, self.depth_margin, self.short_margin)
 
 
 def query_rotate(ix: Index, Q) -> np.ndarray:
@@ -494,3 +535,211 @@ def recall_at_k(found_ids: np.ndarray, gt_d2: np.ndarray, X: np.ndarray, Q: np.n
         d = ((X[ids].astype(np.float64) - Q[i].astype(np.float64)) ** 2).sum(1)
         hits += int(np.sum(d <= gt_d2[i, k - 1] * (1 + rel)))
     return hits / (found_ids.shape[0] * k)
+
+
+# ------------------------------------------- F2: low-precision coarse scoring
+def bf16_rne(x: float) -> int:
+    """BF16 bits of x, round to nearest even."""
+    return int(lib().or_bf16_rne(float(x)))
+
+
+def bf16_to_f32(b: int) -> float:
+    return float(lib().or_bf16_to_f32(int(b)))
+
+
+def e4m3_rne(x: float) -> int:
+    """OCP FP8 E4M3 (fn) bits of x: round to nearest even, saturating to +-448."""
+    return int(lib().or_e4m3_rne(float(x)))
+
+
+def e4m3_to_f32(c: int) -> float:
+    return float(lib().or_e4m3_to_f32(int(c)))
+
+
+def quantize_bf16(Xr) -> np.ndarray:
+    Xr = _c(Xr, np.float32)
+    out = np.empty(Xr.shape, np.uint16)
+    lib().or_quantize_bf16(_p(Xr), Xr.shape[0], Xr.shape[1], _p(out))
+    return out
+
+
+def quantize_e4m3(Xr):
+    """(codes [N][Dp] uint8, per-row scales [N] float32): s = max|x| / 448, code = e4m3(x / s)."""
+    Xr = _c(Xr, np.float32)
+    codes = np.empty(Xr.shape, np.uint8)
+    sc = np.empty(Xr.shape[0], np.float32)
+    lib().or_quantize_e4m3(_p(Xr), Xr.shape[0], Xr.shape[1], _p(codes), _p(sc))
+    return codes, sc
+
+
+def prescore(qr, xb=None, x8=None, s8=0.0) -> np.float32:
+    """CR32 distance of q to a row's dequantised BF16 or E4M3 copy."""
+    qr = _c(qr, np.float32)
+    if xb is not None:
+        xb = _c(xb, np.uint16)
+        return np.float32(lib().or_prescore(_p(xb), None, 0.0, _p(qr), qr.size))
+    x8 = _c(x8, np.uint8)
+    return np.float32(lib().or_prescore(None, _p(x8), float(s8), _p(qr), qr.size))
+
+
+def shortlist(ix: Index, qr, Cand, S, precision="bf16", quant=None):
+    """The S candidates of smallest (coarse distance, id), ascending id."""
+    qr = _c(qr, np.float32)
+    Cand = _c(Cand, np.int32)
+    out = np.empty(max(1, Cand.size), np.int32)
+    if precision == "bf16":
+        Xb = quant if quant is not None else quantize_bf16(ix.Xr)
+        n = lib().or_shortlist(_p(Xb), None, None, ix.Dp, _p(qr), _p(Cand), Cand.size, int(S), _p(out))
+    else:
+        X8, S8 = quant if quant is not None else quantize_e4m3(ix.Xr)
+        n = lib().or_shortlist(None, _p(X8), _p(S8), ix.Dp, _p(qr), _p(Cand), Cand.size, int(S), _p(out))
+    return out[:n].copy()
+
+
+# --------------------------------------- F1: learned re-rank depth (small MLP)
+def erf_as(u: float) -> np.float32:
+    """erf by Abramowitz & Stegun 7.1.28, evaluated in FP32 in the fixed order."""
+    return np.float32(lib().or_erf_as(float(u)))
+
+
+def gelu(z: float) -> np.float32:
+    return np.float32(lib().or_gelu(float(z)))
+
+
+def mlp_param_count(F, H, O):
+    return F * H + H + H * H + H + H * O + O
+
+
+def mlp_unpack(P, F, H, O):
+    P = np.asarray(P)
+    o = 0
+    out = []
+    for shape in ((F, H), (H,), (H, H), (H,), (H, O), (O,)):
+        n = int(np.prod(shape))
+        out.append(P[o:o + n].reshape(shape))
+        o += n
+    return out
+
+
+def mlp_infer(P, F, H, O, x) -> np.ndarray:
+    """The MLP in the engine's FP32 order (fmaf chains, A&S GELU)."""
+    P = _c(P, np.float32)
+    x = _c(x, np.float32)
+    y = np.empty(O, np.float32)
+    lib().or_mlp_infer(_p(P), F, H, O, _p(x), _p(y))
+    return y
+
+
+def _gelu64(z):
+    """GELU with the A&S 7.1.28 erf in FP64, and its derivative."""
+    a1, a2, a3, a4, a5, a6 = 0.0705230784, 0.0422820123, 0.0092705272, 0.0001520143, 0.0002765672, 0.0000430638
+    u = z / np.sqrt(2.0)
+    a = np.abs(u)
+    p = 1 + a * (a1 + a * (a2 + a * (a3 + a * (a4 + a * (a5 + a * a6)))))
+    dp = a1 + a * (2 * a2 + a * (3 * a3 + a * (4 * a4 + a * (5 * a5 + a * 6 * a6))))
+    e = 1 - p ** -16
+    erf = np.sign(u) * e
+    derf = 16 * p ** -17 * dp                  # d erf(u) / du (even in u)
+    g = 0.5 * z * (1 + erf)
+    dg = 0.5 * (1 + erf) + 0.5 * z * derf / np.sqrt(2.0)
+    return g, dg
+
+
+def mlp_forward64(P, F, H, O, X):
+    """FP64 forward of a batch; returns outputs and the cache for mlp_backward64."""
+    W1, b1, W2, b2, W3, b3 = (np.asarray(a, np.float64) for a in mlp_unpack(P, F, H, O))
+    X = np.asarray(X, np.float64)
+    Z1 = X @ W1 + b1
+    H1, dH1 = _gelu64(Z1)
+    Z2 = H1 @ W2 + b2
+    H2, dH2 = _gelu64(Z2)
+    Y = H2 @ W3 + b3
+    return Y, (X, H1, dH1, H2, dH2)
+
+
+def mlp_loss_grad64(P, F, H, O, X, T):
+    """Mean squared error over all outputs and its gradient (FP64, packed like P)."""
+    W1, b1, W2, b2, W3, b3 = (np.asarray(a, np.float64) for a in mlp_unpack(P, F, H, O))
+    Y, (X, H1, dH1, H2, dH2) = mlp_forward64(P, F, H, O, X)
+    B = X.shape[0]
+    dY = 2.0 * (Y - T) / (B * O)
+    loss = float(np.mean((Y - T) ** 2))
+    gW3 = H2.T @ dY
+    gb3 = dY.sum(0)
+    dZ2 = (dY @ W3.T) * dH2
+    gW2 = H1.T @ dZ2
+    gb2 = dZ2.sum(0)
+    dZ1 = (dZ2 @ W2.T) * dH1
+    gW1 = X.T @ dZ1
+    gb1 = dZ1.sum(0)
+    return loss, np.concatenate([g.ravel() for g in (gW1, gb1, gW2, gb2, gW3, gb3)])
+
+
+def features(V, Cand, N, first_cost, last_cost, M, k, t):
+    V = _c(V, np.int32)
+    Cand = _c(Cand, np.int32)
+    fc = _c(first_cost, np.float32)
+    lc = _c(last_cost, np.float32)
+    f = np.empty(2 * M + 68, np.float32)
+    lib().or_features(_p(V), _p(Cand), Cand.size, int(N), _p(fc), _p(lc), M, k, t, _p(f))
+    return f
+
+
+def depth(y, margin, lo, hi) -> int:
+    return int(lib().or_depth(float(y), float(margin), int(lo), int(hi)))
+
+
+def select_by_score(V, Cand, d):
+    V = _c(V, np.int32)
+    Cand = _c(Cand, np.int32)
+    out = np.empty(max(1, Cand.size), np.int32)
+    n = lib().or_select_by_score(_p(V), _p(Cand), Cand.size, int(d), _p(out))
+    return out[:n].copy()
+
+
+def activate_costs(ix: Index, qr, m, phi, k, bud):
+    qr = _c(qr, np.float32)
+    K2 = ix.K * ix.K
+    cells = np.empty(K2, np.int32)
+    w = np.empty(K2, np.uint8)
+    got = C.c_int64()
+    cf, cl = C.c_float(0.0), C.c_float(0.0)
+    n = lib().or_activate_heap_costs(C.byref(ix.st()), _p(qr), m, phi, k, bud, _p(cells), _p(w), C.byref(got),
+                                      C.byref(cf), C.byref(cl))
+    return cells[:n].copy(), w[:n].copy(), got.value, np.float32(cf.value), np.float32(cl.value)
+
+
+def learned_labels(ix: Index, Q, p: SearchParams):
+    """Features and depth labels of each query, from the plain Guaranteed search:
+    the minimal prefix of C by (V desc, id asc) holding the exact top-k over C,
+    and the minimal coarse-score (BF16) prefix of that prefix holding them."""
+    Q = np.atleast_2d(_c(Q, np.float32))
+    if ix.Xb is None:
+        ix.add_copies(bf16=True, fp8=False)
+    F = 2 * ix.M + 68
+    feats = np.empty((Q.shape[0], F), np.float32)
+    labels = np.empty((Q.shape[0], 2), np.int64)
+    for i in range(Q.shape[0]):
+        qr = query_rotate(ix, Q[i])[0]
+        bud = budget(p.rho, ix.N)
+        acts, cf, cl = [], np.zeros(ix.M, np.float32), np.zeros(ix.M, np.float32)
+        for m in range(ix.M):
+            cells, w, got, a, b = activate_costs(ix, qr, m, 0, p.k, bud)
+            acts.append((cells, w, got))
+            cf[m], cl[m] = a, b
+        V = scores_walk(ix, acts)
+        t = tau(p.alpha, ix.M)
+        Cand, _ = cut(V, t, p.k, p.max_candidates)
+        feats[i] = features(V, Cand, ix.N, cf, cl, ix.M, p.k, t)
+        top, _ = rerank(ix, qr, Cand, p.k)
+        top = top[top >= 0]
+        order = Cand[np.lexsort((Cand, -V[Cand]))]          # (V desc, id asc)
+        pos = {int(c): j for j, c in enumerate(order)}
+        dV = max(pos[int(r)] for r in top) + 1 if top.size else p.k
+        P = np.sort(order[:dV])
+        sc = np.array([prescore(qr, xb=ix.Xb[c]) for c in P], np.float32)
+        co = P[np.lexsort((P, sc))]
+        posS = {int(c): j for j, c in enumerate(co)}
+        dS = max(posS[int(r)] for r in top) + 1 if top.size else p.k
+        labels[i] = (dV, dS)
+    return feats, labels

@@ -40,6 +40,11 @@ typedef struct {
     const int32_t *ids;      /* [M][N]        CSR Vectors IDs (§4.2) */
     const float *Xr;         /* [N][Dp]       stored (rotated when triggered) rows */
     const uint32_t *codes;   /* [N][Dp/32]    sign codes b(x) (§3 Binary Quantization) */
+    const uint16_t *Xb;      /* [N][Dp]       BF16 copy (coarse scoring), or NULL */
+    const uint8_t *X8;       /* [N][Dp]       FP8 E4M3 copy, or NULL */
+    const float *S8;         /* [N]           FP8 row scales, or NULL */
+    const float *mlp;        /* learned depth model (F = 2M + 68 -> H -> H -> 2), or NULL */
+    int32_t mlp_H, _pad2;
 } or_index;
 
 typedef struct {
@@ -48,6 +53,10 @@ typedef struct {
     int32_t patience_factor; /* P = patience_factor * k (§4.3.2 Stage 3); <= 0 disables */
     float eps0;              /* ADSampling margin (Eq. 2) */
     int64_t max_candidates;  /* 0 = no cap */
+    int32_t precision;       /* Guaranteed mode coarse scoring: 0 none, 1 BF16, 2 FP8 E4M3 */
+    int32_t shortlist;       /* candidates kept by the coarse score for the FP32 re-rank */
+    float depth_margin;      /* learned mode: margins added to the predicted log2 depths */
+    float short_margin;
 } or_params;
 
 typedef struct {
@@ -308,8 +317,18 @@ static msq_key heap_pop(msq_key *h, int *n) {
  * is 2 when phi = 1 and rank <= k, else 1.  Writes the popped cells (original
  * centroid indices combined as cL*K + cR) and weights in pop order; returns
  * the number popped and the ids retrieved in *retrieved. */
+int or_activate_heap_costs(const or_index *ix, const float *qr, int m, int phi, int k, int64_t budget,
+                           int32_t *cells, uint8_t *w, int64_t *retrieved, float *cost_first, float *cost_last);
+
 int or_activate_heap(const or_index *ix, const float *qr, int m, int phi, int k, int64_t budget,
                      int32_t *cells, uint8_t *w, int64_t *retrieved) {
+    return or_activate_heap_costs(ix, qr, m, phi, k, budget, cells, w, retrieved, NULL, NULL);
+}
+
+/* As or_activate_heap, also reporting the cost of the first and the last
+ * visited cell (learned-mode features). */
+int or_activate_heap_costs(const or_index *ix, const float *qr, int m, int phi, int k, int64_t budget,
+                           int32_t *cells, uint8_t *w, int64_t *retrieved, float *cost_first, float *cost_last) {
     int K = ix->K;
     float d1[256], d2[256], s1[256], s2[256];
     int32_t p1[256], p2[256];
@@ -326,6 +345,8 @@ int or_activate_heap(const or_index *ix, const float *qr, int m, int phi, int k,
     while (got < budget && hn > 0) {
         msq_key t = heap_pop(heap, &hn);
         int cell = p1[t.i] * K + p2[t.j];
+        if (rank == 0 && cost_first) *cost_first = t.cost;
+        if (cost_last) *cost_last = t.cost;
         rank += 1;
         cells[npop] = cell;
         w[npop] = (uint8_t)((phi == 1 && rank <= k) ? 2 : 1);
@@ -552,20 +573,247 @@ int or_verify_opt(const or_index *ix, const float *qr, const uint32_t *qcode, co
     return size;
 }
 
+/* ------------------------------------ F2: low-precision coarse scoring */
+/* BF16 with round-to-nearest-even: the upper 16 bits of the FP32 pattern,
+ * rounded on the lower 16 (ties to an even upper half).  Inputs are finite. */
+uint16_t or_bf16_rne(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+float or_bf16_to_f32(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* OCP FP8 E4M3 ("fn" variant: no infinities, max finite 448), round to nearest
+ * even, saturating to +-448.  Exponent bias 7, 3 mantissa bits; subnormals
+ * m * 2^-9.  Inputs are finite. */
+uint8_t or_e4m3_rne(float x) {
+    uint8_t sign = x < 0.0f || (x == 0.0f && signbit(x)) ? 0x80 : 0x00;
+    double a = fabs((double)x);
+    if (a >= 448.0) return sign | 0x7E;
+    /* candidate values are multiples of 2^(e-3) on [2^e, 2^(e+1)), e >= -6;
+     * below 2^-6 the step is 2^-9 (subnormals) */
+    int ex = 0;
+    if (a > 0) frexp(a, &ex);           /* a = f 2^ex, f in [0.5, 1): binade 2^(ex-1) */
+    int e = a > 0 ? ex - 1 : -7;
+    if (e < -6) e = -6;
+    double step = ldexp(1.0, e - 3);
+    double q = a / step;                 /* exact: step is a power of two */
+    double fl = floor(q);
+    double r = q - fl;
+    double m = fl;
+    if (r > 0.5 || (r == 0.5 && fmod(fl, 2.0) == 1.0)) m = fl + 1.0;
+    double v = m * step;                 /* the rounded magnitude */
+    if (v >= 448.0) return sign | 0x7E;
+    if (v == 0.0) return sign;
+    int evx = 0;
+    frexp(v, &evx);
+    int ev = evx - 1;
+    if (ev < -6) {                       /* subnormal: v = mant * 2^-9 */
+        int mant = (int)(v / ldexp(1.0, -9));
+        return sign | (uint8_t)mant;
+    }
+    int mant = (int)(v / ldexp(1.0, ev - 3)) - 8;
+    return sign | (uint8_t)(((ev + 7) << 3) | mant);
+}
+
+float or_e4m3_to_f32(uint8_t c) {
+    int s = c >> 7, e = (c >> 3) & 0xF, m = c & 7;
+    double v = e == 0 ? m * ldexp(1.0, -9) : (8 + m) * ldexp(1.0, e - 10);
+    return (float)(s ? -v : v);
+}
+
+/* Per-row scale s = fl(max|x| / 448) (1 if the row is zero); codes e4m3(fl(x / s)). */
+void or_quantize_e4m3(const float *Xr, int64_t N, int Dp, uint8_t *X8, float *scale) {
+    for (int64_t n = 0; n < N; ++n) {
+        const float *x = Xr + n * Dp;
+        float mx = 0.0f;
+        for (int d = 0; d < Dp; ++d) mx = fabsf(x[d]) > mx ? fabsf(x[d]) : mx;
+        float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+        scale[n] = s;
+        for (int d = 0; d < Dp; ++d) X8[n * Dp + d] = or_e4m3_rne(x[d] / s);
+    }
+}
+
+void or_quantize_bf16(const float *Xr, int64_t N, int Dp, uint16_t *Xb) {
+    for (int64_t i = 0; i < N * (int64_t)Dp; ++i) Xb[i] = or_bf16_rne(Xr[i]);
+}
+
+/* Coarse distance of one candidate in the CR32 order, the row replaced by its
+ * dequantised copy: BF16 widened exactly, or E4M3 code times the row scale. */
+float or_prescore(const uint16_t *xb, const uint8_t *x8, float s8, const float *q, int Dp) {
+    float x[Dp];
+    for (int d = 0; d < Dp; ++d) x[d] = xb ? or_bf16_to_f32(xb[d]) : or_e4m3_to_f32(x8[d]) * s8;
+    return or_cr32(x, q, Dp);
+}
+
+typedef struct { float d; int32_t id; } did;
+static int did_cmp(const void *a, const void *b) {
+    const did *x = (const did *)a, *y = (const did *)b;
+    if (x->d != y->d) return x->d < y->d ? -1 : 1;
+    return x->id < y->id ? -1 : (x->id > y->id);
+}
+
+/* Shortlist: the S candidates of smallest (coarse distance, id), in ascending id.
+ * Returns the shortlist length min(S, nC). */
+int64_t or_shortlist(const uint16_t *Xb, const uint8_t *X8, const float *S8, int Dp, const float *qr, const int32_t *C,
+                     int64_t nC, int64_t S, int32_t *out) {
+    if (nC <= S) {
+        memcpy(out, C, sizeof(int32_t) * (size_t)nC);
+        return nC;
+    }
+    did *all = (did *)malloc(sizeof(did) * (size_t)nC);
+    for (int64_t c = 0; c < nC; ++c) {
+        int64_t id = C[c];
+        all[c].d = Xb ? or_prescore(Xb + id * Dp, NULL, 0.0f, qr, Dp) : or_prescore(NULL, X8 + id * Dp, S8[id], qr, Dp);
+        all[c].id = C[c];
+    }
+    qsort(all, (size_t)nC, sizeof(did), did_cmp);
+    for (int64_t i = 0; i < S; ++i) out[i] = all[i].id;
+    qsort(out, (size_t)S, sizeof(int32_t), i32_cmp);
+    free(all);
+    return S;
+}
+
+/* --------------------------- F1: learned re-rank depth (small MLP) */
+/* erf by Abramowitz & Stegun 7.1.28 (|error| <= 3e-7): for a >= 0,
+ * erf(a) = 1 - (1 + a1 a + ... + a6 a^6)^-16; odd extension.  Evaluated in
+ * FP32 in a fixed order (Horner with fmaf, four squarings, one division). */
+float or_erf_as(float u) {
+    float a = fabsf(u);
+    float p = 0.0000430638f;
+    p = fmaf(p, a, 0.0002765672f);
+    p = fmaf(p, a, 0.0001520143f);
+    p = fmaf(p, a, 0.0092705272f);
+    p = fmaf(p, a, 0.0422820123f);
+    p = fmaf(p, a, 0.0705230784f);
+    p = fmaf(p, a, 1.0f);
+    float p2 = p * p, p4 = p2 * p2, p8 = p4 * p4, p16 = p8 * p8;
+    float e = 1.0f - 1.0f / p16;
+    return u < 0.0f ? -e : e;
+}
+
+/* GELU(z) = z/2 (1 + erf(z / sqrt 2)), erf as above. */
+float or_gelu(float z) {
+    float u = z * 0.70710678118654752f;
+    return (0.5f * z) * (1.0f + or_erf_as(u));
+}
+
+/* MLP F -> H -> H -> O with GELU on both hidden layers; params packed as
+ * W1 [F][H], b1 [H], W2 [H][H], b2 [H], W3 [H][O], b3 [O].  Every unit is an
+ * fmaf chain over its inputs in order, starting from its bias. */
+void or_mlp_infer(const float *P, int F, int H, int O, const float *x, float *y) {
+    const float *W1 = P, *b1 = W1 + (int64_t)F * H, *W2 = b1 + H, *b2 = W2 + (int64_t)H * H, *W3 = b2 + H,
+                *b3 = W3 + (int64_t)H * O;
+    float h1[1024], h2[1024];
+    for (int j = 0; j < H; ++j) {
+        float z = b1[j];
+        for (int i = 0; i < F; ++i) z = fmaf(x[i], W1[(int64_t)i * H + j], z);
+        h1[j] = or_gelu(z);
+    }
+    for (int j = 0; j < H; ++j) {
+        float z = b2[j];
+        for (int i = 0; i < H; ++i) z = fmaf(h1[i], W2[(int64_t)i * H + j], z);
+        h2[j] = or_gelu(z);
+    }
+    for (int o = 0; o < O; ++o) {
+        float z = b3[o];
+        for (int j = 0; j < H; ++j) z = fmaf(h2[j], W3[(int64_t)j * O + o], z);
+        y[o] = z;
+    }
+}
+
+/* Feature vector of one query (F = 2M + 68), IEEE basic operations only:
+ *  [0, 64)        share of the candidates at each collision score (63 = 63 and above)
+ *  [64, 64+M)     cost of the first visited cell of each subspace / sum of last costs
+ *  [64+M, 64+2M)  cost of the last visited cell of each subspace / sum of last costs
+ *  then |C|/N, floor(log2(|C|+1))/32, k/256, tau/M. */
+void or_features(const int32_t *V, const int32_t *C, int64_t nC, int64_t N, const float *first_cost,
+                 const float *last_cost, int M, int k, int tau, float *f) {
+    int64_t cnt[64];
+    memset(cnt, 0, sizeof cnt);
+    for (int64_t c = 0; c < nC; ++c) {
+        int v = V[C[c]];
+        cnt[v < 63 ? v : 63]++;
+    }
+    float den = (float)(nC > 0 ? nC : 1);
+    for (int s = 0; s < 64; ++s) f[s] = (float)cnt[s] / den;
+    float norm = 0.0f;
+    for (int m = 0; m < M; ++m) norm = norm + last_cost[m];
+    if (!(norm > 0.0f)) norm = 1.0f;
+    for (int m = 0; m < M; ++m) {
+        f[64 + m] = first_cost[m] / norm;
+        f[64 + M + m] = last_cost[m] / norm;
+    }
+    int64_t v = nC + 1;
+    int lg = 0;
+    while (v > 1) { v >>= 1; ++lg; }
+    f[64 + 2 * M] = (float)nC / (float)N;
+    f[64 + 2 * M + 1] = (float)lg / 32.0f;
+    f[64 + 2 * M + 2] = (float)k / 256.0f;
+    f[64 + 2 * M + 3] = (float)tau / (float)M;
+}
+
+/* depth = ceil(2^(j/4)), j = ceil(4 (y + margin)) in FP32, clamped to [lo, hi];
+ * 2^(1/4) and 2^(1/2) from correctly rounded square roots. */
+int64_t or_depth(float y, float margin, int64_t lo, int64_t hi) {
+    float t = 4.0f * (y + margin);
+    if (!(t < 120.0f)) return hi;                 /* also catches NaN */
+    if (t < -120.0f) return lo;
+    int j = (int)ceilf(t);
+    int q = j >= 0 ? j / 4 : -((-j + 3) / 4);
+    int r = j - 4 * q;                            /* 0..3 */
+    double s2 = sqrt(2.0), s4 = sqrt(s2);
+    double fr = r == 0 ? 1.0 : r == 1 ? s4 : r == 2 ? s2 : s2 * s4;
+    double v = ceil(ldexp(fr, q));
+    int64_t d = v > 9.0e18 ? hi : (int64_t)v;
+    if (d < lo) d = lo;
+    if (d > hi) d = hi;
+    return d;
+}
+
+/* The first `depth` candidates by (V desc, id asc), returned in ascending id. */
+int64_t or_select_by_score(const int32_t *V, const int32_t *C, int64_t nC, int64_t depth, int32_t *out) {
+    if (depth >= nC) {
+        memcpy(out, C, sizeof(int32_t) * (size_t)nC);
+        return nC;
+    }
+    vid *all = (vid *)malloc(sizeof(vid) * (size_t)(nC > 0 ? nC : 1));
+    for (int64_t c = 0; c < nC; ++c) { all[c].v = V[C[c]]; all[c].id = C[c]; }
+    qsort(all, (size_t)nC, sizeof(vid), vid_cmp);
+    for (int64_t i = 0; i < depth; ++i) out[i] = all[i].id;
+    qsort(out, (size_t)depth, sizeof(int32_t), i32_cmp);
+    free(all);
+    return depth;
+}
+
 /* ---------------------------------------------- whole query (Algorithm 1) */
+int64_t or_shortlist(const uint16_t *Xb, const uint8_t *X8, const float *S8, int Dp, const float *qr, const int32_t *C,
+                     int64_t nC, int64_t S, int32_t *out);
 /* One query end to end: rotate, activate every subspace, count, cut, verify.
  * Scratch: V [N], C [N], cells/w [M][K^2]. */
 static void search_one(const or_index *ix, const float *q, int ldq, const or_params *p, int64_t *ids, float *d2,
-                       or_stats *st, int32_t *V, int32_t *C, int32_t *cells, uint8_t *w, float *qr, uint32_t *qcode) {
+                       or_stats *st, int32_t *V, int32_t *C, int32_t *C2, int32_t *cells, uint8_t *w, float *qr,
+                       uint32_t *qcode) {
     int K2 = ix->K * ix->K, M = ix->M;
     if (ix->rotated) or_rotate_row(q, ix->R32, ix->D, ix->Dp, qr);
     else { memcpy(qr, q, sizeof(float) * ix->D); for (int j = ix->D; j < ix->Dp; ++j) qr[j] = 0.0f; }
     (void)ldq;
     int32_t ncell[1024];
+    float cfirst[1024], clast[1024];
     int64_t budget = or_budget(p->rho, ix->N), got = 0;
     for (int m = 0; m < M; ++m) {
         int64_t r;
-        ncell[m] = or_activate_heap(ix, qr, m, p->mode == 1, p->k, budget, cells + (int64_t)m * K2, w + (int64_t)m * K2, &r);
+        cfirst[m] = clast[m] = 0.0f;
+        ncell[m] = or_activate_heap_costs(ix, qr, m, p->mode == 1, p->k, budget, cells + (int64_t)m * K2,
+                                          w + (int64_t)m * K2, &r, cfirst + m, clast + m);
         got += r;
     }
     or_scores_walk(ix, ncell, cells, w, V);
@@ -581,6 +829,28 @@ static void search_one(const or_index *ix, const float *q, int ldq, const or_par
         or_sign_codes(qr, 1, ix->Dp, qcode);
         int64_t P = p->patience_factor > 0 ? (int64_t)p->patience_factor * p->k : 0;
         or_verify_opt(ix, qr, qcode, C, nC, p->k, p->eps0, P, ids, d2, &st->n_verified, &st->n_full);
+    } else if (p->mode == 2) {
+        /* learned depths: features -> MLP -> keep the first depth_V by (V desc,
+         * id asc), coarse BF16 scores -> shortlist of depth_S -> FP32 re-rank */
+        int F = 2 * M + 68;
+        float f[2 * 1024 + 68], y[2];
+        or_features(V, C, nC, ix->N, cfirst, clast, M, p->k, tau, f);
+        or_mlp_infer(ix->mlp, F, ix->mlp_H, 2, f, y);
+        int64_t dV = or_depth(y[0], p->depth_margin, p->k, nC > p->k ? nC : p->k);
+        if (dV > nC) dV = nC;
+        int64_t dS = or_depth(y[1], p->short_margin, p->k, dV > p->k ? dV : p->k);
+        int64_t nV = or_select_by_score(V, C, nC, dV, C2);
+        int64_t ns = or_shortlist(ix->Xb, NULL, NULL, ix->Dp, qr, C2, nV, dS, C);
+        or_rerank(ix, qr, C, ns, p->k, ids, d2);
+        st->n_verified = nV;
+        st->n_full = ns;
+    } else if (p->precision > 0) {
+        /* coarse scores on the low-precision copy, FP32 re-rank of the shortlist */
+        int64_t ns = or_shortlist(p->precision == 1 ? ix->Xb : NULL, p->precision == 2 ? ix->X8 : NULL, ix->S8,
+                                  ix->Dp, qr, C, nC, p->shortlist, C2);
+        or_rerank(ix, qr, C2, ns, p->k, ids, d2);
+        st->n_verified = nC;
+        st->n_full = ns;
     } else {
         or_rerank(ix, qr, C, nC, p->k, ids, d2);
         st->n_verified = nC;
@@ -605,14 +875,15 @@ int or_search_batch(const or_index *ix, const float *Q, int64_t nq, int ldq, con
         int K2 = ix->K * ix->K;
         int32_t *V = (int32_t *)malloc(sizeof(int32_t) * (size_t)ix->N);
         int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)ix->N);
+        int32_t *C2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)ix->N);
         int32_t *cells = (int32_t *)malloc(sizeof(int32_t) * (size_t)ix->M * K2);
         uint8_t *w = (uint8_t *)malloc((size_t)ix->M * K2);
         float *qr = (float *)malloc(sizeof(float) * (size_t)ix->Dp);
         uint32_t *qc = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(ix->Dp / 32 + 1));
 #pragma omp for schedule(dynamic)
         for (int64_t i = 0; i < nq; ++i)
-            search_one(ix, Q + i * ldq, ldq, p, ids + i * p->k, d2 + i * p->k, st + i, V, C, cells, w, qr, qc);
-        free(V); free(C); free(cells); free(w); free(qr); free(qc);
+            search_one(ix, Q + i * ldq, ldq, p, ids + i * p->k, d2 + i * p->k, st + i, V, C, C2, cells, w, qr, qc);
+        free(V); free(C); free(C2); free(cells); free(w); free(qr); free(qc);
     }
     return used;
 }

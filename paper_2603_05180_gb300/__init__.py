@@ -34,12 +34,14 @@ class BuildParams(C.Structure):
     _fields_ = [("M", C.c_int32), ("K", C.c_int32), ("tau_cev", C.c_double), ("rotate", C.c_int32),
                 ("kmeans_iters", C.c_int32), ("kmeans_train", C.c_int64), ("seed", C.c_uint64),
                 ("cev_sample", C.c_void_p), ("cev_sample_n", C.c_int64), ("gaussian", C.c_void_p),
-                ("kmeans_sample", C.c_void_p), ("kmeans_sample_n", C.c_int64), ("kmeans_init", C.c_void_p)]
+                ("kmeans_sample", C.c_void_p), ("kmeans_sample_n", C.c_int64), ("kmeans_init", C.c_void_p),
+                ("copies", C.c_uint32)]
 
 
 class SearchParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
-                ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64)]
+                ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64),
+                ("precision", C.c_int32), ("shortlist", C.c_int32)]
 
 
 class QueryStats(C.Structure):
@@ -53,7 +55,7 @@ class IndexInfo(C.Structure):
                 ("H", C.c_int32), ("rotated", C.c_int32), ("cev", C.c_double), ("max_cell", C.c_int32),
                 ("id_tile_log2", C.c_int32), ("device_bytes", C.c_int64), ("R32", C.c_void_p),
                 ("cent", C.c_void_p), ("offsets", C.c_void_p), ("ids", C.c_void_p), ("Xr", C.c_void_p),
-                ("codes", C.c_void_p)]
+                ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p), ("S8", C.c_void_p)]
 
 
 _P, _I32, _I64, _F, _D, _S = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
@@ -62,6 +64,10 @@ _SIGS = {
     "crisp_index_export": [_P, _P, C.POINTER(_S)],
     "crisp_index_import": [_P, _S, _P, C.POINTER(_P)],
     "crisp_index_get_info": [_P, C.POINTER(IndexInfo)],
+    "crisp_index_add_copies": [_P, C.c_uint32, _P],
+    "crisp_quantize_bf16": [_P, _I64, _I32, _P, _P],
+    "crisp_quantize_e4m3": [_P, _I64, _I32, _P, _P, _P],
+    "crisp_shortlist": [_P, _P, _I32, _P, _I64, _P, _I32, _I32, _P, _I64, _P, _P],
     "crisp_search": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
     "crisp_search_host": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
     "crisp_search_scratch_bytes": [_P, _I32, C.POINTER(SearchParams), C.POINTER(_S)],
@@ -195,6 +201,24 @@ def crisp_index_get_info(index: Index) -> IndexInfo:
     return info
 
 
+def crisp_index_add_copies(index, copies, stream=None):
+    """Add BF16 (bit 0) and/or FP8 E4M3 (bit 1) copies of the stored rows."""
+    _call("crisp_index_add_copies", index, copies, _stream(stream))
+
+
+def crisp_quantize_bf16(Xr, N, Dp, Xb, stream=None):
+    _call("crisp_quantize_bf16", _ptr(Xr), N, Dp, _ptr(Xb), _stream(stream))
+
+
+def crisp_quantize_e4m3(Xr, N, Dp, X8, scale, stream=None):
+    _call("crisp_quantize_e4m3", _ptr(Xr), N, Dp, _ptr(X8), _ptr(scale), _stream(stream))
+
+
+def crisp_shortlist(index, Qr, nq, cand, cand_stride, ncand, precision, S, out, out_stride, nout, stream=None):
+    _call("crisp_shortlist", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), precision, S, _ptr(out),
+          out_stride, _ptr(nout), _stream(stream))
+
+
 def crisp_search(index, Q, nq, params: SearchParams, ids, sqdist, stats=None, stream=None):
     _call("crisp_search", index, _ptr(Q), nq, C.byref(params), _ptr(ids), _ptr(sqdist), _ptr(stats), _stream(stream))
 
@@ -297,14 +321,16 @@ def budget(rho: float, N: int) -> int:
     return max(1, int(math.ceil(rho * N - 1e-9)))
 
 
-def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0) -> SearchParams:
-    return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates)
+def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0, precision=0,
+                  shortlist=0) -> SearchParams:
+    return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates, precision, shortlist)
 
 
-def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None):
+def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None,
+                 copies=0):
     """BuildParams; ``draws`` (host numpy arrays: cev_sample, gaussian,
     kmeans_sample, kmeans_init) are referenced by the returned struct."""
-    p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None)
+    p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None, copies)
     p._draws = draws          # the struct holds raw pointers into these arrays: keep them alive with it
     if draws is not None:
         p.cev_sample = draws.cev_sample.ctypes.data

@@ -20,6 +20,9 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
                               cudaStream_t st);
+crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
+                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
                                   int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
@@ -106,6 +109,9 @@ static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->tile_off);
     cudaFree(ix->Xr);
     cudaFree(ix->codes);
+    cudaFree(ix->Xb);
+    cudaFree(ix->X8);
+    cudaFree(ix->S8);
 }
 
 extern "C" void crisp_free(crisp_index *ix) {
@@ -164,6 +170,7 @@ extern "C" crisp_status crisp_index_get_info(const crisp_index *ix, crisp_index_
     o->id_tile_log2 = CRISP_TILE_LOG2; o->device_bytes = ix->bytes;
     o->R32 = ix->R32; o->cent = ix->cent; o->offsets = ix->offsets; o->ids = ix->ids; o->Xr = ix->Xr;
     o->codes = ix->codes;
+    o->Xb = ix->Xb; o->X8 = ix->X8; o->S8 = ix->S8;
     return CRISP_OK;
 }
 
@@ -261,7 +268,7 @@ extern "C" crisp_status crisp_index_import(const void *host_buf, size_t bytes, v
 
 // --------------------------------------------------------------- search
 struct SearchPlan {
-    int32_t tau, phi, k;
+    int32_t tau, phi, k, prec, S;
     int64_t budget, cap, stride;
     int32_t chunk;
     size_t per_query;
@@ -277,12 +284,21 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     CRISP_REQUIRE(p->alpha >= 0.0 && p->alpha <= 1.0, "crisp_search: alpha outside [0, 1]");
     CRISP_REQUIRE(p->max_candidates == 0 || p->max_candidates >= p->k, "crisp_search: 0 < max_candidates < k");
     CRISP_REQUIRE(p->max_candidates >= 0, "crisp_search: max_candidates < 0");
+    CRISP_REQUIRE(p->precision >= 0 && p->precision <= 2, "crisp_search: precision must be 0, 1 or 2");
+    if (p->precision > 0) {
+        CRISP_REQUIRE(p->mode == 0, "crisp_search: coarse scoring (precision > 0) runs in Guaranteed mode");
+        CRISP_REQUIRE(p->shortlist >= p->k, "crisp_search: shortlist < k");
+        CRISP_REQUIRE(p->precision != 1 || ix->Xb, "crisp_search: the index has no BF16 copy (crisp_index_add_copies)");
+        CRISP_REQUIRE(p->precision != 2 || ix->X8, "crisp_search: the index has no FP8 copy (crisp_index_add_copies)");
+    }
     if (ix->M > 127) { crisp_set_error("crisp_search: M > 127 is not supported"); return CRISP_EUNSUPPORTED; }
     pl->tau = crisp_tau(p->alpha, ix->M);
     pl->budget = crisp_budget(p->rho, ix->N);
     pl->phi = p->mode;
     pl->k = p->k;
     pl->cap = p->max_candidates;
+    pl->prec = p->precision;
+    pl->S = p->precision > 0 ? p->shortlist : 0;
     // Every candidate needs V >= tau and the scores sum to at most w * (ids
     // retrieved), each subspace retrieving fewer than budget + largest cell:
     // |C| <= w M (budget + max_cell) / tau; the fallback returns at most k.
@@ -297,7 +313,7 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     pl->stride = std::max<int64_t>(pl->stride, 1);
     const int64_t K2 = (int64_t)ix->K * ix->K;
     pl->per_query = sizeof(float) * ix->Dp + sizeof(int32_t) * ix->M * K2 + sizeof(int32_t) * ix->M +
-                    sizeof(int64_t) * ix->M + sizeof(int32_t) * pl->stride * 2 + 64;
+                    sizeof(int64_t) * ix->M + sizeof(int32_t) * pl->stride * 2 + sizeof(int32_t) * pl->S + 64;
     size_t budget_bytes = (size_t)16 << 30;
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
@@ -338,6 +354,7 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
                           sizeof(int32_t) * (size_t)C * M, sizeof(int64_t) * (size_t)C * M,
                           sizeof(int32_t) * (size_t)C * pl.stride, sizeof(float) * (size_t)C * pl.stride,
                           sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C, sizeof(int64_t) * (size_t)C,
+                          sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C * pl.S,
                           sizeof(int64_t) * (size_t)C};
         for (size_t x : parts) total += (x + 255) / 256 * 256;
     }
@@ -354,6 +371,8 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
     int32_t *how = carve<int32_t>(cur, C);
     int64_t *nver = carve<int64_t>(cur, C);
     int64_t *nfull = carve<int64_t>(cur, C);
+    int32_t *shortl = carve<int32_t>(cur, (size_t)C * pl.S);
+    int64_t *nshort = carve<int64_t>(cur, C);
     for (int32_t c0 = 0; c0 < nq && s == CRISP_OK; c0 += C) {
         int32_t nc = std::min(C, nq - c0);
         const float *Qc = Q + (int64_t)c0 * ix->D;
@@ -363,7 +382,14 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
         if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, pl.k, pl.cap, cand, pl.stride, ncand, nullptr, how, st);
         int64_t *ids_c = ids + (int64_t)c0 * pl.k;
         float *d2_c = d2 + (int64_t)c0 * pl.k;
-        if (!s && p->mode == 0) {
+        if (!s && p->mode == 0 && pl.prec > 0) {
+            // F2: coarse-score every candidate on the low-precision rows, then the
+            // FP32 re-rank of the shortlist
+            s = crisp_run_shortlist(ix, Qr, nc, cand, pl.stride, ncand, pl.prec, pl.S, dist, shortl, pl.S, nshort, st);
+            if (!s) s = crisp_run_rerank(ix, Qr, nc, shortl, pl.S, nshort, pl.k, dist, ids_c, d2_c, st);
+            if (!s && stats)
+                s = launch_write_stats(nc, ncand, how, retr, M, ncand, nshort, pl.tau, stats + c0, st);
+        } else if (!s && p->mode == 0) {
             s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, ncand, pl.k, dist, ids_c, d2_c, st);
             if (!s && stats)
                 s = launch_write_stats(nc, ncand, how, retr, M, nullptr, nullptr, pl.tau, stats + c0, st);

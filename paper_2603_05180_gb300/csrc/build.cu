@@ -17,6 +17,9 @@
 #include <random>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "internal.cuh"
 
 namespace {
@@ -509,6 +512,29 @@ __global__ void k_sign_codes(const float *__restrict__ Xr, long long N, int Dp, 
     }
 }
 
+// ================================================================ F2
+__global__ void k_quant_bf16(const float *__restrict__ X, long long n, uint16_t *__restrict__ Xb) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Xb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(X[i]));
+}
+
+// one warp per row: scale = max|x| / 448 (1 for a zero row), codes of x / scale
+__global__ void k_quant_e4m3(const float *__restrict__ Xr, long long N, int Dp, uint8_t *__restrict__ X8,
+                             float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    for (long long n = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; n < N;
+         n += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const float *x = Xr + n * Dp;
+        float mx = 0.0f;
+        for (int d = lane; d < Dp; d += 32) mx = fmaxf(mx, fabsf(x[d]));
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+        for (int d = lane; d < Dp; d += 32)
+            X8[n * Dp + d] = (uint8_t)__nv_cvt_float_to_fp8(x[d] / s, __NV_SATFINITE, __NV_E4M3);
+        if (lane == 0) scale[n] = s;
+    }
+}
+
 unsigned grid1(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
 
 }  // namespace
@@ -704,6 +730,7 @@ extern "C" crisp_status crisp_sign_codes(const float *Xr, int64_t N, int32_t Dp,
 // ============================================================== crisp_build
 crisp_status crisp_alloc_index(crisp_index *ix);
 crisp_status crisp_finish_index(crisp_index *ix, cudaStream_t st);
+crisp_status crisp_make_copies(crisp_index *ix, uint32_t copies, cudaStream_t st);
 
 static std::vector<int64_t> sample_rows(int64_t N, int64_t S, std::mt19937_64 &rng) {
     // Floyd's algorithm: S distinct rows of 0..N-1, returned sorted
@@ -735,6 +762,7 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
     CRISP_REQUIRE(p->K >= 2 && p->K <= CRISP_KMAX && p->K <= N, "crisp_build: K outside [2, min(64, N)]");
     CRISP_REQUIRE(p->rotate >= -1 && p->rotate <= 1, "crisp_build: rotate must be -1, 0 or 1");
     CRISP_REQUIRE(p->kmeans_iters >= 0, "crisp_build: kmeans_iters < 0");
+    CRISP_REQUIRE((p->copies & ~3u) == 0, "crisp_build: copies must be a mask of 1 (BF16) and 2 (FP8)");
     cudaStream_t st = as_stream(stream);
     const int32_t M = p->M, K = p->K;
     crisp_index *ix = new crisp_index();
@@ -859,6 +887,8 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
                                   ix->ids + (size_t)m * N, st));
         // ---- B5: sign codes
         BSTEP(crisp_sign_codes(ix->Xr, N, ix->Dp, ix->codes, st));
+        // ---- F2: low-precision row copies
+        BSTEP(crisp_make_copies(ix, p->copies, st));
         BCUDA(cudaStreamSynchronize(st));
         cudaFreeAsync(tmp, st);
     }
@@ -872,5 +902,54 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
         return s;
     }
     *out = ix;
+    return CRISP_OK;
+}
+
+// ==================================================================== F2 C ABI
+extern "C" crisp_status crisp_quantize_bf16(const float *Xr, int64_t N, int32_t Dp, uint16_t *Xb, void *stream) {
+    CRISP_REQUIRE(Xr && Xb && N >= 0 && Dp >= 1, "crisp_quantize_bf16: bad arguments");
+    long long n = (long long)N * Dp;
+    if (n == 0) return CRISP_OK;
+    k_quant_bf16<<<(unsigned)std::min<long long>(grid1(n, 256), 152LL * 32), 256, 0, as_stream(stream)>>>(Xr, n, Xb);
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_quantize_e4m3(const float *Xr, int64_t N, int32_t Dp, uint8_t *X8, float *scale,
+                                            void *stream) {
+    CRISP_REQUIRE(Xr && X8 && scale && N >= 0 && Dp >= 1, "crisp_quantize_e4m3: bad arguments");
+    if (N == 0) return CRISP_OK;
+    k_quant_e4m3<<<(unsigned)std::min<long long>(grid1((long long)N * 32, 256), 152LL * 32), 256, 0,
+                   as_stream(stream)>>>(Xr, N, Dp, X8, scale);
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status crisp_make_copies(crisp_index *ix, uint32_t copies, cudaStream_t st) {
+    if ((copies & 1u) && !ix->Xb) {
+        size_t b = sizeof(uint16_t) * (size_t)ix->N * ix->Dp;
+        CRISP_CK(cudaMalloc((void **)&ix->Xb, b));
+        ix->bytes += (int64_t)b;
+        crisp_status s = crisp_quantize_bf16(ix->Xr, ix->N, ix->Dp, ix->Xb, st);
+        if (s) return s;
+    }
+    if ((copies & 2u) && !ix->X8) {
+        size_t b = (size_t)ix->N * ix->Dp, sb = sizeof(float) * (size_t)ix->N;
+        CRISP_CK(cudaMalloc((void **)&ix->X8, b));
+        CRISP_CK(cudaMalloc((void **)&ix->S8, sb));
+        ix->bytes += (int64_t)(b + sb);
+        crisp_status s = crisp_quantize_e4m3(ix->Xr, ix->N, ix->Dp, ix->X8, ix->S8, st);
+        if (s) return s;
+    }
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_index_add_copies(crisp_index *ix, uint32_t copies, void *stream) {
+    CRISP_REQUIRE(ix, "crisp_index_add_copies: null index");
+    CRISP_REQUIRE((copies & ~3u) == 0, "crisp_index_add_copies: copies must be a mask of 1 (BF16) and 2 (FP8)");
+    cudaStream_t st = as_stream(stream);
+    crisp_status s = crisp_make_copies(ix, copies, st);
+    if (s) return s;
+    CRISP_CK(cudaStreamSynchronize(st));
     return CRISP_OK;
 }

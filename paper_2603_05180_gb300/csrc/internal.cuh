@@ -30,6 +30,9 @@ struct crisp_index {
     int32_t *tile_off = nullptr;   // [M][K*K][T+1]
     float *Xr = nullptr;           // [N][Dp]
     uint32_t *codes = nullptr;     // [N][Dp/32]
+    uint16_t *Xb = nullptr;        // [N][Dp] BF16 bits (optional)
+    uint8_t *X8 = nullptr;         // [N][Dp] FP8 E4M3 codes (optional)
+    float *S8 = nullptr;           // [N] FP8 row scales (optional)
     int device = 0;
     int64_t bytes = 0;
 };
@@ -44,6 +47,9 @@ struct IxView {
     const int32_t *tile_off;
     const float *Xr;
     const uint32_t *codes;
+    const uint16_t *Xb;
+    const uint8_t *X8;
+    const float *S8;
 };
 
 static inline IxView ix_view(const crisp_index *ix) {
@@ -51,6 +57,7 @@ static inline IxView ix_view(const crisp_index *ix) {
     v.N = ix->N; v.D = ix->D; v.Dp = ix->Dp; v.M = ix->M; v.K = ix->K; v.H = ix->H; v.T = ix->T;
     v.cent = ix->cent; v.offsets = ix->offsets; v.ids = ix->ids; v.tile_off = ix->tile_off;
     v.Xr = ix->Xr; v.codes = ix->codes;
+    v.Xb = ix->Xb; v.X8 = ix->X8; v.S8 = ix->S8;
     return v;
 }
 

@@ -566,6 +566,64 @@ struct TopkShared {
     int need;
 };
 
+// Block-wide radix select over the FP32 keys dist[0..n) (non-negative, so
+// their bit patterns order like the values): the key of the kk-th smallest
+// (*prefix) and how many entries equal to it are among the kk smallest (*need).
+__device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S, unsigned *out_prefix, int *out_need) {
+    const int tid = threadIdx.x;
+    unsigned prefix = 0, mask = 0;
+    int need = kk;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
+        __syncthreads();
+        for (long long i = tid; i < n; i += RR_NT) {
+            unsigned key = __float_as_uint(distq[i]);
+            if ((key & mask) == prefix) atomicAdd(&S.hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned cum = 0;
+            int b = 0;
+            for (; b < 255; ++b) {
+                if (cum + S.hist[b] >= (unsigned)need) break;
+                cum += S.hist[b];
+            }
+            S.prefix = prefix | ((unsigned)b << shift);
+            S.need = need - (int)cum;
+        }
+        __syncthreads();
+        prefix = S.prefix;
+        need = S.need;
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    *out_prefix = prefix;
+    *out_need = need;
+}
+
+// Visit, in list order, the entries with key < prefix and the first `need`
+// with key == prefix (the list is in ascending id, so ties go to lower ids);
+// f(slot, i) is called for each selected entry i with its output slot.
+template <class F>
+__device__ long long collect_ordered(const float *distq, long long n, unsigned prefix, int need, TopkShared &S, F f) {
+    const int tid = threadIdx.x;
+    long long eq_seen = 0, sel_seen = 0;
+    for (long long c0 = 0; c0 < n; c0 += RR_NT) {
+        long long i = c0 + tid;
+        unsigned key = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
+        int is_eq = (i < n && key == prefix);
+        long long eq_tot;
+        long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
+        int sel = (i < n) && (key < prefix || (is_eq && eq_seen + eq_off < need));
+        long long sel_tot;
+        long long sel_off = block_excl_scan<RR_NT>(sel, S.scan_ws, &sel_tot);
+        if (sel) f(sel_seen + sel_off, i);
+        eq_seen += eq_tot;
+        sel_seen += sel_tot;
+    }
+    return sel_seen;
+}
+
 // Block-wide: the kk smallest (key, id) of n entries (keys from dist[], ids
 // from candq[], ids ascending in list order), sorted, into S.skey / S.sid.
 // Returns the number selected (min(n, kk)).
@@ -576,48 +634,13 @@ __device__ int select_topk(const float *distq, const int *candq, long long n, in
         for (int i = tid; i < n; i += RR_NT) { S.skey[i] = __float_as_uint(distq[i]); S.sid[i] = candq[i]; }
         nsel = (int)n;
     } else {
-        unsigned prefix = 0, mask = 0;
-        int need = kk;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
-            __syncthreads();
-            for (long long i = tid; i < n; i += RR_NT) {
-                unsigned key = __float_as_uint(distq[i]);
-                if ((key & mask) == prefix) atomicAdd(&S.hist[(key >> shift) & 255u], 1u);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                unsigned cum = 0;
-                int b = 0;
-                for (; b < 256; ++b) {
-                    if (cum + S.hist[b] >= (unsigned)need) break;
-                    cum += S.hist[b];
-                }
-                S.prefix = prefix | ((unsigned)b << shift);
-                S.need = need - (int)cum;
-            }
-            __syncthreads();
-            prefix = S.prefix;
-            need = S.need;
-            mask |= 255u << shift;
-            __syncthreads();
-        }
-        // prefix = key of the kk-th smallest; take every key < prefix and the
-        // first `need` (lowest ids, list order) with key == prefix
-        long long eq_seen = 0, sel_seen = 0;
-        for (long long c0 = 0; c0 < n; c0 += RR_NT) {
-            long long i = c0 + tid;
-            unsigned key = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
-            int is_eq = (i < n && key == prefix);
-            long long eq_tot;
-            long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
-            int sel = (i < n) && (key < prefix || (is_eq && eq_seen + eq_off < need));
-            long long sel_tot;
-            long long sel_off = block_excl_scan<RR_NT>(sel, S.scan_ws, &sel_tot);
-            if (sel) { S.skey[sel_seen + sel_off] = key; S.sid[sel_seen + sel_off] = candq[i]; }
-            eq_seen += eq_tot;
-            sel_seen += sel_tot;
-        }
+        unsigned prefix;
+        int need;
+        radix_kth(distq, n, kk, S, &prefix, &need);
+        collect_ordered(distq, n, prefix, need, S, [&](long long slot, long long i) {
+            S.skey[slot] = __float_as_uint(distq[i]);
+            S.sid[slot] = candq[i];
+        });
         nsel = kk;
     }
     __syncthreads();
@@ -683,6 +706,132 @@ __global__ void __launch_bounds__(RR_NT) k_rerank(IxView ix, const float *__rest
         out_ids[(long long)q * kk + r] = ok ? (long long)S.sid[r] : -1LL;
         out_d[(long long)q * kk + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
     }
+}
+
+// ============================================== F2 coarse scoring + shortlist
+// FP8 E4M3 code -> FP32, exact (no infinities; 0x7F/0xFF never produced).
+__device__ __forceinline__ float e4m3_to_f32(unsigned c) {
+    unsigned e = (c >> 3) & 15u, m = c & 7u;
+    float v = e == 0 ? (float)m * 0.001953125f : __uint_as_float(((e + 120u) << 23) | (m << 20));
+    return (c & 0x80u) ? -v : v;
+}
+
+// CR32 distance of q to a BF16 row: an 8-lane group covers two 32-dim blocks
+// (16 B per lane); lane li of a quarter holds the CR32 partials 2li and 2li+1.
+__device__ __forceinline__ float cr32_row_bf16(const uint4 *row, const float *qs, int nb, int gl, int base, unsigned gmask) {
+    const int half = gl >> 2, li = gl & 3;
+    float acc = 0.0f;
+    for (int j = 0; 2 * j < nb; ++j) {
+        const int b = 2 * j + half;
+        float e = 0.0f, o = 0.0f;
+        if (b < nb) {
+            uint4 v = __ldcs(row + 8 * j + gl);
+            const float *qv = qs + 32 * b + 8 * li;
+            unsigned w[4] = {v.x, v.y, v.z, v.w};
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[2 * u] = __uint_as_float(w[u] << 16);
+                x[2 * u + 1] = __uint_as_float(w[u] & 0xFFFF0000u);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                float d = x[t] - qv[t];
+                e = fmaf(d, d, e);
+            }
+#pragma unroll
+            for (int t = 4; t < 8; ++t) {
+                float d = x[t] - qv[t];
+                o = fmaf(d, d, o);
+            }
+        }
+        e = e + __shfl_xor_sync(gmask, e, 2);
+        o = o + __shfl_xor_sync(gmask, o, 2);
+        e = e + __shfl_xor_sync(gmask, e, 1);
+        o = o + __shfl_xor_sync(gmask, o, 1);
+        float s = e + o;
+        float slo = __shfl_sync(gmask, s, base);
+        float shi = __shfl_sync(gmask, s, base + 4);
+        acc = acc + slo;
+        if (2 * j + 1 < nb) acc = acc + shi;
+    }
+    return acc;
+}
+
+// CR32 distance of q to an FP8 row times its scale: an 8-lane group covers four
+// 32-dim blocks (16 codes per lane); the lane pair of a block holds partials 0-3 / 4-7.
+__device__ __forceinline__ float cr32_row_e4m3(const uint4 *row, float sc, const float *qs, int nb, int gl, int base,
+                                               unsigned gmask) {
+    const int h = gl & 1;
+    float acc = 0.0f;
+    for (int j = 0; 4 * j < nb; ++j) {
+        const int b = 4 * j + (gl >> 1);
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (b < nb) {
+            uint4 v = __ldcs(row + 8 * j + gl);
+            const float *qv = qs + 32 * b + 16 * h;
+            unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    float x = e4m3_to_f32((w[u] >> (8 * t)) & 0xFFu) * sc;
+                    float d = x - qv[4 * u + t];
+                    a[u] = fmaf(d, d, a[u]);
+                }
+        }
+        float t0 = a[0] + __shfl_xor_sync(gmask, a[0], 1);
+        float t1 = a[1] + __shfl_xor_sync(gmask, a[1], 1);
+        float t2 = a[2] + __shfl_xor_sync(gmask, a[2], 1);
+        float t3 = a[3] + __shfl_xor_sync(gmask, a[3], 1);
+        float s = (t0 + t2) + (t1 + t3);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float sr = __shfl_sync(gmask, s, base + 2 * r);
+            if (4 * j + r < nb) acc = acc + sr;
+        }
+    }
+    return acc;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(RR_NT) k_shortlist(IxView ix, const float *__restrict__ Qr, int nq,
+                                                     const int *__restrict__ cand, long long stride,
+                                                     const long long *__restrict__ ncand, int S_keep,
+                                                     float *__restrict__ dbuf, int *__restrict__ out,
+                                                     long long out_stride, long long *__restrict__ nout) {
+    extern __shared__ __align__(16) float qs[];
+    __shared__ TopkShared S;
+    const int q = blockIdx.x;
+    const int Dp = ix.Dp, nb = Dp / 32;
+    long long n = ncand[q];
+    if (n > stride) n = stride;
+    for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, gl = threadIdx.x & 7, base = lane & 24;
+    const unsigned gmask = 0xFFu << base;
+    const int *candq = cand + (long long)q * stride;
+    float *distq = dbuf + (long long)q * stride;
+    for (long long i = g; i < n; i += RR_NT / 8) {
+        const long long id = candq[i];
+        float acc;
+        if (PREC == 1) acc = cr32_row_bf16(reinterpret_cast<const uint4 *>(ix.Xb + id * Dp), qs, nb, gl, base, gmask);
+        else acc = cr32_row_e4m3(reinterpret_cast<const uint4 *>(ix.X8 + id * Dp), ix.S8[id], qs, nb, gl, base, gmask);
+        if (gl == 0) distq[i] = acc;
+    }
+    __syncthreads();
+    int *outq = out + (long long)q * out_stride;
+    long long kept;
+    if (n <= S_keep) {
+        for (long long i = threadIdx.x; i < n; i += RR_NT) outq[i] = candq[i];
+        kept = n;
+    } else {
+        unsigned prefix;
+        int need;
+        radix_kth(distq, n, S_keep, S, &prefix, &need);
+        kept = collect_ordered(distq, n, prefix, need, S, [&](long long slot, long long i) { outq[slot] = candq[i]; });
+    }
+    if (threadIdx.x == 0) nout[q] = kept;
 }
 
 __global__ void k_stats(int nq, const long long *ncand, const int *how, const long long *retrieved, int M,
@@ -785,6 +934,28 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
     k_rerank<<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
                                       dbuf, (long long *)ids, d2);
     CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
+                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    size_t smem = sizeof(float) * (size_t)ix->Dp;
+    if (precision == 1) {
+        if (smem > 48 * 1024)
+            CRISP_CK(cudaFuncSetAttribute(k_shortlist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_shortlist<1><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
+                                                 S, dbuf, out, (long long)out_stride, (long long *)nout);
+        CRISP_COUNT_LAUNCH();
+    } else {
+        if (smem > 48 * 1024)
+            CRISP_CK(cudaFuncSetAttribute(k_shortlist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_shortlist<2><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
+                                                 S, dbuf, out, (long long)out_stride, (long long *)nout);
+        CRISP_COUNT_LAUNCH();
+    }
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
@@ -905,4 +1076,23 @@ extern "C" crisp_status crisp_rerank_noalloc(const crisp_index *ix, const float 
     s = noalloc_scratch(&dbuf);
     if (s) return s;
     return crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, as_stream(stream));
+}
+
+extern "C" crisp_status crisp_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                        int64_t cand_stride, const int64_t *ncand, int32_t precision, int32_t S,
+                                        int32_t *out, int64_t out_stride, int64_t *nout, void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(precision == 1 || precision == 2, "crisp_shortlist: precision must be 1 (BF16) or 2 (FP8)");
+    CRISP_REQUIRE(precision != 1 || ix->Xb, "crisp_shortlist: the index has no BF16 copy");
+    CRISP_REQUIRE(precision != 2 || ix->X8, "crisp_shortlist: the index has no FP8 copy");
+    CRISP_REQUIRE(S >= 1 && out_stride >= S && cand_stride >= 1, "crisp_shortlist: need S >= 1, out_stride >= S");
+    CRISP_REQUIRE(nq == 0 || (cand && ncand && out && nout), "crisp_shortlist: null pointer");
+    if (nq == 0) return CRISP_OK;
+    cudaStream_t st = as_stream(stream);
+    float *dbuf = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
+    s = crisp_run_shortlist(ix, Qr, nq, cand, cand_stride, ncand, precision, S, dbuf, out, out_stride, nout, st);
+    crisp_scratch_free(dbuf, st);
+    return s;
 }
