@@ -253,7 +253,8 @@ def run_crisp(args):
 
     def search(point, nqq=nq, Qx=Q, out=(ids, d2, st)):
         sp = crisp.search_params(k=k, mode=point["mode"], rho=point["rho"], alpha=point["alpha"],
-                                 precision=point.get("precision", 0), shortlist=point.get("shortlist", 0))
+                                 precision=point.get("precision", 0), shortlist=point.get("shortlist", 0),
+                                 depth_margin=point.get("depth_margin", 0.0), short_margin=point.get("short_margin", 0.0))
         crisp.crisp_search(ix, Qx, nqq, sp, out[0][:nqq], out[1][:nqq], out[2][:nqq], stream)
 
     def timed(point, steps):
@@ -366,6 +367,11 @@ def run_crisp(args):
             variants[name] = {"precision": name, "shortlist": chosen["shortlist"], "value": q_v, "recall_at_10": r_v,
                               "ms_per_step": ms_v, "speedup_vs_fp32": q_v / qps * world}
 
+    # ---- learned depths + BF16 (F1): train the model on queries of the same law
+    learned = None
+    if not args.no_learned:
+        learned = learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed, qps, world, dev)
+
     # ---- end to end through the host-buffer entry point
     Qh = torch.empty((nq, D), dtype=torch.float32, pin_memory=True)
     Qh.copy_(Q.cpu())
@@ -411,12 +417,70 @@ def run_crisp(args):
                 "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
                         "d2h_bytes_per_step": nq * k * 12},
                 "gpu_launches": launches, "clocks": clk,
-                "coarse_scoring": variants}
+                "coarse_scoring": variants, "learned_bf16": learned}
         if sweep_log:
             line["sweep"] = sweep_log
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed, plain_qps, world, dev):
+    """Learned re-rank depths with BF16 coarse scores: labels from the plain
+    search on training queries, GPU training, margins calibrated on validation
+    queries to the plain path's recall, then timed on the evaluation queries."""
+    N, D, k = args.n, args.dim, args.k
+    M, F, H = info.M, 2 * info.M + 68, 256
+    ntr, nva = args.train_queries, 2000
+    _, Qtr = synthetic.powerlaw(1, D, ntr, seed=args.seed, device="cuda", query_sub=synthetic.SUB_TRAIN)
+    _, Qva = synthetic.powerlaw(1, D, nva, seed=args.seed, device="cuda", query_sub=synthetic.SUB_VALID)
+    sp = crisp.search_params(k=k, mode=0, rho=point["rho"], alpha=point["alpha"])
+    feats = torch.empty((ntr, F), dtype=torch.float32, device=dev)
+    labels = torch.empty((ntr, 2), dtype=torch.int64, device=dev)
+    tg = torch.empty((ntr, 2), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    crisp.crisp_learned_data(ix, Qtr, ntr, sp, feats, labels, tg)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    P = torch.empty(crisp.crisp_mlp_param_count(F, H, 2), dtype=torch.float32, device=dev)
+    crisp.crisp_mlp_init(P, F, H, 2, seed=args.seed + 1)
+    t0 = time.perf_counter()
+    losses = crisp.crisp_mlp_train(P, F, H, 2, feats, tg, ntr, args.epochs, 1024, 1e-3, seed=args.seed + 2)
+    t_train = time.perf_counter() - t0
+    crisp.crisp_index_set_model(ix, P, H)
+    # calibrate the margins on validation queries against the plain path's recall there
+    _, gdv = ground_truth(torch, X, Qva, k)
+    gdv = gdv[:, k - 1].contiguous()
+    vi = torch.empty((nva, k), dtype=torch.int64, device=dev)
+    vd = torch.empty((nva, k), dtype=torch.float32, device=dev)
+    vs = torch.empty((nva, 6), dtype=torch.int64, device=dev)
+    def val(pt):
+        sp2 = crisp.search_params(k=k, mode=pt["mode"], rho=pt["rho"], alpha=pt["alpha"],
+                                  depth_margin=pt.get("depth_margin", 0.0), short_margin=pt.get("short_margin", 0.0))
+        crisp.crisp_search(ix, Qva, nva, sp2, vi, vd, vs)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        crisp.crisp_search(ix, Qva, nva, sp2, vi, vd, vs)
+        b.record()
+        torch.cuda.synchronize()
+        return recall_at_k(torch, X, Qva, vi, gdv), nva / (a.elapsed_time(b) / 1e3)
+    r_plain, _ = val(point)
+    best = None
+    for dm in (0.0, 0.5, 1.0, 1.5, 2.0, 3.0):
+        for sm in (0.0, 1.0, 2.0):
+            pt = dict(point, mode=2, depth_margin=dm, short_margin=sm)
+            r, q = val(pt)
+            if r >= max(r_plain - 0.002, 0.95) and (best is None or q > best[1]):
+                best = (pt, q, r)
+    if best is None:
+        return {"status": "no margin reached the plain recall on the validation queries", "val_recall_plain": r_plain}
+    pt = best[0]
+    q_l, r_l, ms_l = timed(pt, args.steps)
+    return {"value": q_l, "recall_at_10": r_l, "ms_per_step": ms_l, "speedup_vs_fp32": q_l / plain_qps * world,
+            "depth_margin": pt["depth_margin"], "short_margin": pt["short_margin"], "train_queries": ntr,
+            "epochs": args.epochs, "hidden": H, "features": F, "loss_first_epoch": losses[0],
+            "loss_last_epoch": losses[-1], "label_seconds": round(t_data, 2), "train_seconds": round(t_train, 2),
+            "val_recall_plain": r_plain, "val_recall_learned": best[2]}
 
 
 def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
@@ -441,7 +505,7 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     nf = torch.empty((nq,), dtype=torch.int64, device=dev)
     nb = torch.empty((nq,), dtype=torch.int64, device=dev)
     names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
-    kernels = ["k_rotate", "k_activate", "k_count_cut", "k_rerank" if point["mode"] == 0 else "k_verify_opt"]
+    kernels = ["k_rotate", "k_activate", "k_count_cut", "k_dist_flat" if point["mode"] == 0 else "k_verify_opt"]
     acc = {n: 0.0 for n in names}
 
     def one():
@@ -484,7 +548,7 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     }
     if point["mode"] == 0:
         # every candidate row (Dp floats) + its id
-        out["rerank"] = {"ms": acc["rerank"], "bytes": C * (4 * Dp + 4), "kernel": "k_rerank"}
+        out["rerank"] = {"ms": acc["rerank"], "bytes": C * (4 * Dp + 4), "kernel": "k_dist_flat"}
     else:
         blocks = float(nb.sum().item())
         out["verify_opt"] = {"ms": acc["verify_opt"], "bytes": C * (4 * W + 4) + 128 * blocks,
@@ -523,6 +587,9 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="pick the operating point by a recall/QPS sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16 / FP8 coarse-scoring measurements")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-depth + BF16 measurement")
+    ap.add_argument("--train-queries", type=int, default=50000)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = ap.parse_args()

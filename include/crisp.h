@@ -81,7 +81,7 @@ typedef struct {
 /* Search parameters (Algorithm 1, §4.3, Table 1). */
 typedef struct {
     int32_t k;                 /* neighbours returned (k_size), 1 <= k <= 256 */
-    int32_t mode;              /* 0 Guaranteed (phi = 0), 1 Optimized (phi = 1) */
+    int32_t mode;              /* 0 Guaranteed (phi = 0), 1 Optimized (phi = 1), 2 Learned (F1) */
     double rho;                /* coverage: ids retrieved per subspace / N, in (0, 1] */
     double alpha;              /* minimum collision fraction, in [0, 1]; tau = ceil(alpha M) */
     int32_t patience_factor;   /* Optimized: stop after P = patience_factor*k unchanged; <= 0 off */
@@ -91,6 +91,8 @@ typedef struct {
                                   candidate), 1 BF16 rows, 2 FP8 E4M3 rows with per-row scales */
     int32_t shortlist;         /* precision > 0: candidates kept by the coarse score for the FP32
                                   re-rank (>= k) */
+    float depth_margin;        /* mode 2: added to the predicted log2 depths (score prefix, */
+    float short_margin;        /*         coarse shortlist) before quantisation */
 } crisp_search_params;
 
 /* Per-query counters written by crisp_search (device array, may be NULL). */
@@ -172,9 +174,17 @@ uint64_t crisp_kernel_launches(void);
  * Scratch comes from a stream-ordered memory pool the library keeps per device
  * (it holds its memory between calls; crisp_search_scratch_bytes tells how much).
  * EINVAL: k outside [1, 256] or > N, rho outside (0, 1], alpha outside [0, 1],
- * mode outside {0, 1}, 0 < max_candidates < k, nq < 0, precision outside
+ * mode outside {0, 1, 2}, 0 < max_candidates < k, nq < 0, precision outside
  * {0, 1, 2} or used outside Guaranteed mode, shortlist < k, or a precision
- * whose row copy the index lacks. */
+ * whose row copy the index lacks; mode 2 without a model or a BF16 copy.
+ *
+ * Mode 2 (Learned, the engine's F1 extension; the paper's patience and
+ * ordering are what it replaces, §4.3.2 Stage 3): after the Guaranteed cut, a
+ * small MLP (crisp_index_set_model) reads per-query features (crisp_learned_data)
+ * and predicts two log2 depths; the first depth_V candidates by (V desc, id asc)
+ * are scored on the BF16 rows, the depth_S best form the shortlist, and the FP32
+ * re-rank of the shortlist gives the top-k.  Depth = ceil(2^(j/4)), j =
+ * ceil(4 (prediction + margin)), clamped to [k, |C|] and [k, depth_V]. */
 crisp_status crisp_search(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *params,
                           int64_t *ids, float *sqdist, crisp_query_stats *stats, void *stream);
 
@@ -187,6 +197,99 @@ crisp_status crisp_search_host(const crisp_index *index, const float *Q, int32_t
 /* Device bytes of scratch crisp_search needs for nq queries (for admission). */
 crisp_status crisp_search_scratch_bytes(const crisp_index *index, int32_t nq, const crisp_search_params *params,
                                         size_t *bytes);
+
+/* =========================================== serving (continuous batching)
+ * A request server over one index: requests (one query each, any search
+ * parameters) arrive from any thread; a dispatcher thread batches waiting
+ * requests with equal parameters (oldest first, up to max_batch), admits a
+ * batch when one of `streams` stream slots is free and its search scratch
+ * (crisp_search_scratch_bytes) fits within scratch_budget next to the batches
+ * already on the GPU, and runs copy-in, crisp_search and copy-out on that
+ * slot's stream.  Batches on different slots overlap on the GPU.  A request's
+ * result does not depend on the batch it ran in (each query is searched
+ * independently).  The server owns pinned host and device staging buffers. */
+typedef struct crisp_server crisp_server;
+
+typedef struct {
+    int32_t streams;           /* concurrent batches (stream slots), 1..64 */
+    int32_t max_batch;         /* requests per batch */
+    int64_t scratch_budget;    /* device bytes of search scratch in flight (0: 8 GiB) */
+} crisp_server_params;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches;
+    double mean_batch;         /* requests per admitted batch */
+    double p50_us, p99_us, max_us, mean_us;   /* arrival -> completion latency */
+    int64_t scratch_peak;      /* largest scratch in flight (bytes) */
+} crisp_server_stats;
+
+/* Start a server (its dispatcher thread) on the index's device.  The index
+ * must outlive the server. */
+crisp_status crisp_server_create(const crisp_index *index, const crisp_server_params *params, crisp_server **out);
+
+/* Queue one query (host [D] float32, copied) with its search parameters
+ * (validated now: EINVAL as crisp_search).  *ticket identifies the request. */
+crisp_status crisp_server_submit(crisp_server *server, const float *q, const crisp_search_params *params,
+                                 uint64_t *ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit) and take its result: ids /
+ * sqdist host [k], stats and latency (microseconds) may be NULL.  The ticket
+ * is consumed.  ETIMEOUT if it did not finish in time (the ticket stays valid). */
+crisp_status crisp_server_wait(crisp_server *server, uint64_t ticket, int32_t timeout_ms, int64_t *ids,
+                               float *sqdist, crisp_query_stats *stats, double *latency_us);
+
+crisp_status crisp_server_get_stats(crisp_server *server, crisp_server_stats *out);
+crisp_status crisp_server_reset_stats(crisp_server *server);
+
+/* Finish every queued request, stop the dispatcher and free the server. */
+void crisp_server_destroy(crisp_server *server);
+
+/* ================================= F1: learned re-rank depth (small MLP)
+ * MLP F -> H -> H -> O, GELU on both hidden layers, parameters packed in one
+ * device float array: W1 [F][H], b1 [H], W2 [H][H], b2 [H], W3 [H][O], b3 [O]
+ * (crisp_mlp_param_count floats).  GELU(z) = z/2 (1 + erf(z/sqrt 2)) with erf by
+ * Abramowitz & Stegun 7.1.28.  For the search the index's model has F = 2M + 68
+ * features and O = 2 outputs (log2 depths). */
+int64_t crisp_mlp_param_count(int32_t F, int32_t H, int32_t O);
+
+/* Seeded Xavier-uniform weights, zero biases.  EINVAL: H > 256 or O > 8. */
+crisp_status crisp_mlp_init(float *params, int32_t F, int32_t H, int32_t O, uint64_t seed, void *stream);
+
+/* Inference in the fixed FP32 order the search uses: every unit an fmaf chain
+ * over its inputs in order from its bias.  X device [B][F], Y device [B][O]. */
+crisp_status crisp_mlp_infer(const float *params, int32_t F, int32_t H, int32_t O, const float *X, int64_t B, float *Y,
+                             void *stream);
+
+/* Mean squared error of a batch (X [B][F], targets T [B][O]) and its gradient,
+ * packed like params (device [param_count]); *loss is a device float. */
+crisp_status crisp_mlp_loss_grad(const float *params, int32_t F, int32_t H, int32_t O, const float *X, const float *T,
+                                 int64_t B, float *grads, float *loss, void *stream);
+
+/* One Adam step (step number t >= 1) on n parameters; m, v: device state. */
+crisp_status crisp_mlp_adam(float *params, const float *grads, float *m, float *v, int64_t n, float lr, float beta1,
+                            float beta2, float eps, int32_t t, void *stream);
+
+/* Train params (already initialised) on n rows of X / T for `epochs` epochs of
+ * shuffled mini-batches with Adam (lr, betas 0.9 / 0.999, eps 1e-8).  The mean
+ * loss of each epoch goes to epoch_loss (host [epochs], may be NULL).
+ * Synchronous. */
+crisp_status crisp_mlp_train(float *params, int32_t F, int32_t H, int32_t O, const float *X, const float *T,
+                             int64_t n, int32_t epochs, int32_t batch, float lr, uint64_t seed, float *epoch_loss,
+                             void *stream);
+
+/* Attach a learned-depth model (device params, copied) with H hidden units,
+ * F = 2M + 68 inputs and 2 outputs to the index. */
+crisp_status crisp_index_set_model(crisp_index *index, const float *params, int32_t H, void *stream);
+
+/* Training data generated by the plain method: for nq queries (device [nq][D],
+ * original space) with the Guaranteed parameters p (k, rho, alpha,
+ * max_candidates), the feature rows (device [nq][2M+68]) and the labels
+ * (device [nq][2] int64): the smallest prefix of C by (V desc, id asc) that
+ * holds the exact top-k over C, and the smallest BF16 coarse-score prefix of
+ * that prefix that holds them.  targets (device [nq][2] float, may be NULL)
+ * receives log2 of the labels.  Needs the BF16 copy. */
+crisp_status crisp_learned_data(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *p,
+                                float *features, int64_t *labels, float *targets, void *stream);
 
 /* ====================================== steps of the path (one per stage) */
 
@@ -277,6 +380,12 @@ crisp_status crisp_half_dists(const crisp_index *index, const float *Qr, int32_t
  * int32; retrieved: device [nq][M] int64 (may be NULL). */
 crisp_status crisp_activate(const crisp_index *index, const float *Qr, int32_t nq, int32_t phi, int32_t k,
                             int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, void *stream);
+
+/* crisp_activate that also writes the cost of the first and of the last
+ * visited cell of each (query, subspace): device [nq][M] float each (may be NULL). */
+crisp_status crisp_activate_costs(const crisp_index *index, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                                  int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, float *cost_first,
+                                  float *cost_last, void *stream);
 
 /* Q4+Q5 (Eq. 1 collision counting, Algorithm 1 line 20, §4.3.2 Stage 1):
  * V[x] = sum over subspaces of the weight of the activated cell holding x;

@@ -41,13 +41,24 @@ class BuildParams(C.Structure):
 class SearchParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
                 ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64),
-                ("precision", C.c_int32), ("shortlist", C.c_int32)]
+                ("precision", C.c_int32), ("shortlist", C.c_int32), ("depth_margin", C.c_float),
+                ("short_margin", C.c_float)]
 
 
 class QueryStats(C.Structure):
     _fields_ = [("n_candidates", C.c_int64), ("n_verified", C.c_int64), ("n_full", C.c_int64),
                 ("n_retrieved", C.c_int64), ("fallback", C.c_int32), ("capped", C.c_int32), ("tau", C.c_int32),
                 ("_pad", C.c_int32)]
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("streams", C.c_int32), ("max_batch", C.c_int32), ("scratch_budget", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64), ("batches", C.c_uint64),
+                ("mean_batch", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("mean_us", C.c_double), ("scratch_peak", C.c_int64)]
 
 
 class IndexInfo(C.Structure):
@@ -85,6 +96,19 @@ _SIGS = {
     "crisp_count_cut": [_P, _P, _P, _I32, _I32, _I32, _I64, _P, _I64, _P, _P, _P, _P],
     "crisp_rerank": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
     "crisp_rerank_noalloc": [_P, _P, _I32, _P, _I64, _P, _I32, _P, _P, _P],
+    "crisp_activate_costs": [_P, _P, _I32, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P],
+    "crisp_mlp_init": [_P, _I32, _I32, _I32, C.c_uint64, _P],
+    "crisp_mlp_infer": [_P, _I32, _I32, _I32, _P, _I64, _P, _P],
+    "crisp_mlp_loss_grad": [_P, _I32, _I32, _I32, _P, _P, _I64, _P, _P, _P],
+    "crisp_mlp_adam": [_P, _P, _P, _P, _I64, _F, _F, _F, _F, _I32, _P],
+    "crisp_mlp_train": [_P, _I32, _I32, _I32, _P, _P, _I64, _I32, _I32, _F, C.c_uint64, _P, _P],
+    "crisp_index_set_model": [_P, _P, _I32, _P],
+    "crisp_learned_data": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
+    "crisp_server_create": [_P, C.POINTER(ServerParams), C.POINTER(_P)],
+    "crisp_server_submit": [_P, _P, C.POINTER(SearchParams), C.POINTER(C.c_uint64)],
+    "crisp_server_wait": [_P, C.c_uint64, _I32, _P, _P, _P, C.POINTER(C.c_double)],
+    "crisp_server_get_stats": [_P, C.POINTER(ServerStats)],
+    "crisp_server_reset_stats": [_P],
     "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P, _P],
 }
 
@@ -100,6 +124,10 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.crisp_mlp_param_count.argtypes = [_I32, _I32, _I32]
+        L.crisp_mlp_param_count.restype = C.c_int64
+        L.crisp_server_destroy.argtypes = [_P]
+        L.crisp_server_destroy.restype = None
         L.crisp_free.argtypes = [_P]
         L.crisp_free.restype = None
         L.crisp_last_error.argtypes = []
@@ -322,8 +350,9 @@ def budget(rho: float, N: int) -> int:
 
 
 def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0, precision=0,
-                  shortlist=0) -> SearchParams:
-    return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates, precision, shortlist)
+                  shortlist=0, depth_margin=0.0, short_margin=0.0) -> SearchParams:
+    return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates, precision, shortlist, depth_margin,
+                        short_margin)
 
 
 def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None,
@@ -350,3 +379,110 @@ def crisp_kernel_launches() -> int:
 
 def crisp_last_error() -> str:
     return lib().crisp_last_error().decode(errors="replace")
+
+
+def crisp_activate_costs(index, Qr, nq, phi, k, budget, act, nact, retrieved=None, cost_first=None, cost_last=None,
+                         stream=None):
+    _call("crisp_activate_costs", index, _ptr(Qr), nq, phi, k, budget, _ptr(act), _ptr(nact), _ptr(retrieved),
+          _ptr(cost_first), _ptr(cost_last), _stream(stream))
+
+
+# ------------------------------------------------- learned re-rank depth (F1)
+def crisp_mlp_param_count(F, H, O) -> int:
+    return int(lib().crisp_mlp_param_count(F, H, O))
+
+
+def crisp_mlp_init(params, F, H, O, seed=0, stream=None):
+    _call("crisp_mlp_init", _ptr(params), F, H, O, seed, _stream(stream))
+
+
+def crisp_mlp_infer(params, F, H, O, X, B, Y, stream=None):
+    _call("crisp_mlp_infer", _ptr(params), F, H, O, _ptr(X), B, _ptr(Y), _stream(stream))
+
+
+def crisp_mlp_loss_grad(params, F, H, O, X, T, B, grads, loss, stream=None):
+    _call("crisp_mlp_loss_grad", _ptr(params), F, H, O, _ptr(X), _ptr(T), B, _ptr(grads), _ptr(loss), _stream(stream))
+
+
+def crisp_mlp_adam(params, grads, m, v, n, lr, beta1, beta2, eps, t, stream=None):
+    _call("crisp_mlp_adam", _ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, t, _stream(stream))
+
+
+def crisp_mlp_train(params, F, H, O, X, T, n, epochs, batch, lr, seed=0, stream=None):
+    """Train in place; returns the mean loss of each epoch."""
+    losses = (C.c_float * max(1, epochs))()
+    _call("crisp_mlp_train", _ptr(params), F, H, O, _ptr(X), _ptr(T), n, epochs, batch, lr, seed, losses,
+          _stream(stream))
+    return [float(x) for x in losses[:epochs]]
+
+
+def crisp_index_set_model(index, params, H, stream=None):
+    _call("crisp_index_set_model", index, _ptr(params), H, _stream(stream))
+
+
+def crisp_learned_data(index, Q, nq, params: SearchParams, features, labels, targets=None, stream=None):
+    _call("crisp_learned_data", index, _ptr(Q), nq, C.byref(params), _ptr(features), _ptr(labels), _ptr(targets),
+          _stream(stream))
+
+
+# ------------------------------------------------------------ serving (F3)
+class Server:
+    """Owner of a crisp_server handle (crisp_server_destroy on free)."""
+
+    def __init__(self, handle, D):
+        self.handle = handle
+        self.D = D
+
+    def free(self):
+        if self.handle:
+            lib().crisp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return C.c_void_p(self.handle)
+
+
+def crisp_server_create(index, streams=2, max_batch=256, scratch_budget=0) -> Server:
+    out = C.c_void_p()
+    _call("crisp_server_create", index, C.byref(ServerParams(streams, max_batch, scratch_budget)), C.byref(out))
+    return Server(out.value, index.info().D)
+
+
+def crisp_server_submit(server, q, params: SearchParams) -> int:
+    """q: host float32 array of D values."""
+    t = C.c_uint64(0)
+    _call("crisp_server_submit", server, _ptr(q), C.byref(params), C.byref(t))
+    return t.value
+
+
+def crisp_server_wait(server, ticket, k, timeout_ms=-1, with_stats=False):
+    """(ids int64 [k], sqdist float32 [k], latency_us[, stats])."""
+    import numpy as np
+
+    ids = np.empty(k, np.int64)
+    d2 = np.empty(k, np.float32)
+    st = QueryStats()
+    lat = C.c_double(0.0)
+    _call("crisp_server_wait", server, ticket, timeout_ms, _ptr(ids), _ptr(d2), C.byref(st), C.byref(lat))
+    return (ids, d2, lat.value, st) if with_stats else (ids, d2, lat.value)
+
+
+def crisp_server_get_stats(server) -> ServerStats:
+    s = ServerStats()
+    _call("crisp_server_get_stats", server, C.byref(s))
+    return s
+
+
+def crisp_server_reset_stats(server):
+    _call("crisp_server_reset_stats", server)
+
+
+def crisp_server_destroy(server):
+    server.free()

@@ -13,7 +13,8 @@
 
 // launchers defined in query.cu / verify.cu
 crisp_status crisp_run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
-                                int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st);
+                                int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st,
+                                float *cost_first, float *cost_last);
 crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
                                  int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t stride, int64_t *ncand,
                                  uint8_t *score, int32_t *how, cudaStream_t st);
@@ -22,11 +23,27 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
                               cudaStream_t st);
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
-                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st);
+                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
+                                 const int64_t *S_per_query);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
                                   int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
                                   cudaStream_t st);
+
+crisp_status crisp_run_features(const crisp_index *ix, const int32_t *cand, int64_t stride, const int64_t *ncand,
+                                const uint8_t *score, const float *cfirst, const float *clast, int32_t nq, int32_t k,
+                                int32_t tau, float *feats, cudaStream_t st);
+crisp_status crisp_run_mlp_depth(const crisp_index *ix, const float *feats, int32_t nq, const int64_t *ncand,
+                                 int64_t stride, int32_t k, float mV, float mS, int64_t *dV, int64_t *dS,
+                                 cudaStream_t st);
+crisp_status crisp_run_select_score(const int32_t *cand, int64_t stride, const int64_t *ncand, const uint8_t *score,
+                                    const int64_t *depth, int32_t nq, int32_t *out, int64_t *nout, cudaStream_t st);
+crisp_status crisp_run_labels_v(const int32_t *cand, int64_t stride, const int64_t *ncand, const uint8_t *score,
+                                const int64_t *top, int32_t k, int32_t nq, int64_t *dV, cudaStream_t st);
+crisp_status crisp_run_labels_s(const int32_t *P, int64_t stride, const int64_t *nP, const float *dist,
+                                const int64_t *top, int32_t k, int32_t nq, int64_t *dS, cudaStream_t st);
+crisp_status crisp_run_log2_targets(const int64_t *dV, const int64_t *dS, int32_t nq, int64_t *labels, float *targets,
+                                    cudaStream_t st);
 
 // ------------------------------------------------------------ scratch pool
 #include <mutex>
@@ -112,6 +129,7 @@ static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->Xb);
     cudaFree(ix->X8);
     cudaFree(ix->S8);
+    cudaFree(ix->mlp);
 }
 
 extern "C" void crisp_free(crisp_index *ix) {
@@ -269,6 +287,7 @@ extern "C" crisp_status crisp_index_import(const void *host_buf, size_t bytes, v
 // --------------------------------------------------------------- search
 struct SearchPlan {
     int32_t tau, phi, k, prec, S;
+    bool learned;
     int64_t budget, cap, stride;
     int32_t chunk;
     size_t per_query;
@@ -279,7 +298,11 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     CRISP_REQUIRE(nq >= 0, "crisp_search: nq < 0");
     CRISP_REQUIRE(p->k >= 1 && p->k <= CRISP_KOUT_MAX && p->k <= ix->N, "crisp_search: k = %d outside [1, min(256, N)]",
                   p->k);
-    CRISP_REQUIRE(p->mode == 0 || p->mode == 1, "crisp_search: mode must be 0 or 1");
+    CRISP_REQUIRE(p->mode >= 0 && p->mode <= 2, "crisp_search: mode must be 0, 1 or 2");
+    if (p->mode == 2) {
+        CRISP_REQUIRE(ix->mlp, "crisp_search: learned mode needs a model (crisp_index_set_model)");
+        CRISP_REQUIRE(ix->Xb, "crisp_search: learned mode needs the BF16 copy (crisp_index_add_copies)");
+    }
     CRISP_REQUIRE(p->rho > 0.0 && p->rho <= 1.0, "crisp_search: rho outside (0, 1]");
     CRISP_REQUIRE(p->alpha >= 0.0 && p->alpha <= 1.0, "crisp_search: alpha outside [0, 1]");
     CRISP_REQUIRE(p->max_candidates == 0 || p->max_candidates >= p->k, "crisp_search: 0 < max_candidates < k");
@@ -294,7 +317,8 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     if (ix->M > 127) { crisp_set_error("crisp_search: M > 127 is not supported"); return CRISP_EUNSUPPORTED; }
     pl->tau = crisp_tau(p->alpha, ix->M);
     pl->budget = crisp_budget(p->rho, ix->N);
-    pl->phi = p->mode;
+    pl->phi = p->mode == 1 ? 1 : 0;
+    pl->learned = p->mode == 2;
     pl->k = p->k;
     pl->cap = p->max_candidates;
     pl->prec = p->precision;
@@ -314,6 +338,8 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     const int64_t K2 = (int64_t)ix->K * ix->K;
     pl->per_query = sizeof(float) * ix->Dp + sizeof(int32_t) * ix->M * K2 + sizeof(int32_t) * ix->M +
                     sizeof(int64_t) * ix->M + sizeof(int32_t) * pl->stride * 2 + sizeof(int32_t) * pl->S + 64;
+    if (pl->learned)   // scores, traversal costs, features, selected list
+        pl->per_query += pl->stride + sizeof(float) * (2 * ix->M + 2 * ix->M + 68) + sizeof(int32_t) * pl->stride + 64;
     size_t budget_bytes = (size_t)16 << 30;
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
@@ -355,6 +381,11 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
                           sizeof(int32_t) * (size_t)C * pl.stride, sizeof(float) * (size_t)C * pl.stride,
                           sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C, sizeof(int64_t) * (size_t)C,
                           sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C * pl.S,
+                          sizeof(int64_t) * (size_t)C,
+                          pl.learned ? (size_t)C * pl.stride : 0, pl.learned ? sizeof(float) * (size_t)C * M : 0,
+                          pl.learned ? sizeof(float) * (size_t)C * M : 0,
+                          pl.learned ? sizeof(float) * (size_t)C * (2 * M + 68) : 0, sizeof(int64_t) * (size_t)C,
+                          sizeof(int64_t) * (size_t)C, pl.learned ? sizeof(int32_t) * (size_t)C * pl.stride : 0,
                           sizeof(int64_t) * (size_t)C};
         for (size_t x : parts) total += (x + 255) / 256 * 256;
     }
@@ -373,19 +404,39 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
     int64_t *nfull = carve<int64_t>(cur, C);
     int32_t *shortl = carve<int32_t>(cur, (size_t)C * pl.S);
     int64_t *nshort = carve<int64_t>(cur, C);
+    uint8_t *score = pl.learned ? carve<uint8_t>(cur, (size_t)C * pl.stride) : nullptr;
+    float *cfirst = pl.learned ? carve<float>(cur, (size_t)C * M) : nullptr;
+    float *clast = pl.learned ? carve<float>(cur, (size_t)C * M) : nullptr;
+    float *feats = pl.learned ? carve<float>(cur, (size_t)C * (2 * M + 68)) : nullptr;
+    int64_t *dV = pl.learned ? carve<int64_t>(cur, C) : nullptr;
+    int64_t *dS = pl.learned ? carve<int64_t>(cur, C) : nullptr;
+    int32_t *selV = pl.learned ? carve<int32_t>(cur, (size_t)C * pl.stride) : nullptr;
+    int64_t *nsel = pl.learned ? carve<int64_t>(cur, C) : nullptr;
     for (int32_t c0 = 0; c0 < nq && s == CRISP_OK; c0 += C) {
         int32_t nc = std::min(C, nq - c0);
         const float *Qc = Q + (int64_t)c0 * ix->D;
         if (ix->rotated) s = crisp_rotate_rows(Qc, nc, ix->D, ix->D, ix->R32, Qr, ix->Dp, st);
         else s = launch_pad_rows(Qc, nc, ix->D, ix->D, Qr, ix->Dp, st);
-        if (!s) s = crisp_run_activate(ix, Qr, nc, pl.phi, pl.k, pl.budget, act, nact, retr, st);
-        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, pl.k, pl.cap, cand, pl.stride, ncand, nullptr, how, st);
+        if (!s) s = crisp_run_activate(ix, Qr, nc, pl.phi, pl.k, pl.budget, act, nact, retr, st, cfirst, clast);
+        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, pl.k, pl.cap, cand, pl.stride, ncand, score, how, st);
         int64_t *ids_c = ids + (int64_t)c0 * pl.k;
         float *d2_c = d2 + (int64_t)c0 * pl.k;
-        if (!s && p->mode == 0 && pl.prec > 0) {
+        if (!s && pl.learned) {
+            // F1: features -> MLP depths -> score prefix -> BF16 shortlist -> FP32 re-rank
+            s = crisp_run_features(ix, cand, pl.stride, ncand, score, cfirst, clast, nc, pl.k, pl.tau, feats, st);
+            if (!s) s = crisp_run_mlp_depth(ix, feats, nc, ncand, pl.stride, pl.k, p->depth_margin, p->short_margin, dV,
+                                            dS, st);
+            if (!s) s = crisp_run_select_score(cand, pl.stride, ncand, score, dV, nc, selV, nsel, st);
+            if (!s) s = crisp_run_shortlist(ix, Qr, nc, selV, pl.stride, nsel, 1, 1, dist, cand, pl.stride, nshort, st,
+                                            dS);
+            if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, nshort, pl.k, dist, ids_c, d2_c, st);
+            if (!s && stats)
+                s = launch_write_stats(nc, ncand, how, retr, M, nsel, nshort, pl.tau, stats + c0, st);
+        } else if (!s && p->mode == 0 && pl.prec > 0) {
             // F2: coarse-score every candidate on the low-precision rows, then the
             // FP32 re-rank of the shortlist
-            s = crisp_run_shortlist(ix, Qr, nc, cand, pl.stride, ncand, pl.prec, pl.S, dist, shortl, pl.S, nshort, st);
+            s = crisp_run_shortlist(ix, Qr, nc, cand, pl.stride, ncand, pl.prec, pl.S, dist, shortl, pl.S, nshort, st,
+                                    nullptr);
             if (!s) s = crisp_run_rerank(ix, Qr, nc, shortl, pl.S, nshort, pl.k, dist, ids_c, d2_c, st);
             if (!s && stats)
                 s = launch_write_stats(nc, ncand, how, retr, M, ncand, nshort, pl.tau, stats + c0, st);
@@ -440,5 +491,78 @@ extern "C" crisp_status crisp_search_host(const crisp_index *ix, const float *Q,
     crisp_scratch_free(buf, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (!s && e2 != cudaSuccess) s = crisp_cuda_fail(e2, "cudaStreamSynchronize", __FILE__, __LINE__);
+    return s;
+}
+
+// ------------------------------------------------------- learned training data
+extern "C" crisp_status crisp_learned_data(const crisp_index *ix, const float *Q, int32_t nq,
+                                           const crisp_search_params *p, float *features, int64_t *labels,
+                                           float *targets, void *stream) {
+    CRISP_REQUIRE(ix && p, "crisp_learned_data: null index or params");
+    CRISP_REQUIRE(ix->Xb, "crisp_learned_data: the index needs the BF16 copy (crisp_index_add_copies)");
+    crisp_search_params g = *p;
+    g.mode = 0;
+    g.precision = 0;
+    SearchPlan pl;
+    crisp_status s = plan_search(ix, nq, &g, &pl);
+    if (s) return s;
+    if (nq == 0) return CRISP_OK;
+    CRISP_REQUIRE(Q && features && labels, "crisp_learned_data: null pointer");
+    cudaStream_t st = as_stream(stream);
+    const int64_t K2 = (int64_t)ix->K * ix->K;
+    const int32_t M = ix->M, F = 2 * M + 68, k = pl.k;
+    int64_t per = pl.per_query + pl.stride * 5 + sizeof(float) * (4 * M + 2 * k) + 256;
+    int32_t C = (int32_t)std::max<int64_t>(1, std::min<int64_t>(pl.chunk, ((int64_t)16 << 30) / per));
+    C = std::min(C, nq);
+    size_t parts[] = {sizeof(float) * (size_t)C * ix->Dp, sizeof(int32_t) * (size_t)C * M * K2,
+                      sizeof(int32_t) * (size_t)C * M, sizeof(int64_t) * (size_t)C * M, sizeof(float) * (size_t)C * M,
+                      sizeof(float) * (size_t)C * M, sizeof(int32_t) * (size_t)C * pl.stride, (size_t)C * pl.stride,
+                      sizeof(float) * (size_t)C * pl.stride, sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C,
+                      sizeof(int64_t) * (size_t)C * k, sizeof(float) * (size_t)C * k, sizeof(int64_t) * (size_t)C,
+                      sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C * pl.stride, sizeof(int64_t) * (size_t)C,
+                      sizeof(int64_t) * (size_t)C};
+    size_t total = 0;
+    for (size_t x : parts) total += (x + 255) / 256 * 256;
+    uint8_t *base = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&base, total, st));
+    uint8_t *cur = base;
+    float *Qr = carve<float>(cur, (size_t)C * ix->Dp);
+    int32_t *act = carve<int32_t>(cur, (size_t)C * M * K2);
+    int32_t *nact = carve<int32_t>(cur, (size_t)C * M);
+    int64_t *retr = carve<int64_t>(cur, (size_t)C * M);
+    float *cfirst = carve<float>(cur, (size_t)C * M);
+    float *clast = carve<float>(cur, (size_t)C * M);
+    int32_t *cand = carve<int32_t>(cur, (size_t)C * pl.stride);
+    uint8_t *score = carve<uint8_t>(cur, (size_t)C * pl.stride);
+    float *dist = carve<float>(cur, (size_t)C * pl.stride);
+    int64_t *ncand = carve<int64_t>(cur, C);
+    int32_t *how = carve<int32_t>(cur, C);
+    int64_t *top = carve<int64_t>(cur, (size_t)C * k);
+    float *topd = carve<float>(cur, (size_t)C * k);
+    int64_t *dV = carve<int64_t>(cur, C);
+    int64_t *dS = carve<int64_t>(cur, C);
+    int32_t *selV = carve<int32_t>(cur, (size_t)C * pl.stride);
+    int64_t *nsel = carve<int64_t>(cur, C);
+    int64_t *nshort = carve<int64_t>(cur, C);
+    for (int32_t c0 = 0; c0 < nq && s == CRISP_OK; c0 += C) {
+        int32_t nc = std::min(C, nq - c0);
+        const float *Qc = Q + (int64_t)c0 * ix->D;
+        if (ix->rotated) s = crisp_rotate_rows(Qc, nc, ix->D, ix->D, ix->R32, Qr, ix->Dp, st);
+        else s = launch_pad_rows(Qc, nc, ix->D, ix->D, Qr, ix->Dp, st);
+        if (!s) s = crisp_run_activate(ix, Qr, nc, 0, k, pl.budget, act, nact, retr, st, cfirst, clast);
+        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, k, pl.cap, cand, pl.stride, ncand, score, how, st);
+        if (!s) s = crisp_run_features(ix, cand, pl.stride, ncand, score, cfirst, clast, nc, k, pl.tau,
+                                       features + (int64_t)c0 * F, st);
+        if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, ncand, k, dist, top, topd, st);
+        if (!s) s = crisp_run_labels_v(cand, pl.stride, ncand, score, top, k, nc, dV, st);
+        if (!s) s = crisp_run_select_score(cand, pl.stride, ncand, score, dV, nc, selV, nsel, st);
+        // coarse distances of the whole prefix (keep all of it), then the coarse label
+        if (!s) s = crisp_run_shortlist(ix, Qr, nc, selV, pl.stride, nsel, 1, 1, dist, cand, pl.stride, nshort, st,
+                                        nsel);
+        if (!s) s = crisp_run_labels_s(selV, pl.stride, nsel, dist, top, k, nc, dS, st);
+        if (!s) s = crisp_run_log2_targets(dV, dS, nc, labels + 2 * (int64_t)c0,
+                                           targets ? targets + 2 * (int64_t)c0 : nullptr, st);
+    }
+    crisp_scratch_free(base, st);
     return s;
 }

@@ -33,6 +33,8 @@ struct crisp_index {
     uint16_t *Xb = nullptr;        // [N][Dp] BF16 bits (optional)
     uint8_t *X8 = nullptr;         // [N][Dp] FP8 E4M3 codes (optional)
     float *S8 = nullptr;           // [N] FP8 row scales (optional)
+    float *mlp = nullptr;          // learned-depth model (F = 2M + 68 -> H -> H -> 2), optional
+    int32_t mlp_H = 0;
     int device = 0;
     int64_t bytes = 0;
 };

@@ -124,7 +124,8 @@ constexpr int ACT_WARP_WORDS_FIXED = 7 * 64;
 __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const float *__restrict__ Qr, int nq, int phi,
                                                              int kk, long long budget, int *__restrict__ act,
                                                              int *__restrict__ nact, long long *__restrict__ retrieved,
-                                                             float *__restrict__ sorted_out, int *__restrict__ perm_out) {
+                                                             float *__restrict__ sorted_out, int *__restrict__ perm_out,
+                                                             float *__restrict__ cost_first, float *__restrict__ cost_last) {
     extern __shared__ float sm[];
     const int K = ix.K, H = ix.H, K2 = K * K, m = blockIdx.y, M = ix.M;
     float *CtL = sm;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
     __syncwarp();
     long long got = 0;
     int count = 0;
+    float c_first = 0.0f, c_last = 0.0f;
     int *out = act + ((long long)q * M + m) * K2;
     while (got < budget) {
         float bc = FLT_MAX;
@@ -227,6 +229,8 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
         if (!have) break;
         int j = rowlen[bi];
         int cell = p1[bi] * K + p2[j];
+        if (count == 0) c_first = bc;
+        c_last = bc;
         ++count;
         int w = (phi == 1 && count <= kk) ? 2 : 1;
         got += offs[cell + 1] - offs[cell];
@@ -240,6 +244,8 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
     if (lane == 0) {
         nact[(long long)q * M + m] = count;
         if (retrieved) retrieved[(long long)q * M + m] = got;
+        if (cost_first) cost_first[(long long)q * M + m] = c_first;
+        if (cost_last) cost_last[(long long)q * M + m] = c_last;
     }
 }
 
@@ -267,7 +273,6 @@ __global__ void k_tile_off(IxView ix, int *__restrict__ tile_off) {
 
 // ================================================== Q4 + Q5 count and cut
 constexpr int CNT_NT = 512;
-constexpr int CNT_SEG = CRISP_TILE / CNT_NT;   // bytes of counters per thread (128)
 
 struct CountShared {
     int base[129];
@@ -276,56 +281,111 @@ struct CountShared {
     long long w_eqbase[CNT_NT / 32], w_outbase[CNT_NT / 32];
     long long tile_sel, tile_eq;
     int sel_s, sel_need;
+    // one batch of activated cells staged for one tile
+    int e_beg[CNT_NT];          // first position of the cell's ids inside the tile
+    int e_pre[CNT_NT + 1];      // exclusive prefix of the cells' id counts in the tile
+    int e_wm[CNT_NT];           // weight | subspace << 8
+    long long scan_ws[CNT_NT / 32 + 1];
 };
 
+constexpr int CNT_U = 4;   // flat ids per lane in flight
+
 // Count tile t of query q into the byte counters `cnt` (zeroed here): every id
-// of every activated cell that falls in the tile adds its cell's weight.
-__device__ void count_tile(const IxView &ix, const int *__restrict__ actq, const CountShared &S, int E, int t,
+// of every activated cell that falls in the tile adds its cell's weight.  The
+// cells are staged 512 at a time with their id counts in the tile; the flat id
+// range is then cut into one contiguous piece per warp, lanes on consecutive
+// ids (coalesced loads), each lane finding its cell by a short forward scan.
+__device__ void count_tile(const IxView &ix, const int *__restrict__ actq, CountShared &S, int E, int t,
                            uint32_t *cnt) {
     const int K2 = ix.K * ix.K, T = ix.T, M = ix.M;
     uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
     for (int i = threadIdx.x; i < CRISP_TILE / 16; i += CNT_NT) c4[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long tbase = (long long)t << CRISP_TILE_LOG2;
-    const int nbatch = (E + 31) / 32;
-    for (int b = warp; b < nbatch; b += CNT_NT / 32) {
-        int e = b * 32 + lane;
-        int beg = 0, end = 0, w = 0, m = 0;
-        if (e < E) {
-            int lo = 0, hi = M - 1;            // m with base[m] <= e < base[m+1]
+    for (int e0 = 0; e0 < E; e0 += CNT_NT) {
+        const int ne = E - e0 < CNT_NT ? E - e0 : CNT_NT;
+        int beg = 0, len = 0, wm = 0;
+        const int i = threadIdx.x;
+        if (i < ne) {
+            const int e = e0 + i;
+            int lo = 0, hi = M - 1;            // subspace m with base[m] <= e < base[m+1]
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
                 if (S.base[mid] <= e) lo = mid;
                 else hi = mid - 1;
             }
-            m = lo;
-            int ent = actq[(long long)m * K2 + (e - S.base[m])];
-            int cell = ent & 0xFFFF;
-            w = ent >> 16;
-            const int *to = ix.tile_off + ((long long)m * K2 + cell) * (T + 1) + t;
+            const int m = lo;
+            const int ent = actq[(long long)m * K2 + (e - S.base[m])];
+            const int *to = ix.tile_off + ((long long)m * K2 + (ent & 0xFFFF)) * (T + 1) + t;
             beg = to[0];
-            end = to[1];
+            len = to[1] - beg;
+            wm = (ent >> 16) | (m << 8);
         }
-        for (int j = 0; j < 32; ++j) {
-            int bj = __shfl_sync(0xffffffffu, beg, j);
-            int ej = __shfl_sync(0xffffffffu, end, j);
-            int wj = __shfl_sync(0xffffffffu, w, j);
-            int mj = __shfl_sync(0xffffffffu, m, j);
-            const int *idsm = ix.ids + (long long)mj * ix.N;
-            for (int p = bj + lane; p < ej; p += 32) {
-                int local = (int)((long long)__ldg(idsm + p) - tbase);
-                atomicAdd(&cnt[local >> 2], (uint32_t)wj << ((local & 3) * 8));
+        long long tot;
+        const long long ex = block_excl_scan<CNT_NT>(len, S.scan_ws, &tot);
+        if (i < ne) {
+            S.e_beg[i] = beg;
+            S.e_pre[i] = (int)ex;
+            S.e_wm[i] = wm;
+        }
+        if (i == 0) S.e_pre[ne] = (int)tot;
+        __syncthreads();
+        const int total = (int)tot;
+        const int per = (total + CNT_NT / 32 - 1) / (CNT_NT / 32);
+        const int f_lo = warp * per, f_hi = f_lo + per < total ? f_lo + per : total;
+        if (f_lo < f_hi) {
+            // the cell holding flat id f_lo
+            int lo = 0, hi = ne - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (S.e_pre[mid] <= f_lo) lo = mid;
+                else hi = mid - 1;
+            }
+            int ecur = lo;
+            for (int fb = f_lo; fb < f_hi; fb += 32 * CNT_U) {
+                int ids_v[CNT_U], wv[CNT_U];
+                bool act[CNT_U];
+#pragma unroll
+                for (int u = 0; u < CNT_U; ++u) {
+                    const int f = fb + 32 * u + lane;
+                    act[u] = f < f_hi;
+                    const int fc = act[u] ? f : f_hi - 1;
+                    int e = ecur;
+                    while (fc >= S.e_pre[e + 1]) ++e;
+                    const int w = S.e_wm[e];
+                    wv[u] = w & 0xFF;
+                    const int p = S.e_beg[e] + (fc - S.e_pre[e]);
+                    ids_v[u] = act[u] ? __ldg(ix.ids + (long long)(w >> 8) * ix.N + p) : 0;
+                    ecur = __shfl_sync(0xffffffffu, e, 31);
+                }
+#pragma unroll
+                for (int u = 0; u < CNT_U; ++u) {
+                    if (act[u]) {
+                        const int local = (int)((long long)ids_v[u] - tbase);
+                        atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << ((local & 3) * 8));
+                    }
+                }
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
+    __syncthreads();   // zeroing and counting complete before anyone reads the tile (also when E == 0)
 }
 
 // Byte masks (0xFF per byte) of v > s and v == s for the four bytes of w.
+// Counters are scores <= 2M <= 254.  For s in [0, 127] and v <= 127 the sum
+// v + (127 - s) stays below 256 in every byte (no carry into the next byte) and
+// has bit 7 set exactly when v > s; bytes above 127 are caught by their own
+// bit 7.  The general SIMD compare serves the other thresholds.
 __device__ __forceinline__ unsigned gt_mask(unsigned w, int s) {
     if (s < 0) return 0xFFFFFFFFu;
     if (s > 254) return 0u;
+    if (s <= 127) {
+        unsigned hi = w & 0x80808080u;                              // bytes >= 128 (> s)
+        unsigned lo = ((w & 0x7F7F7F7Fu) + (unsigned)(127 - s) * 0x01010101u) & 0x80808080u;
+        unsigned m = hi | lo;                                       // bit 7 of each byte
+        return (m >> 7) * 0xFFu;
+    }
     return __vcmpgtu4(w, (unsigned)s * 0x01010101u);
 }
 __device__ __forceinline__ unsigned eq_mask(unsigned w, int s) {
@@ -356,16 +416,25 @@ __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t 
     const int vlim = lim <= 0 ? 0 : (lim >= CNT_WARP_BYTES ? CNT_WARP_BYTES : (int)lim);
     const uint4 *wc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(cnt) + warp * CNT_WARP_BYTES);
     int c_gt = 0, c_eq = 0;
+    const bool want_eq = need_eq > 0;
 #pragma unroll 4
     for (int r = 0; r < CNT_ROUNDS; ++r) {
         int b0 = r * 512 + lane * 16;
         uint4 v = wc[r * 32 + lane];
         unsigned ws[4] = {v.x, v.y, v.z, v.w};
+        if (b0 + 16 <= vlim) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            unsigned vm = valid_mask(b0 + 4 * u, vlim);
-            c_gt += __popc(gt_mask(ws[u], s_hi) & vm) >> 3;
-            c_eq += __popc(eq_mask(ws[u], s_hi) & vm) >> 3;
+            for (int u = 0; u < 4; ++u) {
+                c_gt += __popc(gt_mask(ws[u], s_hi)) >> 3;
+                if (want_eq) c_eq += __popc(eq_mask(ws[u], s_hi)) >> 3;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                unsigned vm = valid_mask(b0 + 4 * u, vlim);
+                c_gt += __popc(gt_mask(ws[u], s_hi) & vm) >> 3;
+                if (want_eq) c_eq += __popc(eq_mask(ws[u], s_hi) & vm) >> 3;
+            }
         }
     }
 #pragma unroll
@@ -402,7 +471,7 @@ __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t 
             for (int u = 0; u < 4; ++u) {
                 unsigned vm = valid_mask(b0 + 4 * u, vlim);
                 gm[u] = gt_mask(ws[u], s_hi) & vm;
-                em[u] = eq_mask(ws[u], s_hi) & vm;
+                em[u] = want_eq ? eq_mask(ws[u], s_hi) & vm : 0u;
                 g_l += __popc(gm[u]) >> 3;
                 e_l += __popc(em[u]) >> 3;
             }
@@ -453,7 +522,7 @@ __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t 
     return tot_sel;
 }
 
-__global__ void __launch_bounds__(CNT_NT) k_count_cut(IxView ix, const int *__restrict__ act,
+__global__ void __launch_bounds__(CNT_NT, 3) k_count_cut(IxView ix, const int *__restrict__ act,
                                                       const int *__restrict__ nact, int nq, int tau, int kk,
                                                       long long cap, int *__restrict__ cand, long long stride,
                                                       long long *__restrict__ ncand, uint8_t *__restrict__ score,
@@ -576,9 +645,15 @@ __device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S
     for (int shift = 24; shift >= 0; shift -= 8) {
         for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
         __syncthreads();
-        for (long long i = tid; i < n; i += RR_NT) {
-            unsigned key = __float_as_uint(distq[i]);
-            if ((key & mask) == prefix) atomicAdd(&S.hist[(key >> shift) & 255u], 1u);
+        // keys share their leading bytes, so whole warps hit one bin: combine the
+        // lanes of a bin first (one shared atomic per distinct bin per warp)
+        for (long long i0 = 0; i0 < n; i0 += RR_NT) {
+            const long long i = i0 + tid;
+            const unsigned key = i < n ? __float_as_uint(distq[i]) : 0u;
+            const bool hit = i < n && (key & mask) == prefix;
+            const unsigned bin = hit ? (key >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (hit && (__ffs(peers) - 1) == (int)(tid & 31)) atomicAdd(&S.hist[bin], (unsigned)__popc(peers));
         }
         __syncthreads();
         if (tid == 0) {
@@ -799,7 +874,8 @@ __global__ void __launch_bounds__(RR_NT) k_shortlist(IxView ix, const float *__r
                                                      const int *__restrict__ cand, long long stride,
                                                      const long long *__restrict__ ncand, int S_keep,
                                                      float *__restrict__ dbuf, int *__restrict__ out,
-                                                     long long out_stride, long long *__restrict__ nout) {
+                                                     long long out_stride, long long *__restrict__ nout,
+                                                     const long long *__restrict__ S_per_query) {
     extern __shared__ __align__(16) float qs[];
     __shared__ TopkShared S;
     const int q = blockIdx.x;
@@ -822,6 +898,7 @@ __global__ void __launch_bounds__(RR_NT) k_shortlist(IxView ix, const float *__r
     __syncthreads();
     int *outq = out + (long long)q * out_stride;
     long long kept;
+    if (S_per_query) S_keep = (int)(S_per_query[q] < out_stride ? S_per_query[q] : out_stride);
     if (n <= S_keep) {
         for (long long i = threadIdx.x; i < n; i += RR_NT) outq[i] = candq[i];
         kept = n;
@@ -832,6 +909,98 @@ __global__ void __launch_bounds__(RR_NT) k_shortlist(IxView ix, const float *__r
         kept = collect_ordered(distq, n, prefix, need, S, [&](long long slot, long long i) { outq[slot] = candq[i]; });
     }
     if (threadIdx.x == 0) nout[q] = kept;
+}
+
+// ------------------------------------------------ re-rank, streaming form
+// Work items are (query, chunk of RF_CH candidates); item offsets per query
+// come from a scan, and a persistent grid walks the items.  The distances go
+// to dbuf; k_select_rows then picks the top-k of each query.
+constexpr int RF_CH = 512;
+
+__global__ void k_chunk_offsets(const long long *__restrict__ ncand, long long stride, int nq, int ch,
+                                long long *__restrict__ off) {
+    // single block: off[q] = sum over q' < q of ceil(n_q' / ch); off[nq] = total
+    __shared__ long long ws[RR_NT / 32 + 1];
+    long long carry = 0;
+    for (int q0 = 0; q0 < nq; q0 += RR_NT) {
+        int q = q0 + threadIdx.x;
+        long long n = q < nq ? (ncand[q] < stride ? ncand[q] : stride) : 0;
+        long long c = (n + ch - 1) / ch, tot;
+        long long ex = block_excl_scan<RR_NT>(c, ws, &tot);
+        if (q < nq) off[q] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) off[nq] = carry;
+}
+
+__global__ void __launch_bounds__(RR_NT, 5) k_dist_flat(IxView ix, const float *__restrict__ Qr, int nq,
+                                                        const int *__restrict__ cand, long long stride,
+                                                        const long long *__restrict__ ncand,
+                                                        const long long *__restrict__ off, float *__restrict__ dbuf) {
+    extern __shared__ __align__(16) float qs[];
+    __shared__ int s_q;
+    const int Dp = ix.Dp, nb = Dp / 32;
+    const long long total = off[nq];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, l = threadIdx.x & 7;
+    const unsigned gmask = 0xFFu << (lane & 24);
+    int cur_q = -1;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nq - 1;             // query q with off[q] <= w < off[q+1]
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            s_q = lo;
+        }
+        __syncthreads();
+        const int q = s_q;
+        if (q != cur_q) {
+            for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
+            cur_q = q;
+        }
+        __syncthreads();
+        long long n = ncand[q] < stride ? ncand[q] : stride;
+        const long long c0 = (w - off[q]) * RF_CH;
+        const long long c1 = c0 + RF_CH < n ? c0 + RF_CH : n;
+        const int *candq = cand + (long long)q * stride;
+        float *distq = dbuf + (long long)q * stride;
+        for (long long i = c0 + g; i < c1; i += RR_NT / 8) {
+            const float4 *row = reinterpret_cast<const float4 *>(ix.Xr + (long long)candq[i] * Dp) + l;
+            float acc = 0.0f;
+            for (int b0 = 0; b0 < nb; b0 += RR_U) {
+                float4 v[RR_U];
+#pragma unroll
+                for (int u = 0; u < RR_U; ++u)
+                    if (b0 + u < nb) v[u] = __ldcs(row + 8 * (b0 + u));
+#pragma unroll
+                for (int u = 0; u < RR_U; ++u) {
+                    if (b0 + u < nb) {
+                        float4 qv = *reinterpret_cast<const float4 *>(qs + 32 * (b0 + u) + 4 * l);
+                        acc = acc + cr32_block(v[u], qv, gmask);
+                    }
+                }
+            }
+            if (l == 0) distq[i] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__restrict__ cand, long long stride,
+                                                       const long long *__restrict__ ncand, int kk,
+                                                       const float *__restrict__ dbuf, long long *__restrict__ out_ids,
+                                                       float *__restrict__ out_d) {
+    __shared__ TopkShared S;
+    const int q = blockIdx.x;
+    long long n = ncand[q] < stride ? ncand[q] : stride;
+    int nsel = select_topk(dbuf + (long long)q * stride, cand + (long long)q * stride, n, kk, S);
+    for (int r = threadIdx.x; r < kk; r += RR_NT) {
+        bool ok = r < nsel;
+        out_ids[(long long)q * kk + r] = ok ? (long long)S.sid[r] : -1LL;
+        out_d[(long long)q * kk + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
+    }
 }
 
 __global__ void k_stats(int nq, const long long *ncand, const int *how, const long long *retrieved, int M,
@@ -894,21 +1063,23 @@ static size_t activate_smem(const crisp_index *ix) {
 
 static crisp_status run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
                                  int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, float *sorted,
-                                 int32_t *perm, cudaStream_t st) {
+                                 int32_t *perm, cudaStream_t st, float *cost_first = nullptr,
+                                 float *cost_last = nullptr) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = activate_smem(ix);
     CRISP_CK(cudaFuncSetAttribute(k_activate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((nq + ACT_WARPS - 1) / ACT_WARPS, ix->M);
     k_activate<<<grid, ACT_WARPS * 32, smem, st>>>(ix_view(ix), Qr, nq, phi, k, (long long)budget, act, nact,
-                                                   (long long *)retrieved, sorted, perm);
+                                                   (long long *)retrieved, sorted, perm, cost_first, cost_last);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
 
 crisp_status crisp_run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
-                                int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st) {
-    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, st);
+                                int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st,
+                                float *cost_first, float *cost_last) {
+    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, st, cost_first, cost_last);
 }
 
 crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
@@ -929,31 +1100,48 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
                               cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
-    if (smem > 48 * 1024)
-        CRISP_CK(cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rerank<<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
-                                      dbuf, (long long *)ids, d2);
+    long long *off = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
+    k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
     CRISP_COUNT_LAUNCH();
+    if (smem > 48 * 1024)
+        CRISP_CK(cudaFuncSetAttribute(k_dist_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_flat, RR_NT, smem);
+    int grid = sms * (per_sm > 0 ? per_sm : 4);
+    k_dist_flat<<<grid, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, off,
+                                           dbuf);
+    CRISP_COUNT_LAUNCH();
+    k_select_rows<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, dbuf,
+                                        (long long *)ids, d2);
+    CRISP_COUNT_LAUNCH();
+    crisp_scratch_free(off, st);
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
 
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
-                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st) {
+                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
+                                 const int64_t *S_per_query) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
     if (precision == 1) {
         if (smem > 48 * 1024)
             CRISP_CK(cudaFuncSetAttribute(k_shortlist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_shortlist<1><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
-                                                 S, dbuf, out, (long long)out_stride, (long long *)nout);
+                                                 S, dbuf, out, (long long)out_stride, (long long *)nout,
+                                                 (const long long *)S_per_query);
         CRISP_COUNT_LAUNCH();
     } else {
         if (smem > 48 * 1024)
             CRISP_CK(cudaFuncSetAttribute(k_shortlist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_shortlist<2><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
-                                                 S, dbuf, out, (long long)out_stride, (long long *)nout);
+                                                 S, dbuf, out, (long long)out_stride, (long long *)nout,
+                                                 (const long long *)S_per_query);
         CRISP_COUNT_LAUNCH();
     }
     CRISP_CK_LAUNCH();
@@ -1002,6 +1190,18 @@ extern "C" crisp_status crisp_activate(const crisp_index *ix, const float *Qr, i
     CRISP_REQUIRE(budget >= 1, "crisp_activate: budget < 1");
     CRISP_REQUIRE(nq == 0 || (act && nact), "crisp_activate: null output");
     return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, as_stream(stream));
+}
+
+extern "C" crisp_status crisp_activate_costs(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
+                                             int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved,
+                                             float *cost_first, float *cost_last, void *stream) {
+    crisp_status s = check_query_step(ix, Qr, nq);
+    if (s) return s;
+    CRISP_REQUIRE(phi == 0 || phi == 1, "crisp_activate_costs: phi must be 0 or 1");
+    CRISP_REQUIRE(budget >= 1, "crisp_activate_costs: budget < 1");
+    CRISP_REQUIRE(nq == 0 || (act && nact), "crisp_activate_costs: null output");
+    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, as_stream(stream),
+                        cost_first, cost_last);
 }
 
 extern "C" crisp_status crisp_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
@@ -1092,7 +1292,8 @@ extern "C" crisp_status crisp_shortlist(const crisp_index *ix, const float *Qr, 
     cudaStream_t st = as_stream(stream);
     float *dbuf = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
-    s = crisp_run_shortlist(ix, Qr, nq, cand, cand_stride, ncand, precision, S, dbuf, out, out_stride, nout, st);
+    s = crisp_run_shortlist(ix, Qr, nq, cand, cand_stride, ncand, precision, S, dbuf, out, out_stride, nout, st,
+                            nullptr);
     crisp_scratch_free(dbuf, st);
     return s;
 }

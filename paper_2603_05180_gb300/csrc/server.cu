@@ -1,0 +1,333 @@
+// Continuous-batching query server over one index (the engine's serving
+// extension).  Host runtime in C++: requests arrive one at a
+// time from any thread; a dispatcher thread groups waiting requests with equal
+// search parameters into batches, admits a batch when a stream slot is free and
+// the search's scratch fits the memory budget, and runs copy-in, crisp_search and
+// copy-out on that slot's stream.  Batches on different slots overlap on the
+// GPU; completions are found by polling each slot's event.  Every request keeps
+// its arrival and completion time, from which p50 / p99 latency follow.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    std::vector<float> q;
+    crisp_search_params p;
+    int state = 0;                  // 0 waiting, 1 on the GPU, 2 done, 3 failed
+    crisp_status err = CRISP_OK;
+    std::string msg;
+    std::vector<int64_t> ids;
+    std::vector<float> d2;
+    crisp_query_stats st{};
+    Clock::time_point t_arrive, t_done;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t event = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+    int32_t k = 0;
+    size_t scratch = 0;
+    float *hQ = nullptr, *hD = nullptr, *dQ = nullptr, *dD = nullptr;
+    int64_t *hI = nullptr, *dI = nullptr;
+    crisp_query_stats *hS = nullptr, *dS = nullptr;
+};
+
+}  // namespace
+
+struct crisp_server {
+    const crisp_index *ix = nullptr;
+    crisp_server_params prm{};
+    int device = 0;
+    std::vector<Slot> slots;
+    std::deque<uint64_t> waiting;
+    std::unordered_map<uint64_t, Req> reqs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    size_t scratch_in_use = 0, scratch_peak = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_requests = 0;
+    std::vector<double> lat_us;
+};
+
+static void release_slot_buffers(Slot &s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    cudaFreeHost(s.hQ);
+    cudaFreeHost(s.hI);
+    cudaFreeHost(s.hD);
+    cudaFreeHost(s.hS);
+    cudaFree(s.dQ);
+    cudaFree(s.dI);
+    cudaFree(s.dD);
+    cudaFree(s.dS);
+    if (s.event) cudaEventDestroy(s.event);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot();
+}
+
+// Collect finished batches: results to their requests, slot and scratch freed.
+static bool reap(crisp_server *sv) {
+    bool any = false;
+    for (Slot &s : sv->slots) {
+        if (!s.busy) continue;
+        cudaError_t e = cudaEventQuery(s.event);
+        if (e == cudaErrorNotReady) continue;
+        const Clock::time_point now = Clock::now();
+        for (size_t i = 0; i < s.tickets.size(); ++i) {
+            Req &r = sv->reqs[s.tickets[i]];
+            if (e != cudaSuccess) {
+                r.state = 3;
+                r.err = CRISP_ECUDA;
+                r.msg = cudaGetErrorString(e);
+                sv->failed++;
+                continue;
+            }
+            r.ids.assign(s.hI + i * s.k, s.hI + (i + 1) * s.k);
+            r.d2.assign(s.hD + i * s.k, s.hD + (i + 1) * s.k);
+            r.st = s.hS[i];
+            r.state = 2;
+            r.t_done = now;
+            sv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_arrive).count());
+            sv->completed++;
+        }
+        sv->scratch_in_use -= s.scratch;
+        s.busy = false;
+        s.tickets.clear();
+        any = true;
+    }
+    if (any) sv->cv_done.notify_all();
+    return any;
+}
+
+// Admit the oldest waiting request and every other waiting request with the
+// same parameters (arrival order, up to max_batch) onto a free slot.
+static bool admit(crisp_server *sv) {
+    if (sv->waiting.empty()) return false;
+    Slot *free_slot = nullptr;
+    bool any_busy = false;
+    for (Slot &s : sv->slots) {
+        if (!s.busy && !free_slot) free_slot = &s;
+        any_busy |= s.busy;
+    }
+    if (!free_slot) return false;
+    const crisp_search_params key = sv->reqs[sv->waiting.front()].p;
+    std::vector<uint64_t> batch;
+    for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->prm.max_batch; ++it)
+        if (memcmp(&sv->reqs[*it].p, &key, sizeof key) == 0) batch.push_back(*it);
+    const int32_t n = (int32_t)batch.size();
+    size_t need = 0;
+    crisp_status st = crisp_search_scratch_bytes(sv->ix, n, &key, &need);
+    if (st == CRISP_OK && any_busy && sv->scratch_in_use + need > (size_t)sv->prm.scratch_budget) return false;
+    Slot &s = *free_slot;
+    const int32_t D = sv->ix->D;
+    for (int32_t i = 0; i < n; ++i) memcpy(s.hQ + (size_t)i * D, sv->reqs[batch[i]].q.data(), sizeof(float) * D);
+    cudaError_t e = cudaSuccess;
+    if (st == CRISP_OK) {
+        e = cudaMemcpyAsync(s.dQ, s.hQ, sizeof(float) * (size_t)n * D, cudaMemcpyHostToDevice, s.stream);
+        if (e == cudaSuccess) st = crisp_search(sv->ix, s.dQ, n, &key, s.dI, s.dD, s.dS, s.stream);
+        else st = CRISP_ECUDA;
+    }
+    if (st == CRISP_OK) {
+        e = cudaMemcpyAsync(s.hI, s.dI, sizeof(int64_t) * (size_t)n * key.k, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.hD, s.dD, sizeof(float) * (size_t)n * key.k, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.hS, s.dS, sizeof(crisp_query_stats) * n, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s.event, s.stream);
+        if (e != cudaSuccess) st = CRISP_ECUDA;
+    }
+    // the requests leave the waiting queue either way
+    for (uint64_t t : batch) {
+        auto it = std::find(sv->waiting.begin(), sv->waiting.end(), t);
+        if (it != sv->waiting.end()) sv->waiting.erase(it);
+    }
+    if (st != CRISP_OK) {
+        const char *m = crisp_last_error();
+        for (uint64_t t : batch) {
+            Req &r = sv->reqs[t];
+            r.state = 3;
+            r.err = st;
+            r.msg = m ? m : "";
+            sv->failed++;
+        }
+        sv->cv_done.notify_all();
+        return true;
+    }
+    for (uint64_t t : batch) sv->reqs[t].state = 1;
+    s.busy = true;
+    s.tickets = batch;
+    s.k = key.k;
+    s.scratch = need;
+    sv->scratch_in_use += need;
+    sv->scratch_peak = std::max(sv->scratch_peak, sv->scratch_in_use);
+    sv->batches++;
+    sv->batched_requests += n;
+    return true;
+}
+
+static void run(crisp_server *sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        bool busy = false;
+        for (Slot &s : sv->slots) busy |= s.busy;
+        if (sv->stop && sv->waiting.empty() && !busy) break;
+        bool progress = reap(sv);
+        while (admit(sv)) progress = true;
+        if (!progress) {
+            busy = false;
+            for (Slot &s : sv->slots) busy |= s.busy;
+            // poll the GPU every 20 us while work is in flight, else sleep until a submit
+            if (busy) sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+extern "C" crisp_status crisp_server_create(const crisp_index *ix, const crisp_server_params *p, crisp_server **out) {
+    CRISP_REQUIRE(ix && p && out, "crisp_server_create: null pointer");
+    CRISP_REQUIRE(p->streams >= 1 && p->streams <= 64, "crisp_server_create: streams outside [1, 64]");
+    CRISP_REQUIRE(p->max_batch >= 1, "crisp_server_create: max_batch < 1");
+    CRISP_REQUIRE(p->scratch_budget >= 0, "crisp_server_create: scratch_budget < 0");
+    crisp_server *sv = new crisp_server();
+    sv->ix = ix;
+    sv->prm = *p;
+    if (sv->prm.scratch_budget == 0) sv->prm.scratch_budget = (int64_t)8 << 30;
+    sv->device = ix->device;
+    cudaSetDevice(sv->device);
+    sv->slots.resize(p->streams);
+    const size_t B = (size_t)p->max_batch, D = (size_t)ix->D, KO = CRISP_KOUT_MAX;
+    for (Slot &s : sv->slots) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.event, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&s.hQ, sizeof(float) * B * D);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&s.hI, sizeof(int64_t) * B * KO);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&s.hD, sizeof(float) * B * KO);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&s.hS, sizeof(crisp_query_stats) * B);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s.dQ, sizeof(float) * B * D);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s.dI, sizeof(int64_t) * B * KO);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s.dD, sizeof(float) * B * KO);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s.dS, sizeof(crisp_query_stats) * B);
+        if (e != cudaSuccess) {
+            for (Slot &x : sv->slots) release_slot_buffers(x);
+            delete sv;
+            return crisp_cuda_fail(e, "crisp_server_create", __FILE__, __LINE__);
+        }
+    }
+    sv->worker = std::thread(run, sv);
+    *out = sv;
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_server_submit(crisp_server *sv, const float *q, const crisp_search_params *p,
+                                            uint64_t *ticket) {
+    CRISP_REQUIRE(sv && q && p && ticket, "crisp_server_submit: null pointer");
+    size_t probe = 0;
+    crisp_status st = crisp_search_scratch_bytes(sv->ix, 1, p, &probe);   // validates the parameters
+    if (st) return st;
+    Req r;
+    r.q.assign(q, q + sv->ix->D);
+    r.p = *p;
+    r.t_arrive = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        CRISP_REQUIRE(!sv->stop, "crisp_server_submit: server is stopping");
+        *ticket = sv->next_ticket++;
+        sv->reqs.emplace(*ticket, std::move(r));
+        sv->waiting.push_back(*ticket);
+        sv->submitted++;
+    }
+    sv->cv_work.notify_one();
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_server_wait(crisp_server *sv, uint64_t ticket, int32_t timeout_ms, int64_t *ids,
+                                          float *sqdist, crisp_query_stats *stats, double *latency_us) {
+    CRISP_REQUIRE(sv, "crisp_server_wait: null server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    CRISP_REQUIRE(it != sv->reqs.end(), "crisp_server_wait: unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (it->second.state < 2) {
+        if (timeout_ms >= 0 && Clock::now() >= deadline) {
+            crisp_set_error("crisp_server_wait: request %llu not finished within %d ms", (unsigned long long)ticket,
+                            timeout_ms);
+            return CRISP_ETIMEOUT;
+        }
+        if (timeout_ms >= 0) sv->cv_done.wait_until(lk, deadline);
+        else sv->cv_done.wait(lk);
+        it = sv->reqs.find(ticket);
+    }
+    Req &r = it->second;
+    crisp_status st = r.state == 2 ? CRISP_OK : r.err;
+    if (st == CRISP_OK) {
+        if (ids) memcpy(ids, r.ids.data(), sizeof(int64_t) * r.ids.size());
+        if (sqdist) memcpy(sqdist, r.d2.data(), sizeof(float) * r.d2.size());
+        if (stats) *stats = r.st;
+        if (latency_us) *latency_us = std::chrono::duration<double, std::micro>(r.t_done - r.t_arrive).count();
+    } else {
+        crisp_set_error("crisp_server_wait: request %llu failed: %s", (unsigned long long)ticket, r.msg.c_str());
+    }
+    sv->reqs.erase(it);
+    return st;
+}
+
+extern "C" crisp_status crisp_server_get_stats(crisp_server *sv, crisp_server_stats *out) {
+    CRISP_REQUIRE(sv && out, "crisp_server_get_stats: null pointer");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    memset(out, 0, sizeof *out);
+    out->submitted = sv->submitted;
+    out->completed = sv->completed;
+    out->failed = sv->failed;
+    out->batches = sv->batches;
+    out->mean_batch = sv->batches ? (double)sv->batched_requests / (double)sv->batches : 0.0;
+    out->scratch_peak = (int64_t)sv->scratch_peak;
+    if (!sv->lat_us.empty()) {
+        std::vector<double> v = sv->lat_us;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double f) { return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1) + 0.5))]; };
+        out->p50_us = q(0.50);
+        out->p99_us = q(0.99);
+        out->max_us = v.back();
+        double s = 0.0;
+        for (double x : v) s += x;
+        out->mean_us = s / (double)v.size();
+    }
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_server_reset_stats(crisp_server *sv) {
+    CRISP_REQUIRE(sv, "crisp_server_reset_stats: null server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->lat_us.clear();
+    sv->completed = sv->failed = sv->batches = sv->batched_requests = 0;
+    sv->submitted = sv->waiting.size();
+    sv->scratch_peak = sv->scratch_in_use;
+    return CRISP_OK;
+}
+
+extern "C" void crisp_server_destroy(crisp_server *sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Slot &s : sv->slots) release_slot_buffers(s);
+    delete sv;
+}

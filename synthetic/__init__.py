@@ -35,6 +35,7 @@ import numpy as np
 
 # sub-seed offsets: base data, queries, rotation G, k-means, covariance sample
 SUB_DATA, SUB_QUERY, SUB_GAUSS, SUB_KMEANS, SUB_CEV = 0, 1, 2, 3, 4
+SUB_TRAIN, SUB_VALID = 5, 6          # extra query streams of the same law (learned-depth training)
 
 
 def _rng(seed: int, sub: int) -> np.random.Generator:
@@ -70,26 +71,28 @@ def powerlaw_spectrum(D: int, exponent: float = 1.2) -> np.ndarray:
     return np.arange(1, D + 1, dtype=np.float64) ** (-exponent)
 
 
-def powerlaw(N=1_000_000, D=960, nq=10_000, exponent=1.2, seed=0, device="cpu"):
+def powerlaw(N=1_000_000, D=960, nq=10_000, exponent=1.2, seed=0, device="cpu", query_sub=SUB_QUERY):
     """Rows x = U diag(sqrt(lambda)) z with a power-law spectrum and a Haar mix.
 
     With ``device='cuda'`` the Gaussian draws and the mixing product run in
     torch on the GPU (seeded torch generator); the mixing matrix U is always
     drawn on the host.  The two devices give different (equally distributed)
     rows; callers that need the same rows on both sides copy them.
+    ``query_sub`` picks the query stream (training and validation queries of
+    the same law use their own streams).
     """
     U = haar_orthogonal(D, seed * 7919 + 17)
     A = (U * np.sqrt(powerlaw_spectrum(D, exponent))[None, :]).astype(np.float32)  # A = U diag(sqrt l)
     if device == "cpu":
         X = _rng(seed, SUB_DATA).standard_normal((N, D), dtype=np.float32) @ A.T
-        Q = _rng(seed, SUB_QUERY).standard_normal((nq, D), dtype=np.float32) @ A.T
+        Q = _rng(seed, query_sub).standard_normal((nq, D), dtype=np.float32) @ A.T
         return np.ascontiguousarray(X, np.float32), np.ascontiguousarray(Q, np.float32)
     import torch
 
     At = torch.from_numpy(A.T.copy()).to(device)
     g = torch.Generator(device=device)
     out = []
-    for sub, n in ((SUB_DATA, N), (SUB_QUERY, nq)):
+    for sub, n in ((SUB_DATA, N), (query_sub, nq)):
         g.manual_seed(seed * 1000003 + sub)
         Y = torch.empty((n, D), dtype=torch.float32, device=device)
         step = 1 << 18
@@ -196,3 +199,16 @@ def method_draws(N: int, D: int, M: int, K: int = 50, seed: int = 0, kmeans_trai
 def subsample_queries(nq: int, n: int, seed: int = 0) -> np.ndarray:
     """A fixed seeded subset of query positions (for bounded CPU baselines)."""
     return np.sort(_rng(seed, 99).choice(nq, size=min(n, nq), replace=False))
+
+
+def mlp_weights(F: int, H: int, O: int, seed: int = 0, scale: float = 1.0) -> np.ndarray:
+    """Seeded Gaussian parameters for an F -> H -> H -> O network, packed as
+    W1 [F][H], b1 [H], W2 [H][H], b2 [H], W3 [H][O], b3 [O] (weights scaled by
+    1/sqrt(fan_in), small random biases)."""
+    r = _rng(seed, 7)
+    parts = []
+    for shape in ((F, H), (H,), (H, H), (H,), (H, O), (O,)):
+        n = int(np.prod(shape))
+        fan = shape[0] if len(shape) == 2 else 10.0
+        parts.append(scale * r.standard_normal(n) / math.sqrt(fan))
+    return np.concatenate(parts).astype(np.float32)

@@ -1,0 +1,159 @@
+"""The learned re-rank depth (F1) on the GPU: MLP inference bit for bit against
+the oracle, training gradients against the oracle's FP64 gradients, features
+and depth labels bit for bit, the learned search bit for bit (on seeded
+weights), and what a GPU-trained model gains over the plain search."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_05180_gb300 as crisp  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("F,H,O", [(84, 256, 2), (36, 64, 3), (7, 5, 1)])
+def test_mlp_inference_bitexact(F, H, O):
+    P = synthetic.mlp_weights(F, H, O, seed=F)
+    X = np.random.default_rng(F).standard_normal((37, F)).astype(np.float32)
+    Y = torch.empty((37, O), dtype=torch.float32, device=DEV)
+    crisp.crisp_mlp_infer(dev(P), F, H, O, dev(X), 37, Y)
+    Y = Y.cpu().numpy()
+    for i in range(37):
+        assert np.array_equal(Y[i], oracle.mlp_infer(P, F, H, O, X[i])), i
+
+
+def test_mlp_gradients_match_oracle():
+    F, H, O, B = 30, 48, 2, 64
+    P = synthetic.mlp_weights(F, H, O, seed=3)
+    r = np.random.default_rng(4)
+    X = r.standard_normal((B, F)).astype(np.float32)
+    T = r.standard_normal((B, O)).astype(np.float32)
+    G = torch.empty(crisp.crisp_mlp_param_count(F, H, O), dtype=torch.float32, device=DEV)
+    loss = torch.empty(1, dtype=torch.float32, device=DEV)
+    crisp.crisp_mlp_loss_grad(dev(P), F, H, O, dev(X), dev(T), B, G, loss)
+    l64, g64 = oracle.mlp_loss_grad64(P.astype(np.float64), F, H, O, X, T)
+    g = G.cpu().numpy()
+    assert abs(float(loss.item()) - l64) <= 1e-4 * max(1.0, l64)
+    assert np.allclose(g, g64, rtol=2e-3, atol=2e-5 * np.abs(g64).max())
+
+
+def test_mlp_init_and_training_reduce_the_loss():
+    F, H, O, n = 6, 32, 2, 4096
+    P = torch.empty(crisp.crisp_mlp_param_count(F, H, O), dtype=torch.float32, device=DEV)
+    crisp.crisp_mlp_init(P, F, H, O, seed=1)
+    W1 = P[: F * H].cpu().numpy()
+    assert np.abs(W1).max() <= np.sqrt(6.0 / (F + H)) and float(P[F * H:F * H + H].abs().max()) == 0.0
+    r = np.random.default_rng(5)
+    X = r.uniform(-1, 1, (n, F)).astype(np.float32)
+    T = np.stack([np.sin(X[:, 0] * 2) + X[:, 1] ** 2, X[:, 2] * X[:, 3]], 1).astype(np.float32)
+    losses = crisp.crisp_mlp_train(P, F, H, O, dev(X), dev(T), n, 30, 128, 3e-3, seed=2)
+    assert losses[-1] < 0.1 * losses[0]
+
+
+@pytest.fixture(scope="module")
+def c1l():
+    X, Q = synthetic.gmm(N=20000, D=256, nq=48, seed=8)
+    ix_o = oracle.build_index(X, M=8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=8)).add_copies(fp8=False)
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    crisp.crisp_index_add_copies(ix, 1)
+    return X, Q, ix_o, ix
+
+
+def test_learned_data_bitexact(c1l):
+    X, Q, ix_o, ix = c1l
+    p = oracle.SearchParams(k=10, mode=0, rho=0.02, alpha=0.25)
+    nq, F = Q.shape[0], 2 * ix_o.M + 68
+    feats = torch.empty((nq, F), dtype=torch.float32, device=DEV)
+    labels = torch.empty((nq, 2), dtype=torch.int64, device=DEV)
+    tg = torch.empty((nq, 2), dtype=torch.float32, device=DEV)
+    crisp.crisp_learned_data(ix, dev(Q), nq, crisp.search_params(k=10, rho=0.02, alpha=0.25), feats, labels, tg)
+    of, ol = oracle.learned_labels(ix_o, Q, p)
+    assert np.array_equal(feats.cpu().numpy(), of)
+    assert np.array_equal(labels.cpu().numpy(), ol)
+    assert np.allclose(tg.cpu().numpy(), np.log2(ol), rtol=1e-6)
+
+
+@pytest.mark.parametrize("margins", [(0.0, 0.0), (1.0, 0.5), (-1.0, 3.0)])
+def test_learned_search_bitexact_on_seeded_weights(c1l, margins):
+    X, Q, ix_o, ix = c1l
+    F, H = 2 * ix_o.M + 68, 64
+    P = synthetic.mlp_weights(F, H, 2, seed=11, scale=1.0)
+    P[-2:] += np.float32(6.5)          # outputs near log2(90): depths inside the candidate range
+    ix_o.set_model(P, H)
+    crisp.crisp_index_set_model(ix, dev(P), H)
+    kw = dict(k=10, mode=2, rho=0.02, alpha=0.25, depth_margin=margins[0], short_margin=margins[1])
+    nq = Q.shape[0]
+    ids = torch.empty((nq, 10), dtype=torch.int64, device=DEV)
+    d2 = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    st = torch.empty((nq, 6), dtype=torch.int64, device=DEV)
+    crisp.crisp_search(ix, dev(Q), nq, crisp.search_params(**kw), ids, d2, st)
+    oi, od, ost, _ = oracle.search(ix_o, Q, oracle.SearchParams(**kw))
+    assert np.array_equal(ids.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    s = st.cpu().numpy()
+    assert np.array_equal(s[:, 1], ost["n_verified"]) and np.array_equal(s[:, 2], ost["n_full"])
+    assert (s[:, 1] < s[:, 0]).any()   # the prefix really cut some candidate lists
+
+
+def test_trained_model_gain_over_plain():
+    """Train on the GPU with the plain method's labels; at equal recall the
+    learned search must touch far fewer candidate rows than the plain one."""
+    X, Q = synthetic.gmm(N=20000, D=256, nq=3000, seed=12)
+    Xd = dev(X)
+    ix = crisp.crisp_build(Xd, 20000, 256, crisp.build_params(8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=12),
+                                                             copies=1))
+    M, F, H = 8, 2 * 8 + 68, 128
+    base = dict(k=10, rho=0.06, alpha=0.125)   # a wide cut (tau = 1): the score order has room to help
+    ntr = 2000
+    Qd = dev(Q)
+    feats = torch.empty((ntr, F), dtype=torch.float32, device=DEV)
+    labels = torch.empty((ntr, 2), dtype=torch.int64, device=DEV)
+    tg = torch.empty((ntr, 2), dtype=torch.float32, device=DEV)
+    crisp.crisp_learned_data(ix, Qd[:ntr], ntr, crisp.search_params(**base), feats, labels, tg)
+    P = torch.empty(crisp.crisp_mlp_param_count(F, H, 2), dtype=torch.float32, device=DEV)
+    crisp.crisp_mlp_init(P, F, H, 2, seed=3)
+    losses = crisp.crisp_mlp_train(P, F, H, 2, feats, tg, ntr, 40, 128, 2e-3, seed=4)
+    assert losses[-1] < losses[0]
+    crisp.crisp_index_set_model(ix, P, H)
+    Qe = Qd[ntr:]
+    ne = Qe.shape[0]
+    gi, gd = oracle.knn_f64(X, Q[ntr:], 10)
+
+    def run(**kw):
+        ids = torch.empty((ne, 10), dtype=torch.int64, device=DEV)
+        d2 = torch.empty((ne, 10), dtype=torch.float32, device=DEV)
+        st = torch.empty((ne, 6), dtype=torch.int64, device=DEV)
+        crisp.crisp_search(ix, Qe, ne, crisp.search_params(**base, **kw), ids, d2, st)
+        s = st.cpu().numpy()
+        return oracle.recall_at_k(ids.cpu().numpy(), gd, X, Q[ntr:], 10), s[:, 1].mean(), s[:, 2].mean()
+
+    r0, v0, f0 = run(mode=0)
+    rb, vb, fb = run(mode=0, precision=1, shortlist=50)      # BF16 coarse scores, fixed shortlist, no model
+    best = None
+    for m in (0.0, 0.5, 1.0, 1.5, 2.0, 3.0):
+        r, v, f = run(mode=2, depth_margin=m, short_margin=m)
+        if r >= r0 - 0.005:
+            best = (m, r, v, f)
+            break
+    assert best is not None, "no margin reached the plain recall"
+    m, r, v, f = best
+    # bytes per dimension: plain reads every candidate in FP32, the coarse forms
+    # read their BF16 rows and an FP32 shortlist
+    plain_bytes, bf16_bytes, learned_bytes = 4 * f0, 2 * vb + 4 * fb, 2 * v + 4 * f
+    print(f"plain FP32: recall {r0:.4f}, {f0:.0f} FP32 rows | BF16, S=50: recall {rb:.4f}, {vb:.0f} + {fb:.0f} rows | "
+          f"learned+BF16 (margin {m}): recall {r:.4f}, {v:.0f} BF16 + {f:.0f} FP32 rows | row bytes vs plain: "
+          f"BF16 x{plain_bytes / bf16_bytes:.2f}, learned x{plain_bytes / learned_bytes:.2f}")
+    # learned+BF16 moves fewer row bytes than plain FP32 at equal recall, and never more than BF16 alone
+    assert learned_bytes < 0.55 * plain_bytes
+    assert learned_bytes <= bf16_bytes * 1.001
