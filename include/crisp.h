@@ -238,6 +238,22 @@ crisp_status crisp_server_submit(crisp_server *server, const float *q, const cri
 crisp_status crisp_server_wait(crisp_server *server, uint64_t ticket, int32_t timeout_ms, int64_t *ids,
                                float *sqdist, crisp_query_stats *stats, double *latency_us);
 
+/* Open-loop trace replay (a load generator for measuring the server; the
+ * paper has no counterpart).  Request i (of n) asks query Q[qidx[i]] (host
+ * [nq][D] float32) with params[pidx[i]] (host [n_params]) and enters the server at arrival_us[i]
+ * microseconds after the call starts (nondecreasing), whatever the server's
+ * state; its latency counts from that scheduled time.  The calling thread
+ * submits on schedule, then waits for every request: results go to ids /
+ * sqdist (host [n][kmax], -1 / +inf padded past each request's k), latencies
+ * to latency_us (host [n], NaN for a failed request), the whole replay's wall
+ * time to *wall_us (may be NULL).  EINVAL (nothing submitted) for an index
+ * outside its array, k > kmax or unsorted arrivals; otherwise the first failed
+ * request's status after all have finished. */
+crisp_status crisp_server_replay(crisp_server *server, const float *Q, int32_t nq, int64_t n, const int32_t *qidx,
+                                 const crisp_search_params *params, int32_t n_params, const int32_t *pidx,
+                                 const double *arrival_us, int32_t kmax, int64_t *ids, float *sqdist,
+                                 double *latency_us, double *wall_us);
+
 crisp_status crisp_server_get_stats(crisp_server *server, crisp_server_stats *out);
 crisp_status crisp_server_reset_stats(crisp_server *server);
 
@@ -320,6 +336,20 @@ crisp_status crisp_rotation_from_gaussian(const double *G, int32_t D, double *R,
 crisp_status crisp_rotate_rows(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
                                int32_t ldy, void *stream);
 
+/* B2 on the tensor cores (tcgen05, TF32 pipe): Y = X R with each product
+ * split as a_hi b_hi + a_hi b_lo + a_lo b_hi (hi = the value with its low 13
+ * mantissa bits cleared, lo = the rest), FP32 accumulation in tensor memory.
+ * The result agrees with the FP32 product to about 1e-6 of |x| |R e_j| per
+ * output, but not bitwise with crisp_rotate_rows (another summation order).
+ * The build uses it for the rows of the index (§4.1: X' = X R); queries keep
+ * crisp_rotate_rows.  X device [N][ldx], 16-byte aligned with ldx a multiple
+ * of 4 (rows are fetched by TMA); R device [D][D] float32; Y device [N][ldy],
+ * ldy >= D, columns D..ldy-1 zeroed; Y must not overlap X.  Synchronous on
+ * the stream (it reads back the kernel's error word): ECUDA if a pipeline
+ * wait of the kernel timed out. */
+crisp_status crisp_rotate_rows_tc(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                                  int32_t ldy, void *stream);
+
 /* B3 (§4.2, IMI codebooks): Lloyd's k-means over dims [off, off+h) of the S
  * training rows T (device [S][ldt] float32): centroids start at the rows
  * init (device [K] int32 < S) and are updated `iters` times (assignment by
@@ -334,6 +364,16 @@ crisp_status crisp_kmeans(const float *T, int64_t S, int32_t ldt, int32_t off, i
  * cent: device [M][2][K][H]; cells: device [M][N] uint16. */
 crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
                                 int32_t H, const float *cent, uint16_t *cells, void *stream);
+
+/* B3 on the tensor cores (tcgen05, TF32 pipe), same result as
+ * crisp_assign_cells bit for bit: the tensor cores score every centroid
+ * (|c|^2 - 2 x.c), and the centroids whose score is within its proven error
+ * bound of the best are re-measured with the SEQ distance (ties to the lowest
+ * index).  The build uses it for every row.  Xr must be 16-byte aligned with
+ * Dp a multiple of 32 (rows are fetched by TMA); K <= 64.  Synchronous on the
+ * stream: ECUDA if a pipeline wait of the kernel timed out. */
+crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
+                                   int32_t H, const float *cent, uint16_t *cells, void *stream);
 
 /* B4 (§4.2 CSR): for one subspace, Offsets (device [K2+1] int32) and ids
  * (device [N] int32): ids grouped by ascending cell, ascending inside a cell.

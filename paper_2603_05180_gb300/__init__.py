@@ -87,8 +87,10 @@ _SIGS = {
     "crisp_cev": [_P, _I64, _I32, _I32, _P, _I64, C.POINTER(_D), _P],
     "crisp_rotation_from_gaussian": [_P, _I32, _P, _P],
     "crisp_rotate_rows": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
+    "crisp_rotate_rows_tc": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
     "crisp_kmeans": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P, _P],
     "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
+    "crisp_assign_cells_tc": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
     "crisp_csr_build": [_P, _I64, _I32, _P, _P, _P],
     "crisp_sign_codes": [_P, _I64, _I32, _P, _P],
     "crisp_half_dists": [_P, _P, _I32, _P, _P, _P],
@@ -109,6 +111,7 @@ _SIGS = {
     "crisp_server_wait": [_P, C.c_uint64, _I32, _P, _P, _P, C.POINTER(C.c_double)],
     "crisp_server_get_stats": [_P, C.POINTER(ServerStats)],
     "crisp_server_reset_stats": [_P],
+    "crisp_server_replay": [_P, _P, _I32, _I64, _P, _P, _I32, _P, _P, _I32, _P, _P, _P, C.POINTER(C.c_double)],
     "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P, _P],
 }
 
@@ -284,12 +287,20 @@ def crisp_rotate_rows(X, N, D, ldx, R, Y, ldy, stream=None):
     _call("crisp_rotate_rows", _ptr(X), N, D, ldx, _ptr(R), _ptr(Y), ldy, _stream(stream))
 
 
+def crisp_rotate_rows_tc(X, N, D, ldx, R, Y, ldy, stream=None):
+    _call("crisp_rotate_rows_tc", _ptr(X), N, D, ldx, _ptr(R), _ptr(Y), ldy, _stream(stream))
+
+
 def crisp_kmeans(T, S, ldt, off, h, K, H, init, iters, Cout, stream=None):
     _call("crisp_kmeans", _ptr(T), S, ldt, off, h, K, H, _ptr(init), iters, _ptr(Cout), _stream(stream))
 
 
 def crisp_assign_cells(Xr, N, D, Dp, M, K, H, cent, cells, stream=None):
     _call("crisp_assign_cells", _ptr(Xr), N, D, Dp, M, K, H, _ptr(cent), _ptr(cells), _stream(stream))
+
+
+def crisp_assign_cells_tc(Xr, N, D, Dp, M, K, H, cent, cells, stream=None):
+    _call("crisp_assign_cells_tc", _ptr(Xr), N, D, Dp, M, K, H, _ptr(cent), _ptr(cells), _stream(stream))
 
 
 def crisp_csr_build(cells, N, K2, offsets, ids, stream=None):
@@ -482,6 +493,28 @@ def crisp_server_get_stats(server) -> ServerStats:
 
 def crisp_server_reset_stats(server):
     _call("crisp_server_reset_stats", server)
+
+
+def crisp_server_replay(server, Q, qidx, params, pidx, arrival_us, kmax):
+    """Open-loop replay of a request trace (host arrays): request i asks
+    Q[qidx[i]] with params[pidx[i]] at arrival_us[i].  Returns
+    (ids int64 [n][kmax], sqdist float32 [n][kmax], latency_us float64 [n], wall_us)."""
+    import numpy as np
+
+    Q = np.ascontiguousarray(Q, np.float32)
+    qidx = np.ascontiguousarray(qidx, np.int32)
+    pidx = np.ascontiguousarray(pidx, np.int32)
+    arr = np.ascontiguousarray(arrival_us, np.float64)
+    n = qidx.shape[0]
+    P = (SearchParams * max(1, len(params)))(*params)
+    ids = np.empty((n, kmax), np.int64)
+    d2 = np.empty((n, kmax), np.float32)
+    lat = np.empty(n, np.float64)
+    wall = C.c_double(0.0)
+    _call("crisp_server_replay", server, _ptr(Q), Q.shape[0], n, _ptr(qidx), C.cast(P, C.c_void_p), len(params),
+          _ptr(pidx),
+          _ptr(arr), kmax, _ptr(ids), _ptr(d2), _ptr(lat), C.byref(wall))
+    return ids, d2, lat, wall.value
 
 
 def crisp_server_destroy(server):

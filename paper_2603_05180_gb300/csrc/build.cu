@@ -652,8 +652,12 @@ extern "C" crisp_status crisp_rotation_from_gaussian(const double *G, int32_t D,
     return CRISP_OK;
 }
 
+// tc_D > 0: the jobs are the 2M subspace halves of a D-dim index in order and T
+// has the index's row pitch, so the assignment step runs on the tensor cores
+// (same assignments as k_km_assign, see crisp_assign_cells_tc).
 static crisp_status kmeans_batched(const float *T, int64_t S, int32_t ldt, const std::vector<KmJob> &jobs, int32_t K,
-                                   int32_t H, const int32_t *init_dev, int32_t iters, float *C, cudaStream_t st) {
+                                   int32_t H, const int32_t *init_dev, int32_t iters, float *C, cudaStream_t st,
+                                   int32_t tc_D = 0) {
     int nj = (int)jobs.size();
     KmJob *djobs = nullptr;
     int *asg = nullptr;
@@ -664,7 +668,16 @@ static crisp_status kmeans_batched(const float *T, int64_t S, int32_t ldt, const
     size_t smem = sizeof(float) * (size_t)K * H;
     CRISP_CK(cudaFuncSetAttribute(k_km_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int it = 0; it < iters; ++it) {
-        k_km_assign<<<dim3(grid1(S, 128), nj), 128, smem, st>>>(T, S, ldt, djobs, K, H, C, asg);
+        if (tc_D > 0) {
+            crisp_status s = crisp_tc_assign(T, S, tc_D, ldt, nj / 2, K, H, C, nullptr, asg, st);
+            if (s) {
+                cudaFreeAsync(asg, st);
+                cudaFreeAsync(djobs, st);
+                return s;
+            }
+        } else {
+            k_km_assign<<<dim3(grid1(S, 128), nj), 128, smem, st>>>(T, S, ldt, djobs, K, H, C, asg);
+        }
         k_km_update<<<dim3(K, nj), 256, 0, st>>>(T, S, ldt, djobs, K, H, asg, C);
     }
     cudaError_t e = cudaGetLastError();
@@ -833,7 +846,17 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
         }
         BCUDA(cudaStreamSynchronize(st));   // G (host) must outlive its copy
         if (dG) cudaFreeAsync(dG, st);
-        BSTEP(crisp_rotate_rows(X, N, D, D, ix->R32, ix->Xr, ix->Dp, st));
+        // X' = X R on the tensor cores; TMA needs 16-byte aligned rows, so other
+        // shapes go through a zero-padded copy first
+        if (((uintptr_t)X % 16) == 0 && D % 4 == 0) {
+            BSTEP(crisp_rotate_rows_tc(X, N, D, D, ix->R32, ix->Xr, ix->Dp, st));
+        } else if (s == CRISP_OK) {
+            float *Xp = nullptr;
+            BCUDA(cudaMallocAsync((void **)&Xp, sizeof(float) * (size_t)N * ix->Dp, st));
+            BSTEP(launch_pad_rows(X, N, D, D, Xp, ix->Dp, st));
+            BSTEP(crisp_rotate_rows_tc(Xp, N, D, ix->Dp, ix->R32, ix->Xr, ix->Dp, st));
+            if (Xp) cudaFreeAsync(Xp, st);
+        }
     } else if (s == CRISP_OK) {
         BSTEP(launch_pad_rows(X, N, D, D, ix->Xr, ix->Dp, st));
     }
@@ -879,8 +902,9 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
             BCUDA(cudaGetLastError());
         }
         // centroids are laid out [M][2][K][H] = jobs in order
-        BSTEP(kmeans_batched(T, TS, ix->Dp, jobs, K, H, dinit, p->kmeans_iters, ix->cent, st));
-        BSTEP(crisp_assign_cells(ix->Xr, N, D, ix->Dp, M, K, H, ix->cent, cells, st));
+        // Lloyd's assignment steps and the final cells on the tensor cores
+        BSTEP(kmeans_batched(T, TS, ix->Dp, jobs, K, H, dinit, p->kmeans_iters, ix->cent, st, D));
+        BSTEP(crisp_tc_assign(ix->Xr, N, D, ix->Dp, M, K, H, ix->cent, cells, nullptr, st));
         // ---- B4: CSR per subspace
         for (int32_t m = 0; m < M && s == CRISP_OK; ++m)
             BSTEP(crisp_csr_build(cells + (size_t)m * N, N, K * K, ix->offsets + (size_t)m * (K * K + 1),

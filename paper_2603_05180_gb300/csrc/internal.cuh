@@ -97,6 +97,10 @@ cudaError_t crisp_scratch_alloc(void **p, size_t bytes, cudaStream_t st);
 void crisp_scratch_free(void *p, cudaStream_t st);
 
 // ------------------------------------------------ internal launchers
+// Tensor-core cell assignment (tc.cu): cells [M][N], or per-half centroid
+// indices asg [2M][N] when asg is not null.  Synchronous on st.
+crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
+                             const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st);
 crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
                              cudaStream_t st);
 crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);

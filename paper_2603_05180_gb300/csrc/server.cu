@@ -1,11 +1,12 @@
 // Continuous-batching query server over one index (the engine's serving
-// extension).  Host runtime in C++: requests arrive one at a
+// extension; the paper has no serving loop).  Host runtime in C++: requests arrive one at a
 // time from any thread; a dispatcher thread groups waiting requests with equal
 // search parameters into batches, admits a batch when a stream slot is free and
 // the search's scratch fits the memory budget, and runs copy-in, crisp_search and
 // copy-out on that slot's stream.  Batches on different slots overlap on the
 // GPU; completions are found by polling each slot's event.  Every request keeps
 // its arrival and completion time, from which p50 / p99 latency follow.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -49,12 +50,20 @@ struct Slot {
 
 }  // namespace
 
+// Waiting requests of one parameter set, oldest first (tickets increase with
+// arrival, so the oldest waiting request overall heads one of these queues).
+struct ParamClass {
+    crisp_search_params p;
+    std::deque<uint64_t> q;
+};
+
 struct crisp_server {
     const crisp_index *ix = nullptr;
     crisp_server_params prm{};
     int device = 0;
     std::vector<Slot> slots;
-    std::deque<uint64_t> waiting;
+    std::vector<ParamClass> classes;
+    size_t n_waiting = 0;
     std::unordered_map<uint64_t, Req> reqs;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -115,10 +124,10 @@ static bool reap(crisp_server *sv) {
     return any;
 }
 
-// Admit the oldest waiting request and every other waiting request with the
-// same parameters (arrival order, up to max_batch) onto a free slot.
+// Admit the oldest waiting request and the next waiting requests with the same
+// parameters (arrival order, up to max_batch) onto a free slot.
 static bool admit(crisp_server *sv) {
-    if (sv->waiting.empty()) return false;
+    if (sv->n_waiting == 0) return false;
     Slot *free_slot = nullptr;
     bool any_busy = false;
     for (Slot &s : sv->slots) {
@@ -126,14 +135,17 @@ static bool admit(crisp_server *sv) {
         any_busy |= s.busy;
     }
     if (!free_slot) return false;
-    const crisp_search_params key = sv->reqs[sv->waiting.front()].p;
-    std::vector<uint64_t> batch;
-    for (auto it = sv->waiting.begin(); it != sv->waiting.end() && (int)batch.size() < sv->prm.max_batch; ++it)
-        if (memcmp(&sv->reqs[*it].p, &key, sizeof key) == 0) batch.push_back(*it);
-    const int32_t n = (int32_t)batch.size();
+    ParamClass *pc = nullptr;
+    for (ParamClass &c : sv->classes)
+        if (!c.q.empty() && (!pc || c.q.front() < pc->q.front())) pc = &c;
+    const crisp_search_params key = pc->p;
+    const int32_t n = (int32_t)std::min<size_t>(pc->q.size(), (size_t)sv->prm.max_batch);
     size_t need = 0;
     crisp_status st = crisp_search_scratch_bytes(sv->ix, n, &key, &need);
     if (st == CRISP_OK && any_busy && sv->scratch_in_use + need > (size_t)sv->prm.scratch_budget) return false;
+    std::vector<uint64_t> batch(pc->q.begin(), pc->q.begin() + n);
+    pc->q.erase(pc->q.begin(), pc->q.begin() + n);    // the requests leave the waiting queue either way
+    sv->n_waiting -= (size_t)n;
     Slot &s = *free_slot;
     const int32_t D = sv->ix->D;
     for (int32_t i = 0; i < n; ++i) memcpy(s.hQ + (size_t)i * D, sv->reqs[batch[i]].q.data(), sizeof(float) * D);
@@ -149,11 +161,6 @@ static bool admit(crisp_server *sv) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.hS, s.dS, sizeof(crisp_query_stats) * n, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.event, s.stream);
         if (e != cudaSuccess) st = CRISP_ECUDA;
-    }
-    // the requests leave the waiting queue either way
-    for (uint64_t t : batch) {
-        auto it = std::find(sv->waiting.begin(), sv->waiting.end(), t);
-        if (it != sv->waiting.end()) sv->waiting.erase(it);
     }
     if (st != CRISP_OK) {
         const char *m = crisp_last_error();
@@ -185,7 +192,7 @@ static void run(crisp_server *sv) {
     for (;;) {
         bool busy = false;
         for (Slot &s : sv->slots) busy |= s.busy;
-        if (sv->stop && sv->waiting.empty() && !busy) break;
+        if (sv->stop && sv->n_waiting == 0 && !busy) break;
         bool progress = reap(sv);
         while (admit(sv)) progress = true;
         if (!progress) {
@@ -233,26 +240,89 @@ extern "C" crisp_status crisp_server_create(const crisp_index *ix, const crisp_s
     return CRISP_OK;
 }
 
-extern "C" crisp_status crisp_server_submit(crisp_server *sv, const float *q, const crisp_search_params *p,
-                                            uint64_t *ticket) {
-    CRISP_REQUIRE(sv && q && p && ticket, "crisp_server_submit: null pointer");
+// The parameter struct has no padding, so equal parameters are equal bytes.
+static_assert(sizeof(crisp_search_params) == 56, "crisp_search_params has padding");
+
+static crisp_status submit_at(crisp_server *sv, const float *q, const crisp_search_params *p, Clock::time_point t_arrive,
+                              uint64_t *ticket) {
     size_t probe = 0;
     crisp_status st = crisp_search_scratch_bytes(sv->ix, 1, p, &probe);   // validates the parameters
     if (st) return st;
     Req r;
     r.q.assign(q, q + sv->ix->D);
     r.p = *p;
-    r.t_arrive = Clock::now();
+    r.t_arrive = t_arrive;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         CRISP_REQUIRE(!sv->stop, "crisp_server_submit: server is stopping");
+        ParamClass *pc = nullptr;
+        for (ParamClass &c : sv->classes)
+            if (memcmp(&c.p, p, sizeof *p) == 0) pc = &c;
+        if (!pc) {
+            sv->classes.push_back(ParamClass{*p, {}});
+            pc = &sv->classes.back();
+        }
         *ticket = sv->next_ticket++;
         sv->reqs.emplace(*ticket, std::move(r));
-        sv->waiting.push_back(*ticket);
+        pc->q.push_back(*ticket);
+        sv->n_waiting++;
         sv->submitted++;
     }
     sv->cv_work.notify_one();
     return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_server_submit(crisp_server *sv, const float *q, const crisp_search_params *p,
+                                            uint64_t *ticket) {
+    CRISP_REQUIRE(sv && q && p && ticket, "crisp_server_submit: null pointer");
+    return submit_at(sv, q, p, Clock::now(), ticket);
+}
+
+extern "C" crisp_status crisp_server_replay(crisp_server *sv, const float *Q, int32_t nq, int64_t n,
+                                            const int32_t *qidx, const crisp_search_params *params,
+                                            int32_t n_params, const int32_t *pidx, const double *arrival_us, int32_t kmax,
+                                            int64_t *ids, float *sqdist, double *latency_us, double *wall_us) {
+    CRISP_REQUIRE(sv && Q && qidx && params && pidx && arrival_us && ids && sqdist && latency_us,
+                  "crisp_server_replay: null pointer");
+    CRISP_REQUIRE(nq >= 1 && n >= 0 && kmax >= 1 && n_params >= 1,
+                  "crisp_server_replay: nq < 1, n < 0, kmax < 1 or n_params < 1");
+    for (int64_t i = 0; i < n; ++i) {
+        CRISP_REQUIRE(qidx[i] >= 0 && qidx[i] < nq, "crisp_server_replay: qidx[%lld] outside [0, nq)", (long long)i);
+        CRISP_REQUIRE(pidx[i] >= 0 && pidx[i] < n_params, "crisp_server_replay: pidx[%lld] outside [0, n_params)",
+                      (long long)i);
+        CRISP_REQUIRE(params[pidx[i]].k <= kmax, "crisp_server_replay: request %lld has k > kmax", (long long)i);
+        CRISP_REQUIRE(i == 0 || arrival_us[i] >= arrival_us[i - 1], "crisp_server_replay: arrivals not sorted");
+    }
+    const int32_t D = sv->ix->D;
+    std::vector<uint64_t> tickets((size_t)n);
+    const Clock::time_point t0 = Clock::now();
+    // open loop: request i enters at t0 + arrival_us[i] whatever the server's state;
+    // its latency counts from that scheduled time even if this thread runs late
+    for (int64_t i = 0; i < n; ++i) {
+        const Clock::time_point due = t0 + std::chrono::nanoseconds((int64_t)(arrival_us[i] * 1e3));
+        while (Clock::now() < due) {
+            if (due - Clock::now() > std::chrono::microseconds(200)) std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        crisp_status st = submit_at(sv, Q + (size_t)qidx[i] * D, &params[pidx[i]], due, &tickets[(size_t)i]);
+        if (st) {
+            for (int64_t j = 0; j < i; ++j) crisp_server_wait(sv, tickets[(size_t)j], -1, nullptr, nullptr, nullptr, nullptr);
+            return st;
+        }
+    }
+    crisp_status first_err = CRISP_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t *oi = ids + (size_t)i * kmax;
+        float *od = sqdist + (size_t)i * kmax;
+        for (int32_t j = 0; j < kmax; ++j) {
+            oi[j] = -1;
+            od[j] = INFINITY;
+        }
+        latency_us[i] = NAN;
+        crisp_status st = crisp_server_wait(sv, tickets[(size_t)i], -1, oi, od, nullptr, &latency_us[i]);
+        if (st && !first_err) first_err = st;
+    }
+    if (wall_us) *wall_us = std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
+    return first_err;
 }
 
 extern "C" crisp_status crisp_server_wait(crisp_server *sv, uint64_t ticket, int32_t timeout_ms, int64_t *ids,
@@ -315,7 +385,7 @@ extern "C" crisp_status crisp_server_reset_stats(crisp_server *sv) {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->lat_us.clear();
     sv->completed = sv->failed = sv->batches = sv->batched_requests = 0;
-    sv->submitted = sv->waiting.size();
+    sv->submitted = sv->n_waiting;
     sv->scratch_peak = sv->scratch_in_use;
     return CRISP_OK;
 }

@@ -1,0 +1,698 @@
+// Tensor-core (tcgen05) contractions of the index build.
+//
+//   k_rotate_tc   B2  X' = X R (the adaptive rotation of §4.1 applied to every
+//                     row), a dense N x D x D contraction on the 5th-generation
+//                     tensor cores.  FP32 accuracy from the TF32 pipe by the
+//                     three-product split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,
+//                     where a_hi is a with its low 13 mantissa bits cleared and
+//                     a_lo = a - a_hi (exact in FP32).
+//
+// Data movement: the rows of X and of R^T (split into hi / lo once, D x D) are
+// fetched by TMA (cp.async.bulk.tensor) as 128-row x 32-float boxes in the
+// 128-byte swizzled layout that tcgen05.mma reads directly; the X tile is split
+// in shared memory (hi in place, lo beside it) by the CTA's threads.  One
+// thread issues the MMAs into a 128 x BN FP32 accumulator in tensor memory
+// (TMEM) and signals stage reuse through tcgen05.commit -> mbarrier; the four
+// warps then read their 32 TMEM lanes (one output row per thread) with
+// tcgen05.ld and store the rows.  Every mbarrier wait is bounded in time: a
+// wait that gives up records an error word, the CTA skips the rest of its
+// work, waits (bounded) for what it still has in flight, frees its TMEM and
+// returns, and the host reports CRISP_ECUDA.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TC_BM = 128;      // output rows per tile = UMMA M
+constexpr int TC_BK = 32;       // floats per k-block: one 128-byte swizzle row
+constexpr int TC_NT = 128;      // four warps
+constexpr int TC_TMEM_COLS = 256;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // 1 s per wait
+
+__device__ unsigned int g_tc_error;   // first failing wait: 1 + its site code
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after TC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (now_ns() - t0 > TC_WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: 8-row groups of 128-byte rows, groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF)      // start address
+           | ((uint64_t)1 << 16)                 // leading byte offset (unused for this layout)
+           | ((uint64_t)(1024 >> 4) << 32)       // stride byte offset: next 8-row group
+           | ((uint64_t)1 << 46)                 // descriptor version
+           | ((uint64_t)2 << 61);                // layout: 128-byte swizzle
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-collective: the warp is reconverged first (.sync.aligned needs every lane).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void record_error(unsigned int site) { atomicCAS(&g_tc_error, 0u, 1u + site); }
+
+struct RotArgs {
+    long long N;      // rows of X and Y
+    int nk;           // k-blocks of 32 over the contraction (ceil(D / 32))
+    int BN;           // output columns per tile (multiple of 16, <= 256)
+    int nt;           // column tiles
+    int ncols;        // output columns written (Y[:, 0:ncols])
+    int ldy;
+    int vec;          // 1: Y rows 16-byte aligned (float4 stores)
+    float *Y;
+};
+
+// One CTA per (128-row tile, column tile); column tiles of a row tile are
+// adjacent in launch order so the X tile is read from HBM about once.
+__global__ void __launch_bounds__(TC_NT, 1) k_rotate_tc(const __grid_constant__ CUtensorMap tmX,
+                                                        const __grid_constant__ CUtensorMap tmBh,
+                                                        const __grid_constant__ CUtensorMap tmBl, RotArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    const uint32_t A_BYTES = TC_BM * 128, B_BYTES = (uint32_t)a.BN * 128;
+    const uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    uint64_t *bars = (uint64_t *)(sm + 2 * STAGE);     // full[2], empty[2], done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 5);
+    int *abort_flag = (int *)(bars + 6);
+    auto sA = [&](int s) { return sm + s * STAGE; };
+    auto sAlo = [&](int s) { return sm + s * STAGE + A_BYTES; };
+    auto sBh = [&](int s) { return sm + s * STAGE + 2 * A_BYTES; };
+    auto sBl = [&](int s) { return sm + s * STAGE + 2 * A_BYTES + B_BYTES; };
+    const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]), done = smem_addr(&bars[4]);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ct = (int)(blockIdx.x % (unsigned)a.nt);
+    const long long row0 = (long long)(blockIdx.x / (unsigned)a.nt) * TC_BM;
+    const int col0 = ct * a.BN;
+    const int nk = a.nk;
+
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(smem_addr(&bars[i]), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // loads issued / consumed (thread 0 keeps the count of issued ones)
+    int issued = 0;
+    auto issue = [&](int kb) {
+        const int s = kb & 1;
+        const uint32_t fb = full0 + 8u * s;
+        mbar_expect_tx(fb, A_BYTES + 2 * B_BYTES);
+        tma_load_2d(smem_addr(sA(s)), &tmX, kb * TC_BK, (int)row0, fb);
+        tma_load_2d(smem_addr(sBh(s)), &tmBh, kb * TC_BK, col0, fb);
+        tma_load_2d(smem_addr(sBl(s)), &tmBl, kb * TC_BK, col0, fb);
+    };
+    if (tid == 0)
+        for (; issued < 2 && issued < nk; ++issued) issue(issued);
+
+    const uint32_t idesc = tf32_idesc(a.BN);
+    int consumed = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb & 1;
+        const uint32_t ph = (uint32_t)(kb >> 1) & 1u;
+        if (!mbar_wait(full0 + 8u * s, ph)) {
+            record_error(0);
+            *abort_flag = 1;
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        consumed = kb + 1;
+        // split the X tile: hi (low 13 mantissa bits cleared) in place, lo = x - hi beside it
+        float4 *pa = (float4 *)sA(s);
+        float4 *pl = (float4 *)sAlo(s);
+#pragma unroll 4
+        for (int i = tid; i < TC_BM * TC_BK / 4; i += TC_NT) {
+            float4 v = pa[i], h;
+            h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+            h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+            h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+            h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+            pl[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            pa[i] = h;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 32) {
+            tc_fence_after();
+            const uint32_t ah = smem_addr(sA(s)), al = smem_addr(sAlo(s)), bh = smem_addr(sBh(s)),
+                           bl = smem_addr(sBl(s));
+#pragma unroll
+            for (int j = 0; j < TC_BK / 8; ++j) {   // UMMA K = 8 floats = 32 bytes
+                const uint32_t o = 32u * j;
+                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (kb | j) != 0);
+                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1);
+                mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1);
+            }
+            mma_commit(empty0 + 8u * s);
+        }
+        if (tid == 0 && issued < nk) {
+            // stage s is free again once the MMAs just issued have read it
+            if (mbar_wait(empty0 + 8u * s, ph)) {
+                issue(issued);
+                ++issued;
+            } else {
+                record_error(1);
+                *abort_flag = 1;
+            }
+        }
+    }
+    // every MMA issued so far completes before the accumulator is read or freed
+    if (tid == 32) mma_commit(done);
+    if (!mbar_wait(done, 0)) {
+        record_error(2);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    const bool ok = !*abort_flag;   // the same for every thread: tcgen05.ld below is warp-collective
+    tc_fence_after();
+    if (ok) {
+        const long long r = row0 + warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < a.BN; c += 16) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + (uint32_t)c, v);        // all 32 lanes of the warp take part
+            const int gc = col0 + c;
+            if (r >= a.N || gc >= a.ncols) continue;
+            float *y = a.Y + r * (long long)a.ldy + gc;
+            if (a.vec && gc + 16 <= a.ncols) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    reinterpret_cast<float4 *>(y)[q] =
+                        make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                    __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            } else {
+                for (int q = 0; q < 16 && gc + q < a.ncols; ++q) y[q] = __uint_as_float(v[q]);
+            }
+        }
+    }
+    // loads still in flight after an abort land before the CTA's shared memory goes away
+    if (tid == 0)
+        for (int kb = consumed; kb < issued; ++kb)
+            if (!mbar_wait(full0 + 8u * (kb & 1), (uint32_t)(kb >> 1) & 1u)) record_error(3);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// BT_hi / BT_lo [Dp][Dp]: BT[n][k] = R[k][n] split into hi + lo, zero outside D x D.
+__global__ void k_split_rt(const float *__restrict__ R, int D, int Dp, float *__restrict__ hi, float *__restrict__ lo) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)Dp * Dp) return;
+    int n = (int)(e / Dp), k = (int)(e % Dp);
+    float v = (n < D && k < D) ? R[(long long)k * D + n] : 0.0f;
+    float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    hi[e] = h;
+    lo[e] = v - h;
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
+// 2-D FP32 map over rows x cols (row pitch ld floats), box 32 floats x box_rows,
+// 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t rot_smem(int BN) { return 1024 + 2 * (2 * (size_t)TC_BM * 128 + 2 * (size_t)BN * 128) + 64; }
+
+}  // namespace
+
+extern "C" crisp_status crisp_rotate_rows_tc(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                                             int32_t ldy, void *stream) {
+    CRISP_REQUIRE(N >= 0 && D >= 1 && ldx >= D && ldy >= D, "crisp_rotate_rows_tc: bad sizes");
+    CRISP_REQUIRE(N == 0 || (X && R && Y), "crisp_rotate_rows_tc: null pointer");
+    CRISP_REQUIRE((const void *)X != (const void *)Y, "crisp_rotate_rows_tc: Y overlaps X");
+    CRISP_REQUIRE(((uintptr_t)X % 16) == 0 && ((size_t)ldx * sizeof(float)) % 16 == 0,
+                  "crisp_rotate_rows_tc: X must be 16-byte aligned with a row pitch of a multiple of 4 floats");
+    if (N == 0) return CRISP_OK;
+    cudaStream_t st = as_stream(stream);
+    const int Dp = (D + TC_BK - 1) / TC_BK * TC_BK;
+    const int ncols = ldy < Dp ? ldy : Dp;              // columns D..ncols-1 come out zero
+    const int nt = (ncols + 255) / 256;
+    const int BN = ((ncols + nt - 1) / nt + 15) / 16 * 16;
+    float *bt = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&bt, sizeof(float) * 2 * (size_t)Dp * Dp, st));
+    crisp_status s = CRISP_OK;
+    do {
+        k_split_rt<<<(unsigned)(((long long)Dp * Dp + 255) / 256), 256, 0, st>>>(R, D, Dp, bt, bt + (size_t)Dp * Dp);
+        CRISP_COUNT_LAUNCH();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_split_rt", __FILE__, __LINE__); break; }
+        CUtensorMap mx, mh, ml;
+        if (!make_map(&mx, X, N, D, ldx, TC_BM) || !make_map(&mh, bt, Dp, Dp, Dp, BN) ||
+            !make_map(&ml, bt + (size_t)Dp * Dp, Dp, Dp, Dp, BN)) {
+            crisp_set_error("crisp_rotate_rows_tc: tensor map encoding failed");
+            s = CRISP_ECUDA;
+            break;
+        }
+        const size_t smem = rot_smem(BN);
+        e = cudaFuncSetAttribute(k_rotate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        unsigned int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "reset error word", __FILE__, __LINE__); break; }
+        RotArgs a;
+        a.N = N;
+        a.nk = Dp / TC_BK;
+        a.BN = BN;
+        a.nt = nt;
+        a.ncols = ncols;
+        a.ldy = ldy;
+        a.vec = ((uintptr_t)Y % 16 == 0) && (ldy % 4 == 0);
+        a.Y = Y;
+        const long long tiles = (N + TC_BM - 1) / TC_BM * nt;
+        if (tiles > 0x7FFFFFFFLL) {
+            crisp_set_error("crisp_rotate_rows_tc: too many rows");
+            s = CRISP_EINVAL;
+            break;
+        }
+        k_rotate_tc<<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mh, ml, a);
+        CRISP_COUNT_LAUNCH();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rotate_tc", __FILE__, __LINE__); break; }
+        if (ldy > ncols) {
+            e = cudaMemset2DAsync(Y + ncols, sizeof(float) * (size_t)ldy, 0, sizeof(float) * (size_t)(ldy - ncols),
+                                  (size_t)N, st);
+            if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemset2DAsync", __FILE__, __LINE__); break; }
+        }
+        unsigned int err = 0;
+        e = cudaMemcpyFromSymbolAsync(&err, g_tc_error, sizeof err, 0, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rotate_tc", __FILE__, __LINE__); break; }
+        if (err) {
+            crisp_set_error("crisp_rotate_rows_tc: a pipeline wait timed out (site %u)", err - 1);
+            s = CRISP_ECUDA;
+        }
+    } while (0);
+    cudaFreeAsync(bt, st);
+    return s;
+}
+
+// ============================================================================
+//   k_assign_tc   B3  u_m(x) = Combine(argmin_left, argmin_right) for every row
+//                     and subspace (§3 IMI cells).  The tensor cores (TF32, one
+//                     pass) give every row its scores s_c = |c|^2 - 2 x.c against
+//                     the K centroids of both halves; each score is within a
+//                     proven bound E_c of the exact |x - c|^2 - |x|^2, so only
+//                     centroids with s_c - E_c <= min(s + E) can be the argmin.
+//                     Those few are re-measured with the FP32 SEQ distance (an
+//                     fmaf chain over the half's dims, ties to the lowest index),
+//                     which makes the result identical to crisp_assign_cells.
+//
+// Operand layout: the subspace's columns of Xr come by TMA as 32-float k-blocks
+// starting at the 32-aligned column below the subspace; the centroids sit in a
+// prepared matrix whose row c (one per centroid, 64 rows per half) holds c at
+// the same columns and zeros elsewhere, so columns outside a half contribute
+// nothing.  Two 128 x 64 FP32 accumulators (left, right) live in TMEM.
+namespace {
+
+constexpr int AS_KPAD = 64;     // centroid rows per half (K <= 64)
+
+struct AsgArgs {
+    long long N;
+    int D, Dp, M, K, H, KB;
+    const float *Xr;
+    const float *cent;      // [M][2][K][H]
+    const float *cn2;       // [M][2][64] |c|^2 (FP32)
+    const float *cn;        // [M][2][64] |c|
+    uint16_t *cells;        // [M][N] cell ids, or (when asg is set)
+    int *asg;               // [2M][N] per-half centroid indices (k-means)
+};
+
+// TF32 score error bound (both operands truncated to 10 mantissa bits, FP32
+// accumulation) plus the FP32 rounding of the exact distances, generously.
+__device__ __forceinline__ float asg_bound(float nx, float nx2, float c, float c2) {
+    return 6e-3f * nx * c + 1e-4f * (nx2 + c2);
+}
+
+__global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUtensorMap tmX,
+                                                     const __grid_constant__ CUtensorMap tmB, AsgArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    constexpr uint32_t A_BYTES = TC_BM * 128, B_BYTES = AS_KPAD * 128, STAGE = A_BYTES + 2 * B_BYTES;
+    uint64_t *bars = (uint64_t *)(sm + 2 * STAGE);     // full[2], empty[2], done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 5);
+    int *abort_flag = (int *)(bars + 6);
+    const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]), done = smem_addr(&bars[4]);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = (int)(blockIdx.x % (unsigned)a.M);
+    const long long row0 = (long long)(blockIdx.x / (unsigned)a.M) * TC_BM;
+    const int lo = (int)(((long long)m * a.D) / a.M), hi_ = (int)(((long long)(m + 1) * a.D) / a.M);
+    const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl;
+    const int base = lo & ~(TC_BK - 1);
+    const int nk = (hi_ - base + TC_BK - 1) / TC_BK;
+
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(smem_addr(&bars[i]), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(2 * AS_KPAD)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int last_use[2] = {-1, -1};   // producer: last k-block loaded into each stage
+    auto issue = [&](int kb) {
+        const int s = kb & 1;
+        const uint32_t fb = full0 + 8u * s;
+        uint8_t *st = sm + s * STAGE;
+        mbar_expect_tx(fb, STAGE);
+        tma_load_2d(smem_addr(st), &tmX, base + kb * TC_BK, (int)row0, fb);
+        tma_load_2d(smem_addr(st + A_BYTES), &tmB, kb * TC_BK, (m * 2 + 0) * AS_KPAD, fb);
+        tma_load_2d(smem_addr(st + A_BYTES + B_BYTES), &tmB, kb * TC_BK, (m * 2 + 1) * AS_KPAD, fb);
+        last_use[s] = kb;
+    };
+    if (tid == 0) {
+        int issued = 0;
+        for (; issued < 2 && issued < nk; ++issued) issue(issued);
+        for (int kb = 0; issued < nk; ++kb, ++issued) {
+            // reuse stage kb & 1 once the MMAs of k-block kb have read it
+            if (!mbar_wait(empty0 + 8u * (kb & 1), (uint32_t)(kb >> 1) & 1u)) {
+                record_error(10);
+                break;
+            }
+            issue(issued);
+        }
+    } else if (tid == 32) {
+        const uint32_t idesc = tf32_idesc(AS_KPAD);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb & 1;
+            if (!mbar_wait(full0 + 8u * s, (uint32_t)(kb >> 1) & 1u)) {
+                record_error(11);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_addr(sm + s * STAGE), sl = sa + A_BYTES, sr = sa + A_BYTES + B_BYTES;
+#pragma unroll
+            for (int j = 0; j < TC_BK / 8; ++j) {
+                const uint32_t o = 32u * j, acc = (kb | j) != 0;
+                mma_tf32(tmem, sw128_desc(sa + o), sw128_desc(sl + o), idesc, acc);
+                mma_tf32(tmem + AS_KPAD, sw128_desc(sa + o), sw128_desc(sr + o), idesc, acc);
+            }
+            mma_commit(empty0 + 8u * s);
+        }
+        mma_commit(done);
+    }
+    if (!mbar_wait(done, 0)) {
+        record_error(12);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    const bool ok = !*abort_flag;
+    tc_fence_after();
+    if (ok) {
+        const long long r = row0 + warp * 32 + lane;
+        const bool live = r < a.N;
+        const float *x = a.Xr + (live ? r : 0) * (long long)a.Dp + lo;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        int arg[2];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float *xh = x + (half ? hl : 0);
+            const int h = half ? hr : hl;
+            const float *C = a.cent + (((long long)m * 2 + half) * a.K) * a.H;
+            const float *c2 = a.cn2 + (m * 2 + half) * AS_KPAD;
+            const float *c1 = a.cn + (m * 2 + half) * AS_KPAD;
+            float nx2 = 0.0f;
+            for (int d = 0; d < h; ++d) nx2 = fmaf(xh[d], xh[d], nx2);
+            const float nx = sqrtf(nx2);
+            float U = INFINITY;
+            for (int c0 = 0; c0 < AS_KPAD; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(lane_base + (uint32_t)(half * AS_KPAD + c0), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + q;
+                    if (c < a.K) {
+                        const float sc = c2[c] - 2.0f * __uint_as_float(v[q]);
+                        U = fminf(U, sc + asg_bound(nx, nx2, c1[c], c2[c]));
+                    }
+                }
+            }
+            float best = INFINITY;
+            int bc = 0;
+            for (int c0 = 0; c0 < AS_KPAD; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(lane_base + (uint32_t)(half * AS_KPAD + c0), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + q;
+                    if (c >= a.K) continue;
+                    const float sc = c2[c] - 2.0f * __uint_as_float(v[q]);
+                    if (!(sc - asg_bound(nx, nx2, c1[c], c2[c]) <= U)) continue;
+                    const float *cc = C + (long long)c * a.H;
+                    float acc = 0.0f;
+                    for (int d = 0; d < h; ++d) {
+                        const float diff = xh[d] - cc[d];
+                        acc = fmaf(diff, diff, acc);
+                    }
+                    if (acc < best) {   // ascending c: the first minimum wins ties
+                        best = acc;
+                        bc = c;
+                    }
+                }
+            }
+            arg[half] = bc;
+        }
+        if (live) {
+            if (a.asg) {
+                a.asg[(2LL * m) * a.N + r] = arg[0];
+                a.asg[(2LL * m + 1) * a.N + r] = arg[1];
+            } else {
+                a.cells[(long long)m * a.N + r] = (uint16_t)(arg[0] * a.K + arg[1]);
+            }
+        }
+    }
+    if (tid == 0)
+        for (int s = 0; s < 2; ++s)
+            if (last_use[s] >= 0 && !mbar_wait(full0 + 8u * s, (uint32_t)(last_use[s] >> 1) & 1u)) record_error(13);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * AS_KPAD) : "memory");
+    }
+}
+
+// Bm [M][2][64][KB*32]: row c of half h holds centroid c at the Xr columns of
+// that half (relative to the subspace's 32-aligned base column), zeros
+// elsewhere; cn2 / cn: |c|^2 and |c| (zero rows past K).
+__global__ void k_asg_prep(const float *__restrict__ cent, int D, int M, int K, int H, int KB, float *__restrict__ Bm,
+                           float *__restrict__ cn2, float *__restrict__ cn) {
+    const int W = KB * TC_BK;
+    const long long tot = (long long)M * 2 * AS_KPAD * W;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % W);
+        const long long rowi = e / W;
+        const int c = (int)(rowi % AS_KPAD), half = (int)((rowi / AS_KPAD) % 2), m = (int)(rowi / (2 * AS_KPAD));
+        const int lo = (int)(((long long)m * D) / M), hi_ = (int)(((long long)(m + 1) * D) / M);
+        const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl;
+        const int start = lo + (half ? hl : 0) - (lo & ~(TC_BK - 1)), h = half ? hr : hl;
+        float v = 0.0f;
+        if (c < K && j >= start && j < start + h) v = cent[(((long long)m * 2 + half) * K + c) * H + (j - start)];
+        Bm[e] = v;
+        if (j == 0) {
+            float s = 0.0f;
+            if (c < K)
+                for (int d = 0; d < h; ++d) {
+                    const float t = cent[(((long long)m * 2 + half) * K + c) * H + d];
+                    s = fmaf(t, t, s);
+                }
+            cn2[rowi] = s;
+            cn[rowi] = sqrtf(s);
+        }
+    }
+}
+
+}  // namespace
+
+crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
+                             const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st) {
+    CRISP_REQUIRE(Xr && cent && (cells || asg), "crisp_assign_cells_tc: null pointer");
+    CRISP_REQUIRE(K >= 2 && K <= AS_KPAD && M >= 1 && 2 * M <= D && Dp >= D && N >= 1 && H >= 1,
+                  "crisp_assign_cells_tc: bad sizes");
+    CRISP_REQUIRE(Dp % TC_BK == 0 && ((uintptr_t)Xr % 16) == 0,
+                  "crisp_assign_cells_tc: Xr must be 16-byte aligned with Dp a multiple of 32");
+    int KB = 1;
+    for (int m = 0; m < M; ++m) {
+        const int lo = (int)(((long long)m * D) / M), hi_ = (int)(((long long)(m + 1) * D) / M);
+        KB = std::max(KB, (hi_ - (lo & ~(TC_BK - 1)) + TC_BK - 1) / TC_BK);
+    }
+    const size_t bm_n = (size_t)M * 2 * AS_KPAD * KB * TC_BK, nn = (size_t)M * 2 * AS_KPAD;
+    float *buf = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&buf, sizeof(float) * (bm_n + 2 * nn), st));
+    float *Bm = buf, *cn2 = buf + bm_n, *cn = cn2 + nn;
+    crisp_status s = CRISP_OK;
+    do {
+        k_asg_prep<<<(unsigned)std::min<size_t>((bm_n + 255) / 256, 4096), 256, 0, st>>>(cent, D, M, K, H, KB, Bm, cn2,
+                                                                                         cn);
+        CRISP_COUNT_LAUNCH();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_asg_prep", __FILE__, __LINE__); break; }
+        CUtensorMap mx, mb;
+        if (!make_map(&mx, Xr, N, Dp, Dp, TC_BM) || !make_map(&mb, Bm, (long long)M * 2 * AS_KPAD, KB * TC_BK,
+                                                              KB * TC_BK, AS_KPAD)) {
+            crisp_set_error("crisp_assign_cells_tc: tensor map encoding failed");
+            s = CRISP_ECUDA;
+            break;
+        }
+        const size_t smem = 1024 + 2 * ((size_t)TC_BM * 128 + 2 * (size_t)AS_KPAD * 128) + 64;
+        e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        unsigned int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "reset error word", __FILE__, __LINE__); break; }
+        const long long tiles = (N + TC_BM - 1) / TC_BM * M;
+        if (tiles > 0x7FFFFFFFLL) {
+            crisp_set_error("crisp_assign_cells_tc: too many rows");
+            s = CRISP_EINVAL;
+            break;
+        }
+        AsgArgs a{N, D, Dp, M, K, H, KB, Xr, cent, cn2, cn, cells, asg};
+        k_assign_tc<<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mb, a);
+        CRISP_COUNT_LAUNCH();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_assign_tc", __FILE__, __LINE__); break; }
+        unsigned int err = 0;
+        e = cudaMemcpyFromSymbolAsync(&err, g_tc_error, sizeof err, 0, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_assign_tc", __FILE__, __LINE__); break; }
+        if (err) {
+            crisp_set_error("crisp_assign_cells_tc: a pipeline wait timed out (site %u)", err - 1);
+            s = CRISP_ECUDA;
+        }
+    } while (0);
+    cudaFreeAsync(buf, st);
+    return s;
+}
+
+extern "C" crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
+                                              int32_t H, const float *cent, uint16_t *cells, void *stream) {
+    CRISP_REQUIRE(cells, "crisp_assign_cells_tc: null pointer");
+    return crisp_tc_assign(Xr, N, D, Dp, M, K, H, cent, cells, nullptr, as_stream(stream));
+}

@@ -106,3 +106,44 @@ def test_submit_validates_and_wait_times_out(served):
     with pytest.raises(crisp.CrispError):
         crisp.crisp_server_wait(sv, t, 5, timeout_ms=10)        # consumed ticket
     sv.free()
+
+
+def test_replay_open_loop_matches_alone(served):
+    """A Poisson trace (20k requests/s offered) of mixed k and modes through the
+    native replay: every result equals the query searched alone, latencies are
+    finite and counted from the scheduled arrivals."""
+    X, Q, ix = served
+    n = 400
+    r = np.random.default_rng(3)
+    arrival = np.cumsum(r.exponential(1e6 / 20000.0, n))
+    params = [_params(i) for i in range(15)]
+    pidx = r.integers(0, 15, n).astype(np.int32)
+    qidx = r.integers(0, Q.shape[0], n).astype(np.int32)
+    sv = crisp.crisp_server_create(ix, streams=4, max_batch=64)
+    ids, d2, lat, wall = crisp.crisp_server_replay(sv, Q, qidx, params, pidx, arrival, 100)
+    st = crisp.crisp_server_get_stats(sv)
+    sv.free()
+    assert st.completed == n and st.failed == 0
+    assert np.all(np.isfinite(lat)) and np.all(lat > 0) and wall >= arrival[-1]
+    for i in range(0, n, 7):
+        p = params[pidx[i]]
+        a_ids, a_d2 = _alone(ix, Q[qidx[i]], p)
+        assert np.array_equal(ids[i, :p.k], a_ids) and np.array_equal(d2[i, :p.k], a_d2), i
+        assert np.all(ids[i, p.k:] == -1)
+
+
+def test_replay_rejects_bad_traces(served):
+    X, Q, ix = served
+    sv = crisp.crisp_server_create(ix, streams=1, max_batch=4)
+    p = [crisp.search_params(k=10, rho=0.02, alpha=0.25)]
+    with pytest.raises(crisp.CrispError):          # unsorted arrivals
+        crisp.crisp_server_replay(sv, Q, [0, 1], p, [0, 0], [5.0, 1.0], 10)
+    with pytest.raises(crisp.CrispError):          # query index out of range
+        crisp.crisp_server_replay(sv, Q, [Q.shape[0]], p, [0], [0.0], 10)
+    with pytest.raises(crisp.CrispError):          # k > kmax
+        crisp.crisp_server_replay(sv, Q, [0], p, [0], [0.0], 5)
+    with pytest.raises(crisp.CrispError):          # parameter index out of range
+        crisp.crisp_server_replay(sv, Q, [0], p, [1], [0.0], 10)
+    st = crisp.crisp_server_get_stats(sv)
+    sv.free()
+    assert st.submitted == 0
