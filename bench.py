@@ -496,7 +496,7 @@ def learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed
             "val_recall_plain": r_plain, "val_recall_learned": best[2]}
 
 
-SERVE_WORKLOAD = ("serving: powerlaw N=5,000,000 D=1024 (lambda_i = i^-1.2, Haar mix), M=8; open-loop Poisson "
+SERVE_WORKLOAD = ("serving: powerlaw N=5,000,000 D=1024 (lambda_i = i^-1.2, Haar mix), M=32; open-loop Poisson "
                   "arrivals; k in {1, 10, 100} uniform; mode Guaranteed : Optimized : Learned = 1 : 2 : 2")
 
 
@@ -537,7 +537,7 @@ def serving_leg(args, torch, crisp, synthetic, dev):
 
     # coverage / threshold: the cheapest rung of the ladder whose Guaranteed recall@10 reaches 0.955
     rho, alpha = 0.03, 0.3
-    for r_, a_ in ((0.002, 0.25), (0.004, 0.25), (0.006, 0.25), (0.01, 0.25), (0.015, 0.3), (0.02, 0.3)):
+    for r_, a_ in ((0.01, 0.2), (0.015, 0.2), (0.02, 0.2), (0.025, 0.25), (0.03, 0.25)):
         if val(crisp.search_params(k=k10, mode=0, rho=r_, alpha=a_)) >= 0.955:
             rho, alpha = r_, a_
             break
@@ -733,7 +733,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
     ap.add_argument("--serve-n", type=int, default=5_000_000)
     ap.add_argument("--serve-dim", type=int, default=1024)
-    ap.add_argument("--serve-M", type=int, default=8)
+    ap.add_argument("--serve-M", type=int, default=32)
     ap.add_argument("--serve-pool", type=int, default=4096, help="distinct queries the requests draw from")
     ap.add_argument("--serve-train", type=int, default=20000)
     ap.add_argument("--serve-streams", type=int, default=4)

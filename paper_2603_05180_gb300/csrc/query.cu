@@ -1,12 +1,18 @@
 // Query-side kernels of the CRISP engine (Algorithm 1, §4.3) for sm_103a.
 //
-//   k_rotate      Q1 / B2  y = x R, FP32, each output an fmaf chain over d in order
-//   k_activate    Q2 + Q3  half distances, sorted lists, multi-sequence cell walk
-//   k_count_cut   Q4 + Q5  collision counting in shared-memory id tiles + threshold cut
-//   k_rerank      Q6       exact CR32 distances of the candidates, radix select + bitonic top-k
+//   k_rotate        Q1       y = x R, FP32, each output an fmaf chain over d in order
+//   k_activate      Q2 + Q3  half distances, sorted lists, multi-sequence cell walk
+//   k_count_cut     Q4 + Q5  collision counting in shared-memory id tiles + threshold cut
+//   k_dist_flat     Q6       exact CR32 distances of all (query, candidate) pairs, persistent
+//   k_select_rows   Q6       per query: radix select + bitonic top-k of those distances
+//   k_score_flat    F2       BF16 / FP8 E4M3 coarse CR32 scores, persistent
+//   k_short_select  F2       per query: the shortlist of the best coarse scores
 #include <float.h>
 #include <limits.h>
 #include <math.h>
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "internal.cuh"
 
@@ -281,10 +287,11 @@ struct CountShared {
     long long w_eqbase[CNT_NT / 32], w_outbase[CNT_NT / 32];
     long long tile_sel, tile_eq;
     int sel_s, sel_need;
-    // one batch of activated cells staged for one tile
-    int e_beg[CNT_NT];          // first position of the cell's ids inside the tile
-    int e_pre[CNT_NT + 1];      // exclusive prefix of the cells' id counts in the tile
-    int e_wm[CNT_NT];           // weight | subspace << 8
+    // one batch of activated cells staged for one tile; only the cells with ids
+    // in the tile are kept, so their flat starts strictly increase
+    int c_pre[CNT_NT + 33];     // flat start of each kept cell; then the total, then INT_MAX
+    int c_gd[CNT_NT + 1];       // id-array position of the cell's flat id 0: m N + first - c_pre
+    int c_w[CNT_NT + 1];        // the cell's weight (entry CNT_NT: read by lanes past the end, unused)
     long long scan_ws[CNT_NT / 32 + 1];
 };
 
@@ -292,19 +299,23 @@ constexpr int CNT_U = 4;   // flat ids per lane in flight
 
 // Count tile t of query q into the byte counters `cnt` (zeroed here): every id
 // of every activated cell that falls in the tile adds its cell's weight.  The
-// cells are staged 512 at a time with their id counts in the tile; the flat id
-// range is then cut into one contiguous piece per warp, lanes on consecutive
-// ids (coalesced loads), each lane finding its cell by a short forward scan.
+// cells are staged 512 at a time, keeping those with ids in the tile; the flat
+// id range is then cut into one contiguous piece per warp, lanes on consecutive
+// ids (coalesced loads).  A lane finds its cell from the cell starts inside its
+// warp's 32 ids: lane j marks bit (start of cell ecur+1+j) - first id, the OR of
+// the marks over the warp has one bit per start (starts are distinct), and a
+// lane's cell is ecur plus the marks at or below its own position.
 __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, CountShared &S, int E, int t,
                            uint32_t *cnt) {
     const int K2 = ix.K * ix.K, T = ix.T, M = ix.M;
     uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
     for (int i = threadIdx.x; i < CRISP_TILE / 16; i += CNT_NT) c4[i] = make_uint4(0, 0, 0, 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long tbase = (long long)t << CRISP_TILE_LOG2;
+    const int tbase = t << CRISP_TILE_LOG2;
+    const unsigned upto = 0xFFFFFFFFu >> (31 - lane);    // bits 0..lane
     for (int e0 = 0; e0 < E; e0 += CNT_NT) {
         const int ne = E - e0 < CNT_NT ? E - e0 : CNT_NT;
-        int beg = 0, len = 0, wm = 0;
+        int beg = 0, len = 0, w = 0, m = 0;
         const int i = threadIdx.x;
         if (i < ne) {
             const int e = e0 + i;
@@ -314,54 +325,52 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
                 if (S.base[mid] <= e) lo = mid;
                 else hi = mid - 1;
             }
-            const int m = lo;
+            m = lo;
             const int ent = actq[(long long)m * K2 + (e - S.base[m])];
             const int *to = ix.tile_off + ((long long)m * K2 + (ent & 0xFFFF)) * (T + 1) + t;
             beg = to[0];
             len = to[1] - beg;
-            wm = (ent >> 16) | (m << 8);
+            w = ent >> 16;
         }
+        // one scan: id counts in the high word, kept-cell flags in the low word
         long long tot;
-        const long long ex = block_excl_scan<CNT_NT>(len, S.scan_ws, &tot);
-        if (i < ne) {
-            S.e_beg[i] = beg;
-            S.e_pre[i] = (int)ex;
-            S.e_wm[i] = wm;
+        const long long ex = block_excl_scan<CNT_NT>(((long long)len << 32) | (len > 0 ? 1 : 0), S.scan_ws, &tot);
+        const int total = (int)(tot >> 32), nne = (int)(tot & 0xFFFFFFFF);
+        if (len > 0) {
+            const int ci = (int)(ex & 0xFFFFFFFF), pre = (int)(ex >> 32);
+            S.c_pre[ci] = pre;
+            S.c_gd[ci] = m * (int)ix.N + beg - pre;
+            S.c_w[ci] = w;
         }
-        if (i == 0) S.e_pre[ne] = (int)tot;
+        if (i <= 32) S.c_pre[nne + i] = i == 0 ? total : INT_MAX;
         __syncthreads();
-        const int total = (int)tot;
         const int per = (total + CNT_NT / 32 - 1) / (CNT_NT / 32);
         const int f_lo = warp * per, f_hi = f_lo + per < total ? f_lo + per : total;
         if (f_lo < f_hi) {
-            // the cell holding flat id f_lo
-            int lo = 0, hi = ne - 1;
+            // the kept cell holding flat id f_lo
+            int lo = 0, hi = nne - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (S.e_pre[mid] <= f_lo) lo = mid;
+                if (S.c_pre[mid] <= f_lo) lo = mid;
                 else hi = mid - 1;
             }
             int ecur = lo;
             for (int fb = f_lo; fb < f_hi; fb += 32 * CNT_U) {
                 int ids_v[CNT_U], wv[CNT_U];
-                bool act[CNT_U];
 #pragma unroll
                 for (int u = 0; u < CNT_U; ++u) {
-                    const int f = fb + 32 * u + lane;
-                    act[u] = f < f_hi;
-                    const int fc = act[u] ? f : f_hi - 1;
-                    int e = ecur;
-                    while (fc >= S.e_pre[e + 1]) ++e;
-                    const int w = S.e_wm[e];
-                    wv[u] = w & 0xFF;
-                    const int p = S.e_beg[e] + (fc - S.e_pre[e]);
-                    ids_v[u] = act[u] ? __ldg(ix.ids + (long long)(w >> 8) * ix.N + p) : 0;
+                    const int f0 = fb + 32 * u, f = f0 + lane;
+                    const int B = S.c_pre[ecur + 1 + lane] - f0;     // > 0: cell ecur holds f0
+                    const unsigned marks = __reduce_or_sync(0xffffffffu, (unsigned)B < 32u ? 1u << B : 0u);
+                    const int e = ecur + __popc(marks & upto);
+                    wv[u] = S.c_w[e];
+                    ids_v[u] = f < f_hi ? __ldg(ix.ids + (S.c_gd[e] + f)) : -1;
                     ecur = __shfl_sync(0xffffffffu, e, 31);
                 }
 #pragma unroll
                 for (int u = 0; u < CNT_U; ++u) {
-                    if (act[u]) {
-                        const int local = (int)((long long)ids_v[u] - tbase);
+                    if (ids_v[u] >= 0) {
+                        const int local = ids_v[u] - tbase;
                         atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << ((local & 3) * 8));
                     }
                 }
@@ -740,177 +749,6 @@ __device__ int select_topk(const float *distq, const int *candq, long long n, in
     return nsel;
 }
 
-__global__ void __launch_bounds__(RR_NT) k_rerank(IxView ix, const float *__restrict__ Qr, int nq,
-                                                  const int *__restrict__ cand, long long stride,
-                                                  const long long *__restrict__ ncand, int kk, float *__restrict__ dbuf,
-                                                  long long *__restrict__ out_ids, float *__restrict__ out_d) {
-    extern __shared__ __align__(16) float qs[];
-    __shared__ TopkShared S;
-    const int q = blockIdx.x;
-    const int Dp = ix.Dp, nb = Dp / 32;
-    long long n = ncand[q];
-    if (n > stride) n = stride;
-    for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, l = threadIdx.x & 7;
-    const unsigned gmask = 0xFFu << (lane & 24);
-    const int *candq = cand + (long long)q * stride;
-    float *distq = dbuf + (long long)q * stride;
-    for (long long i = g; i < n; i += RR_NT / 8) {
-        const float4 *row = reinterpret_cast<const float4 *>(ix.Xr + (long long)candq[i] * Dp) + l;
-        float acc = 0.0f;
-        for (int b0 = 0; b0 < nb; b0 += RR_U) {
-            float4 v[RR_U];
-#pragma unroll
-            for (int u = 0; u < RR_U; ++u)
-                if (b0 + u < nb) v[u] = __ldcs(row + 8 * (b0 + u));
-#pragma unroll
-            for (int u = 0; u < RR_U; ++u) {
-                if (b0 + u < nb) {
-                    float4 qv = *reinterpret_cast<const float4 *>(qs + 32 * (b0 + u) + 4 * l);
-                    acc = acc + cr32_block(v[u], qv, gmask);
-                }
-            }
-        }
-        if (l == 0) distq[i] = acc;
-    }
-    __syncthreads();
-    int nsel = select_topk(distq, candq, n, kk, S);
-    for (int r = threadIdx.x; r < kk; r += RR_NT) {
-        bool ok = r < nsel;
-        out_ids[(long long)q * kk + r] = ok ? (long long)S.sid[r] : -1LL;
-        out_d[(long long)q * kk + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
-    }
-}
-
-// ============================================== F2 coarse scoring + shortlist
-// FP8 E4M3 code -> FP32, exact (no infinities; 0x7F/0xFF never produced).
-__device__ __forceinline__ float e4m3_to_f32(unsigned c) {
-    unsigned e = (c >> 3) & 15u, m = c & 7u;
-    float v = e == 0 ? (float)m * 0.001953125f : __uint_as_float(((e + 120u) << 23) | (m << 20));
-    return (c & 0x80u) ? -v : v;
-}
-
-// CR32 distance of q to a BF16 row: an 8-lane group covers two 32-dim blocks
-// (16 B per lane); lane li of a quarter holds the CR32 partials 2li and 2li+1.
-__device__ __forceinline__ float cr32_row_bf16(const uint4 *row, const float *qs, int nb, int gl, int base, unsigned gmask) {
-    const int half = gl >> 2, li = gl & 3;
-    float acc = 0.0f;
-    for (int j = 0; 2 * j < nb; ++j) {
-        const int b = 2 * j + half;
-        float e = 0.0f, o = 0.0f;
-        if (b < nb) {
-            uint4 v = __ldcs(row + 8 * j + gl);
-            const float *qv = qs + 32 * b + 8 * li;
-            unsigned w[4] = {v.x, v.y, v.z, v.w};
-            float x[8];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                x[2 * u] = __uint_as_float(w[u] << 16);
-                x[2 * u + 1] = __uint_as_float(w[u] & 0xFFFF0000u);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                float d = x[t] - qv[t];
-                e = fmaf(d, d, e);
-            }
-#pragma unroll
-            for (int t = 4; t < 8; ++t) {
-                float d = x[t] - qv[t];
-                o = fmaf(d, d, o);
-            }
-        }
-        e = e + __shfl_xor_sync(gmask, e, 2);
-        o = o + __shfl_xor_sync(gmask, o, 2);
-        e = e + __shfl_xor_sync(gmask, e, 1);
-        o = o + __shfl_xor_sync(gmask, o, 1);
-        float s = e + o;
-        float slo = __shfl_sync(gmask, s, base);
-        float shi = __shfl_sync(gmask, s, base + 4);
-        acc = acc + slo;
-        if (2 * j + 1 < nb) acc = acc + shi;
-    }
-    return acc;
-}
-
-// CR32 distance of q to an FP8 row times its scale: an 8-lane group covers four
-// 32-dim blocks (16 codes per lane); the lane pair of a block holds partials 0-3 / 4-7.
-__device__ __forceinline__ float cr32_row_e4m3(const uint4 *row, float sc, const float *qs, int nb, int gl, int base,
-                                               unsigned gmask) {
-    const int h = gl & 1;
-    float acc = 0.0f;
-    for (int j = 0; 4 * j < nb; ++j) {
-        const int b = 4 * j + (gl >> 1);
-        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (b < nb) {
-            uint4 v = __ldcs(row + 8 * j + gl);
-            const float *qv = qs + 32 * b + 16 * h;
-            unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    float x = e4m3_to_f32((w[u] >> (8 * t)) & 0xFFu) * sc;
-                    float d = x - qv[4 * u + t];
-                    a[u] = fmaf(d, d, a[u]);
-                }
-        }
-        float t0 = a[0] + __shfl_xor_sync(gmask, a[0], 1);
-        float t1 = a[1] + __shfl_xor_sync(gmask, a[1], 1);
-        float t2 = a[2] + __shfl_xor_sync(gmask, a[2], 1);
-        float t3 = a[3] + __shfl_xor_sync(gmask, a[3], 1);
-        float s = (t0 + t2) + (t1 + t3);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            float sr = __shfl_sync(gmask, s, base + 2 * r);
-            if (4 * j + r < nb) acc = acc + sr;
-        }
-    }
-    return acc;
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(RR_NT) k_shortlist(IxView ix, const float *__restrict__ Qr, int nq,
-                                                     const int *__restrict__ cand, long long stride,
-                                                     const long long *__restrict__ ncand, int S_keep,
-                                                     float *__restrict__ dbuf, int *__restrict__ out,
-                                                     long long out_stride, long long *__restrict__ nout,
-                                                     const long long *__restrict__ S_per_query) {
-    extern __shared__ __align__(16) float qs[];
-    __shared__ TopkShared S;
-    const int q = blockIdx.x;
-    const int Dp = ix.Dp, nb = Dp / 32;
-    long long n = ncand[q];
-    if (n > stride) n = stride;
-    for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, gl = threadIdx.x & 7, base = lane & 24;
-    const unsigned gmask = 0xFFu << base;
-    const int *candq = cand + (long long)q * stride;
-    float *distq = dbuf + (long long)q * stride;
-    for (long long i = g; i < n; i += RR_NT / 8) {
-        const long long id = candq[i];
-        float acc;
-        if (PREC == 1) acc = cr32_row_bf16(reinterpret_cast<const uint4 *>(ix.Xb + id * Dp), qs, nb, gl, base, gmask);
-        else acc = cr32_row_e4m3(reinterpret_cast<const uint4 *>(ix.X8 + id * Dp), ix.S8[id], qs, nb, gl, base, gmask);
-        if (gl == 0) distq[i] = acc;
-    }
-    __syncthreads();
-    int *outq = out + (long long)q * out_stride;
-    long long kept;
-    if (S_per_query) S_keep = (int)(S_per_query[q] < out_stride ? S_per_query[q] : out_stride);
-    if (n <= S_keep) {
-        for (long long i = threadIdx.x; i < n; i += RR_NT) outq[i] = candq[i];
-        kept = n;
-    } else {
-        unsigned prefix;
-        int need;
-        radix_kth(distq, n, S_keep, S, &prefix, &need);
-        kept = collect_ordered(distq, n, prefix, need, S, [&](long long slot, long long i) { outq[slot] = candq[i]; });
-    }
-    if (threadIdx.x == 0) nout[q] = kept;
-}
-
 // ------------------------------------------------ re-rank, streaming form
 // Work items are (query, chunk of RF_CH candidates); item offsets per query
 // come from a scan, and a persistent grid walks the items.  The distances go
@@ -986,6 +824,196 @@ __global__ void __launch_bounds__(RR_NT, 5) k_dist_flat(IxView ix, const float *
         }
         __syncthreads();
     }
+}
+
+// Coarse scores of every (query, candidate) pair, streaming form of the F2
+// scorers: the same persistent walk over (query, chunk) items as k_dist_flat,
+// rows read with several 16-byte loads in flight per lane.  The arithmetic is
+// the CR32 order of cr32_row_bf16 / cr32_row_e4m3 (lane partials, xor tree,
+// blocks in order), so the scores are the same bits.
+constexpr int SB_U = 8;    // BF16: 16-byte loads in flight per lane (2 blocks per group each)
+constexpr int SE_U = 4;    // E4M3: 16-byte loads in flight per lane (4 blocks per group each)
+
+__device__ __forceinline__ float cr32_row_bf16_stream(const uint4 *row, const float *qs, int nb, int gl, int base,
+                                                      unsigned gmask) {
+    const int half = gl >> 2, li = gl & 3;
+    const int nj = (nb + 1) >> 1;
+    float acc = 0.0f;
+    for (int j0 = 0; j0 < nj; j0 += SB_U) {
+        uint4 v[SB_U];
+#pragma unroll
+        for (int u = 0; u < SB_U; ++u) {
+            const int j = j0 + u;
+            if (j < nj && 2 * j + half < nb) v[u] = __ldcs(row + 8 * j + gl);
+            else v[u] = make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < SB_U; ++u) {
+            const int j = j0 + u;
+            if (j >= nj) break;                 // uniform over the group
+            const int b = 2 * j + half;
+            float e = 0.0f, o = 0.0f;
+            if (b < nb) {
+                const float *qv = qs + 32 * b + 8 * li;
+                const unsigned w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    float d = __uint_as_float(w[t] << 16) - qv[2 * t];
+                    e = fmaf(d, d, e);
+                    d = __uint_as_float(w[t] & 0xFFFF0000u) - qv[2 * t + 1];
+                    e = fmaf(d, d, e);
+                }
+#pragma unroll
+                for (int t = 2; t < 4; ++t) {
+                    float d = __uint_as_float(w[t] << 16) - qv[2 * t];
+                    o = fmaf(d, d, o);
+                    d = __uint_as_float(w[t] & 0xFFFF0000u) - qv[2 * t + 1];
+                    o = fmaf(d, d, o);
+                }
+            }
+            e = e + __shfl_xor_sync(gmask, e, 2);
+            o = o + __shfl_xor_sync(gmask, o, 2);
+            e = e + __shfl_xor_sync(gmask, e, 1);
+            o = o + __shfl_xor_sync(gmask, o, 1);
+            const float sm = e + o;
+            const float slo = __shfl_sync(gmask, sm, base);
+            const float shi = __shfl_sync(gmask, sm, base + 4);
+            acc = acc + slo;
+            if (2 * j + 1 < nb) acc = acc + shi;
+        }
+    }
+    return acc;
+}
+
+// two E4M3 codes (low half of c) -> two FP32 values, exactly (E4M3 values are FP16 values)
+__device__ __forceinline__ float2 e4m3x2_to_f32(unsigned c) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(c & 0xFFFFu), __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+
+__device__ __forceinline__ float cr32_row_e4m3_stream(const uint4 *row, float sc, const float *qs, int nb, int gl,
+                                                      int base, unsigned gmask) {
+    const int h = gl & 1;
+    const int nj = (nb + 3) >> 2;
+    float acc = 0.0f;
+    for (int j0 = 0; j0 < nj; j0 += SE_U) {
+        uint4 v[SE_U];
+#pragma unroll
+        for (int u = 0; u < SE_U; ++u) {
+            const int j = j0 + u;
+            if (j < nj && 4 * j + (gl >> 1) < nb) v[u] = __ldcs(row + 8 * j + gl);
+            else v[u] = make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < SE_U; ++u) {
+            const int j = j0 + u;
+            if (j >= nj) break;                 // uniform over the group
+            const int b = 4 * j + (gl >> 1);
+            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (b < nb) {
+                const float *qv = qs + 32 * b + 16 * h;
+                const unsigned w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float2 x01 = e4m3x2_to_f32(w[t]), x23 = e4m3x2_to_f32(w[t] >> 16);
+                    float d = x01.x * sc - qv[4 * t];
+                    a[t] = fmaf(d, d, a[t]);
+                    d = x01.y * sc - qv[4 * t + 1];
+                    a[t] = fmaf(d, d, a[t]);
+                    d = x23.x * sc - qv[4 * t + 2];
+                    a[t] = fmaf(d, d, a[t]);
+                    d = x23.y * sc - qv[4 * t + 3];
+                    a[t] = fmaf(d, d, a[t]);
+                }
+            }
+            const float t0 = a[0] + __shfl_xor_sync(gmask, a[0], 1);
+            const float t1 = a[1] + __shfl_xor_sync(gmask, a[1], 1);
+            const float t2 = a[2] + __shfl_xor_sync(gmask, a[2], 1);
+            const float t3 = a[3] + __shfl_xor_sync(gmask, a[3], 1);
+            const float sm = (t0 + t2) + (t1 + t3);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float sr = __shfl_sync(gmask, sm, base + 2 * r);
+                if (4 * j + r < nb) acc = acc + sr;
+            }
+        }
+    }
+    return acc;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float *__restrict__ Qr, int nq,
+                                                         const int *__restrict__ cand, long long stride,
+                                                         const long long *__restrict__ ncand,
+                                                         const long long *__restrict__ off, float *__restrict__ dbuf) {
+    extern __shared__ __align__(16) float qs[];
+    __shared__ int s_q;
+    const int Dp = ix.Dp, nb = Dp / 32;
+    const long long total = off[nq];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, gl = threadIdx.x & 7, base = lane & 24;
+    const unsigned gmask = 0xFFu << base;
+    int cur_q = -1;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nq - 1;             // query q with off[q] <= w < off[q+1]
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            s_q = lo;
+        }
+        __syncthreads();
+        const int q = s_q;
+        if (q != cur_q) {
+            for (int d = threadIdx.x; d < Dp; d += RR_NT) qs[d] = Qr[(long long)q * Dp + d];
+            cur_q = q;
+        }
+        __syncthreads();
+        const long long n = ncand[q] < stride ? ncand[q] : stride;
+        const long long c0 = (w - off[q]) * RF_CH;
+        const long long c1 = c0 + RF_CH < n ? c0 + RF_CH : n;
+        const int *candq = cand + (long long)q * stride;
+        float *distq = dbuf + (long long)q * stride;
+        for (long long i = c0 + g; i < c1; i += RR_NT / 8) {
+            const long long id = candq[i];
+            float acc;
+            if (PREC == 1)
+                acc = cr32_row_bf16_stream(reinterpret_cast<const uint4 *>(ix.Xb + id * Dp), qs, nb, gl, base, gmask);
+            else
+                acc = cr32_row_e4m3_stream(reinterpret_cast<const uint4 *>(ix.X8 + id * Dp), ix.S8[id], qs, nb, gl,
+                                           base, gmask);
+            if (gl == 0) distq[i] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// The S_keep best (score, list position) of each query's scored candidates, in
+// list (ascending id) order: the shortlist for the FP32 re-rank.
+__global__ void __launch_bounds__(RR_NT) k_short_select(int nq, const int *__restrict__ cand, long long stride,
+                                                        const long long *__restrict__ ncand, int S_keep,
+                                                        const float *__restrict__ dbuf, int *__restrict__ out,
+                                                        long long out_stride, long long *__restrict__ nout,
+                                                        const long long *__restrict__ S_per_query) {
+    __shared__ TopkShared S;
+    const int q = blockIdx.x;
+    const long long n = ncand[q] < stride ? ncand[q] : stride;
+    const int *candq = cand + (long long)q * stride;
+    const float *distq = dbuf + (long long)q * stride;
+    int *outq = out + (long long)q * out_stride;
+    if (S_per_query) S_keep = (int)(S_per_query[q] < out_stride ? S_per_query[q] : out_stride);
+    long long kept;
+    if (n <= S_keep) {
+        for (long long i = threadIdx.x; i < n; i += RR_NT) outq[i] = candq[i];
+        kept = n;
+    } else {
+        unsigned prefix;
+        int need;
+        radix_kth(distq, n, S_keep, S, &prefix, &need);
+        kept = collect_ordered(distq, n, prefix, need, S, [&](long long slot, long long i) { outq[slot] = candq[i]; });
+    }
+    if (threadIdx.x == 0) nout[q] = kept;
 }
 
 __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__restrict__ cand, long long stride,
@@ -1086,6 +1114,7 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
                                  int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t stride, int64_t *ncand,
                                  uint8_t *score, int32_t *how, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
+    CRISP_REQUIRE((int64_t)ix->M * ix->N < ((int64_t)1 << 31), "count: M * N must stay below 2^31");
     size_t smem = CRISP_TILE;
     CRISP_CK(cudaFuncSetAttribute(k_count_cut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_count_cut<<<nq, CNT_NT, smem, st>>>(ix_view(ix), act, nact, nq, tau, k, (long long)cap, cand,
@@ -1129,21 +1158,31 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
                                  const int64_t *S_per_query) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
+    long long *off = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
+    k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
+    CRISP_COUNT_LAUNCH();
+    int dev = 0, sms = 152, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (precision == 1) {
         if (smem > 48 * 1024)
-            CRISP_CK(cudaFuncSetAttribute(k_shortlist<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_shortlist<1><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
-                                                 S, dbuf, out, (long long)out_stride, (long long *)nout,
-                                                 (const long long *)S_per_query);
-        CRISP_COUNT_LAUNCH();
+            CRISP_CK(cudaFuncSetAttribute(k_score_flat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_flat<1>, RR_NT, smem);
+        k_score_flat<1><<<sms * (per_sm > 0 ? per_sm : 4), RR_NT, smem, st>>>(
+            ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, off, dbuf);
     } else {
         if (smem > 48 * 1024)
-            CRISP_CK(cudaFuncSetAttribute(k_shortlist<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_shortlist<2><<<nq, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand,
-                                                 S, dbuf, out, (long long)out_stride, (long long *)nout,
-                                                 (const long long *)S_per_query);
-        CRISP_COUNT_LAUNCH();
+            CRISP_CK(cudaFuncSetAttribute(k_score_flat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_flat<2>, RR_NT, smem);
+        k_score_flat<2><<<sms * (per_sm > 0 ? per_sm : 4), RR_NT, smem, st>>>(
+            ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, off, dbuf);
     }
+    CRISP_COUNT_LAUNCH();
+    k_short_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, S, dbuf, out,
+                                         (long long)out_stride, (long long *)nout, (const long long *)S_per_query);
+    CRISP_COUNT_LAUNCH();
+    crisp_scratch_free(off, st);
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
