@@ -338,6 +338,7 @@ def run_crisp(args):
 
     # ---- stage-timed pass through the step entry points (same kernels, same launch shapes)
     stage = stage_pass(torch, crisp, ix, info, Q, point, k, args.steps, stream, flush)
+    sl_stage = stage.pop("shortlist_bf16", None)
     shares = {n: v["ms"] for n, v in stage.items()}
     dom = max((n for n in stage if stage[n]["bytes"]), key=lambda n: stage[n]["ms"])
     dbytes, dms = stage[dom]["bytes"], stage[dom]["ms"]
@@ -349,6 +350,14 @@ def run_crisp(args):
                 "stage_ms": {n: round(v, 4) for n, v in shares.items()},
                 "algorithmic_bytes_per_launch": dbytes}
     step_bytes = sum(v["bytes"] for v in stage.values())
+    roofline_bf16 = None
+    if sl_stage:
+        a_bf = sl_stage["bytes"] / (sl_stage["ms"] / 1e3) / 1e9
+        roofline_bf16 = {"kernel": sl_stage["kernel"], "bound": "hbm", "achieved": a_bf, "peak": peak, "unit": "GB/s",
+                         "frac": a_bf / peak, "traffic": _ncu_traffic("shortlist_bf16"),
+                         "ms": round(sl_stage["ms"], 4), "algorithmic_bytes_per_launch": sl_stage["bytes"],
+                         "note": "BF16 coarse scoring of the same candidates (the learned+BF16 path's dominant "
+                                 "kernel), shortlist of 50, timed on its own"}
 
     # ---- coarse-scoring variants (BF16 / FP8 rows, FP32 re-rank of a shortlist)
     variants = {}
@@ -418,7 +427,7 @@ def run_crisp(args):
                 "step_p50_ms": statistics.median(step_ms), "step_p99_ms": float(np.percentile(step_ms, 99)),
                 "hbm_frac_step": step_bytes / (total_ms / args.steps / 1e3) / 1e9 / peak,
                 "candidates_mean": float(stats[:, 0].mean()), "full_distances_mean": float(stats[:, 2].mean()),
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "roofline_bf16": roofline_bf16, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
                         "d2h_bytes_per_step": nq * k * 12},
                 "gpu_launches": launches, "clocks": clk,
@@ -645,6 +654,12 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     nb = torch.empty((nq,), dtype=torch.int64, device=dev)
     names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
     kernels = ["k_rotate", "k_activate", "k_count_cut", "k_dist_flat" if point["mode"] == 0 else "k_verify_opt"]
+    bf16 = bool(info.Xb) and point["mode"] == 0
+    if bf16:            # the F2 coarse-scoring kernel on the same candidates (timed on its own)
+        names.append("shortlist_bf16")
+        kernels.append("k_score_flat<BF16>")
+        sl = torch.empty((nq, 64), dtype=torch.int32, device=dev)
+        nsl = torch.empty((nq,), dtype=torch.int64, device=dev)
     acc = {n: 0.0 for n in names}
 
     def one():
@@ -663,10 +678,13 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
         else:
             crisp.crisp_verify_opt(ix, Qr, nq, cand, stride, ncand, k, 2.1, 40 * k, ids, d2, nv, nf, nb, stream)
         yield
+        if bf16:
+            crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 1, 50, sl, 64, nsl, stream)
+            yield
 
     for s in range(steps + 1):
         flush.zero_()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         evs[0].record(stream)
         for i, _ in enumerate(one()):
             evs[i + 1].record(stream)
@@ -692,6 +710,9 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
         blocks = float(nb.sum().item())
         out["verify_opt"] = {"ms": acc["verify_opt"], "bytes": C * (4 * W + 4) + 128 * blocks,
                              "kernel": "k_verify_opt"}
+    if bf16:
+        # every candidate's BF16 row (2 Dp bytes) + its id; the shortlist written is small
+        out["shortlist_bf16"] = {"ms": acc["shortlist_bf16"], "bytes": C * (2 * Dp + 4)}
     for n, kn in zip(names, kernels):
         out[n]["kernel"] = kn
     return out
