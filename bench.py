@@ -140,6 +140,22 @@ def recall_at_k(torch, X, Q, ids, gdk, rel=1e-5):
     return hits / (ids.shape[0] * ids.shape[1])
 
 
+def d2_error(torch, X, Q, ids, d2):
+    """Relative error of the returned FP32 squared distances against FP64
+    distances recomputed from the original (unrotated) rows."""
+    mx, tot, n = 0.0, 0.0, 0
+    for s in range(0, ids.shape[0], 2000):
+        i = ids[s:s + 2000]
+        ok = i >= 0
+        ex = ((X[i.clamp(min=0)].double() - Q[s:s + 2000].double()[:, None, :]) ** 2).sum(-1)
+        rel = ((d2[s:s + 2000].double() - ex).abs() / ex.clamp(min=1e-30))[ok]
+        if rel.numel():
+            mx = max(mx, float(rel.max()))
+            tot += float(rel.sum())
+            n += rel.numel()
+    return {"max_rel": mx, "mean_rel": tot / max(n, 1), "vs": "FP64 distances of the returned ids, original rows"}
+
+
 def make_workload(args, device):
     import synthetic
 
@@ -333,6 +349,7 @@ def run_crisp(args):
         total_ms = float(tt.item())
     rec = recall_at_k(torch, X, Q, ids, gdk)
     rec_sub = recall_at_k(torch, X, Q[:2000], ids[:2000], gdk[:2000])
+    d2_err = d2_error(torch, X, Q, ids, d2)
     stats = st.cpu().numpy()
     qps = world * nq * args.steps / (total_ms / 1e3)
 
@@ -423,7 +440,7 @@ def run_crisp(args):
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed before every timed step (512 MB write, outside the timed events)",
                            "index_rotated": bool(info.rotated), "cev": info.cev, "build_s": round(build_s, 3)},
-                "recall_at_10": rec,
+                "recall_at_10": rec, "sqdist_error": d2_err,
                 "step_p50_ms": statistics.median(step_ms), "step_p99_ms": float(np.percentile(step_ms, 99)),
                 "hbm_frac_step": step_bytes / (total_ms / args.steps / 1e3) / 1e9 / peak,
                 "candidates_mean": float(stats[:, 0].mean()), "full_distances_mean": float(stats[:, 2].mean()),

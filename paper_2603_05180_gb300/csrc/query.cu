@@ -397,6 +397,13 @@ __device__ __forceinline__ unsigned gt_mask(unsigned w, int s) {
     }
     return __vcmpgtu4(w, (unsigned)s * 0x01010101u);
 }
+// Bit 7 of each byte of w set where that byte is > s (the other bits clear).
+__device__ __forceinline__ unsigned gt_bits(unsigned w, int s) {
+    if (s < 0) return 0x80808080u;
+    if (s > 254) return 0u;
+    if (s <= 127) return (((w & 0x7F7F7F7Fu) + (unsigned)(127 - s) * 0x01010101u) | w) & 0x80808080u;
+    return __vcmpgtu4(w, (unsigned)s * 0x01010101u) & 0x80808080u;
+}
 __device__ __forceinline__ unsigned eq_mask(unsigned w, int s) {
     if (s < 0 || s > 255) return 0u;
     return __vcmpeq4(w, (unsigned)s * 0x01010101u);
@@ -417,8 +424,88 @@ constexpr int CNT_ROUNDS = CNT_WARP_BYTES / 512;             // 16 bytes per lan
 // start of the query (*eq_seen holds how many came before this tile).  Each
 // warp owns a contiguous 4 KB of counters, read 512 B per round without bank
 // conflicts.  Returns the number emitted (block-uniform).
+// Fast form of emit_tile for need_eq == 0 (only v > s_hi selected): count per
+// warp, then each warp re-reads the rounds that hold selections and writes
+// each lane's selected ids by walking the set bits of its masks.
+__device__ long long emit_tile_gt(const IxView &ix, CountShared &S, const uint32_t *cnt, int t, int s_hi,
+                                  long long out_base, int *candq, uint8_t *scoreq, long long stride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long id0 = ((long long)t << CRISP_TILE_LOG2) + (long long)warp * CNT_WARP_BYTES;
+    long long lim = ix.N - id0;
+    const int vlim = lim <= 0 ? 0 : (lim >= CNT_WARP_BYTES ? CNT_WARP_BYTES : (int)lim);
+    const uint4 *wc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(cnt) + warp * CNT_WARP_BYTES);
+    int c_gt = 0;
+#pragma unroll 4
+    for (int r = 0; r < CNT_ROUNDS; ++r) {
+        const int b0 = r * 512 + lane * 16;
+        const uint4 v = wc[r * 32 + lane];
+        const unsigned ws[4] = {v.x, v.y, v.z, v.w};
+        if (b0 + 16 <= vlim) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c_gt += __popc(gt_bits(ws[u], s_hi));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c_gt += __popc(gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c_gt += __shfl_xor_sync(0xffffffffu, c_gt, o);
+    if (lane == 0) S.w_gt[warp] = c_gt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long outb = out_base;
+        for (int w = 0; w < CNT_NT / 32; ++w) {
+            S.w_outbase[w] = outb;
+            outb += S.w_gt[w];
+        }
+        S.tile_sel = outb - out_base;
+    }
+    __syncthreads();
+    const long long tot_sel = S.tile_sel;
+    if (S.w_gt[warp] > 0) {
+        long long pos_run = S.w_outbase[warp];
+        for (int r = 0; r < CNT_ROUNDS; ++r) {
+            const int b0 = r * 512 + lane * 16;
+            const uint4 v = wc[r * 32 + lane];
+            const unsigned ws[4] = {v.x, v.y, v.z, v.w};
+            unsigned gm[4];
+            int g_l = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                gm[u] = gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim);
+                g_l += __popc(gm[u]);
+            }
+            if (!__any_sync(0xffffffffu, g_l > 0)) continue;
+            int s_in = g_l;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s_in, o);
+                if (lane >= o) s_in += y;
+            }
+            long long pos = pos_run + (s_in - g_l);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                unsigned m = gm[u];
+                while (m) {
+                    const int bb = (__ffs(m) - 1) >> 3;     // byte of the lowest set bit 7 + 8 bb
+                    m &= m - 1;
+                    if (pos < stride) {
+                        candq[pos] = (int)(id0 + b0 + 4 * u + bb);
+                        if (scoreq) scoreq[pos] = (uint8_t)((ws[u] >> (8 * bb)) & 0xFFu);
+                    }
+                    ++pos;
+                }
+            }
+            pos_run += __shfl_sync(0xffffffffu, s_in, 31);
+        }
+    }
+    __syncthreads();
+    return tot_sel;
+}
+
 __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t *cnt, int t, int s_hi, long long need_eq,
                                long long *eq_seen, long long out_base, int *candq, uint8_t *scoreq, long long stride) {
+    if (need_eq <= 0) return emit_tile_gt(ix, S, cnt, t, s_hi, out_base, candq, scoreq, stride);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long id0 = ((long long)t << CRISP_TILE_LOG2) + (long long)warp * CNT_WARP_BYTES;
     long long lim = ix.N - id0;
@@ -834,6 +921,10 @@ __global__ void __launch_bounds__(RR_NT, 5) k_dist_flat(IxView ix, const float *
 constexpr int SB_U = 8;    // BF16: 16-byte loads in flight per lane (2 blocks per group each)
 constexpr int SE_U = 4;    // E4M3: 16-byte loads in flight per lane (4 blocks per group each)
 
+// CR32 distance of q to a BF16 row: an 8-lane group covers two 32-dim blocks
+// per 16-byte slice j (lanes 0-3 block 2j, lanes 4-7 block 2j+1; lane li holds
+// the CR32 lane partials 2li and 2li+1); SB_U slices are loaded before any is
+// summed.
 __device__ __forceinline__ float cr32_row_bf16_stream(const uint4 *row, const float *qs, int nb, int gl, int base,
                                                       unsigned gmask) {
     const int half = gl >> 2, li = gl & 3;
