@@ -38,7 +38,7 @@ def _flags(extra=()):
 def _stale(obj, src):
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "crisp.h")]
+    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "ptx.cuh"), os.path.join(INCLUDE, "crisp.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -15,6 +15,7 @@
 #include <cuda_fp8.h>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -1068,6 +1069,13 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
         float *distq = dbuf + (long long)q * stride;
         for (long long i = c0 + g; i < c1; i += RR_NT / 8) {
             const long long id = candq[i];
+            // the row this group scores next comes into L2 while this one is summed
+            const long long inext = i + RR_NT / 8;
+            if (gl == 0 && inext < c1) {
+                const long long idn = candq[inext];
+                if (PREC == 1) bulk_prefetch_l2(ix.Xb + idn * Dp, (uint32_t)Dp * 2);
+                else bulk_prefetch_l2(ix.X8 + idn * Dp, (uint32_t)Dp);
+            }
             float acc;
             if (PREC == 1)
                 acc = cr32_row_bf16_stream(reinterpret_cast<const uint4 *>(ix.Xb + id * Dp), qs, nb, gl, base, gmask);

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -30,55 +31,8 @@ constexpr int TC_BM = 128;      // output rows per tile = UMMA M
 constexpr int TC_BK = 32;       // floats per k-block: one 128-byte swizzle row
 constexpr int TC_NT = 128;      // four warps
 constexpr int TC_TMEM_COLS = 256;
-constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // 1 s per wait
 
 __device__ unsigned int g_tc_error;   // first failing wait: 1 + its site code
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase with the given parity to complete; false after TC_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = now_ns();
-    for (;;) {
-        if (mbar_test(bar, parity)) return true;
-        if (now_ns() - t0 > TC_WAIT_NS) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte
 // swizzled layout: 8-row groups of 128-byte rows, groups 1024 bytes apart.
@@ -439,24 +393,32 @@ __device__ __forceinline__ float asg_bound(float nx, float nx2, float c, float c
     return 6e-3f * nx * c + 1e-4f * (nx2 + c2);
 }
 
+// Dynamic shared memory: two 32 KB stages (X tile, left and right centroid
+// tiles), the subspace's centroids [2][K][HS], |c|^2 and |c| [2][64], barriers.
+__host__ __device__ constexpr uint32_t asg_stage_bytes() { return TC_BM * 128 + 2 * AS_KPAD * 128; }
+__host__ __device__ inline size_t asg_smem_bytes(int K, int HS) {
+    return 1024 + 2 * (size_t)asg_stage_bytes() + sizeof(float) * (2 * (size_t)K * HS + 4 * AS_KPAD) + 64;
+}
+
 __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUtensorMap tmX,
                                                      const __grid_constant__ CUtensorMap tmB, AsgArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
-    uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-    constexpr uint32_t A_BYTES = TC_BM * 128, B_BYTES = AS_KPAD * 128, STAGE = A_BYTES + 2 * B_BYTES;
-    uint64_t *bars = (uint64_t *)(sm + 2 * STAGE);     // full[2], empty[2], done
-    uint32_t *tmem_slot = (uint32_t *)(bars + 5);
-    int *abort_flag = (int *)(bars + 6);
-    const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]), done = smem_addr(&bars[4]);
-
+    uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzled tiles need 1024-byte alignment
+    constexpr uint32_t A_BYTES = TC_BM * 128, B_BYTES = AS_KPAD * 128, STAGE = asg_stage_bytes();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = (int)(blockIdx.x % (unsigned)a.M);
     const long long row0 = (long long)(blockIdx.x / (unsigned)a.M) * TC_BM;
     const int lo = (int)(((long long)m * a.D) / a.M), hi_ = (int)(((long long)(m + 1) * a.D) / a.M);
-    const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl;
+    const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl, HS = hr;     // hr >= hl
     const int base = lo & ~(TC_BK - 1);
     const int nk = (hi_ - base + TC_BK - 1) / TC_BK;
+    float *sC = (float *)(sm + 2 * STAGE);                             // [2][K][HS]
+    float *sN2 = sC + 2 * a.K * HS, *sN1 = sN2 + 2 * AS_KPAD;           // [2][64] each
+    uint64_t *bars = (uint64_t *)(sN1 + 2 * AS_KPAD);                  // full[2], empty[2], done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 5);
+    int *abort_flag = (int *)(bars + 6);
+    const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[2]), done = smem_addr(&bars[4]);
 
     if (tid == 0) {
         for (int i = 0; i < 5; ++i) mbar_init(smem_addr(&bars[i]), 1);
@@ -517,6 +479,16 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
         }
         mma_commit(done);
     }
+    // while the tiles load: the subspace's centroids and their norms into shared memory
+    for (int e = tid; e < 2 * a.K * HS; e += TC_NT) {
+        const int half = e / (a.K * HS), rem = e % (a.K * HS), c = rem / HS, d = rem % HS;
+        const int h = half ? hr : hl;
+        sC[e] = d < h ? a.cent[(((long long)m * 2 + half) * a.K + c) * a.H + d] : 0.0f;
+    }
+    for (int e = tid; e < 2 * AS_KPAD; e += TC_NT) {
+        sN2[e] = a.cn2[m * 2 * AS_KPAD + e];
+        sN1[e] = a.cn[m * 2 * AS_KPAD + e];
+    }
     if (!mbar_wait(done, 0)) {
         record_error(12);
         *abort_flag = 1;
@@ -525,20 +497,31 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
     const bool ok = !*abort_flag;
     tc_fence_after();
     if (ok) {
-        const long long r = row0 + warp * 32 + lane;
+        const int rl = warp * 32 + lane;                 // row within the tile = TMEM lane
+        const long long r = row0 + rl;
         const bool live = r < a.N;
-        const float *x = a.Xr + (live ? r : 0) * (long long)a.Dp + lo;
+        // the row's subspace values: from the resident tiles when the subspace
+        // spans at most the two stages, else from global memory
+        const bool resident = nk <= 2;
+        const float *xg = a.Xr + (live ? r : 0) * (long long)a.Dp + lo;
+        auto xval = [&](int j) -> float {               // j: column relative to lo
+            if (!resident) return xg[j];
+            const int jj = lo - base + j;
+            const float *tile = (const float *)(sm + (jj >> 5) * STAGE);
+            return tile[rl * 32 + ((((jj & 31) >> 2) ^ (rl & 7)) << 2) + (jj & 3)];
+        };
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         int arg[2];
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-            const float *xh = x + (half ? hl : 0);
-            const int h = half ? hr : hl;
-            const float *C = a.cent + (((long long)m * 2 + half) * a.K) * a.H;
-            const float *c2 = a.cn2 + (m * 2 + half) * AS_KPAD;
-            const float *c1 = a.cn + (m * 2 + half) * AS_KPAD;
+            const int off = half ? hl : 0, h = half ? hr : hl;
+            const float *C = sC + half * a.K * HS;
+            const float *c2 = sN2 + half * AS_KPAD, *c1 = sN1 + half * AS_KPAD;
             float nx2 = 0.0f;
-            for (int d = 0; d < h; ++d) nx2 = fmaf(xh[d], xh[d], nx2);
+            for (int d = 0; d < h; ++d) {
+                const float t = xval(off + d);
+                nx2 = fmaf(t, t, nx2);
+            }
             const float nx = sqrtf(nx2);
             float U = INFINITY;
             for (int c0 = 0; c0 < AS_KPAD; c0 += 16) {
@@ -564,10 +547,10 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
                     if (c >= a.K) continue;
                     const float sc = c2[c] - 2.0f * __uint_as_float(v[q]);
                     if (!(sc - asg_bound(nx, nx2, c1[c], c2[c]) <= U)) continue;
-                    const float *cc = C + (long long)c * a.H;
+                    const float *cc = C + c * HS;
                     float acc = 0.0f;
                     for (int d = 0; d < h; ++d) {
-                        const float diff = xh[d] - cc[d];
+                        const float diff = xval(off + d) - cc[d];
                         acc = fmaf(diff, diff, acc);
                     }
                     if (acc < best) {   // ascending c: the first minimum wins ties
@@ -661,7 +644,12 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
             s = CRISP_ECUDA;
             break;
         }
-        const size_t smem = 1024 + 2 * ((size_t)TC_BM * 128 + 2 * (size_t)AS_KPAD * 128) + 64;
+        int HS = 1;
+        for (int m = 0; m < M; ++m) {
+            const int w = (int)(((long long)(m + 1) * D) / M) - (int)(((long long)m * D) / M);
+            HS = std::max(HS, w - w / 2);
+        }
+        const size_t smem = asg_smem_bytes(K, HS);
         e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
         unsigned int zero = 0;
