@@ -494,6 +494,12 @@ def verify_opt(ix: Index, qr, Cand, k, eps0=2.1, P=400):
 def search(ix: Index, Q, params: SearchParams, nthreads: int = 0):
     """Algorithm 1 for a batch of queries: (ids [nq,k] int64, d2 [nq,k] f32, stats, threads used)."""
     Q = np.atleast_2d(_c(Q, np.float32))
+    if params.precision == 1 and ix.Xb is None:
+        raise ValueError("search: precision 1 needs the index's BF16 copy (Index.add_copies)")
+    if params.precision == 2 and ix.X8 is None:
+        raise ValueError("search: precision 2 needs the index's FP8 copy (Index.add_copies)")
+    if params.mode == 2 and (getattr(ix, "mlp", None) is None or ix.Xb is None):
+        raise ValueError("search: mode 2 needs a model (Index.set_model) and the BF16 copy (Index.add_copies)")
     nq = Q.shape[0]
     ids = np.empty((nq, params.k), np.int64)
     d2 = np.empty((nq, params.k), np.float32)

@@ -117,3 +117,16 @@ def test_bf16_shortlist_keeps_recall(gmm_q):
     r0 = oracle.recall_at_k(oracle.search(ix, Q, p0)[0], gd, X, Q, 10)
     r1 = oracle.recall_at_k(oracle.search(ix, Q, p1)[0], gd, X, Q, 10)
     assert r1 >= r0 - 0.02
+
+
+def test_search_rejects_missing_copies_and_model():
+    """Asking for coarse scores or learned depths without the copy or the model
+    is an error on the host, not a read through a null pointer."""
+    import oracle as o
+    import synthetic as sy
+
+    X, Q = sy.small_gaussian(400, 64, 3, seed=4)
+    ix = o.build_index(X, M=2, K=8, draws=sy.method_draws(400, 64, 2, 8, seed=4, kmeans_train=400))
+    for kw in (dict(precision=1, shortlist=5), dict(precision=2, shortlist=5), dict(mode=2)):
+        with pytest.raises(ValueError):
+            o.search(ix, Q, o.SearchParams(k=3, rho=0.5, alpha=0.5, **kw))
