@@ -20,7 +20,7 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
                                  uint8_t *score, int32_t *how, cudaStream_t st);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st);
+                              cudaStream_t st, bool no_alloc = false);
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,

@@ -866,19 +866,25 @@ __global__ void __launch_bounds__(RR_NT, 5) k_dist_flat(IxView ix, const float *
     extern __shared__ __align__(16) float qs[];
     __shared__ int s_q;
     const int Dp = ix.Dp, nb = Dp / 32;
-    const long long total = off[nq];
+    // off == nullptr: every query has ceil(stride / RF_CH) items (empty ones end at once)
+    const long long cpq = (stride + RF_CH - 1) / RF_CH;
+    const long long total = off ? off[nq] : (long long)nq * cpq;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 3, l = threadIdx.x & 7;
     const unsigned gmask = 0xFFu << (lane & 24);
     int cur_q = -1;
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         if (threadIdx.x == 0) {
-            int lo = 0, hi = nq - 1;             // query q with off[q] <= w < off[q+1]
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= w) lo = mid;
-                else hi = mid - 1;
+            if (off) {
+                int lo = 0, hi = nq - 1;             // query q with off[q] <= w < off[q+1]
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (off[mid] <= w) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_q = lo;
+            } else {
+                s_q = (int)(w / cpq);
             }
-            s_q = lo;
         }
         __syncthreads();
         const int q = s_q;
@@ -888,7 +894,7 @@ __global__ void __launch_bounds__(RR_NT, 5) k_dist_flat(IxView ix, const float *
         }
         __syncthreads();
         long long n = ncand[q] < stride ? ncand[q] : stride;
-        const long long c0 = (w - off[q]) * RF_CH;
+        const long long c0 = (off ? w - off[q] : w % cpq) * RF_CH;
         const long long c1 = c0 + RF_CH < n ? c0 + RF_CH : n;
         const int *candq = cand + (long long)q * stride;
         float *distq = dbuf + (long long)q * stride;
@@ -1225,13 +1231,15 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
 
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool no_alloc = false) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
-    long long *off = nullptr;
-    CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
-    k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
-    CRISP_COUNT_LAUNCH();
+    long long *off = nullptr;           // no_alloc: a fixed number of items per query, no offsets
+    if (!no_alloc) {
+        CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
+        k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
+        CRISP_COUNT_LAUNCH();
+    }
     if (smem > 48 * 1024)
         CRISP_CK(cudaFuncSetAttribute(k_dist_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 152;
@@ -1246,7 +1254,7 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
     k_select_rows<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, dbuf,
                                         (long long *)ids, d2);
     CRISP_COUNT_LAUNCH();
-    crisp_scratch_free(off, st);
+    if (off) crisp_scratch_free(off, st);
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
@@ -1413,7 +1421,7 @@ extern "C" crisp_status crisp_rerank_noalloc(const crisp_index *ix, const float 
     float *dbuf = nullptr;
     s = noalloc_scratch(&dbuf);
     if (s) return s;
-    return crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, as_stream(stream));
+    return crisp_run_rerank(ix, Qr, nq, cand, cand_stride, ncand, k, dbuf, ids, sqdist, as_stream(stream), true);
 }
 
 extern "C" crisp_status crisp_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,

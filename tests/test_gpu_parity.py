@@ -315,3 +315,60 @@ def test_invalid_params_raise_and_write_nothing(c1, kw):
         crisp.crisp_search(ix, dev(Q[:4]), 4, crisp.search_params(**base), ids, d2)
     assert e.value.status == crisp.CRISP_EINVAL
     assert bool((ids == -7).all()) and bool((d2 == -7.0).all())
+
+
+# ------------------------------------------------ large batches (grouped scoring)
+@pytest.fixture(scope="module")
+def c1_big():
+    """The parity index with 640 queries of the same law: batches this large are
+    scored in MinHash-ordered query groups (each row read once per group)."""
+    X, Q = synthetic.gmm(nq=640)
+    ix_o = oracle.build_index(X, M=8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=0)).add_copies()
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    crisp.crisp_index_add_copies(ix, 3)
+    return X, Q, ix_o, ix
+
+
+@pytest.mark.parametrize("kw", [dict(k=10, mode=0, rho=0.02, alpha=0.25),
+                                dict(k=100, mode=0, rho=0.05, alpha=0.125),
+                                dict(k=10, mode=0, rho=0.02, alpha=0.25, precision=1, shortlist=20),
+                                dict(k=10, mode=0, rho=0.03, alpha=0.25, precision=2, shortlist=40)])
+def test_large_batch_search_bitexact(c1_big, kw):
+    X, Q, ix_o, ix = c1_big
+    nq = Q.shape[0]
+    ids = empty((nq, kw["k"]), torch.int64)
+    d2 = empty((nq, kw["k"]), torch.float32)
+    crisp.crisp_search(ix, dev(Q), nq, crisp.search_params(**kw), ids, d2)
+    oi, od, _, _ = oracle.search(ix_o, Q, oracle.SearchParams(**kw))
+    assert np.array_equal(ids.cpu().numpy(), oi)
+    assert np.array_equal(d2.cpu().numpy(), od)
+
+
+def test_large_batch_rerank_and_shortlist_steps(c1_big):
+    X, Q, ix_o, ix = c1_big
+    nq, M, K2 = Q.shape[0], ix_o.M, ix_o.K * ix_o.K
+    Qr = gpu_qr(ix_o, ix, Q)
+    act = empty((nq, M, K2), torch.int32)
+    nact = empty((nq, M), torch.int32)
+    crisp.crisp_activate(ix, Qr, nq, 0, 10, crisp.budget(0.03, ix_o.N), act, nact)
+    stride = ix_o.N
+    cand = empty((nq, stride), torch.int32)
+    ncand = empty((nq,), torch.int64)
+    crisp.crisp_count_cut(ix, act, nact, nq, crisp.tau(0.25, M), 10, 0, cand, stride, ncand)
+    n = ncand.cpu().numpy()
+    c = cand.cpu().numpy()
+    Qr_h = Qr.cpu().numpy()
+    ids = empty((nq, 10), torch.int64)
+    d2 = empty((nq, 10), torch.float32)
+    crisp.crisp_rerank(ix, Qr, nq, cand, stride, ncand, 10, ids, d2)
+    sl = empty((nq, 64), torch.int32)
+    nsl = empty((nq,), torch.int64)
+    crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 1, 30, sl, 64, nsl)
+    gi, gd, gs, gns = ids.cpu().numpy(), d2.cpu().numpy(), sl.cpu().numpy(), nsl.cpu().numpy()
+    Xb = oracle.quantize_bf16(ix_o.Xr)
+    for q in range(0, nq, 37):
+        cq = c[q, :n[q]].astype(np.int64)
+        ri, rd = oracle.rerank(ix_o, Qr_h[q], cq, 10)
+        assert np.array_equal(gi[q], ri) and np.array_equal(gd[q], rd), q
+        ro = oracle.shortlist(ix_o, Qr_h[q], cq, 30, "bf16", quant=Xb)
+        assert gns[q] == len(ro) and np.array_equal(gs[q, :gns[q]], ro), q
