@@ -20,7 +20,7 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
                                  uint8_t *score, int32_t *how, cudaStream_t st);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st, bool no_alloc = false);
+                              cudaStream_t st, bool no_alloc = false, bool may_group = true);
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
@@ -429,7 +429,8 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
             if (!s) s = crisp_run_select_score(cand, pl.stride, ncand, score, dV, nc, selV, nsel, st);
             if (!s) s = crisp_run_shortlist(ix, Qr, nc, selV, pl.stride, nsel, 1, 1, dist, cand, pl.stride, nshort, st,
                                             dS);
-            if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, nshort, pl.k, dist, ids_c, d2_c, st);
+            // shortlists are short whatever the list stride: stream them per query
+            if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, nshort, pl.k, dist, ids_c, d2_c, st, false, false);
             if (!s && stats)
                 s = launch_write_stats(nc, ncand, how, retr, M, nsel, nshort, pl.tau, stats + c0, st);
         } else if (!s && p->mode == 0 && pl.prec > 0) {

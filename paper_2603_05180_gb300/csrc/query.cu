@@ -1094,6 +1094,482 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
     }
 }
 
+// ------------------------------------------- grouped scoring (row reuse)
+// The candidate sets of a large batch overlap: on the 1M-row workload a row is a
+// candidate of about 200 of 10,000 queries.  Queries are ordered by the MinHash
+// of their candidate sets and cut into groups of GS_G; the id space into ranges
+// of GS_SPAN ids.  k_gunion lists, for each (group, range), the rows some member
+// needs, with the member mask and where each (row, member) distance goes in
+// that member's list.  k_gscore then reads each listed row once and scores it
+// against every member that needs it, loading the next row while it computes.
+// The per-(row, query) arithmetic is the streaming kernels' CR32 order, and
+// every distance lands in its own slot, so results do not depend on grouping.
+constexpr int GS_G = 32;            // members per group (bit mask)
+constexpr int GS_SPAN = 4096;       // ids per range
+constexpr int SCH_MAXQ = 32768;     // the ordering sorts 15-bit query numbers in one CTA
+constexpr int GS_MINQ = 1024;       // batches smaller than this stream per query
+constexpr int GS_MINSTRIDE = 2048;  // so do short candidate lists (shortlists)
+constexpr int GU_NT = 256;
+constexpr int GK_NT = 1024;
+
+// key[q] = (min over the candidates of a 24-bit multiplicative hash of the id,
+// clamped to 17 bits) << 15 | q: one block per query.
+__global__ void __launch_bounds__(RR_NT) k_minhash_key(const int *__restrict__ cand, long long stride,
+                                                       const long long *__restrict__ ncand, int nq,
+                                                       unsigned *__restrict__ key) {
+    __shared__ unsigned wmin[RR_NT / 32];
+    const int q = blockIdx.x;
+    const long long n = ncand[q] < stride ? ncand[q] : stride;
+    const int *c = cand + (long long)q * stride;
+    unsigned m = 0xFFFFFFFFu;
+    for (long long i = threadIdx.x; i < n; i += RR_NT) {
+        const unsigned h = ((unsigned)c[i] * 2654435761u) >> 8;
+        m = h < m ? h : m;
+    }
+    m = __reduce_min_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned b = wmin[0];
+        for (int w = 1; w < RR_NT / 32; ++w) b = wmin[w] < b ? wmin[w] : b;
+        b = b > 0x1FFFFu ? 0x1FFFFu : b;
+        key[q] = (b << 15) | (unsigned)q;
+    }
+}
+
+// One CTA: bitonic sort of the nq (<= 32768) keys; qord = their low 15 bits.
+__global__ void __launch_bounds__(1024) k_sort_queries(const unsigned *__restrict__ key, int nq, int *__restrict__ qord) {
+    extern __shared__ unsigned sk[];
+    int n2 = 1;
+    while (n2 < nq) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += 1024) sk[i] = i < nq ? key[i] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int st = size >> 1; st > 0; st >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += 1024) {
+                const int j = i ^ st;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned a = sk[i], b = sk[j];
+                    if ((a > b) == up) { sk[i] = b; sk[j] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < nq; i += 1024) qord[i] = (int)(sk[i] & 0x7FFFu);
+}
+
+// pos[q][r] = first list position with id >= r GS_SPAN (r = 0..R).
+__global__ void k_sched_pos(const int *__restrict__ cand, long long stride, const long long *__restrict__ ncand,
+                            int nq, int R, int *__restrict__ pos) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nq * (R + 1)) return;
+    const int q = (int)(e / (R + 1)), r = (int)(e % (R + 1));
+    const long long n = ncand[q] < stride ? ncand[q] : stride;
+    const int *c = cand + (long long)q * stride;
+    const long long bound = (long long)r * GS_SPAN;
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if ((long long)c[mid] < bound) lo = mid + 1;
+        else hi = mid;
+    }
+    pos[e] = (int)lo;
+}
+
+
+struct GUnion {
+    const int *qord;            // [nq]
+    const int *pos;             // [nq][R + 1]
+    int *ent_row;               // [cap] row id
+    unsigned *ent_mask;         // [cap] members that need the row
+    int *ent_pb;                // [cap] first pair slot of the row
+    int *pair_pos;              // [cap] list position of each (row, member) pair, members in bit order
+    int2 *items;                // [ngroups][R] (first entry, entries)
+    unsigned long long *counts; // [0] entries, [1] pairs, [2] scoring item counter
+    long long cap;
+    int R, nq;
+};
+
+// One block per (range r, group g): the group's candidates in the range, their
+// rows' member masks, and the pair slots.
+__global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, long long stride, GUnion u) {
+    __shared__ unsigned mask[GS_SPAN];
+    __shared__ int pbl[GS_SPAN];
+    __shared__ int s_q[GS_G], s_base[GS_G], s_off[GS_G + 1];
+    __shared__ long long scan_ws[GU_NT / 32 + 1];
+    __shared__ long long s_eb, s_pb;
+    __shared__ int s_np;
+    const int r = blockIdx.x, g = blockIdx.y, lane = threadIdx.x & 31;
+    const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
+    if (threadIdx.x < 32) {
+        int a = 0, b = 0, q = 0;
+        if (lane < gsize) {
+            q = u.qord[g * GS_G + lane];
+            const long long row = (long long)q * (u.R + 1) + r;
+            a = u.pos[row];
+            b = u.pos[row + 1];
+        }
+        const int cnt = b - a;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        s_q[lane] = q;
+        s_base[lane] = a;
+        s_off[lane] = incl - cnt;
+        if (lane == 31) {
+            s_off[32] = incl;
+            s_np = incl;
+        }
+    }
+    for (int o = threadIdx.x; o < GS_SPAN; o += GU_NT) mask[o] = 0u;
+    __syncthreads();
+    const int np = s_np;
+    const long long lo_id = (long long)r * GS_SPAN;
+    for (int e = threadIdx.x; e < np; e += GU_NT) {
+        int lo = 0, hi = GS_G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + (e - s_off[lo])];
+        atomicOr(&mask[id - lo_id], 1u << lo);
+    }
+    __syncthreads();
+    // first pair slot of each row (exclusive prefix of its member counts) and the
+    // number of rows some member needs (one packed scan: pairs high, rows low)
+    long long carry = 0;
+    for (int o0 = 0; o0 < GS_SPAN; o0 += GU_NT) {
+        const int o = o0 + threadIdx.x;
+        const int c = __popc(mask[o]);
+        long long tot;
+        const long long ex = block_excl_scan<GU_NT>(((long long)c << 32) | (c > 0 ? 1 : 0), scan_ws, &tot);
+        pbl[o] = (int)((carry + ex) >> 32);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        const long long ne = carry & 0xFFFFFFFF;
+        s_eb = (long long)atomicAdd(&u.counts[0], (unsigned long long)ne);
+        s_pb = (long long)atomicAdd(&u.counts[1], (unsigned long long)np);
+        const bool fits = s_eb + ne <= u.cap && s_pb + np <= u.cap;
+        u.items[(long long)g * u.R + r] = make_int2(fits ? (int)s_eb : 0, fits ? (int)ne : 0);
+        if (!fits) { s_eb = -1; }
+    }
+    __syncthreads();
+    if (s_eb < 0) return;
+    // entries (recomputing each row's entry number with the same scan)
+    carry = 0;
+    for (int o0 = 0; o0 < GS_SPAN; o0 += GU_NT) {
+        const int o = o0 + threadIdx.x;
+        const unsigned m = mask[o];
+        const int c = __popc(m);
+        long long tot;
+        const long long ex = block_excl_scan<GU_NT>(c > 0 ? 1 : 0, scan_ws, &tot);
+        if (c > 0) {
+            const long long ei = s_eb + carry + ex;
+            u.ent_row[ei] = (int)(lo_id + o);
+            u.ent_mask[ei] = m;
+            u.ent_pb[ei] = (int)(s_pb + pbl[o]);
+        }
+        carry += tot;
+    }
+    // pair slots: member j of row o goes to slot first(o) + (members of o below j)
+    for (int e = threadIdx.x; e < np; e += GU_NT) {
+        int lo = 0, hi = GS_G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int t = e - s_off[lo];
+        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + t];
+        const int o = id - (int)lo_id;
+        const int slot = (int)s_pb + pbl[o] + __popc(mask[o] & ((1u << lo) - 1u));
+        u.pair_pos[slot] = s_base[lo] + t;
+    }
+}
+
+// Lane-per-block layout of the grouped scorer: lane l holds the row's 32-dim
+// block l (FP32: 8 float4; BF16: 4 x 16 bytes), so the CR32 lane partials and
+// their xor tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers; the
+// block sums then go through shared memory and are added in block order.
+// Query blocks sit in shared memory with float4 u of block b at slot
+// u ^ (b & 7), so the eight lanes of a quarter-warp read distinct banks.
+__device__ __forceinline__ float block_tree(const float (&a)[8]) {
+    return ((a[0] + a[4]) + (a[2] + a[6])) + ((a[1] + a[5]) + (a[3] + a[7]));
+}
+
+template <int PREC>
+__device__ __forceinline__ void row_load_lb(uint4 (&v)[8], const IxView &ix, long long id, int nb) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (lane < nb && (PREC == 0 || u < 4)) {
+            if (PREC == 0) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * ix.Dp + 32 * lane + 4 * u));
+            else v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xb + id * ix.Dp + 32 * lane + 8 * u));
+        } else {
+            v[u] = make_uint4(0, 0, 0, 0);
+        }
+    }
+}
+
+// CR32 block sum of this lane's block against query q (swizzled in shared memory).
+template <int PREC>
+__device__ __forceinline__ float block_sum_lb(const uint4 (&v)[8], const float4 *q, int nb) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= nb) return 0.0f;
+    const float4 *qb = q + 8 * lane;
+    const int sw = lane & 7;
+    float a[8];
+    if (PREC == 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 qq = qb[u ^ sw];
+            float x = 0.0f, t;
+            t = __uint_as_float(v[u].x) - qq.x;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[u].y) - qq.y;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[u].z) - qq.z;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[u].w) - qq.w;
+            x = fmaf(t, t, x);
+            a[u] = x;
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {                       // 16 bytes = lane partials 2h, 2h+1
+            const float4 q0 = qb[(2 * h) ^ sw], q1 = qb[(2 * h + 1) ^ sw];
+            const unsigned w0 = v[h].x, w1 = v[h].y, w2 = v[h].z, w3 = v[h].w;
+            float x = 0.0f, y = 0.0f, t;
+            t = __uint_as_float(w0 << 16) - q0.x;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(w0 & 0xFFFF0000u) - q0.y;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(w1 << 16) - q0.z;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(w1 & 0xFFFF0000u) - q0.w;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(w2 << 16) - q1.x;
+            y = fmaf(t, t, y);
+            t = __uint_as_float(w2 & 0xFFFF0000u) - q1.y;
+            y = fmaf(t, t, y);
+            t = __uint_as_float(w3 << 16) - q1.z;
+            y = fmaf(t, t, y);
+            t = __uint_as_float(w3 & 0xFFFF0000u) - q1.w;
+            y = fmaf(t, t, y);
+            a[2 * h] = x;
+            a[2 * h + 1] = y;
+        }
+    }
+    return block_tree(a);
+}
+
+// Warp layout for FP32 rows: lane l holds dims 128 c + 4 l (8 x 16 bytes,
+// coalesced).  The CR32 terms of one query come in phases that keep the chains
+// independent: all lane partials, then each level of the xor tree across the
+// chunks, then the block sums gathered and added in block order.  The query is
+// read from a plain (unswizzled) shared copy.
+__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int d = c * 128 + 4 * lane;
+        v[c] = d < Dp ? __ldcs(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
+    }
+}
+
+__device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q4, int Dp) {
+    const int lane = threadIdx.x & 31;
+    float a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int d = c * 128 + 4 * lane;
+        float x = 0.0f;
+        if (d < Dp) {
+            const float4 qq = q4[d >> 2];
+            float t = __uint_as_float(v[c].x) - qq.x;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].y) - qq.y;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].z) - qq.z;
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].w) - qq.w;
+            x = fmaf(t, t, x);
+        }
+        a[c] = x;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 4);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 2);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 1);
+    float acc = 0.0f;
+    const int nb = Dp >> 5;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int gq = 0; gq < 4; ++gq) {
+            const float sbv = __shfl_sync(0xffffffffu, a[c], 8 * gq);
+            if (4 * c + gq < nb) acc = acc + sbv;
+        }
+    return acc;
+}
+
+// Persistent: CTAs take (group, range) items in order; warps take the item's
+// rows (lane-per-block layout) and score each against its members.
+template <int PREC>
+__global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
+                                                    GUnion u, float *__restrict__ dbuf) {
+    extern __shared__ __align__(16) float4 gq4[];                // [GS_G][Dp / 4], swizzled per block
+    __shared__ long long s_it;
+    __shared__ int s_mem[GS_G];
+    __shared__ __align__(16) float s_bs[GK_NT / 32][2][32];      // block sums, two buffers per warp
+    const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ngroups = (u.nq + GS_G - 1) / GS_G;
+    const long long items = (long long)ngroups * u.R;
+    int cur_g = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
+        __syncthreads();
+        const long long it = s_it;
+        if (it >= items) break;
+        const int g = (int)(it / u.R);
+        const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
+        if (g != cur_g) {
+            if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GS_G + threadIdx.x];
+            __syncthreads();
+            const int n4 = Dp >> 2;
+            for (int e = threadIdx.x; e < gsize * n4; e += GK_NT) {
+                const int j = e / n4, f = e % n4, b = f >> 3, uu = f & 7;
+                // BF16 (lane-per-block) reads a swizzled copy, FP32 (warp layout) a plain one
+                gq4[(size_t)j * n4 + (PREC == 0 ? f : 8 * b + (uu ^ (b & 7)))] =
+                    reinterpret_cast<const float4 *>(Qr + (long long)s_mem[j] * Dp)[f];
+            }
+            cur_g = g;
+        }
+        __syncthreads();
+        const int2 itm = u.items[it];
+        const int e0 = itm.x, ne = itm.y;
+        uint4 v[8];
+        int buf = 0;
+        for (int e = warp; e < ne; e += GK_NT / 32) {
+            if (PREC == 0) row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
+            else row_load_lb<PREC>(v, ix, (long long)u.ent_row[e0 + e], nb);
+            const unsigned m0 = u.ent_mask[e0 + e];
+            const int pb = u.ent_pb[e0 + e];
+            unsigned m = m0;
+            float mine = 0.0f;
+            for (int i = 0; m; ++i) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                if (PREC == 0) {
+                    const float acc = row_cr32_w(v, gq4 + (size_t)j * (Dp >> 2), Dp);
+                    if (lane == i) mine = acc;
+                    continue;
+                }
+                const float bs = block_sum_lb<PREC>(v, gq4 + (size_t)j * (Dp >> 2), nb);
+                s_bs[warp][buf][lane] = bs;
+                __syncwarp();
+                float acc = 0.0f;
+                const float4 *sb4 = reinterpret_cast<const float4 *>(s_bs[warp][buf]);
+#pragma unroll
+                for (int b4 = 0; b4 < 8; ++b4) {
+                    const float4 t4 = sb4[b4];
+                    if (4 * b4 < nb) acc = acc + t4.x;
+                    if (4 * b4 + 1 < nb) acc = acc + t4.y;
+                    if (4 * b4 + 2 < nb) acc = acc + t4.z;
+                    if (4 * b4 + 3 < nb) acc = acc + t4.w;
+                }
+                if (lane == i) mine = acc;
+                buf ^= 1;
+            }
+            const int n = __popc(m0);
+            if (lane < n) {
+                unsigned mm = m0;
+                for (int k = 0; k < lane; ++k) mm &= mm - 1;
+                const int j = __ffs(mm) - 1;
+                dbuf[(long long)s_mem[j] * stride + u.pair_pos[pb + lane]] = mine;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Grouped scoring of a batch into dbuf, or *done = false when the batch does not
+// qualify (then the caller streams per query).
+template <int PREC>
+static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand, int64_t stride,
+                                const int64_t *ncand, float *dbuf, cudaStream_t st, bool *done) {
+    *done = false;
+    if (nq < GS_MINQ || nq > SCH_MAXQ || ix->Dp > 1024 || stride < GS_MINSTRIDE) return CRISP_OK;
+    const int R = (int)((ix->N + GS_SPAN - 1) / GS_SPAN);
+    const int ngroups = (nq + GS_G - 1) / GS_G;
+    const long long cap = (long long)nq * std::min<int64_t>(stride, ix->N);
+    if (cap > (1LL << 31) - 1) return CRISP_OK;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += (b + 255) / 256 * 256; return o; };
+    const size_t o_cnt = take(3 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned) * nq),
+                 o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
+                 o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)cap),
+                 o_mask = take(sizeof(unsigned) * (size_t)cap), o_pb = take(sizeof(int) * (size_t)cap),
+                 o_pp = take(sizeof(int) * (size_t)cap);
+    uint8_t *buf = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
+    GUnion u;
+    u.counts = (unsigned long long *)(buf + o_cnt);
+    unsigned *key = (unsigned *)(buf + o_key);
+    u.qord = (int *)(buf + o_qord);
+    u.pos = (int *)(buf + o_pos);
+    u.items = (int2 *)(buf + o_items);
+    u.ent_row = (int *)(buf + o_row);
+    u.ent_mask = (unsigned *)(buf + o_mask);
+    u.ent_pb = (int *)(buf + o_pb);
+    u.pair_pos = (int *)(buf + o_pp);
+    u.cap = cap;
+    u.R = R;
+    u.nq = nq;
+    crisp_status s = CRISP_OK;
+    do {
+        cudaError_t e = cudaMemsetAsync(u.counts, 0, 3 * sizeof(unsigned long long), st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__); break; }
+        k_minhash_key<<<nq, RR_NT, 0, st>>>(cand, (long long)stride, (const long long *)ncand, nq, key);
+        CRISP_COUNT_LAUNCH();
+        int n2 = 1;
+        while (n2 < nq) n2 <<= 1;
+        e = cudaFuncSetAttribute(k_sort_queries, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned) * n2));
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        k_sort_queries<<<1, 1024, sizeof(unsigned) * n2, st>>>(key, nq, (int *)u.qord);
+        CRISP_COUNT_LAUNCH();
+        const long long npos = (long long)nq * (R + 1);
+        k_sched_pos<<<(unsigned)((npos + 255) / 256), 256, 0, st>>>(cand, (long long)stride,
+                                                                    (const long long *)ncand, nq, R, (int *)u.pos);
+        CRISP_COUNT_LAUNCH();
+        k_gunion<<<dim3(R, ngroups), GU_NT, 0, st>>>(cand, (long long)stride, u);
+        CRISP_COUNT_LAUNCH();
+        const size_t smem = sizeof(float) * (size_t)GS_G * ix->Dp;
+        e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
+        CRISP_COUNT_LAUNCH();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "grouped scoring", __FILE__, __LINE__); break; }
+        *done = true;
+    } while (0);
+    crisp_scratch_free(buf, st);
+    return s;
+}
+
 // The S_keep best (score, list position) of each query's scored candidates, in
 // list (ascending id) order: the shortlist for the FP32 re-rank.
 __global__ void __launch_bounds__(RR_NT) k_short_select(int nq, const int *__restrict__ cand, long long stride,
@@ -1231,26 +1707,33 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
 
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st, bool no_alloc = false) {
+                              cudaStream_t st, bool no_alloc = false, bool may_group = true) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
+    bool grouped = false;
+    if (!no_alloc && may_group) {
+        crisp_status gs = run_grouped<0>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
+        if (gs) return gs;
+    }
     long long *off = nullptr;           // no_alloc: a fixed number of items per query, no offsets
-    if (!no_alloc) {
+    if (!grouped && !no_alloc) {
         CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
         k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
         CRISP_COUNT_LAUNCH();
     }
     if (smem > 48 * 1024)
         CRISP_CK(cudaFuncSetAttribute(k_dist_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_flat, RR_NT, smem);
-    int grid = sms * (per_sm > 0 ? per_sm : 4);
-    k_dist_flat<<<grid, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, off,
-                                           dbuf);
-    CRISP_COUNT_LAUNCH();
+    if (!grouped) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_flat, RR_NT, smem);
+        int grid = sms * (per_sm > 0 ? per_sm : 4);
+        k_dist_flat<<<grid, RR_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride,
+                                               (const long long *)ncand, off, dbuf);
+        CRISP_COUNT_LAUNCH();
+    }
     k_select_rows<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, dbuf,
                                         (long long *)ids, d2);
     CRISP_COUNT_LAUNCH();
@@ -1265,6 +1748,19 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
                                  const int64_t *S_per_query) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
+    bool grouped = false;
+    if (precision == 1) {
+        crisp_status gs = run_grouped<1>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
+        if (gs) return gs;
+    }
+    if (grouped) {
+        k_short_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, S, dbuf, out,
+                                             (long long)out_stride, (long long *)nout,
+                                             (const long long *)S_per_query);
+        CRISP_COUNT_LAUNCH();
+        CRISP_CK_LAUNCH();
+        return CRISP_OK;
+    }
     long long *off = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
     k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
