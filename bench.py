@@ -363,6 +363,7 @@ def run_crisp(args):
     traffic = _ncu_traffic(dom)
     roofline = {"kernel": stage[dom]["kernel"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "dram_gbs": traffic / (dms / 1e3) / 1e9 if traffic else None,
                 "note": ("algorithmic bytes count every (query, candidate) row read; the grouped kernel reads a row "
                          "once for all queries of its group that need it, so DRAM traffic (ncu) is below them and "
                          "frac can exceed 1") if stage[dom]["kernel"].startswith("k_gscore") else None,
