@@ -652,6 +652,89 @@ def serving_leg(args, torch, crisp, synthetic, dev):
     return out
 
 
+def run_ablation(args):
+    """The paper's ablations (§6, "Ablation Study") on the synthetic workloads:
+    (1) the rotation threshold tau_CEV: per dataset its CEV, and recall@100 and
+    QPS with the rotation forced off and on, then what each tau_CEV would
+    choose; (2) the patience factor of the Optimized mode (20 / 40 / 60);
+    (3) the verification sub-components: full (Hamming order + ADSampling),
+    exact L2 (ADSampling off, eps0 = inf) and id order (Hamming re-ranking off).
+    Prints one JSON line."""
+    import torch
+
+    import paper_2603_05180_gb300 as crisp
+    import synthetic
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+
+    def measure(ix, X, Q, gd, sp, k):
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        crisp.crisp_search(ix, Q, nq, sp, ids, d2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        crisp.crisp_search(ix, Q, nq, sp, ids, d2)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        return {"recall": recall_at_k(torch, X, Q, ids, gd[:, k - 1].contiguous()), "qps": nq / (ms / 1e3),
+                "ms_per_query_batch": ms}
+
+    out = {"workloads": {}}
+    # (1) tau_CEV
+    sets = []
+    Xg, Qg = synthetic.gmm(N=20000, D=256, nq=1000)
+    sets.append(("gmm 20k x 256", torch.from_numpy(Xg).to(dev), torch.from_numpy(Qg).to(dev), 8))
+    Xp, Qp = synthetic.powerlaw(200000, 960, 1000, device="cuda")
+    sets.append(("powerlaw 200k x 960", Xp, Qp, 20))
+    Xv, Qv = synthetic.vmf(N=100000, D=768, nq=1000, n_comp=200)
+    sets.append(("vmf 100k x 768", torch.from_numpy(Xv).to(dev), torch.from_numpy(Qv).to(dev), 16))
+    Xl, Ql = synthetic.lowrank(N=100000, D=1024, nq=1000)
+    sets.append(("lowrank 100k x 1024", torch.from_numpy(Xl).to(dev), torch.from_numpy(Ql).to(dev), 16))
+    rows = []
+    for name, X, Q, M in sets:
+        N, D = X.shape
+        _, gd = ground_truth(torch, X, Q, 100)
+        res = {}
+        cev = None
+        for rot in (0, 1):
+            ix = crisp.crisp_build(X, N, D, crisp.build_params(M, rotate=rot, draws=synthetic.method_draws(N, D, M, 50)))
+            cev = ix.info().cev
+            res[rot] = measure(ix, X, Q, gd, crisp.search_params(k=100, mode=0, rho=0.02, alpha=0.25), 100)
+            ix.free()
+        rows.append({"dataset": name, "N": N, "D": D, "M": M, "cev": cev, "no_rotation": res[0], "rotation": res[1]})
+    out["tau_cev"] = {"point": "Guaranteed, k=100, rho=0.02, alpha=0.25, 1,000 queries", "datasets": rows,
+                      "by_threshold": [{"tau_cev": t,
+                                        "rotated": [r["dataset"] for r in rows if r["cev"] > t],
+                                        "mean_recall_at_100": float(np.mean([(r["rotation"] if r["cev"] > t else
+                                                                              r["no_rotation"])["recall"]
+                                                                             for r in rows]))}
+                                       for t in (0.7, 0.75, 0.8, 0.85, 0.9, 0.95)]}
+    del sets, Xp, Qp
+    torch.cuda.empty_cache()
+    # (2) patience and (3) sub-components on the 1M x 960 power-law index
+    N, D, M = 1_000_000, 960, 20
+    X, Q = synthetic.powerlaw(N, D, 2000, device="cuda")
+    ix = crisp.crisp_build(X, N, D, crisp.build_params(M, draws=synthetic.method_draws(N, D, M, 50)))
+    _, gd = ground_truth(torch, X, Q, 100)
+    out["patience"] = [dict(patience_factor=pf, **measure(ix, X, Q, gd, crisp.search_params(
+        k=100, mode=1, rho=0.03, alpha=0.3, patience_factor=pf, max_candidates=OPT_CAP), 100)) for pf in (20, 40, 60)]
+    sub = []
+    for rho in (0.01, 0.02, 0.03):
+        for name, kw in (("full", dict(eps0=2.1, verify_order=0)), ("exact L2 (no ADSampling)",
+                                                                    dict(eps0=float("inf"), verify_order=0)),
+                         ("no Hamming re-ranking", dict(eps0=2.1, verify_order=1))):
+            sub.append(dict(config=name, rho=rho, **measure(ix, X, Q, gd, crisp.search_params(
+                k=10, mode=1, rho=rho, alpha=0.3, max_candidates=OPT_CAP, **kw), 10)))
+    out["subcomponents"] = {"point": "Optimized, k=10, alpha=0.3, patience 40 k, 2,000 queries, 1M x 960",
+                            "points": sub}
+    out["workloads"] = {"tau_cev": "gmm, powerlaw, vmf (200 components, kappa 200), lowrank (rank 128, 5% x10)",
+                        "patience_subcomponents": "powerlaw 1M x 960, M=20"}
+    print(json.dumps({"ablation": out}), flush=True)
+
+
 def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     """Time each kernel of the search path with CUDA events on the launching stream,
     and count the algorithmic bytes each launch must move (DESIGN: per-stage units)."""
@@ -777,6 +860,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
+    ap.add_argument("--ablation", action="store_true", help="run the paper's ablations (tau_CEV, patience, "
+                                                            "verification sub-components) instead of the benchmark")
     ap.add_argument("--serve-n", type=int, default=5_000_000)
     ap.add_argument("--serve-dim", type=int, default=1024)
     ap.add_argument("--serve-M", type=int, default=32)
@@ -792,7 +877,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.ablation:
+        run_ablation(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_crisp(args)

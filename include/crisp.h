@@ -93,6 +93,9 @@ typedef struct {
                                   re-rank (>= k) */
     float depth_margin;        /* mode 2: added to the predicted log2 depths (score prefix, */
     float short_margin;        /*         coarse shortlist) before quantisation */
+    int32_t verify_order;      /* Optimized mode: 0 candidates by (Hamming distance, id) (§4.3.2 Stage 2),
+                                  1 by id alone (the paper's ablation without Hamming re-ranking) */
+    int32_t reserved;          /* 0 */
 } crisp_search_params;
 
 /* Per-query counters written by crisp_search (device array, may be NULL). */
@@ -484,7 +487,7 @@ crisp_status crisp_rerank_noalloc(const crisp_index *index, const float *Qr, int
  * EUNSUPPORTED: a query with more than 32768 candidates (cap them). */
 crisp_status crisp_verify_opt(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t cand_stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
-                              int64_t *ids, float *sqdist, int64_t *n_verified, int64_t *n_full,
+                              int32_t order, int64_t *ids, float *sqdist, int64_t *n_verified, int64_t *n_full,
                               int64_t *n_blocks, void *stream);
 
 #ifdef __cplusplus

@@ -54,7 +54,7 @@ class _OrParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
                 ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64),
                 ("precision", C.c_int32), ("shortlist", C.c_int32), ("depth_margin", C.c_float),
-                ("short_margin", C.c_float)]
+                ("short_margin", C.c_float), ("verify_order", C.c_int32), ("_pad", C.c_int32)]
 
 
 STATS_DTYPE = np.dtype([("n_candidates", np.int64), ("n_verified", np.int64), ("n_full", np.int64),
@@ -88,7 +88,7 @@ def _declare(L):
         "or_cut": (_I64, [_P, _I64, _I32, _I32, _I64, _P, _P]),
         "or_rerank": (_I32, [_P, _P, _P, _I64, _I32, _P, _P]),
         "or_ads_factor": (_F, [_I32, _I32, _F]),
-        "or_verify_opt": (_I32, [_P, _P, _P, _P, _I64, _I32, _F, _I64, _P, _P, _P, _P]),
+        "or_verify_opt": (_I32, [_P, _P, _P, _P, _I64, _I32, _F, _I64, _I32, _P, _P, _P, _P]),
         "or_search_batch": (_I32, [_P, _P, _I64, _I32, _P, _P, _P, _P, _I32]),
         "or_knn_f64": (None, [_P, _I64, _I32, _I32, _P, _I64, _I32, _I32, _P, _P]),
         "or_bf16_rne": (C.c_uint16, [_F]),
@@ -400,10 +400,12 @@ class SearchParams:
     shortlist: int = 0            # candidates kept for the FP32 re-rank when precision > 0
     depth_margin: float = 0.0     # learned mode (2): margins on the predicted log2 depths
     short_margin: float = 0.0
+    verify_order: int = 0         # Optimized mode: 0 (Hamming, id) order, 1 id order (ablation)
 
     def st(self) -> _OrParams:
         return _OrParams(self.k, self.mode, self.rho, self.alpha, self.patience_factor, self.eps0,
-                         self.max_candidates, self.precision, self.shortlist, self.depth_margin, self.short_margin)
+                         self.max_candidates, self.precision, self.shortlist, self.depth_margin, self.short_margin,
+                         self.verify_order, 0)
 
 
 def query_rotate(ix: Index, Q) -> np.ndarray:
@@ -479,14 +481,14 @@ def ads_factor(t, D, eps0) -> np.float32:
     return np.float32(lib().or_ads_factor(int(t), int(D), float(eps0)))
 
 
-def verify_opt(ix: Index, qr, Cand, k, eps0=2.1, P=400):
+def verify_opt(ix: Index, qr, Cand, k, eps0=2.1, P=400, order=0):
     qr = _c(qr, np.float32)
     Cand = _c(Cand, np.int32)
     qcode = sign_codes(qr.reshape(1, -1))[0]
     ids = np.empty(k, np.int64)
     d2 = np.empty(k, np.float32)
     nv, nf = C.c_int64(), C.c_int64()
-    lib().or_verify_opt(C.byref(ix.st()), _p(qr), _p(qcode), _p(Cand), Cand.size, k, float(eps0), int(P),
+    lib().or_verify_opt(C.byref(ix.st()), _p(qr), _p(qcode), _p(Cand), Cand.size, k, float(eps0), int(P), int(order),
                         _p(ids), _p(d2), C.byref(nv), C.byref(nf))
     return ids, d2, nv.value, nf.value
 

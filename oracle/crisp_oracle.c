@@ -57,6 +57,8 @@ typedef struct {
     int32_t shortlist;       /* candidates kept by the coarse score for the FP32 re-rank */
     float depth_margin;      /* learned mode: margins added to the predicted log2 depths */
     float short_margin;
+    int32_t verify_order;    /* Optimized mode: 0 by (Hamming, id) (§4.3.2 Stage 2), 1 by id (ablation) */
+    int32_t _pad;
 } or_params;
 
 typedef struct {
@@ -525,14 +527,15 @@ float or_ads_factor(int t, int D, float eps0) {
  * offer; the patience counter grows on every candidate that leaves the top-k
  * unchanged, resets otherwise, and the walk stops once it reaches P. */
 int or_verify_opt(const or_index *ix, const float *qr, const uint32_t *qcode, const int32_t *C, int64_t nC,
-                  int k, float eps0, int64_t P, int64_t *ids, float *d2, int64_t *n_verified, int64_t *n_full) {
+                  int k, float eps0, int64_t P, int order, int64_t *ids, float *d2, int64_t *n_verified,
+                  int64_t *n_full) {
     int W = ix->Dp / 32, nb = ix->Dp / 32, D = ix->D;
     hid *ord = (hid *)malloc(sizeof(hid) * (size_t)(nC > 0 ? nC : 1));
     for (int64_t c = 0; c < nC; ++c) {
         const uint32_t *bx = ix->codes + (int64_t)C[c] * W;
         int ham = 0;
         for (int w = 0; w < W; ++w) ham += __builtin_popcount(bx[w] ^ qcode[w]);
-        ord[c].ham = ham;
+        ord[c].ham = order ? 0 : ham;   /* order 1: the ablation without Hamming re-ranking (id order) */
         ord[c].id = C[c];
     }
     qsort(ord, (size_t)nC, sizeof(hid), hid_cmp);
@@ -828,7 +831,8 @@ static void search_one(const or_index *ix, const float *q, int ldq, const or_par
     if (p->mode == 1) {
         or_sign_codes(qr, 1, ix->Dp, qcode);
         int64_t P = p->patience_factor > 0 ? (int64_t)p->patience_factor * p->k : 0;
-        or_verify_opt(ix, qr, qcode, C, nC, p->k, p->eps0, P, ids, d2, &st->n_verified, &st->n_full);
+        or_verify_opt(ix, qr, qcode, C, nC, p->k, p->eps0, P, p->verify_order, ids, d2, &st->n_verified,
+                      &st->n_full);
     } else if (p->mode == 2) {
         /* learned depths: features -> MLP -> keep the first depth_V by (V desc,
          * id asc), coarse BF16 scores -> shortlist of depth_S -> FP32 re-rank */

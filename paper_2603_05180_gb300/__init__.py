@@ -42,7 +42,7 @@ class SearchParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("mode", C.c_int32), ("rho", C.c_double), ("alpha", C.c_double),
                 ("patience_factor", C.c_int32), ("eps0", C.c_float), ("max_candidates", C.c_int64),
                 ("precision", C.c_int32), ("shortlist", C.c_int32), ("depth_margin", C.c_float),
-                ("short_margin", C.c_float)]
+                ("short_margin", C.c_float), ("verify_order", C.c_int32), ("reserved", C.c_int32)]
 
 
 class QueryStats(C.Structure):
@@ -112,7 +112,7 @@ _SIGS = {
     "crisp_server_get_stats": [_P, C.POINTER(ServerStats)],
     "crisp_server_reset_stats": [_P],
     "crisp_server_replay": [_P, _P, _I32, _I64, _P, _P, _I32, _P, _P, _I32, _P, _P, _P, C.POINTER(C.c_double)],
-    "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _P, _P, _P, _P, _P, _P],
+    "crisp_verify_opt": [_P, _P, _I32, _P, _I64, _P, _I32, _F, _I64, _I32, _P, _P, _P, _P, _P, _P],
 }
 
 
@@ -340,9 +340,9 @@ CRISP_RERANK_NOALLOC_MAX = 4 * 1024 * 1024
 
 
 def crisp_verify_opt(index, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified=None,
-                     n_full=None, n_blocks=None, stream=None):
+                     n_full=None, n_blocks=None, stream=None, order=0):
     _call("crisp_verify_opt", index, _ptr(Qr), nq, _ptr(cand), cand_stride, _ptr(ncand), k, float(eps0), patience,
-          _ptr(ids), _ptr(sqdist), _ptr(n_verified), _ptr(n_full), _ptr(n_blocks), _stream(stream))
+          order, _ptr(ids), _ptr(sqdist), _ptr(n_verified), _ptr(n_full), _ptr(n_blocks), _stream(stream))
 
 
 # ------------------------------------------------------------ conveniences
@@ -361,9 +361,9 @@ def budget(rho: float, N: int) -> int:
 
 
 def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0, precision=0,
-                  shortlist=0, depth_margin=0.0, short_margin=0.0) -> SearchParams:
+                  shortlist=0, depth_margin=0.0, short_margin=0.0, verify_order=0) -> SearchParams:
     return SearchParams(k, mode, rho, alpha, patience_factor, eps0, max_candidates, precision, shortlist, depth_margin,
-                        short_margin)
+                        short_margin, verify_order, 0)
 
 
 def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None,

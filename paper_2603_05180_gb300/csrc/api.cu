@@ -27,7 +27,7 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
                                  const int64_t *S_per_query);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
-                                  int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
+                                  int32_t order, int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
                                   cudaStream_t st);
 
 crisp_status crisp_run_features(const crisp_index *ix, const int32_t *cand, int64_t stride, const int64_t *ncand,
@@ -306,6 +306,8 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     CRISP_REQUIRE(p->rho > 0.0 && p->rho <= 1.0, "crisp_search: rho outside (0, 1]");
     CRISP_REQUIRE(p->alpha >= 0.0 && p->alpha <= 1.0, "crisp_search: alpha outside [0, 1]");
     CRISP_REQUIRE(p->max_candidates == 0 || p->max_candidates >= p->k, "crisp_search: 0 < max_candidates < k");
+    CRISP_REQUIRE(p->verify_order == 0 || p->verify_order == 1, "crisp_search: verify_order must be 0 or 1");
+    CRISP_REQUIRE(p->reserved == 0, "crisp_search: reserved must be 0");
     CRISP_REQUIRE(p->max_candidates >= 0, "crisp_search: max_candidates < 0");
     CRISP_REQUIRE(p->precision >= 0 && p->precision <= 2, "crisp_search: precision must be 0, 1 or 2");
     if (p->precision > 0) {
@@ -447,8 +449,8 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
                 s = launch_write_stats(nc, ncand, how, retr, M, nullptr, nullptr, pl.tau, stats + c0, st);
         } else if (!s) {
             int64_t P = p->patience_factor > 0 ? (int64_t)p->patience_factor * pl.k : 0;
-            s = crisp_run_verify_opt(ix, Qr, nc, cand, pl.stride, ncand, pl.k, p->eps0, P, ids_c, d2_c, nver, nfull,
-                                     nullptr, st);
+            s = crisp_run_verify_opt(ix, Qr, nc, cand, pl.stride, ncand, pl.k, p->eps0, P, p->verify_order, ids_c,
+                                     d2_c, nver, nfull, nullptr, st);
             if (!s && stats) s = launch_write_stats(nc, ncand, how, retr, M, nver, nfull, pl.tau, stats + c0, st);
         }
     }

@@ -241,7 +241,7 @@ extern "C" crisp_status crisp_server_create(const crisp_index *ix, const crisp_s
 }
 
 // The parameter struct has no padding, so equal parameters are equal bytes.
-static_assert(sizeof(crisp_search_params) == 56, "crisp_search_params has padding");
+static_assert(sizeof(crisp_search_params) == 64, "crisp_search_params has padding");
 
 static crisp_status submit_at(crisp_server *sv, const float *q, const crisp_search_params *p, Clock::time_point t_arrive,
                               uint64_t *ticket) {

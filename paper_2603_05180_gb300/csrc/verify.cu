@@ -62,7 +62,7 @@ __device__ __forceinline__ int first_prune(const float *cs, const float *ft, int
 __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__restrict__ Qr, int nq,
                                                       const int *__restrict__ cand, long long stride,
                                                       const long long *__restrict__ ncand, int kk, float eps0,
-                                                      long long patience, int cap_keys,
+                                                      long long patience, int order, int cap_keys,
                                                       long long *__restrict__ out_ids, float *__restrict__ out_d,
                                                       long long *__restrict__ out_nver, long long *__restrict__ out_nfull,
                                                       long long *__restrict__ out_nblk) {
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
             h += __shfl_xor_sync(gmask, h, 4);
             h += __shfl_xor_sync(gmask, h, 2);
             h += __shfl_xor_sync(gmask, h, 1);
-            if (l == 0) keys[i] = ((uint32_t)h << 15) | (uint32_t)i;
+            if (l == 0) keys[i] = ((uint32_t)(order ? 0 : h) << 15) | (uint32_t)i;   // order 1: ids only
         }
     }
     for (long long i = n + tid; i < npow; i += VO_NT) keys[i] = 0xFFFFFFFFu;
@@ -268,6 +268,7 @@ size_t vo_smem(const crisp_index *ix, int cap_keys) {
 
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
+                                  int32_t order,
                                   int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
                                   cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
@@ -292,7 +293,7 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
     size_t smem = vo_smem(ix, cap_keys);
     CRISP_CK(cudaFuncSetAttribute(k_verify_opt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_verify_opt<<<nq, VO_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
-                                          eps0, (long long)patience, cap_keys, (long long *)ids, d2,
+                                          eps0, (long long)patience, order, cap_keys, (long long *)ids, d2,
                                           (long long *)nver, (long long *)nfull, (long long *)nblk);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
@@ -301,12 +302,13 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
 
 extern "C" crisp_status crisp_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                          int64_t cand_stride, const int64_t *ncand, int32_t k, float eps0,
-                                         int64_t patience, int64_t *ids, float *sqdist, int64_t *n_verified,
-                                         int64_t *n_full, int64_t *n_blocks, void *stream) {
+                                         int64_t patience, int32_t order, int64_t *ids, float *sqdist,
+                                         int64_t *n_verified, int64_t *n_full, int64_t *n_blocks, void *stream) {
     CRISP_REQUIRE(ix != nullptr, "null index");
     CRISP_REQUIRE(nq >= 0 && k >= 1 && k <= CRISP_KOUT_MAX, "crisp_verify_opt: bad nq or k");
     CRISP_REQUIRE(nq == 0 || (Qr && cand && ncand && ids && sqdist), "crisp_verify_opt: null pointer");
     CRISP_REQUIRE(cand_stride >= 1, "crisp_verify_opt: cand_stride < 1");
-    return crisp_run_verify_opt(ix, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, ids, sqdist, n_verified,
+    CRISP_REQUIRE(order == 0 || order == 1, "crisp_verify_opt: order must be 0 (Hamming) or 1 (id)");
+    return crisp_run_verify_opt(ix, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, order, ids, sqdist, n_verified,
                                 n_full, n_blocks, as_stream(stream));
 }

@@ -198,7 +198,8 @@ def test_q6_rerank_bitexact(c1, k):
 
 @pytest.mark.parametrize("k,eps0,P", [(10, 2.1, 400), (10, 0.0, 400), (10, float("inf"), 0), (1, 2.1, 1),
                                       (100, 2.1, 4000), (10, 1.0, 20)])
-def test_q7_optimized_verification_bitexact(c1, k, eps0, P):
+@pytest.mark.parametrize("order", [0, 1])
+def test_q7_optimized_verification_bitexact(c1, k, eps0, P, order):
     X, Q, ix_o, ix = c1
     p = oracle.SearchParams(k=k, mode=1, rho=0.03, alpha=0.25)
     cand, ncand, _, _ = _count_case(ix_o, ix, Q, p, with_score=False)
@@ -208,11 +209,11 @@ def test_q7_optimized_verification_bitexact(c1, k, eps0, P):
     d2 = empty((nq, k), torch.float32)
     nv = empty((nq,), torch.int64)
     nf = empty((nq,), torch.int64)
-    crisp.crisp_verify_opt(ix, Qr, nq, dev(cand), cand.shape[1], dev(ncand), k, eps0, P, ids, d2, nv, nf)
+    crisp.crisp_verify_opt(ix, Qr, nq, dev(cand), cand.shape[1], dev(ncand), k, eps0, P, ids, d2, nv, nf, order=order)
     ids, d2, nv, nf = (t.cpu().numpy() for t in (ids, d2, nv, nf))
     qr = oracle.query_rotate(ix_o, Q)
     for i in range(nq):
-        oi, od, onv, onf = oracle.verify_opt(ix_o, qr[i], cand[i, :ncand[i]], k, eps0, P)
+        oi, od, onv, onf = oracle.verify_opt(ix_o, qr[i], cand[i, :ncand[i]], k, eps0, P, order=order)
         assert np.array_equal(ids[i], oi) and np.array_equal(d2[i], od), i
         assert (nv[i], nf[i]) == (onv, onf), (i, nv[i], nf[i], onv, onf)
 
@@ -225,6 +226,7 @@ SEARCH_CASES = [
     dict(k=100, mode=1, rho=0.03, alpha=0.25, patience_factor=20),
     dict(k=5, mode=0, rho=0.002, alpha=1.0),
     dict(k=10, mode=1, rho=0.04, alpha=0.125, max_candidates=400),
+    dict(k=10, mode=1, rho=0.03, alpha=0.25, verify_order=1),
 ]
 
 
@@ -304,6 +306,7 @@ def test_search_edge_cases():
 
 
 @pytest.mark.parametrize("kw", [dict(k=0), dict(k=257), dict(mode=2), dict(rho=0.0), dict(rho=1.5), dict(alpha=-0.1),
+                                dict(mode=1, verify_order=2),
                                 dict(alpha=1.1), dict(k=10, max_candidates=5)])
 def test_invalid_params_raise_and_write_nothing(c1, kw):
     X, Q, ix_o, ix = c1
@@ -320,9 +323,9 @@ def test_invalid_params_raise_and_write_nothing(c1, kw):
 # ------------------------------------------------ large batches (grouped scoring)
 @pytest.fixture(scope="module")
 def c1_big():
-    """The parity index with 640 queries of the same law: batches this large are
-    scored in MinHash-ordered query groups (each row read once per group)."""
-    X, Q = synthetic.gmm(nq=640)
+    """The parity index with 1,100 queries of the same law: batches this large
+    are scored in MinHash-ordered query groups (each row read once per group)."""
+    X, Q = synthetic.gmm(nq=1100)
     ix_o = oracle.build_index(X, M=8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=0)).add_copies()
     ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
     crisp.crisp_index_add_copies(ix, 3)
@@ -366,7 +369,7 @@ def test_large_batch_rerank_and_shortlist_steps(c1_big):
     crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 1, 30, sl, 64, nsl)
     gi, gd, gs, gns = ids.cpu().numpy(), d2.cpu().numpy(), sl.cpu().numpy(), nsl.cpu().numpy()
     Xb = oracle.quantize_bf16(ix_o.Xr)
-    for q in range(0, nq, 37):
+    for q in range(0, nq, 53):
         cq = c[q, :n[q]].astype(np.int64)
         ri, rd = oracle.rerank(ix_o, Qr_h[q], cq, 10)
         assert np.array_equal(gi[q], ri) and np.array_equal(gd[q], rd), q

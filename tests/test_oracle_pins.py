@@ -415,6 +415,34 @@ def test_verify_opt_patience_hand_example():
     assert ids[0] == int(g["best_P1"][0]) and nv == int(g["processed_P1"][0])
 
 
+def test_verify_opt_id_order_hand_example():
+    """The ablation without Hamming re-ranking (order 1) verifies in id order.
+    The rows of the hand example get their distances back, but now their
+    Hamming distances fall with the id (row r has 4 - r dims flipped), so only
+    order 1 walks them 0, 1, 2, 3, 4 as the hand-worked results assume; order
+    0 walks them the other way round."""
+    g = load_golden("verify_opt_tiny.txt")
+    D = 32
+    rows = []
+    for r, tgt in enumerate(float(v) for v in g["targets"]):
+        x = np.ones(D, np.float32)
+        nneg = 4 - r
+        x[:nneg] = -0.0
+        x[D - 1] = 1.0 + math.sqrt(tgt - nneg)
+        rows.append(x)
+    ix = _opt_index(D, rows)
+    q = np.ones(32, np.float32)
+    C = np.arange(5, dtype=np.int32)
+    ids, d2, nv, nf = oracle.verify_opt(ix, q, C, 1, float("inf"), 2, order=1)
+    assert ids[0] == int(g["best_P2"][0]) and nv == 5
+    ids, d2, nv, nf = oracle.verify_opt(ix, q, C, 1, float("inf"), 1, order=1)
+    assert ids[0] == int(g["best_P1"][0]) and nv == int(g["processed_P1"][0])
+    # exhaustive verification does not depend on the order
+    a = oracle.verify_opt(ix, q, C, 3, float("inf"), 0, order=0)
+    b = oracle.verify_opt(ix, q, C, 3, float("inf"), 0, order=1)
+    assert a[0].tolist() == b[0].tolist() and a[1].tolist() == b[1].tolist()
+
+
 def test_verify_opt_adsampling_prune_hand_example():
     D = 64
     a = np.ones(D, np.float32)
