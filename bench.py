@@ -652,6 +652,9 @@ def serving_leg(args, torch, crisp, synthetic, dev):
     return out
 
 
+TAU_POINTS = {"low": dict(rho=0.02, alpha=0.25), "high": dict(rho=0.1, alpha=0.2)}
+
+
 def run_ablation(args):
     """The paper's ablations (§6, "Ablation Study") on the synthetic workloads:
     (1) the rotation threshold tau_CEV: per dataset its CEV, and recall@100 and
@@ -702,15 +705,17 @@ def run_ablation(args):
         for rot in (0, 1):
             ix = crisp.crisp_build(X, N, D, crisp.build_params(M, rotate=rot, draws=synthetic.method_draws(N, D, M, 50)))
             cev = ix.info().cev
-            res[rot] = measure(ix, X, Q, gd, crisp.search_params(k=100, mode=0, rho=0.02, alpha=0.25), 100)
+            res[rot] = {pname: measure(ix, X, Q, gd, crisp.search_params(k=100, mode=0, **pt), 100)
+                        for pname, pt in TAU_POINTS.items()}
             ix.free()
         rows.append({"dataset": name, "N": N, "D": D, "M": M, "cev": cev, "no_rotation": res[0], "rotation": res[1]})
-    out["tau_cev"] = {"point": "Guaranteed, k=100, rho=0.02, alpha=0.25, 1,000 queries", "datasets": rows,
+    out["tau_cev"] = {"points": {k: f"Guaranteed, k=100, rho={v['rho']}, alpha={v['alpha']}, 1,000 queries"
+                                 for k, v in TAU_POINTS.items()}, "datasets": rows,
                       "by_threshold": [{"tau_cev": t,
                                         "rotated": [r["dataset"] for r in rows if r["cev"] > t],
-                                        "mean_recall_at_100": float(np.mean([(r["rotation"] if r["cev"] > t else
-                                                                              r["no_rotation"])["recall"]
-                                                                             for r in rows]))}
+                                        **{f"mean_recall_at_100_{pn}": float(np.mean(
+                                            [(r["rotation"] if r["cev"] > t else r["no_rotation"])[pn]["recall"]
+                                             for r in rows])) for pn in TAU_POINTS}}
                                        for t in (0.7, 0.75, 0.8, 0.85, 0.9, 0.95)]}
     del sets, Xp, Qp
     torch.cuda.empty_cache()
