@@ -42,8 +42,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "QPS at recall@10≥0.95 on 1 GB300 (plain FP32 vs learned+BF16), % HBM peak, p99 ms"
-WORKLOAD = ("powerlaw N=1,000,000 D=960 (lambda_i = i^-1.2, Haar mix), 10,000 held-out queries, k=10, "
-            "M=20 subspaces, K=50 centroids per half")
+def workload_name(args):
+    return (f"powerlaw N={args.n:,} D={args.dim} (lambda_i = i^-1.2, Haar mix), {args.nq:,} held-out queries, "
+            f"k={args.k}, M={args.M} subspaces, K=50 centroids per half")
 # operating point of the plain FP32 engine on this workload (recall@10 >= 0.95)
 DEFAULT_POINT = dict(mode=0, rho=0.03, alpha=0.3)
 
@@ -227,7 +228,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, **point, "k": args.k},
+            "config": {"workload": workload_name(args), **point, "k": args.k},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -358,9 +359,10 @@ def run_crisp(args):
     sl_stage = stage.pop("shortlist_bf16", None)
     shares = {n: v["ms"] for n, v in stage.items()}
     dom = max((n for n in stage if stage[n]["bytes"]), key=lambda n: stage[n]["ms"])
+    traffic_key = {"N": N, "D": D, "nq": nq, "M": args.M, "rho": point["rho"], "alpha": point["alpha"]}
     dbytes, dms = stage[dom]["bytes"], stage[dom]["ms"]
     achieved = dbytes / (dms / 1e3) / 1e9
-    traffic = _ncu_traffic(dom)
+    traffic = _ncu_traffic(dom, traffic_key)
     roofline = {"kernel": stage[dom]["kernel"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "dram_gbs": traffic / (dms / 1e3) / 1e9 if traffic else None,
@@ -375,7 +377,7 @@ def run_crisp(args):
     if sl_stage:
         a_bf = sl_stage["bytes"] / (sl_stage["ms"] / 1e3) / 1e9
         roofline_bf16 = {"kernel": sl_stage["kernel"], "bound": "hbm", "achieved": a_bf, "peak": peak, "unit": "GB/s",
-                         "frac": a_bf / peak, "traffic": _ncu_traffic("shortlist_bf16"),
+                         "frac": a_bf / peak, "traffic": _ncu_traffic("shortlist_bf16", traffic_key),
                          "ms": round(sl_stage["ms"], 4), "algorithmic_bytes_per_launch": sl_stage["bytes"],
                          "note": "BF16 coarse scoring of the same candidates (the learned+BF16 path's dominant "
                                  "kernel), shortlist of 50, timed on its own"}
@@ -439,7 +441,7 @@ def run_crisp(args):
         line = {"metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": N, "D": D, "nq": nq, "k": k, "M": args.M, "K": 50,
+                "config": {"workload": workload_name(args), "N": N, "D": D, "nq": nq, "k": k, "M": args.M, "K": 50,
                            "mode": mode_name, "rho": point["rho"], "alpha": point["alpha"],
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed before every timed step (512 MB write, outside the timed events)",
@@ -831,14 +833,16 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     return out
 
 
-def _ncu_traffic(stage):
-    """DRAM bytes per launch from the committed ncu summary, when one exists for this kernel."""
+def _ncu_traffic(stage, workload):
+    """DRAM bytes per launch from the committed ncu summary, when one exists for
+    this kernel and was taken on this workload (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        v = d.get(stage)
-        return v
+        if d.get("workload") != workload:
+            return None
+        return d.get("bytes_per_launch", {}).get(stage)
     return None
 
 

@@ -1110,7 +1110,7 @@ constexpr int SCH_MAXQ = 32768;     // the ordering sorts 15-bit query numbers i
 constexpr int GS_MINQ = 1024;       // batches smaller than this stream per query
 constexpr int GS_MINSTRIDE = 2048;  // so do short candidate lists (shortlists)
 constexpr int GU_NT = 256;
-constexpr int GK_NT = 1024;
+constexpr int GK_NT = 768;        // 24 warps: 80 registers a thread, no spills
 
 // key[q] = (min over the candidates of a 24-bit multiplicative hash of the id,
 // clamped to 17 bits) << 15 | q: one block per query.
@@ -1318,63 +1318,52 @@ __device__ __forceinline__ void row_load_lb(uint4 (&v)[8], const IxView &ix, lon
     }
 }
 
-// CR32 block sum of this lane's block against query q (swizzled in shared memory).
-template <int PREC>
-__device__ __forceinline__ float block_sum_lb(const uint4 (&v)[8], const float4 *q, int nb) {
+// BF16 row slice widened to FP32 once per row (exact): xr[8 h + 2 i] and
+// xr[8 h + 2 i + 1] are the low and high halves of word i of v[h].
+__device__ __forceinline__ void widen_bf16(const uint4 (&v)[8], float (&xr)[32]) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const unsigned w[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xr[8 * h + 2 * i] = __uint_as_float(w[i] << 16);
+            xr[8 * h + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+    }
+}
+
+// CR32 block sum of this lane's widened BF16 block against query q (swizzled).
+__device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const float4 *q, int nb) {
     const int lane = threadIdx.x & 31;
     if (lane >= nb) return 0.0f;
     const float4 *qb = q + 8 * lane;
     const int sw = lane & 7;
     float a[8];
-    if (PREC == 0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const float4 qq = qb[u ^ sw];
-            float x = 0.0f, t;
-            t = __uint_as_float(v[u].x) - qq.x;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[u].y) - qq.y;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[u].z) - qq.z;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[u].w) - qq.w;
-            x = fmaf(t, t, x);
-            a[u] = x;
-        }
-    } else {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {                       // 16 bytes = lane partials 2h, 2h+1
-            const float4 q0 = qb[(2 * h) ^ sw], q1 = qb[(2 * h + 1) ^ sw];
-            const unsigned w0 = v[h].x, w1 = v[h].y, w2 = v[h].z, w3 = v[h].w;
-            float x = 0.0f, y = 0.0f, t;
-            t = __uint_as_float(w0 << 16) - q0.x;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(w0 & 0xFFFF0000u) - q0.y;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(w1 << 16) - q0.z;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(w1 & 0xFFFF0000u) - q0.w;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(w2 << 16) - q1.x;
-            y = fmaf(t, t, y);
-            t = __uint_as_float(w2 & 0xFFFF0000u) - q1.y;
-            y = fmaf(t, t, y);
-            t = __uint_as_float(w3 << 16) - q1.z;
-            y = fmaf(t, t, y);
-            t = __uint_as_float(w3 & 0xFFFF0000u) - q1.w;
-            y = fmaf(t, t, y);
-            a[2 * h] = x;
-            a[2 * h + 1] = y;
-        }
+    for (int u = 0; u < 8; ++u) {
+        const float4 qq = qb[u ^ sw];
+        float x = 0.0f, t;
+        t = xr[4 * u] - qq.x;
+        x = fmaf(t, t, x);
+        t = xr[4 * u + 1] - qq.y;
+        x = fmaf(t, t, x);
+        t = xr[4 * u + 2] - qq.z;
+        x = fmaf(t, t, x);
+        t = xr[4 * u + 3] - qq.w;
+        x = fmaf(t, t, x);
+        a[u] = x;
     }
     return block_tree(a);
 }
 
 // Warp layout for FP32 rows: lane l holds dims 128 c + 4 l (8 x 16 bytes,
-// coalesced).  The CR32 terms of one query come in phases that keep the chains
-// independent: all lane partials, then each level of the xor tree across the
-// chunks, then the block sums gathered and added in block order.  The query is
-// read from a plain (unswizzled) shared copy.
+// coalesced), i.e. lane partial l & 7 of block 4 c + (l >> 3).  The query is read
+// from a plain (unswizzled) shared copy.  The CR32 reduction goes through the
+// warp's shared scratch tp[288] instead of shuffles: the partials land at
+// tp[8 block + partial], lane b reads block b's eight partials (halves swapped
+// on lanes with bit 2 set, so a quarter-warp touches 32 distinct banks), adds
+// them in the xor-tree order, and the block sums are summed in block order from
+// tp[256..288) by every lane.
 __device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -1384,9 +1373,8 @@ __device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long
     }
 }
 
-__device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q4, int Dp) {
+__device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q4, int Dp, float *tp) {
     const int lane = threadIdx.x & 31;
-    float a[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int d = c * 128 + 4 * lane;
@@ -1402,35 +1390,42 @@ __device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q
             t = __uint_as_float(v[c].w) - qq.w;
             x = fmaf(t, t, x);
         }
-        a[c] = x;
+        tp[32 * c + lane] = x;
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 4);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 2);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = a[c] + __shfl_xor_sync(0xffffffffu, a[c], 1);
+    __syncwarp();
+    // h0/h1 are partials 0..3 and 4..7, or 4..7 and 0..3 on the swapped lanes:
+    // the tree adds p and p + 4 first, and IEEE addition commutes, so the same
+    // expression gives the same block sum either way
+    const int sw = (lane >> 2) & 1;
+    const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
+    const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
+    tp[256 + lane] = ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
+    __syncwarp();
+    // blocks at or past Dp / 32 sum to +0, and acc >= +0 (or NaN), so adding
+    // all 32 block sums leaves acc as the sum over the first Dp / 32
+    const float4 *sb4 = reinterpret_cast<const float4 *>(tp + 256);
     float acc = 0.0f;
-    const int nb = Dp >> 5;
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-#pragma unroll
-        for (int gq = 0; gq < 4; ++gq) {
-            const float sbv = __shfl_sync(0xffffffffu, a[c], 8 * gq);
-            if (4 * c + gq < nb) acc = acc + sbv;
-        }
+    for (int b4 = 0; b4 < 8; ++b4) {
+        const float4 t4 = sb4[b4];
+        acc = acc + t4.x;
+        acc = acc + t4.y;
+        acc = acc + t4.z;
+        acc = acc + t4.w;
+    }
     return acc;
 }
 
-// Persistent: CTAs take (group, range) items in order; warps take the item's
-// rows (lane-per-block layout) and score each against its members.
+// Persistent: CTAs take (range, group) items in order; warps take the item's
+// rows and score each against its members.
 template <int PREC>
 __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
                                                     GUnion u, float *__restrict__ dbuf) {
     extern __shared__ __align__(16) float4 gq4[];                // [GS_G][Dp / 4], swizzled per block
     __shared__ long long s_it;
     __shared__ int s_mem[GS_G];
-    __shared__ __align__(16) float s_bs[GK_NT / 32][2][32];      // block sums, two buffers per warp
+    // per warp: BF16 block sums (two buffers), FP32 CR32 partials and block sums
+    __shared__ __align__(16) float s_bs[GK_NT / 32][PREC == 0 ? 288 : 64];
     const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ngroups = (u.nq + GS_G - 1) / GS_G;
     const long long items = (long long)ngroups * u.R;
@@ -1440,7 +1435,9 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         __syncthreads();
         const long long it = s_it;
         if (it >= items) break;
-        const int g = (int)(it / u.R);
+        // range-major: the CTAs in flight score the same GS_SPAN rows for
+        // different groups, so a row comes from DRAM about once per batch
+        const int g = (int)(it % ngroups), r = (int)(it / ngroups);
         const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
         if (g != cur_g) {
             if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GS_G + threadIdx.x];
@@ -1455,13 +1452,15 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             cur_g = g;
         }
         __syncthreads();
-        const int2 itm = u.items[it];
+        const int2 itm = u.items[(long long)g * u.R + r];
         const int e0 = itm.x, ne = itm.y;
         uint4 v[8];
         int buf = 0;
         for (int e = warp; e < ne; e += GK_NT / 32) {
             if (PREC == 0) row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
             else row_load_lb<PREC>(v, ix, (long long)u.ent_row[e0 + e], nb);
+            float xr[32];
+            if (PREC == 1) widen_bf16(v, xr);
             const unsigned m0 = u.ent_mask[e0 + e];
             const int pb = u.ent_pb[e0 + e];
             unsigned m = m0;
@@ -1470,22 +1469,22 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
                 if (PREC == 0) {
-                    const float acc = row_cr32_w(v, gq4 + (size_t)j * (Dp >> 2), Dp);
+                    const float acc = row_cr32_w(v, gq4 + (size_t)j * (Dp >> 2), Dp, s_bs[warp]);
                     if (lane == i) mine = acc;
                     continue;
                 }
-                const float bs = block_sum_lb<PREC>(v, gq4 + (size_t)j * (Dp >> 2), nb);
-                s_bs[warp][buf][lane] = bs;
+                const float bs = block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb);
+                s_bs[warp][32 * buf + lane] = bs;
                 __syncwarp();
                 float acc = 0.0f;
-                const float4 *sb4 = reinterpret_cast<const float4 *>(s_bs[warp][buf]);
+                const float4 *sb4 = reinterpret_cast<const float4 *>(s_bs[warp] + 32 * buf);
 #pragma unroll
-                for (int b4 = 0; b4 < 8; ++b4) {
+                for (int b4 = 0; b4 < 8; ++b4) {     // lanes >= nb hold +0 (see row_cr32_w)
                     const float4 t4 = sb4[b4];
-                    if (4 * b4 < nb) acc = acc + t4.x;
-                    if (4 * b4 + 1 < nb) acc = acc + t4.y;
-                    if (4 * b4 + 2 < nb) acc = acc + t4.z;
-                    if (4 * b4 + 3 < nb) acc = acc + t4.w;
+                    acc = acc + t4.x;
+                    acc = acc + t4.y;
+                    acc = acc + t4.z;
+                    acc = acc + t4.w;
                 }
                 if (lane == i) mine = acc;
                 buf ^= 1;
