@@ -1110,7 +1110,8 @@ constexpr int SCH_MAXQ = 32768;     // the ordering sorts 15-bit query numbers i
 constexpr int GS_MINQ = 1024;       // batches smaller than this stream per query
 constexpr int GS_MINSTRIDE = 2048;  // so do short candidate lists (shortlists)
 constexpr int GU_NT = 256;
-constexpr int GK_NT = 768;        // 24 warps: 80 registers a thread, no spills
+// scorer CTA: 24 warps, 80 registers a thread at most, no spills
+constexpr int GK_NT = 768;
 
 // key[q] = (min over the candidates of a 24-bit multiplicative hash of the id,
 // clamped to 17 bits) << 15 | q: one block per query.
@@ -1192,11 +1193,20 @@ struct GUnion {
     int R, nq;
 };
 
+// Entry bucket of a member mask: 33 * lowest member + next member (32 if none).
+constexpr int GU_NBK = 32 * 33;
+__device__ __forceinline__ int gu_bucket(unsigned m) {
+    const int lo = __ffs(m) - 1;
+    const unsigned rest = m & (m - 1);
+    return 33 * lo + (rest ? __ffs(rest) - 1 : 32);
+}
+
 // One block per (range r, group g): the group's candidates in the range, their
 // rows' member masks, and the pair slots.
 __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, long long stride, GUnion u) {
     __shared__ unsigned mask[GS_SPAN];
     __shared__ int pbl[GS_SPAN];
+    __shared__ int bk[GU_NBK];
     __shared__ int s_q[GS_G], s_base[GS_G], s_off[GS_G + 1];
     __shared__ long long scan_ws[GU_NT / 32 + 1];
     __shared__ long long s_eb, s_pb;
@@ -1262,21 +1272,46 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
     }
     __syncthreads();
     if (s_eb < 0) return;
-    // entries (recomputing each row's entry number with the same scan)
-    carry = 0;
-    for (int o0 = 0; o0 < GS_SPAN; o0 += GU_NT) {
-        const int o = o0 + threadIdx.x;
+    // entries, bucketed by (lowest member, next member): rows that share their
+    // first members sit next to each other, so the scorer's row pairs can share
+    // query loads.  The order inside a bucket is arbitrary (every pair has its
+    // own slot, so results do not depend on it).
+    for (int i = threadIdx.x; i < GU_NBK; i += GU_NT) bk[i] = 0;
+    __syncthreads();
+    for (int o = threadIdx.x; o < GS_SPAN; o += GU_NT) {
         const unsigned m = mask[o];
-        const int c = __popc(m);
+        if (m) atomicAdd(&bk[gu_bucket(m)], 1);
+    }
+    __syncthreads();
+    {
+        constexpr int PER = (GU_NBK + GU_NT - 1) / GU_NT;
+        int loc[PER], sum = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x * PER + k;
+            loc[k] = i < GU_NBK ? bk[i] : 0;
+            sum += loc[k];
+        }
         long long tot;
-        const long long ex = block_excl_scan<GU_NT>(c > 0 ? 1 : 0, scan_ws, &tot);
-        if (c > 0) {
-            const long long ei = s_eb + carry + ex;
+        int run = (int)block_excl_scan<GU_NT>(sum, scan_ws, &tot);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x * PER + k;
+            if (i < GU_NBK) {
+                bk[i] = run;
+                run += loc[k];
+            }
+        }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < GS_SPAN; o += GU_NT) {
+        const unsigned m = mask[o];
+        if (m) {
+            const long long ei = s_eb + atomicAdd(&bk[gu_bucket(m)], 1);
             u.ent_row[ei] = (int)(lo_id + o);
             u.ent_mask[ei] = m;
             u.ent_pb[ei] = (int)(s_pb + pbl[o]);
         }
-        carry += tot;
     }
     // pair slots: member j of row o goes to slot first(o) + (members of o below j)
     for (int e = threadIdx.x; e < np; e += GU_NT) {
@@ -1358,12 +1393,12 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 
 // Warp layout for FP32 rows: lane l holds dims 128 c + 4 l (8 x 16 bytes,
 // coalesced), i.e. lane partial l & 7 of block 4 c + (l >> 3).  The query is read
-// from a plain (unswizzled) shared copy.  The CR32 reduction goes through the
-// warp's shared scratch tp[288] instead of shuffles: the partials land at
-// tp[8 block + partial], lane b reads block b's eight partials (halves swapped
-// on lanes with bit 2 set, so a quarter-warp touches 32 distinct banks), adds
-// them in the xor-tree order, and the block sums are summed in block order from
-// tp[256..288) by every lane.
+// from a plain (unswizzled) shared copy.  The partials are transposed through
+// the warp's shared scratch tp[256] instead of shuffles: they land at
+// tp[8 block + partial], and lane b reads block b's eight partials (halves
+// swapped on lanes with bit 2 set, so a quarter-warp touches 32 distinct banks)
+// and adds them in the xor-tree order.  Returns the sum of block `lane` (+0 for
+// blocks at or past Dp / 32).
 __device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -1399,37 +1434,52 @@ __device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q
     const int sw = (lane >> 2) & 1;
     const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
     const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
-    tp[256 + lane] = ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
-    __syncwarp();
-    // blocks at or past Dp / 32 sum to +0, and acc >= +0 (or NaN), so adding
-    // all 32 block sums leaves acc as the sum over the first Dp / 32
-    const float4 *sb4 = reinterpret_cast<const float4 *>(tp + 256);
-    float acc = 0.0f;
-#pragma unroll
-    for (int b4 = 0; b4 < 8; ++b4) {
-        const float4 t4 = sb4[b4];
-        acc = acc + t4.x;
-        acc = acc + t4.y;
-        acc = acc + t4.z;
-        acc = acc + t4.w;
-    }
-    return acc;
+    return ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
 }
 
-// Persistent: CTAs take (range, group) items in order; warps take the item's
-// rows and score each against its members.
+// Batched gather of the block sums: each scored (row, member) pair leaves its
+// 32 block sums as one row of the warp's gather buffer (row stride GB_LD, so a
+// column read by 32 lanes hits 32 banks); once GB_K pairs are pending, lane p
+// adds row p in block order and stores pair p's distance.
+constexpr int GB_K = 16;
+constexpr int GB_LD = 33;
+// per-warp scratch: FP32 partials, then the gather rows
+template <int PREC> __host__ __device__ constexpr int gw_floats() { return (PREC == 0 ? 256 : 0) + GB_K * GB_LD; }
+
 template <int PREC>
 __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
                                                     GUnion u, float *__restrict__ dbuf) {
-    extern __shared__ __align__(16) float4 gq4[];                // [GS_G][Dp / 4], swizzled per block
+    constexpr int NT = GK_NT, NW = GK_NT / 32;
+    // [GS_G][Dp / 4] query copies (swizzled per block for BF16), then gw_floats per warp
+    extern __shared__ __align__(16) float4 gq4[];
     __shared__ long long s_it;
     __shared__ int s_mem[GS_G];
-    // per warp: BF16 block sums (two buffers), FP32 CR32 partials and block sums
-    __shared__ __align__(16) float s_bs[GK_NT / 32][PREC == 0 ? 288 : 64];
     const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tp = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
+    float *gb = tp + (PREC == 0 ? 256 : 0);
     const int ngroups = (u.nq + GS_G - 1) / GS_G;
     const long long items = (long long)ngroups * u.R;
     int cur_g = -1;
+    int npend = 0, pj = 0, ppos = 0;     // pending pairs; lane p < npend: member and list position of pair p
+    // one scored pair: its block sums become gather row npend
+    auto push = [&](float bs, int j, int slot) {
+        gb[npend * GB_LD + lane] = bs;
+        if (lane == npend) {
+            pj = j;
+            ppos = u.pair_pos[slot];
+        }
+        __syncwarp();                   // partial reads and gather writes done before reuse
+        if (++npend == GB_K) {
+            if (lane < npend) {
+                const float *row = gb + lane * GB_LD;
+                float acc = 0.0f;
+                for (int b = 0; b < nb; ++b) acc = acc + row[b];
+                dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+            }
+            __syncwarp();
+            npend = 0;
+        }
+    };
     for (;;) {
         if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
         __syncthreads();
@@ -1443,7 +1493,7 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GS_G + threadIdx.x];
             __syncthreads();
             const int n4 = Dp >> 2;
-            for (int e = threadIdx.x; e < gsize * n4; e += GK_NT) {
+            for (int e = threadIdx.x; e < gsize * n4; e += NT) {
                 const int j = e / n4, f = e % n4, b = f >> 3, uu = f & 7;
                 // BF16 (lane-per-block) reads a swizzled copy, FP32 (warp layout) a plain one
                 gq4[(size_t)j * n4 + (PREC == 0 ? f : 8 * b + (uu ^ (b & 7)))] =
@@ -1455,8 +1505,7 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         const int2 itm = u.items[(long long)g * u.R + r];
         const int e0 = itm.x, ne = itm.y;
         uint4 v[8];
-        int buf = 0;
-        for (int e = warp; e < ne; e += GK_NT / 32) {
+        for (int e = warp; e < ne; e += NW) {
             if (PREC == 0) row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
             else row_load_lb<PREC>(v, ix, (long long)u.ent_row[e0 + e], nb);
             float xr[32];
@@ -1464,39 +1513,21 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             const unsigned m0 = u.ent_mask[e0 + e];
             const int pb = u.ent_pb[e0 + e];
             unsigned m = m0;
-            float mine = 0.0f;
             for (int i = 0; m; ++i) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
-                if (PREC == 0) {
-                    const float acc = row_cr32_w(v, gq4 + (size_t)j * (Dp >> 2), Dp, s_bs[warp]);
-                    if (lane == i) mine = acc;
-                    continue;
-                }
-                const float bs = block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb);
-                s_bs[warp][32 * buf + lane] = bs;
-                __syncwarp();
-                float acc = 0.0f;
-                const float4 *sb4 = reinterpret_cast<const float4 *>(s_bs[warp] + 32 * buf);
-#pragma unroll
-                for (int b4 = 0; b4 < 8; ++b4) {     // lanes >= nb hold +0 (see row_cr32_w)
-                    const float4 t4 = sb4[b4];
-                    acc = acc + t4.x;
-                    acc = acc + t4.y;
-                    acc = acc + t4.z;
-                    acc = acc + t4.w;
-                }
-                if (lane == i) mine = acc;
-                buf ^= 1;
-            }
-            const int n = __popc(m0);
-            if (lane < n) {
-                unsigned mm = m0;
-                for (int k = 0; k < lane; ++k) mm &= mm - 1;
-                const int j = __ffs(mm) - 1;
-                dbuf[(long long)s_mem[j] * stride + u.pair_pos[pb + lane]] = mine;
+                const float4 *qj = gq4 + (size_t)j * (Dp >> 2);
+                push(PREC == 0 ? row_cr32_w(v, qj, Dp, tp) : block_sum_lb_w(xr, qj, nb), j, pb + i);
             }
         }
+        if (lane < npend) {                     // the item's last pairs (s_mem changes with the group)
+            const float *row = gb + lane * GB_LD;
+            float acc = 0.0f;
+            for (int b = 0; b < nb; ++b) acc = acc + row[b];
+            dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+        }
+        __syncwarp();
+        npend = 0;
         __syncthreads();
     }
 }
@@ -1553,7 +1584,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
         CRISP_COUNT_LAUNCH();
         k_gunion<<<dim3(R, ngroups), GU_NT, 0, st>>>(cand, (long long)stride, u);
         CRISP_COUNT_LAUNCH();
-        const size_t smem = sizeof(float) * (size_t)GS_G * ix->Dp;
+        const size_t smem = sizeof(float) * ((size_t)GS_G * ix->Dp + (size_t)(GK_NT / 32) * gw_floats<PREC>());
         e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
         int dev = 0, sms = 152;
