@@ -1344,9 +1344,10 @@ __device__ __forceinline__ void row_load_lb(uint4 (&v)[8], const IxView &ix, lon
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        if (lane < nb && (PREC == 0 || u < 4)) {
+        if (lane < nb && (PREC == 0 || (PREC == 1 && u < 4) || (PREC == 2 && u < 2))) {
             if (PREC == 0) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * ix.Dp + 32 * lane + 4 * u));
-            else v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xb + id * ix.Dp + 32 * lane + 8 * u));
+            else if (PREC == 1) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xb + id * ix.Dp + 32 * lane + 8 * u));
+            else v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.X8 + id * ix.Dp + 32 * lane + 16 * u));
         } else {
             v[u] = make_uint4(0, 0, 0, 0);
         }
@@ -1367,7 +1368,24 @@ __device__ __forceinline__ void widen_bf16(const uint4 (&v)[8], float (&xr)[32])
     }
 }
 
-// CR32 block sum of this lane's widened BF16 block against query q (swizzled).
+// E4M3 row slice dequantised once per row: xr[4 i + k] = e4m3(byte k of word i)
+// times the row scale, one FP32 product each (the F2 definition).
+__device__ __forceinline__ void widen_e4m3(const uint4 (&v)[8], float sc, float (&xr)[32]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const unsigned w[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 x01 = e4m3x2_to_f32(w[i]), x23 = e4m3x2_to_f32(w[i] >> 16);
+            xr[16 * h + 4 * i] = x01.x * sc;
+            xr[16 * h + 4 * i + 1] = x01.y * sc;
+            xr[16 * h + 4 * i + 2] = x23.x * sc;
+            xr[16 * h + 4 * i + 3] = x23.y * sc;
+        }
+    }
+}
+
+// CR32 block sum of this lane's widened BF16 / E4M3 block against query q (swizzled).
 __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const float4 *q, int nb) {
     const int lane = threadIdx.x & 31;
     if (lane >= nb) return 0.0f;
@@ -1404,7 +1422,8 @@ __device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int d = c * 128 + 4 * lane;
-        v[c] = d < Dp ? __ldcs(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
+        // a plain load: the other groups score the same rows next (range-major items)
+        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -1506,10 +1525,12 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         const int e0 = itm.x, ne = itm.y;
         uint4 v[8];
         for (int e = warp; e < ne; e += NW) {
-            if (PREC == 0) row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
-            else row_load_lb<PREC>(v, ix, (long long)u.ent_row[e0 + e], nb);
+            const long long id = u.ent_row[e0 + e];
+            if (PREC == 0) row_load_w(v, ix, id, Dp);
+            else row_load_lb<PREC>(v, ix, id, nb);
             float xr[32];
             if (PREC == 1) widen_bf16(v, xr);
+            if (PREC == 2) widen_e4m3(v, ix.S8[id], xr);
             const unsigned m0 = u.ent_mask[e0 + e];
             const int pb = u.ent_pb[e0 + e];
             unsigned m = m0;
@@ -1779,8 +1800,9 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
     bool grouped = false;
-    if (precision == 1) {
-        crisp_status gs = run_grouped<1>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
+    {
+        crisp_status gs = precision == 1 ? run_grouped<1>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped)
+                                         : run_grouped<2>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
         if (gs) return gs;
     }
     if (grouped) {

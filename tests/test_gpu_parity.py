@@ -367,7 +367,11 @@ def test_large_batch_rerank_and_shortlist_steps(c1_big):
     sl = empty((nq, 64), torch.int32)
     nsl = empty((nq,), torch.int64)
     crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 1, 30, sl, 64, nsl)
+    sl8 = empty((nq, 64), torch.int32)
+    nsl8 = empty((nq,), torch.int64)
+    crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 2, 45, sl8, 64, nsl8)
     gi, gd, gs, gns = ids.cpu().numpy(), d2.cpu().numpy(), sl.cpu().numpy(), nsl.cpu().numpy()
+    gs8, gns8 = sl8.cpu().numpy(), nsl8.cpu().numpy()
     Xb = oracle.quantize_bf16(ix_o.Xr)
     for q in range(0, nq, 53):
         cq = c[q, :n[q]].astype(np.int64)
@@ -375,3 +379,5 @@ def test_large_batch_rerank_and_shortlist_steps(c1_big):
         assert np.array_equal(gi[q], ri) and np.array_equal(gd[q], rd), q
         ro = oracle.shortlist(ix_o, Qr_h[q], cq, 30, "bf16", quant=Xb)
         assert gns[q] == len(ro) and np.array_equal(gs[q, :gns[q]], ro), q
+        r8 = oracle.shortlist(ix_o, Qr_h[q], cq, 45, "fp8", quant=(ix_o.X8, ix_o.S8))
+        assert gns8[q] == len(r8) and np.array_equal(gs8[q, :gns8[q]], r8), q
