@@ -1191,6 +1191,7 @@ struct GUnion {
     unsigned long long *counts; // [0] entries, [1] pairs, [2] scoring item counter
     long long cap;
     int R, nq;
+    int G;                      // queries per group (<= GS_G)
 };
 
 // Entry bucket of a member mask: 33 * lowest member + next member (32 if none).
@@ -1212,11 +1213,11 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
     __shared__ long long s_eb, s_pb;
     __shared__ int s_np;
     const int r = blockIdx.x, g = blockIdx.y, lane = threadIdx.x & 31;
-    const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
+    const int gsize = (g + 1) * u.G <= u.nq ? u.G : u.nq - g * u.G;
     if (threadIdx.x < 32) {
         int a = 0, b = 0, q = 0;
         if (lane < gsize) {
-            q = u.qord[g * GS_G + lane];
+            q = u.qord[g * u.G + lane];
             const long long row = (long long)q * (u.R + 1) + r;
             a = u.pos[row];
             b = u.pos[row + 1];
@@ -1553,6 +1554,180 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
     }
 }
 
+// ------------------------------ FP32 grouped scorer, queries in tensor memory
+// The group's queries sit in TMEM, so the per-pair query reads leave the L1 /
+// shared-memory pipe that bounds the scorer: member j of the group occupies
+// columns [32 j, 32 j + 32) of every lane quarter, lane l holding dims
+// 128 c + 4 l + k at column 32 j + 4 c + k (the warp layout of row_load_w).
+// 16 members x 32 columns fill the 512 columns of one CTA.
+constexpr int GT_G = 16;
+constexpr int GT_COLS = 512;
+
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// CR32 block sum of block `lane` for the row in v (warp layout) against the
+// member whose query starts at TMEM address tq; same arithmetic as row_cr32_w.
+__device__ __forceinline__ float row_cr32_tm(const uint4 (&v)[8], uint32_t tq, float *tp) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t q[16];
+        tm_ld16(tq + 16 * h, q);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = 4 * h + cc;
+            float x = 0.0f;
+            float t = __uint_as_float(v[c].x) - __uint_as_float(q[4 * cc]);
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].y) - __uint_as_float(q[4 * cc + 1]);
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].z) - __uint_as_float(q[4 * cc + 2]);
+            x = fmaf(t, t, x);
+            t = __uint_as_float(v[c].w) - __uint_as_float(q[4 * cc + 3]);
+            x = fmaf(t, t, x);
+            tp[32 * c + lane] = x;             // past Dp: row and query are 0, so x = +0
+        }
+    }
+    __syncwarp();
+    const int sw = (lane >> 2) & 1;
+    const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
+    const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
+    return ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
+}
+
+__global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *__restrict__ Qr, long long stride,
+                                                       GUnion u, float *__restrict__ dbuf) {
+    constexpr int NW = GK_NT / 32;
+    extern __shared__ __align__(16) float gsm[];          // gw_floats<0>() per warp
+    __shared__ long long s_it;
+    __shared__ int s_mem[GT_G];
+    __shared__ uint32_t s_tmem;
+    const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tp = gsm + (size_t)warp * gw_floats<0>();
+    float *gb = tp + 256;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(GT_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tq0 = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16);    // this warp's lane quarter
+    const int ngroups = (u.nq + GT_G - 1) / GT_G;
+    const long long items = (long long)ngroups * u.R;
+    int cur_g = -1;
+    int npend = 0, pj = 0, ppos = 0;
+    auto push = [&](float bs, int j, int slot) {
+        gb[npend * GB_LD + lane] = bs;
+        if (lane == npend) {
+            pj = j;
+            ppos = u.pair_pos[slot];
+        }
+        __syncwarp();
+        if (++npend == GB_K) {
+            if (lane < npend) {
+                const float *row = gb + lane * GB_LD;
+                float acc = 0.0f;
+                for (int b = 0; b < nb; ++b) acc = acc + row[b];
+                dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+            }
+            __syncwarp();
+            npend = 0;
+        }
+    };
+    for (;;) {
+        if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        const long long it = s_it;
+        if (it >= items) break;
+        const int g = (int)(it % ngroups), r = (int)(it / ngroups);
+        const int gsize = (g + 1) * GT_G <= u.nq ? GT_G : u.nq - g * GT_G;
+        if (g != cur_g) {
+            if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GT_G + threadIdx.x];
+            __syncthreads();
+            // the warps of each lane quarter write that quarter's copy (members
+            // past the group's end are zero and never read)
+            for (int j = warp >> 2; j < GT_G; j += NW / 4) {
+                const float *qrow = Qr + (long long)(j < gsize ? s_mem[j] : 0) * Dp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t q[16];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int d = (4 * h + cc) * 128 + 4 * lane;
+                        const uint4 x = j < gsize && d < Dp ? __ldg(reinterpret_cast<const uint4 *>(qrow + d))
+                                                            : make_uint4(0, 0, 0, 0);
+                        q[4 * cc] = x.x;
+                        q[4 * cc + 1] = x.y;
+                        q[4 * cc + 2] = x.z;
+                        q[4 * cc + 3] = x.w;
+                    }
+                    __syncwarp();
+                    tm_st16(tq0 + 32 * j + 16 * h, q);
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            cur_g = g;
+            tm_fence_before();
+            __syncthreads();
+            tm_fence_after();
+        }
+        const int2 itm = u.items[(long long)g * u.R + r];
+        const int e0 = itm.x, ne = itm.y;
+        uint4 v[8];
+        for (int e = warp; e < ne; e += NW) {
+            row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
+            const unsigned m0 = u.ent_mask[e0 + e];
+            const int pb = u.ent_pb[e0 + e];
+            unsigned m = m0;
+            for (int i = 0; m; ++i) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                __syncwarp();
+                push(row_cr32_tm(v, tq0 + 32 * j, tp), j, pb + i);
+            }
+        }
+        if (lane < npend) {
+            const float *row = gb + lane * GB_LD;
+            float acc = 0.0f;
+            for (int b = 0; b < nb; ++b) acc = acc + row[b];
+            dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+        }
+        __syncwarp();
+        npend = 0;
+    }
+    tm_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tm_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(GT_COLS) : "memory");
+    }
+}
+
 // Grouped scoring of a batch into dbuf, or *done = false when the batch does not
 // qualify (then the caller streams per query).
 template <int PREC>
@@ -1561,7 +1736,8 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     *done = false;
     if (nq < GS_MINQ || nq > SCH_MAXQ || ix->Dp > 1024 || stride < GS_MINSTRIDE) return CRISP_OK;
     const int R = (int)((ix->N + GS_SPAN - 1) / GS_SPAN);
-    const int ngroups = (nq + GS_G - 1) / GS_G;
+    const int G = PREC == 0 ? GT_G : GS_G;
+    const int ngroups = (nq + G - 1) / G;
     const long long cap = (long long)nq * std::min<int64_t>(stride, ix->N);
     if (cap > (1LL << 31) - 1) return CRISP_OK;
     size_t off = 0;
@@ -1586,6 +1762,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     u.cap = cap;
     u.R = R;
     u.nq = nq;
+    u.G = G;
     crisp_status s = CRISP_OK;
     do {
         cudaError_t e = cudaMemsetAsync(u.counts, 0, 3 * sizeof(unsigned long long), st);
@@ -1605,13 +1782,21 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
         CRISP_COUNT_LAUNCH();
         k_gunion<<<dim3(R, ngroups), GU_NT, 0, st>>>(cand, (long long)stride, u);
         CRISP_COUNT_LAUNCH();
-        const size_t smem = sizeof(float) * ((size_t)GS_G * ix->Dp + (size_t)(GK_NT / 32) * gw_floats<PREC>());
-        e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
+        if constexpr (PREC == 0) {
+            // one CTA per SM (its registers fill the SM), so its 512 TMEM columns are always free
+            const size_t smem = sizeof(float) * (size_t)(GK_NT / 32) * gw_floats<0>();
+            e = cudaFuncSetAttribute(k_gscore_tm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+            k_gscore_tm<<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
+        } else {
+            const size_t smem = sizeof(float) * ((size_t)GS_G * ix->Dp + (size_t)(GK_NT / 32) * gw_floats<PREC>());
+            e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+            k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
+        }
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "grouped scoring", __FILE__, __LINE__); break; }
