@@ -768,7 +768,7 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     # MinHash-ordered query groups (k_gunion + k_gscore); smaller ones stream (k_dist_flat)
     grouped = nq >= 1024 and stride >= 2048 and Dp <= 1024
     kernels = ["k_rotate", "k_activate", "k_count_cut",
-               ("k_gscore<FP32>" if grouped else "k_dist_flat") if point["mode"] == 0 else "k_verify_opt"]
+               ("k_gscore_tm (FP32)" if grouped else "k_dist_flat") if point["mode"] == 0 else "k_verify_opt"]
     bf16 = bool(info.Xb) and point["mode"] == 0
     if bf16:            # the F2 coarse-scoring kernel on the same candidates (timed on its own)
         names.append("shortlist_bf16")

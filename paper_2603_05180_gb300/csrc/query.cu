@@ -1330,12 +1330,17 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
     }
 }
 
-// Lane-per-block layout of the grouped scorer: lane l holds the row's 32-dim
-// block l (FP32: 8 float4; BF16: 4 x 16 bytes), so the CR32 lane partials and
-// their xor tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers; the
-// block sums then go through shared memory and are added in block order.
-// Query blocks sit in shared memory with float4 u of block b at slot
-// u ^ (b & 7), so the eight lanes of a quarter-warp read distinct banks.
+// The grouped scorers.  A CTA (one per SM) takes (id range, group) items; a
+// warp takes one listed row at a time, keeps it in registers and scores it
+// against every member of the group that needs it.
+//  - BF16 / E4M3 rows (k_gscore): lane l holds the row's 32-dim block l, widened
+//    (dequantised) to FP32 once per row, so the CR32 lane partials and their xor
+//    tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers.  The group's
+//    32 queries sit in shared memory with float4 u of block b at slot
+//    u ^ (b & 7), so the eight lanes of a quarter-warp read distinct banks.
+//  - FP32 rows (k_gscore_tm): warp layout, queries in tensor memory (below).
+// Either way each pair ends with the sum of block `lane` in every lane, and the
+// block sums are added in block order by the batched gather.
 __device__ __forceinline__ float block_tree(const float (&a)[8]) {
     return ((a[0] + a[4]) + (a[2] + a[6])) + ((a[1] + a[5]) + (a[3] + a[7]));
 }
@@ -1345,9 +1350,8 @@ __device__ __forceinline__ void row_load_lb(uint4 (&v)[8], const IxView &ix, lon
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        if (lane < nb && (PREC == 0 || (PREC == 1 && u < 4) || (PREC == 2 && u < 2))) {
-            if (PREC == 0) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * ix.Dp + 32 * lane + 4 * u));
-            else if (PREC == 1) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xb + id * ix.Dp + 32 * lane + 8 * u));
+        if (lane < nb && ((PREC == 1 && u < 4) || (PREC == 2 && u < 2))) {
+            if (PREC == 1) v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.Xb + id * ix.Dp + 32 * lane + 8 * u));
             else v[u] = __ldg(reinterpret_cast<const uint4 *>(ix.X8 + id * ix.Dp + 32 * lane + 16 * u));
         } else {
             v[u] = make_uint4(0, 0, 0, 0);
@@ -1410,73 +1414,26 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
     return block_tree(a);
 }
 
-// Warp layout for FP32 rows: lane l holds dims 128 c + 4 l (8 x 16 bytes,
-// coalesced), i.e. lane partial l & 7 of block 4 c + (l >> 3).  The query is read
-// from a plain (unswizzled) shared copy.  The partials are transposed through
-// the warp's shared scratch tp[256] instead of shuffles: they land at
-// tp[8 block + partial], and lane b reads block b's eight partials (halves
-// swapped on lanes with bit 2 set, so a quarter-warp touches 32 distinct banks)
-// and adds them in the xor-tree order.  Returns the sum of block `lane` (+0 for
-// blocks at or past Dp / 32).
-__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int d = c * 128 + 4 * lane;
-        // a plain load: the other groups score the same rows next (range-major items)
-        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
-    }
-}
-
-__device__ __forceinline__ float row_cr32_w(const uint4 (&v)[8], const float4 *q4, int Dp, float *tp) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int d = c * 128 + 4 * lane;
-        float x = 0.0f;
-        if (d < Dp) {
-            const float4 qq = q4[d >> 2];
-            float t = __uint_as_float(v[c].x) - qq.x;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].y) - qq.y;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].z) - qq.z;
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].w) - qq.w;
-            x = fmaf(t, t, x);
-        }
-        tp[32 * c + lane] = x;
-    }
-    __syncwarp();
-    // h0/h1 are partials 0..3 and 4..7, or 4..7 and 0..3 on the swapped lanes:
-    // the tree adds p and p + 4 first, and IEEE addition commutes, so the same
-    // expression gives the same block sum either way
-    const int sw = (lane >> 2) & 1;
-    const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
-    const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
-    return ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
-}
-
 // Batched gather of the block sums: each scored (row, member) pair leaves its
 // 32 block sums as one row of the warp's gather buffer (row stride GB_LD, so a
 // column read by 32 lanes hits 32 banks); once GB_K pairs are pending, lane p
 // adds row p in block order and stores pair p's distance.
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
-// per-warp scratch: FP32 partials, then the gather rows
+// per-warp shared scratch: FP32 partials (k_gscore_tm only), then the gather rows
 template <int PREC> __host__ __device__ constexpr int gw_floats() { return (PREC == 0 ? 256 : 0) + GB_K * GB_LD; }
 
 template <int PREC>
 __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
                                                     GUnion u, float *__restrict__ dbuf) {
+    static_assert(PREC == 1 || PREC == 2, "FP32 rows are scored by k_gscore_tm");
     constexpr int NT = GK_NT, NW = GK_NT / 32;
-    // [GS_G][Dp / 4] query copies (swizzled per block for BF16), then gw_floats per warp
+    // [GS_G][Dp / 4] query copies (swizzled per block), then gw_floats per warp
     extern __shared__ __align__(16) float4 gq4[];
     __shared__ long long s_it;
     __shared__ int s_mem[GS_G];
     const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *tp = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
-    float *gb = tp + (PREC == 0 ? 256 : 0);
+    float *gb = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
     const int ngroups = (u.nq + GS_G - 1) / GS_G;
     const long long items = (long long)ngroups * u.R;
     int cur_g = -1;
@@ -1515,8 +1472,7 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             const int n4 = Dp >> 2;
             for (int e = threadIdx.x; e < gsize * n4; e += NT) {
                 const int j = e / n4, f = e % n4, b = f >> 3, uu = f & 7;
-                // BF16 (lane-per-block) reads a swizzled copy, FP32 (warp layout) a plain one
-                gq4[(size_t)j * n4 + (PREC == 0 ? f : 8 * b + (uu ^ (b & 7)))] =
+                gq4[(size_t)j * n4 + 8 * b + (uu ^ (b & 7))] =
                     reinterpret_cast<const float4 *>(Qr + (long long)s_mem[j] * Dp)[f];
             }
             cur_g = g;
@@ -1527,19 +1483,17 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         uint4 v[8];
         for (int e = warp; e < ne; e += NW) {
             const long long id = u.ent_row[e0 + e];
-            if (PREC == 0) row_load_w(v, ix, id, Dp);
-            else row_load_lb<PREC>(v, ix, id, nb);
+            row_load_lb<PREC>(v, ix, id, nb);
             float xr[32];
             if (PREC == 1) widen_bf16(v, xr);
-            if (PREC == 2) widen_e4m3(v, ix.S8[id], xr);
+            else widen_e4m3(v, ix.S8[id], xr);
             const unsigned m0 = u.ent_mask[e0 + e];
             const int pb = u.ent_pb[e0 + e];
             unsigned m = m0;
             for (int i = 0; m; ++i) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
-                const float4 *qj = gq4 + (size_t)j * (Dp >> 2);
-                push(PREC == 0 ? row_cr32_w(v, qj, Dp, tp) : block_sum_lb_w(xr, qj, nb), j, pb + i);
+                push(block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb), j, pb + i);
             }
         }
         if (lane < npend) {                     // the item's last pairs (s_mem changes with the group)
@@ -1555,11 +1509,26 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
 }
 
 // ------------------------------ FP32 grouped scorer, queries in tensor memory
-// The group's queries sit in TMEM, so the per-pair query reads leave the L1 /
+// Warp layout for FP32 rows: lane l holds dims 128 c + 4 l .. + 3 (coalesced
+// 16-byte loads), i.e. CR32 lane partial l & 7 of block 4 c + (l >> 3).  The
+// group's queries sit in TMEM, so the per-pair query reads leave the L1 /
 // shared-memory pipe that bounds the scorer: member j of the group occupies
 // columns [32 j, 32 j + 32) of every lane quarter, lane l holding dims
-// 128 c + 4 l + k at column 32 j + 4 c + k (the warp layout of row_load_w).
-// 16 members x 32 columns fill the 512 columns of one CTA.
+// 128 c + 4 l + k at column 32 j + 4 c + k.  16 members x 32 columns fill the
+// 512 columns of one CTA.  The partials are transposed through the warp's
+// shared scratch tp[256]: they land at tp[8 block + partial], and lane b reads
+// block b's eight partials (halves swapped on lanes with bit 2 set, so a
+// quarter-warp touches 32 distinct banks) and adds them in the xor-tree order.
+__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int d = c * 128 + 4 * lane;
+        // a plain load: the other groups score the same rows next (range-major items)
+        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
+    }
+}
+
 constexpr int GT_G = 16;
 constexpr int GT_COLS = 512;
 
