@@ -139,6 +139,17 @@ def _count_case(ix_o, ix, Q, p, stride=None, with_score=True):
     return cand.cpu().numpy(), ncand.cpu().numpy(), (score.cpu().numpy() if with_score else None), how.cpu().numpy()
 
 
+def _oracle_cuts(ix_o, Q, p, cand, ncand):
+    """The oracle's own rotated query and cut per query (the inputs of the
+    oracle's re-rank / verification below); the GPU's lists must equal them."""
+    out = []
+    for i in range(Q.shape[0]):
+        det = oracle.query_detail(ix_o, Q[i], p)
+        assert np.array_equal(cand[i, :ncand[i]], det["C"]), i
+        out.append((det["qr"], det["C"]))
+    return out
+
+
 @pytest.mark.parametrize("mode,rho,alpha,cap", [
     (0, 0.01, 0.3, 0),      # plain cut
     (1, 0.02, 0.25, 0),     # weighted scores
@@ -190,9 +201,8 @@ def test_q6_rerank_bitexact(c1, k):
     d2 = empty((nq, k), torch.float32)
     crisp.crisp_rerank(ix, Qr, nq, dev(cand), cand.shape[1], dev(ncand), k, ids, d2)
     ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
-    qr = oracle.query_rotate(ix_o, Q)
-    for i in range(nq):
-        oi, od = oracle.rerank(ix_o, qr[i], cand[i, :ncand[i]], k)
+    for i, (qr, C) in enumerate(_oracle_cuts(ix_o, Q, p, cand, ncand)):
+        oi, od = oracle.rerank(ix_o, qr, C, k)
         assert np.array_equal(ids[i], oi) and np.array_equal(d2[i], od)
 
 
@@ -211,9 +221,8 @@ def test_q7_optimized_verification_bitexact(c1, k, eps0, P, order):
     nf = empty((nq,), torch.int64)
     crisp.crisp_verify_opt(ix, Qr, nq, dev(cand), cand.shape[1], dev(ncand), k, eps0, P, ids, d2, nv, nf, order=order)
     ids, d2, nv, nf = (t.cpu().numpy() for t in (ids, d2, nv, nf))
-    qr = oracle.query_rotate(ix_o, Q)
-    for i in range(nq):
-        oi, od, onv, onf = oracle.verify_opt(ix_o, qr[i], cand[i, :ncand[i]], k, eps0, P, order=order)
+    for i, (qr, C) in enumerate(_oracle_cuts(ix_o, Q, p, cand, ncand)):
+        oi, od, onv, onf = oracle.verify_opt(ix_o, qr, C, k, eps0, P, order=order)
         assert np.array_equal(ids[i], oi) and np.array_equal(d2[i], od), i
         assert (nv[i], nf[i]) == (onv, onf), (i, nv[i], nf[i], onv, onf)
 
@@ -360,7 +369,6 @@ def test_large_batch_rerank_and_shortlist_steps(c1_big):
     crisp.crisp_count_cut(ix, act, nact, nq, crisp.tau(0.25, M), 10, 0, cand, stride, ncand)
     n = ncand.cpu().numpy()
     c = cand.cpu().numpy()
-    Qr_h = Qr.cpu().numpy()
     ids = empty((nq, 10), torch.int64)
     d2 = empty((nq, 10), torch.float32)
     crisp.crisp_rerank(ix, Qr, nq, cand, stride, ncand, 10, ids, d2)
@@ -374,10 +382,13 @@ def test_large_batch_rerank_and_shortlist_steps(c1_big):
     gs8, gns8 = sl8.cpu().numpy(), nsl8.cpu().numpy()
     Xb = oracle.quantize_bf16(ix_o.Xr)
     for q in range(0, nq, 53):
-        cq = c[q, :n[q]].astype(np.int64)
-        ri, rd = oracle.rerank(ix_o, Qr_h[q], cq, 10)
+        # the oracle's own rotated query and cut (the GPU's list must match it)
+        dq = oracle.query_detail(ix_o, Q[q], oracle.SearchParams(k=10, mode=0, rho=0.03, alpha=0.25))
+        assert np.array_equal(c[q, :n[q]], dq["C"]), q
+        cq = dq["C"].astype(np.int64)
+        ri, rd = oracle.rerank(ix_o, dq["qr"], cq, 10)
         assert np.array_equal(gi[q], ri) and np.array_equal(gd[q], rd), q
-        ro = oracle.shortlist(ix_o, Qr_h[q], cq, 30, "bf16", quant=Xb)
+        ro = oracle.shortlist(ix_o, dq["qr"], cq, 30, "bf16", quant=Xb)
         assert gns[q] == len(ro) and np.array_equal(gs[q, :gns[q]], ro), q
-        r8 = oracle.shortlist(ix_o, Qr_h[q], cq, 45, "fp8", quant=(ix_o.X8, ix_o.S8))
+        r8 = oracle.shortlist(ix_o, dq["qr"], cq, 45, "fp8", quant=(ix_o.X8, ix_o.S8))
         assert gns8[q] == len(r8) and np.array_equal(gs8[q, :gns8[q]], r8), q

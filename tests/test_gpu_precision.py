@@ -73,10 +73,13 @@ def test_shortlist_bitexact(c1q, precision, S):
     nout = torch.empty((nq,), dtype=torch.int64, device=DEV)
     crisp.crisp_shortlist(ix, Qr, nq, cand, ix_o.N, ncand, precision, S, out, S, nout)
     out, nout, cand, ncand = out.cpu().numpy(), nout.cpu().numpy(), cand.cpu().numpy(), ncand.cpu().numpy()
-    qr = oracle.query_rotate(ix_o, Q)
     quant = ix_o.Xb if precision == 1 else (ix_o.X8, ix_o.S8)
+    p = oracle.SearchParams(k=10, mode=0, rho=0.02, alpha=0.25)
     for i in range(nq):
-        ref = oracle.shortlist(ix_o, qr[i], cand[i, :ncand[i]], S, "bf16" if precision == 1 else "fp8", quant)
+        # the oracle's own rotated query and cut (the GPU's list must match it)
+        det = oracle.query_detail(ix_o, Q[i], p)
+        assert np.array_equal(cand[i, :ncand[i]], det["C"]), i
+        ref = oracle.shortlist(ix_o, det["qr"], det["C"], S, "bf16" if precision == 1 else "fp8", quant)
         assert nout[i] == ref.size and np.array_equal(out[i, :nout[i]], ref), i
 
 
