@@ -1252,16 +1252,26 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
         atomicOr(&mask[id - lo_id], 1u << lo);
     }
     __syncthreads();
-    // first pair slot of each row (exclusive prefix of its member counts) and the
-    // number of rows some member needs (one packed scan: pairs high, rows low)
-    long long carry = 0;
-    for (int o0 = 0; o0 < GS_SPAN; o0 += GU_NT) {
-        const int o = o0 + threadIdx.x;
-        const int c = __popc(mask[o]);
-        long long tot;
-        const long long ex = block_excl_scan<GU_NT>(((long long)c << 32) | (c > 0 ? 1 : 0), scan_ws, &tot);
-        pbl[o] = (int)((carry + ex) >> 32);
-        carry += tot;
+    // first pair slot of each row and the number of rows some member needs.  Any
+    // assignment that gives each row popc(mask) consecutive slots will do, so
+    // thread t takes the slots t, t + GU_NT, ... (conflict-free reads) and one
+    // packed block scan (pairs high, rows low) places the threads.
+    long long carry;
+    {
+        int pairs = 0, rows = 0;
+#pragma unroll
+        for (int k = 0; k < GS_SPAN / GU_NT; ++k) {
+            const int c = __popc(mask[threadIdx.x + k * GU_NT]);
+            pairs += c;
+            rows += c > 0 ? 1 : 0;
+        }
+        int run = (int)(block_excl_scan<GU_NT>(((long long)pairs << 32) | rows, scan_ws, &carry) >> 32);
+#pragma unroll
+        for (int k = 0; k < GS_SPAN / GU_NT; ++k) {
+            const int o = threadIdx.x + k * GU_NT;
+            pbl[o] = run;
+            run += __popc(mask[o]);
+        }
     }
     if (threadIdx.x == 0) {
         const long long ne = carry & 0xFFFFFFFF;
@@ -1274,9 +1284,10 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
     __syncthreads();
     if (s_eb < 0) return;
     // entries, bucketed by (lowest member, next member): rows that share their
-    // first members sit next to each other, so the scorer's row pairs can share
-    // query loads.  The order inside a bucket is arbitrary (every pair has its
-    // own slot, so results do not depend on it).
+    // first members sit next to each other, so the warps of a scoring CTA work on
+    // the same few members at a time (measured faster than id order).  The order
+    // inside a bucket is arbitrary (every pair has its own slot, so results do
+    // not depend on it).
     for (int i = threadIdx.x; i < GU_NBK; i += GU_NT) bk[i] = 0;
     __syncthreads();
     for (int o = threadIdx.x; o < GS_SPAN; o += GU_NT) {
@@ -1420,8 +1431,8 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 // adds row p in block order and stores pair p's distance.
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
-// per-warp shared scratch: FP32 partials (k_gscore_tm only), then the gather rows
-template <int PREC> __host__ __device__ constexpr int gw_floats() { return (PREC == 0 ? 256 : 0) + GB_K * GB_LD; }
+// per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
+template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
 
 template <int PREC>
 __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
@@ -1519,15 +1530,6 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
 // shared scratch tp[256]: they land at tp[8 block + partial], and lane b reads
 // block b's eight partials (halves swapped on lanes with bit 2 set, so a
 // quarter-warp touches 32 distinct banks) and adds them in the xor-tree order.
-__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int d = c * 128 + 4 * lane;
-        // a plain load: the other groups score the same rows next (range-major items)
-        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
-    }
-}
 
 constexpr int GT_G = 16;
 constexpr int GT_COLS = 512;
@@ -1554,8 +1556,18 @@ __device__ __forceinline__ void tm_st16(uint32_t taddr, const uint32_t (&r)[16])
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int d = c * 128 + 4 * lane;
+        // a plain load: the other groups score the same rows next (range-major items)
+        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
+    }
+}
+
 // CR32 block sum of block `lane` for the row in v (warp layout) against the
-// member whose query starts at TMEM address tq; same arithmetic as row_cr32_w.
+// member whose query starts at TMEM address tq.
 __device__ __forceinline__ float row_cr32_tm(const uint4 (&v)[8], uint32_t tq, float *tp) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
