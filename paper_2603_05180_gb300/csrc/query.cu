@@ -1492,8 +1492,11 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         const int2 itm = u.items[(long long)g * u.R + r];
         const int e0 = itm.x, ne = itm.y;
         uint4 v[8];
+        // the next row's id is loaded a step ahead, so a row costs one L2 round trip
+        int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
         for (int e = warp; e < ne; e += NW) {
-            const long long id = u.ent_row[e0 + e];
+            const long long id = id_next;
+            if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
             row_load_lb<PREC>(v, ix, id, nb);
             float xr[32];
             if (PREC == 1) widen_bf16(v, xr);
@@ -1680,8 +1683,12 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *
         const int2 itm = u.items[(long long)g * u.R + r];
         const int e0 = itm.x, ne = itm.y;
         uint4 v[8];
+        // the next row's id is loaded a step ahead, so a row costs one L2 round trip
+        int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
         for (int e = warp; e < ne; e += NW) {
-            row_load_w(v, ix, (long long)u.ent_row[e0 + e], Dp);
+            const int id = id_next;
+            if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
+            row_load_w(v, ix, (long long)id, Dp);
             const unsigned m0 = u.ent_mask[e0 + e];
             const int pb = u.ent_pb[e0 + e];
             unsigned m = m0;
