@@ -783,6 +783,8 @@ __device__ long long collect_ordered(const float *distq, long long n, unsigned p
     for (long long c0 = 0; c0 < n; c0 += RR_NT) {
         long long i = c0 + tid;
         unsigned key = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
+        // most chunks hold nothing at or below the k-th key: one vote skips them
+        if (!__syncthreads_or(i < n && key <= prefix)) continue;
         int is_eq = (i < n && key == prefix);
         long long eq_tot;
         long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
