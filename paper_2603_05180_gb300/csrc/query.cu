@@ -1433,6 +1433,7 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 // adds row p in block order and stores pair p's distance.
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
+constexpr int GT_RB = 4;            // ranges per scoring item (one query load per block)
 // per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
 template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
 
@@ -1448,7 +1449,8 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
     const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *gb = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
     const int ngroups = (u.nq + GS_G - 1) / GS_G;
-    const long long items = (long long)ngroups * u.R;
+    const int nrb = (u.R + GT_RB - 1) / GT_RB;
+    const long long items = (long long)ngroups * nrb;
     int cur_g = -1;
     int npend = 0, pj = 0, ppos = 0;     // pending pairs; lane p < npend: member and list position of pair p
     // one scored pair: its block sums become gather row npend
@@ -1475,9 +1477,10 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         __syncthreads();
         const long long it = s_it;
         if (it >= items) break;
-        // range-major: the CTAs in flight score the same GS_SPAN rows for
-        // different groups, so a row comes from DRAM about once per batch
-        const int g = (int)(it % ngroups), r = (int)(it / ngroups);
+        // items are (block of GT_RB ranges, group), range-block-major: one query
+        // load per block, and the CTAs in flight score the same few ranges of
+        // rows for different groups, so a row comes from DRAM about once per batch
+        const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
         const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
         if (g != cur_g) {
             if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GS_G + threadIdx.x];
@@ -1491,25 +1494,28 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             cur_g = g;
         }
         __syncthreads();
-        const int2 itm = u.items[(long long)g * u.R + r];
-        const int e0 = itm.x, ne = itm.y;
-        uint4 v[8];
-        // the next row's id is loaded a step ahead, so a row costs one L2 round trip
-        int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
-        for (int e = warp; e < ne; e += NW) {
-            const long long id = id_next;
-            if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
-            row_load_lb<PREC>(v, ix, id, nb);
-            float xr[32];
-            if (PREC == 1) widen_bf16(v, xr);
-            else widen_e4m3(v, ix.S8[id], xr);
-            const unsigned m0 = u.ent_mask[e0 + e];
-            const int pb = u.ent_pb[e0 + e];
-            unsigned m = m0;
-            for (int i = 0; m; ++i) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                push(block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb), j, pb + i);
+        const int r_end = (rb + 1) * GT_RB < u.R ? (rb + 1) * GT_RB : u.R;
+        for (int r = rb * GT_RB; r < r_end; ++r) {      // no barrier between the block's ranges
+            const int2 itm = u.items[(long long)g * u.R + r];
+            const int e0 = itm.x, ne = itm.y;
+            uint4 v[8];
+            // the next row's id is loaded a step ahead, so a row costs one L2 round trip
+            int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
+            for (int e = warp; e < ne; e += NW) {
+                const long long id = id_next;
+                if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
+                row_load_lb<PREC>(v, ix, id, nb);
+                float xr[32];
+                if (PREC == 1) widen_bf16(v, xr);
+                else widen_e4m3(v, ix.S8[id], xr);
+                const unsigned m0 = u.ent_mask[e0 + e];
+                const int pb = u.ent_pb[e0 + e];
+                unsigned m = m0;
+                for (int i = 0; m; ++i) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    push(block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb), j, pb + i);
+                }
             }
         }
         if (lane < npend) {                     // the item's last pairs (s_mem changes with the group)
@@ -1622,7 +1628,8 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *
     tm_fence_after();
     const uint32_t tq0 = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16);    // this warp's lane quarter
     const int ngroups = (u.nq + GT_G - 1) / GT_G;
-    const long long items = (long long)ngroups * u.R;
+    const int nrb = (u.R + GT_RB - 1) / GT_RB;
+    const long long items = (long long)ngroups * nrb;
     int cur_g = -1;
     int npend = 0, pj = 0, ppos = 0;
     auto push = [&](float bs, int j, int slot) {
@@ -1650,7 +1657,9 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *
         tm_fence_after();
         const long long it = s_it;
         if (it >= items) break;
-        const int g = (int)(it % ngroups), r = (int)(it / ngroups);
+        // items are (block of GT_RB ranges, group), range-block-major: one query
+        // load per block, and the CTAs in flight share GT_RB ranges of rows in L2
+        const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
         const int gsize = (g + 1) * GT_G <= u.nq ? GT_G : u.nq - g * GT_G;
         if (g != cur_g) {
             if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GT_G + threadIdx.x];
@@ -1682,23 +1691,26 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *
             __syncthreads();
             tm_fence_after();
         }
-        const int2 itm = u.items[(long long)g * u.R + r];
-        const int e0 = itm.x, ne = itm.y;
-        uint4 v[8];
-        // the next row's id is loaded a step ahead, so a row costs one L2 round trip
-        int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
-        for (int e = warp; e < ne; e += NW) {
-            const int id = id_next;
-            if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
-            row_load_w(v, ix, (long long)id, Dp);
-            const unsigned m0 = u.ent_mask[e0 + e];
-            const int pb = u.ent_pb[e0 + e];
-            unsigned m = m0;
-            for (int i = 0; m; ++i) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                __syncwarp();
-                push(row_cr32_tm(v, tq0 + 32 * j, tp), j, pb + i);
+        const int r_end = (rb + 1) * GT_RB < u.R ? (rb + 1) * GT_RB : u.R;
+        for (int r = rb * GT_RB; r < r_end; ++r) {      // no barrier between the block's ranges
+            const int2 itm = u.items[(long long)g * u.R + r];
+            const int e0 = itm.x, ne = itm.y;
+            uint4 v[8];
+            // the next row's id is loaded a step ahead, so a row costs one L2 round trip
+            int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
+            for (int e = warp; e < ne; e += NW) {
+                const int id = id_next;
+                if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
+                row_load_w(v, ix, (long long)id, Dp);
+                const unsigned m0 = u.ent_mask[e0 + e];
+                const int pb = u.ent_pb[e0 + e];
+                unsigned m = m0;
+                for (int i = 0; m; ++i) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    __syncwarp();
+                    push(row_cr32_tm(v, tq0 + 32 * j, tp), j, pb + i);
+                }
             }
         }
         if (lane < npend) {
