@@ -1433,7 +1433,7 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 // adds row p in block order and stores pair p's distance.
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
-constexpr int GT_RB = 4;            // ranges per scoring item (one query load per block)
+constexpr int GT_RB = 8;            // ranges per scoring item (one query load per block)
 // per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
 template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
 
