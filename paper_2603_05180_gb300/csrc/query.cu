@@ -723,6 +723,8 @@ __device__ __forceinline__ float cr32_block(float4 x, float4 qv, unsigned gmask)
     return a;
 }
 
+constexpr int SEL_U = 8;    // keys a thread loads before using them (top-k passes)
+
 struct TopkShared {
     unsigned hist[256];
     long long scan_ws[RR_NT / 32 + 1];
@@ -743,14 +745,23 @@ __device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S
         for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
         __syncthreads();
         // keys share their leading bytes, so whole warps hit one bin: combine the
-        // lanes of a bin first (one shared atomic per distinct bin per warp)
-        for (long long i0 = 0; i0 < n; i0 += RR_NT) {
-            const long long i = i0 + tid;
-            const unsigned key = i < n ? __float_as_uint(distq[i]) : 0u;
-            const bool hit = i < n && (key & mask) == prefix;
-            const unsigned bin = hit ? (key >> shift) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
-            if (hit && (__ffs(peers) - 1) == (int)(tid & 31)) atomicAdd(&S.hist[bin], (unsigned)__popc(peers));
+        // lanes of a bin first (one shared atomic per distinct bin per warp).
+        // SEL_U keys a thread are loaded before any is binned (independent loads).
+        for (long long i0 = 0; i0 < n; i0 += (long long)RR_NT * SEL_U) {
+            unsigned key[SEL_U];
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u) {
+                const long long i = i0 + (long long)u * RR_NT + tid;
+                key[u] = i < n ? __float_as_uint(distq[i]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u) {
+                const long long i = i0 + (long long)u * RR_NT + tid;
+                const bool hit = i < n && (key[u] & mask) == prefix;
+                const unsigned bin = hit ? (key[u] >> shift) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                if (hit && (__ffs(peers) - 1) == (int)(tid & 31)) atomicAdd(&S.hist[bin], (unsigned)__popc(peers));
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -780,20 +791,32 @@ template <class F>
 __device__ long long collect_ordered(const float *distq, long long n, unsigned prefix, int need, TopkShared &S, F f) {
     const int tid = threadIdx.x;
     long long eq_seen = 0, sel_seen = 0;
-    for (long long c0 = 0; c0 < n; c0 += RR_NT) {
-        long long i = c0 + tid;
-        unsigned key = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
+    for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {
+        unsigned keys[SEL_U];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const long long i = c00 + (long long)u * RR_NT + tid;
+            keys[u] = i < n ? __float_as_uint(distq[i]) : 0xFFFFFFFFu;
+            any = any || (i < n && keys[u] <= prefix);
+        }
         // most chunks hold nothing at or below the k-th key: one vote skips them
-        if (!__syncthreads_or(i < n && key <= prefix)) continue;
-        int is_eq = (i < n && key == prefix);
-        long long eq_tot;
-        long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
-        int sel = (i < n) && (key < prefix || (is_eq && eq_seen + eq_off < need));
-        long long sel_tot;
-        long long sel_off = block_excl_scan<RR_NT>(sel, S.scan_ws, &sel_tot);
-        if (sel) f(sel_seen + sel_off, i);
-        eq_seen += eq_tot;
-        sel_seen += sel_tot;
+        if (!__syncthreads_or(any)) continue;
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {                  // chunks in list order
+            const long long i = c00 + (long long)u * RR_NT + tid;
+            const unsigned key = keys[u];
+            if (!__syncthreads_or(i < n && key <= prefix)) continue;
+            int is_eq = (i < n && key == prefix);
+            long long eq_tot;
+            long long eq_off = block_excl_scan<RR_NT>(is_eq, S.scan_ws, &eq_tot);
+            int sel = (i < n) && (key < prefix || (is_eq && eq_seen + eq_off < need));
+            long long sel_tot;
+            long long sel_off = block_excl_scan<RR_NT>(sel, S.scan_ws, &sel_tot);
+            if (sel) f(sel_seen + sel_off, i);
+            eq_seen += eq_tot;
+            sel_seen += sel_tot;
+        }
     }
     return sel_seen;
 }
