@@ -1377,8 +1377,31 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
 //  - FP32 rows (k_gscore_tm): warp layout, queries in tensor memory (below).
 // Either way each pair ends with the sum of block `lane` in every lane, and the
 // block sums are added in block order by the batched gather.
+// Packed FP32 pairs (sm_100 family): each half is one IEEE round-to-nearest
+// subtraction or addition, exactly the scalar instruction's result.
+__device__ __forceinline__ float2 sub2(float a0, float a1, float b0, float b1) {
+    float2 d;
+    asm("{.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tsub.rn.f32x2 d, a, b;\n\t"
+        "mov.b64 {%0, %1}, d;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    return d;
+}
+
+__device__ __forceinline__ float2 add2(float a0, float a1, float b0, float b1) {
+    float2 d;
+    asm("{.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tadd.rn.f32x2 d, a, b;\n\t"
+        "mov.b64 {%0, %1}, d;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    return d;
+}
+
+// ((a0 + a4) + (a2 + a6)) + ((a1 + a5) + (a3 + a7)), the first two levels as pairs
 __device__ __forceinline__ float block_tree(const float (&a)[8]) {
-    return ((a[0] + a[4]) + (a[2] + a[6])) + ((a[1] + a[5]) + (a[3] + a[7]));
+    const float2 s01 = add2(a[0], a[1], a[4], a[5]), s23 = add2(a[2], a[3], a[6], a[7]);
+    const float2 u = add2(s01.x, s01.y, s23.x, s23.y);
+    return u.x + u.y;
 }
 
 template <int PREC>
@@ -1436,15 +1459,13 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const float4 qq = qb[u ^ sw];
-        float x = 0.0f, t;
-        t = xr[4 * u] - qq.x;
-        x = fmaf(t, t, x);
-        t = xr[4 * u + 1] - qq.y;
-        x = fmaf(t, t, x);
-        t = xr[4 * u + 2] - qq.z;
-        x = fmaf(t, t, x);
-        t = xr[4 * u + 3] - qq.w;
-        x = fmaf(t, t, x);
+        const float2 t01 = sub2(xr[4 * u], xr[4 * u + 1], qq.x, qq.y);
+        const float2 t23 = sub2(xr[4 * u + 2], xr[4 * u + 3], qq.z, qq.w);
+        float x = 0.0f;
+        x = fmaf(t01.x, t01.x, x);
+        x = fmaf(t01.y, t01.y, x);
+        x = fmaf(t23.x, t23.x, x);
+        x = fmaf(t23.y, t23.y, x);
         a[u] = x;
     }
     return block_tree(a);
@@ -1611,15 +1632,15 @@ __device__ __forceinline__ float row_cr32_tm(const uint4 (&v)[8], uint32_t tq, f
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             const int c = 4 * h + cc;
+            const float2 t01 = sub2(__uint_as_float(v[c].x), __uint_as_float(v[c].y), __uint_as_float(q[4 * cc]),
+                                    __uint_as_float(q[4 * cc + 1]));
+            const float2 t23 = sub2(__uint_as_float(v[c].z), __uint_as_float(v[c].w), __uint_as_float(q[4 * cc + 2]),
+                                    __uint_as_float(q[4 * cc + 3]));
             float x = 0.0f;
-            float t = __uint_as_float(v[c].x) - __uint_as_float(q[4 * cc]);
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].y) - __uint_as_float(q[4 * cc + 1]);
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].z) - __uint_as_float(q[4 * cc + 2]);
-            x = fmaf(t, t, x);
-            t = __uint_as_float(v[c].w) - __uint_as_float(q[4 * cc + 3]);
-            x = fmaf(t, t, x);
+            x = fmaf(t01.x, t01.x, x);
+            x = fmaf(t01.y, t01.y, x);
+            x = fmaf(t23.x, t23.x, x);
+            x = fmaf(t23.y, t23.y, x);
             tp[32 * c + lane] = x;             // past Dp: row and query are 0, so x = +0
         }
     }
@@ -1627,7 +1648,10 @@ __device__ __forceinline__ float row_cr32_tm(const uint4 (&v)[8], uint32_t tq, f
     const int sw = (lane >> 2) & 1;
     const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
     const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
-    return ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w));
+    // ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w))
+    const float2 sxy = add2(h0.x, h0.y, h1.x, h1.y), szw = add2(h0.z, h0.w, h1.z, h1.w);
+    const float2 t = add2(sxy.x, sxy.y, szw.x, szw.y);
+    return t.x + t.y;
 }
 
 __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *__restrict__ Qr, long long stride,
