@@ -1477,7 +1477,10 @@ __device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const flo
 // adds row p in block order and stores pair p's distance.
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
-constexpr int GT_RB = 8;            // ranges per scoring item (one query load per block)
+// id ranges per scoring item (one query load per item): the CTAs in flight share
+// one block of ranges, which must stay in L2 (FP32 rows: 63 MB at D = 960)
+constexpr int GT_RB = 4;            // FP32 (k_gscore_tm)
+constexpr int GS_RB = 8;            // BF16 / E4M3 (k_gscore)
 // per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
 template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
 
@@ -1493,7 +1496,7 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
     const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *gb = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
     const int ngroups = (u.nq + GS_G - 1) / GS_G;
-    const int nrb = (u.R + GT_RB - 1) / GT_RB;
+    const int nrb = (u.R + GS_RB - 1) / GS_RB;
     const long long items = (long long)ngroups * nrb;
     int cur_g = -1;
     int npend = 0, pj = 0, ppos = 0;     // pending pairs; lane p < npend: member and list position of pair p
@@ -1521,7 +1524,7 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
         __syncthreads();
         const long long it = s_it;
         if (it >= items) break;
-        // items are (block of GT_RB ranges, group), range-block-major: one query
+        // items are (block of GS_RB ranges, group), range-block-major: one query
         // load per block, and the CTAs in flight score the same few ranges of
         // rows for different groups, so a row comes from DRAM about once per batch
         const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
@@ -1538,8 +1541,8 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__r
             cur_g = g;
         }
         __syncthreads();
-        const int r_end = (rb + 1) * GT_RB < u.R ? (rb + 1) * GT_RB : u.R;
-        for (int r = rb * GT_RB; r < r_end; ++r) {      // no barrier between the block's ranges
+        const int r_end = (rb + 1) * GS_RB < u.R ? (rb + 1) * GS_RB : u.R;
+        for (int r = rb * GS_RB; r < r_end; ++r) {      // no barrier between the block's ranges
             const int2 itm = u.items[(long long)g * u.R + r];
             const int e0 = itm.x, ne = itm.y;
             uint4 v[8];
