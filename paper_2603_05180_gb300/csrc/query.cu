@@ -420,14 +420,74 @@ __device__ __forceinline__ unsigned valid_mask(int first, int nvalid) {
 constexpr int CNT_WARP_BYTES = CRISP_TILE / (CNT_NT / 32);  // 4096 bytes of counters per warp
 constexpr int CNT_ROUNDS = CNT_WARP_BYTES / 512;             // 16 bytes per lane per round
 
-// Emit, in ascending id, the ids of tile t whose counter v satisfies v > s_hi,
-// or v == s_hi and the id is among the first need_eq such ids counted from the
-// start of the query (*eq_seen holds how many came before this tile).  Each
-// warp owns a contiguous 4 KB of counters, read 512 B per round without bank
-// conflicts.  Returns the number emitted (block-uniform).
-// Fast form of emit_tile for need_eq == 0 (only v > s_hi selected): count per
-// warp, then each warp re-reads the rounds that hold selections and writes
-// each lane's selected ids by walking the set bits of its masks.
+// Bit 7 of each byte of w that is > s, for s in [0, 127] (addc = (127 - s)
+// 0x01010101): the branch-free core of gt_bits.
+__device__ __forceinline__ unsigned gt_bits_lo(unsigned w, unsigned addc) {
+    return (((w & 0x7F7F7F7Fu) + addc) | w) & 0x80808080u;
+}
+
+// One warp's emit over its counters: FAST (every byte valid and s_hi in
+// [0, 127]) uses gt_bits_lo without the valid-byte masks.
+template <bool FAST>
+__device__ __forceinline__ int emit_count(const uint4 *wc, int s_hi, unsigned addc, int vlim) {
+    const int lane = threadIdx.x & 31;
+    int c_gt = 0;
+#pragma unroll 4
+    for (int r = 0; r < CNT_ROUNDS; ++r) {
+        const int b0 = r * 512 + lane * 16;
+        const uint4 v = wc[r * 32 + lane];
+        const unsigned ws[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            c_gt += __popc(FAST ? gt_bits_lo(ws[u], addc) : gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim));
+    }
+    return c_gt;
+}
+
+template <bool FAST>
+__device__ __forceinline__ void emit_write(const uint4 *wc, int s_hi, unsigned addc, int vlim, long long pos_run,
+                                           long long id0, int *candq, uint8_t *scoreq, long long stride) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < CNT_ROUNDS; ++r) {
+        const int b0 = r * 512 + lane * 16;
+        const uint4 v = wc[r * 32 + lane];
+        const unsigned ws[4] = {v.x, v.y, v.z, v.w};
+        unsigned gm[4];
+        int g_l = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            gm[u] = FAST ? gt_bits_lo(ws[u], addc) : gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim);
+            g_l += __popc(gm[u]);
+        }
+        if (!__any_sync(0xffffffffu, g_l > 0)) continue;
+        int s_in = g_l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s_in, o);
+            if (lane >= o) s_in += y;
+        }
+        long long pos = pos_run + (s_in - g_l);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            unsigned m = gm[u];
+            while (m) {
+                const int bb = (__ffs(m) - 1) >> 3;     // byte of the lowest set bit 7 + 8 bb
+                m &= m - 1;
+                if (pos < stride) {
+                    candq[pos] = (int)(id0 + b0 + 4 * u + bb);
+                    if (scoreq) scoreq[pos] = (uint8_t)((ws[u] >> (8 * bb)) & 0xFFu);
+                }
+                ++pos;
+            }
+        }
+        pos_run += __shfl_sync(0xffffffffu, s_in, 31);
+    }
+}
+
+// Emit, in ascending id, the ids of tile t whose counter v satisfies v > s_hi
+// (the need_eq == 0 form of emit_tile): count per warp, then each warp re-reads
+// its counters and writes each lane's selected ids by walking the set bits of
+// its masks.
 __device__ long long emit_tile_gt(const IxView &ix, CountShared &S, const uint32_t *cnt, int t, int s_hi,
                                   long long out_base, int *candq, uint8_t *scoreq, long long stride) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -435,20 +495,9 @@ __device__ long long emit_tile_gt(const IxView &ix, CountShared &S, const uint32
     long long lim = ix.N - id0;
     const int vlim = lim <= 0 ? 0 : (lim >= CNT_WARP_BYTES ? CNT_WARP_BYTES : (int)lim);
     const uint4 *wc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(cnt) + warp * CNT_WARP_BYTES);
-    int c_gt = 0;
-#pragma unroll 4
-    for (int r = 0; r < CNT_ROUNDS; ++r) {
-        const int b0 = r * 512 + lane * 16;
-        const uint4 v = wc[r * 32 + lane];
-        const unsigned ws[4] = {v.x, v.y, v.z, v.w};
-        if (b0 + 16 <= vlim) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) c_gt += __popc(gt_bits(ws[u], s_hi));
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) c_gt += __popc(gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim));
-        }
-    }
+    const bool fast = vlim == CNT_WARP_BYTES && s_hi >= 0 && s_hi <= 127;    // warp-uniform
+    const unsigned addc = fast ? (unsigned)(127 - s_hi) * 0x01010101u : 0u;
+    int c_gt = fast ? emit_count<true>(wc, s_hi, addc, vlim) : emit_count<false>(wc, s_hi, addc, vlim);
 #pragma unroll
     for (int o = 16; o; o >>= 1) c_gt += __shfl_xor_sync(0xffffffffu, c_gt, o);
     if (lane == 0) S.w_gt[warp] = c_gt;
@@ -464,46 +513,18 @@ __device__ long long emit_tile_gt(const IxView &ix, CountShared &S, const uint32
     __syncthreads();
     const long long tot_sel = S.tile_sel;
     if (S.w_gt[warp] > 0) {
-        long long pos_run = S.w_outbase[warp];
-        for (int r = 0; r < CNT_ROUNDS; ++r) {
-            const int b0 = r * 512 + lane * 16;
-            const uint4 v = wc[r * 32 + lane];
-            const unsigned ws[4] = {v.x, v.y, v.z, v.w};
-            unsigned gm[4];
-            int g_l = 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                gm[u] = gt_bits(ws[u], s_hi) & valid_mask(b0 + 4 * u, vlim);
-                g_l += __popc(gm[u]);
-            }
-            if (!__any_sync(0xffffffffu, g_l > 0)) continue;
-            int s_in = g_l;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, s_in, o);
-                if (lane >= o) s_in += y;
-            }
-            long long pos = pos_run + (s_in - g_l);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                unsigned m = gm[u];
-                while (m) {
-                    const int bb = (__ffs(m) - 1) >> 3;     // byte of the lowest set bit 7 + 8 bb
-                    m &= m - 1;
-                    if (pos < stride) {
-                        candq[pos] = (int)(id0 + b0 + 4 * u + bb);
-                        if (scoreq) scoreq[pos] = (uint8_t)((ws[u] >> (8 * bb)) & 0xFFu);
-                    }
-                    ++pos;
-                }
-            }
-            pos_run += __shfl_sync(0xffffffffu, s_in, 31);
-        }
+        if (fast) emit_write<true>(wc, s_hi, addc, vlim, S.w_outbase[warp], id0, candq, scoreq, stride);
+        else emit_write<false>(wc, s_hi, addc, vlim, S.w_outbase[warp], id0, candq, scoreq, stride);
     }
     __syncthreads();
     return tot_sel;
 }
 
+// Emit, in ascending id, the ids of tile t whose counter v satisfies v > s_hi,
+// or v == s_hi and the id is among the first need_eq such ids counted from the
+// start of the query (*eq_seen holds how many came before this tile).  Each
+// warp owns a contiguous 4 KB of counters, read 512 B per round without bank
+// conflicts.  Returns the number emitted (block-uniform).
 __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t *cnt, int t, int s_hi, long long need_eq,
                                long long *eq_seen, long long out_base, int *candq, uint8_t *scoreq, long long stride) {
     if (need_eq <= 0) return emit_tile_gt(ix, S, cnt, t, s_hi, out_base, candq, scoreq, stride);
@@ -1122,14 +1143,14 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
 // ------------------------------------------- grouped scoring (row reuse)
 // The candidate sets of a large batch overlap: on the 1M-row workload a row is a
 // candidate of about 200 of 10,000 queries.  Queries are ordered by the MinHash
-// of their candidate sets and cut into groups of GS_G; the id space into ranges
-// of GS_SPAN ids.  k_gunion lists, for each (group, range), the rows some member
-// needs, with the member mask and where each (row, member) distance goes in
-// that member's list.  k_gscore then reads each listed row once and scores it
-// against every member that needs it, loading the next row while it computes.
-// The per-(row, query) arithmetic is the streaming kernels' CR32 order, and
+// of their candidate sets and cut into groups (of GT_G, at most GS_G); the id
+// space into ranges of GS_SPAN ids.  k_gunion lists, for each (group, range),
+// the rows some member needs, with the member mask and where each (row, member)
+// distance goes in that member's list.  The scorers (k_gscore_tm, k_gscore)
+// then read each listed row once and score it against every member that needs
+// it.  The per-(row, query) arithmetic is the streaming kernels' CR32 order, and
 // every distance lands in its own slot, so results do not depend on grouping.
-constexpr int GS_G = 32;            // members per group (bit mask)
+constexpr int GS_G = 32;            // most members a group can have (bit mask)
 constexpr int GS_SPAN = 4096;       // ids per range
 constexpr int SCH_MAXQ = 32768;     // the ordering sorts 15-bit query numbers in one CTA
 constexpr int GS_MINQ = 1024;       // batches smaller than this stream per query
@@ -1366,15 +1387,16 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
     }
 }
 
-// The grouped scorers.  A CTA (one per SM) takes (id range, group) items; a
-// warp takes one listed row at a time, keeps it in registers and scores it
-// against every member of the group that needs it.
+// The grouped scorers.  A CTA (one per SM) takes (block of id ranges, group)
+// items; a warp takes one listed row at a time, keeps it in registers and scores
+// it against every member of the group that needs it.  The group's 16 queries
+// sit in tensor memory (TMEM), so a pair's query read stays out of the L1 /
+// shared-memory pipe.
 //  - BF16 / E4M3 rows (k_gscore): lane l holds the row's 32-dim block l, widened
 //    (dequantised) to FP32 once per row, so the CR32 lane partials and their xor
-//    tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers.  The group's
-//    32 queries sit in shared memory with float4 u of block b at slot
-//    u ^ (b & 7), so the eight lanes of a quarter-warp read distinct banks.
-//  - FP32 rows (k_gscore_tm): warp layout, queries in tensor memory (below).
+//    tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers.
+//  - FP32 rows (k_gscore_tm): warp layout (coalesced row loads), partials
+//    transposed through shared memory (below).
 // Either way each pair ends with the sum of block `lane` in every lane, and the
 // block sums are added in block order by the batched gather.
 // Packed FP32 pairs (sm_100 family): each half is one IEEE round-to-nearest
@@ -1449,28 +1471,6 @@ __device__ __forceinline__ void widen_e4m3(const uint4 (&v)[8], float sc, float 
     }
 }
 
-// CR32 block sum of this lane's widened BF16 / E4M3 block against query q (swizzled).
-__device__ __forceinline__ float block_sum_lb_w(const float (&xr)[32], const float4 *q, int nb) {
-    const int lane = threadIdx.x & 31;
-    if (lane >= nb) return 0.0f;
-    const float4 *qb = q + 8 * lane;
-    const int sw = lane & 7;
-    float a[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const float4 qq = qb[u ^ sw];
-        const float2 t01 = sub2(xr[4 * u], xr[4 * u + 1], qq.x, qq.y);
-        const float2 t23 = sub2(xr[4 * u + 2], xr[4 * u + 3], qq.z, qq.w);
-        float x = 0.0f;
-        x = fmaf(t01.x, t01.x, x);
-        x = fmaf(t01.y, t01.y, x);
-        x = fmaf(t23.x, t23.x, x);
-        x = fmaf(t23.y, t23.y, x);
-        a[u] = x;
-    }
-    return block_tree(a);
-}
-
 // Batched gather of the block sums: each scored (row, member) pair leaves its
 // 32 block sums as one row of the warp's gather buffer (row stride GB_LD, so a
 // column read by 32 lanes hits 32 banks); once GB_K pairs are pending, lane p
@@ -1483,99 +1483,6 @@ constexpr int GT_RB = 4;            // FP32 (k_gscore_tm)
 constexpr int GS_RB = 8;            // BF16 / E4M3 (k_gscore)
 // per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
 template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
-
-template <int PREC>
-__global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
-                                                    GUnion u, float *__restrict__ dbuf) {
-    static_assert(PREC == 1 || PREC == 2, "FP32 rows are scored by k_gscore_tm");
-    constexpr int NT = GK_NT, NW = GK_NT / 32;
-    // [GS_G][Dp / 4] query copies (swizzled per block), then gw_floats per warp
-    extern __shared__ __align__(16) float4 gq4[];
-    __shared__ long long s_it;
-    __shared__ int s_mem[GS_G];
-    const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *gb = reinterpret_cast<float *>(gq4 + (size_t)GS_G * (Dp >> 2)) + (size_t)warp * gw_floats<PREC>();
-    const int ngroups = (u.nq + GS_G - 1) / GS_G;
-    const int nrb = (u.R + GS_RB - 1) / GS_RB;
-    const long long items = (long long)ngroups * nrb;
-    int cur_g = -1;
-    int npend = 0, pj = 0, ppos = 0;     // pending pairs; lane p < npend: member and list position of pair p
-    // one scored pair: its block sums become gather row npend
-    auto push = [&](float bs, int j, int slot) {
-        gb[npend * GB_LD + lane] = bs;
-        if (lane == npend) {
-            pj = j;
-            ppos = u.pair_pos[slot];
-        }
-        __syncwarp();                   // partial reads and gather writes done before reuse
-        if (++npend == GB_K) {
-            if (lane < npend) {
-                const float *row = gb + lane * GB_LD;
-                float acc = 0.0f;
-                for (int b = 0; b < nb; ++b) acc = acc + row[b];
-                dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
-            }
-            __syncwarp();
-            npend = 0;
-        }
-    };
-    for (;;) {
-        if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
-        __syncthreads();
-        const long long it = s_it;
-        if (it >= items) break;
-        // items are (block of GS_RB ranges, group), range-block-major: one query
-        // load per block, and the CTAs in flight score the same few ranges of
-        // rows for different groups, so a row comes from DRAM about once per batch
-        const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
-        const int gsize = (g + 1) * GS_G <= u.nq ? GS_G : u.nq - g * GS_G;
-        if (g != cur_g) {
-            if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GS_G + threadIdx.x];
-            __syncthreads();
-            const int n4 = Dp >> 2;
-            for (int e = threadIdx.x; e < gsize * n4; e += NT) {
-                const int j = e / n4, f = e % n4, b = f >> 3, uu = f & 7;
-                gq4[(size_t)j * n4 + 8 * b + (uu ^ (b & 7))] =
-                    reinterpret_cast<const float4 *>(Qr + (long long)s_mem[j] * Dp)[f];
-            }
-            cur_g = g;
-        }
-        __syncthreads();
-        const int r_end = (rb + 1) * GS_RB < u.R ? (rb + 1) * GS_RB : u.R;
-        for (int r = rb * GS_RB; r < r_end; ++r) {      // no barrier between the block's ranges
-            const int2 itm = u.items[(long long)g * u.R + r];
-            const int e0 = itm.x, ne = itm.y;
-            uint4 v[8];
-            // the next row's id is loaded a step ahead, so a row costs one L2 round trip
-            int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
-            for (int e = warp; e < ne; e += NW) {
-                const long long id = id_next;
-                if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
-                row_load_lb<PREC>(v, ix, id, nb);
-                float xr[32];
-                if (PREC == 1) widen_bf16(v, xr);
-                else widen_e4m3(v, ix.S8[id], xr);
-                const unsigned m0 = u.ent_mask[e0 + e];
-                const int pb = u.ent_pb[e0 + e];
-                unsigned m = m0;
-                for (int i = 0; m; ++i) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    push(block_sum_lb_w(xr, gq4 + (size_t)j * (Dp >> 2), nb), j, pb + i);
-                }
-            }
-        }
-        if (lane < npend) {                     // the item's last pairs (s_mem changes with the group)
-            const float *row = gb + lane * GB_LD;
-            float acc = 0.0f;
-            for (int b = 0; b < nb; ++b) acc = acc + row[b];
-            dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
-        }
-        __syncwarp();
-        npend = 0;
-        __syncthreads();
-    }
-}
 
 // ------------------------------ FP32 grouped scorer, queries in tensor memory
 // Warp layout for FP32 rows: lane l holds dims 128 c + 4 l .. + 3 (coalesced
@@ -1780,6 +1687,152 @@ __global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *
     }
 }
 
+// BF16 / E4M3 rows, lane per block, the group's 16 queries in TMEM laid out the
+// same way (member j at columns [32 j, 32 j + 32), lane l holding dims
+// 32 l .. 32 l + 31 of block l): sum of block `lane` of the widened row xr.
+__device__ __forceinline__ float block_sum_tm(const float (&xr)[32], uint32_t tq) {
+    float a[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t q[16];
+        tm_ld16(tq + 16 * h, q);
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) {
+            const int u = 4 * h + uu;
+            const float2 t01 = sub2(xr[4 * u], xr[4 * u + 1], __uint_as_float(q[4 * uu]), __uint_as_float(q[4 * uu + 1]));
+            const float2 t23 = sub2(xr[4 * u + 2], xr[4 * u + 3], __uint_as_float(q[4 * uu + 2]), __uint_as_float(q[4 * uu + 3]));
+            float x = 0.0f;
+            x = fmaf(t01.x, t01.x, x);
+            x = fmaf(t01.y, t01.y, x);
+            x = fmaf(t23.x, t23.x, x);
+            x = fmaf(t23.y, t23.y, x);
+            a[u] = x;
+        }
+    }
+    return block_tree(a);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(GK_NT, 1) k_gscore(IxView ix, const float *__restrict__ Qr, long long stride,
+                                                    GUnion u, float *__restrict__ dbuf) {
+    constexpr int NW = GK_NT / 32;
+    extern __shared__ __align__(16) float gsm[];
+    __shared__ long long s_it;
+    __shared__ int s_mem[GT_G];
+    __shared__ uint32_t s_tmem;
+    const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *gb = gsm + (size_t)warp * gw_floats<PREC>();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(GT_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tq0 = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const int ngroups = (u.nq + GT_G - 1) / GT_G;
+    const int nrb = (u.R + GS_RB - 1) / GS_RB;
+    const long long items = (long long)ngroups * nrb;
+    int cur_g = -1;
+    int npend = 0, pj = 0, ppos = 0;
+    auto push = [&](float bs, int j, int slot) {
+        gb[npend * GB_LD + lane] = bs;
+        if (lane == npend) {
+            pj = j;
+            ppos = u.pair_pos[slot];
+        }
+        __syncwarp();
+        if (++npend == GB_K) {
+            if (lane < npend) {
+                const float *row = gb + lane * GB_LD;
+                float acc = 0.0f;
+                for (int b = 0; b < nb; ++b) acc = acc + row[b];
+                dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+            }
+            __syncwarp();
+            npend = 0;
+        }
+    };
+    for (;;) {
+        if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        const long long it = s_it;
+        if (it >= items) break;
+        const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
+        const int gsize = (g + 1) * GT_G <= u.nq ? GT_G : u.nq - g * GT_G;
+        if (g != cur_g) {
+            if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GT_G + threadIdx.x];
+            __syncthreads();
+            for (int j = warp >> 2; j < GT_G; j += NW / 4) {
+                const float *qrow = Qr + (long long)(j < gsize ? s_mem[j] : 0) * Dp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t q[16];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int d = 32 * lane + 16 * h + 4 * cc;
+                        const uint4 x = j < gsize && d < Dp ? __ldg(reinterpret_cast<const uint4 *>(qrow + d))
+                                                            : make_uint4(0, 0, 0, 0);
+                        q[4 * cc] = x.x;
+                        q[4 * cc + 1] = x.y;
+                        q[4 * cc + 2] = x.z;
+                        q[4 * cc + 3] = x.w;
+                    }
+                    __syncwarp();
+                    tm_st16(tq0 + 32 * j + 16 * h, q);
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            cur_g = g;
+            tm_fence_before();
+            __syncthreads();
+            tm_fence_after();
+        }
+        const int r_end = (rb + 1) * GS_RB < u.R ? (rb + 1) * GS_RB : u.R;
+        for (int r = rb * GS_RB; r < r_end; ++r) {
+            const int2 itm = u.items[(long long)g * u.R + r];
+            const int e0 = itm.x, ne = itm.y;
+            uint4 v[8];
+            int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
+            for (int e = warp; e < ne; e += NW) {
+                const long long id = id_next;
+                if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
+                row_load_lb<PREC>(v, ix, id, nb);
+                float xr[32];
+                if (PREC == 1) widen_bf16(v, xr);
+                else widen_e4m3(v, ix.S8[id], xr);
+                const unsigned m0 = u.ent_mask[e0 + e];
+                const int pb = u.ent_pb[e0 + e];
+                unsigned m = m0;
+                for (int i = 0; m; ++i) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    __syncwarp();
+                    push(block_sum_tm(xr, tq0 + 32 * j), j, pb + i);
+                }
+            }
+        }
+        if (lane < npend) {
+            const float *row = gb + lane * GB_LD;
+            float acc = 0.0f;
+            for (int b = 0; b < nb; ++b) acc = acc + row[b];
+            dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
+        }
+        __syncwarp();
+        npend = 0;
+    }
+    tm_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tm_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(GT_COLS) : "memory");
+    }
+}
+
 // Grouped scoring of a batch into dbuf, or *done = false when the batch does not
 // qualify (then the caller streams per query).
 template <int PREC>
@@ -1788,7 +1841,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     *done = false;
     if (nq < GS_MINQ || nq > SCH_MAXQ || ix->Dp > 1024 || stride < GS_MINSTRIDE) return CRISP_OK;
     const int R = (int)((ix->N + GS_SPAN - 1) / GS_SPAN);
-    const int G = PREC == 0 ? GT_G : GS_G;
+    const int G = GT_G;
     const int ngroups = (nq + G - 1) / G;
     const long long cap = (long long)nq * std::min<int64_t>(stride, ix->N);
     if (cap > (1LL << 31) - 1) return CRISP_OK;
@@ -1837,14 +1890,13 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // one CTA per SM (its registers fill the SM), so its 512 TMEM columns are always free
+        const size_t smem = sizeof(float) * (size_t)(GK_NT / 32) * gw_floats<PREC>();
         if constexpr (PREC == 0) {
-            // one CTA per SM (its registers fill the SM), so its 512 TMEM columns are always free
-            const size_t smem = sizeof(float) * (size_t)(GK_NT / 32) * gw_floats<0>();
             e = cudaFuncSetAttribute(k_gscore_tm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
             k_gscore_tm<<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
         } else {
-            const size_t smem = sizeof(float) * ((size_t)GS_G * ix->Dp + (size_t)(GK_NT / 32) * gw_floats<PREC>());
             e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
             k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
