@@ -4,8 +4,16 @@
 //   k_activate      Q2 + Q3  half distances, sorted lists, multi-sequence cell walk
 //   k_count_cut     Q4 + Q5  collision counting in shared-memory id tiles + threshold cut
 //   k_dist_flat     Q6       exact CR32 distances of all (query, candidate) pairs, persistent
+//                            (batches under 1,024 queries)
+//   k_minhash_key, k_sort_queries, k_sched_pos, k_gunion
+//                   Q6 / F2  large batches: MinHash query groups, and per (group, id
+//                            range) the rows some member needs
+//   k_gscore_tm     Q6       large batches: each such row read once and scored in FP32
+//                            against its members, queries in tensor memory
 //   k_select_rows   Q6       per query: radix select + bitonic top-k of those distances
-//   k_score_flat    F2       BF16 / FP8 E4M3 coarse CR32 scores, persistent
+//   k_score_flat    F2       BF16 / FP8 E4M3 coarse CR32 scores, persistent (small batches)
+//   k_gscore        F2       the same coarse scores for large batches, grouped like
+//                            k_gscore_tm
 //   k_short_select  F2       per query: the shortlist of the best coarse scores
 #include <float.h>
 #include <limits.h>
