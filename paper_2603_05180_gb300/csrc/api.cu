@@ -345,7 +345,7 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
     size_t budget_bytes = (size_t)16 << 30;
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
-    chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, 32768));
+    chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, CRISP_GROUP_MAXQ));   // chunks stay groupable
     pl->chunk = (int32_t)std::min<int64_t>(chunk, std::max<int32_t>(nq, 1));
     return CRISP_OK;
 }

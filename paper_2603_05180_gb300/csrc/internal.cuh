@@ -16,6 +16,7 @@
 #define CRISP_KMAX 64
 #define CRISP_KOUT_MAX 256
 #define CRISP_OPT_MAX_CAND 32768
+#define CRISP_GROUP_MAXQ 16384   // largest batch the grouped scorers order (one CTA sorts its keys)
 
 struct crisp_index {
     int64_t N = 0;

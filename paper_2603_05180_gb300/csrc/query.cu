@@ -1160,44 +1160,56 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
 // every distance lands in its own slot, so results do not depend on grouping.
 constexpr int GS_G = 32;            // most members a group can have (bit mask)
 constexpr int GS_SPAN = 4096;       // ids per range
-constexpr int SCH_MAXQ = 32768;     // the ordering sorts 15-bit query numbers in one CTA
+constexpr int SCH_MAXQ = CRISP_GROUP_MAXQ;  // the ordering sorts 64-bit keys of 14-bit query numbers in one CTA
 constexpr int GS_MINQ = 1024;       // batches smaller than this stream per query
 constexpr int GS_MINSTRIDE = 2048;  // so do short candidate lists (shortlists)
 constexpr int GU_NT = 256;
 // scorer CTA: 24 warps, 80 registers a thread at most, no spills
 constexpr int GK_NT = 768;
 
-// key[q] = (min over the candidates of a 24-bit multiplicative hash of the id,
-// clamped to 17 bits) << 15 | q: one block per query.
+// key[q] = h1 << 34 | h2 << 14 | q, where h1 and h2 are the minima over the
+// candidates of two 24-bit multiplicative hashes of the id, clamped to 20 bits:
+// queries sorted by (h1, h2) put those that share their first and second
+// min-hash candidates next to each other.  One block per query.
 __global__ void __launch_bounds__(RR_NT) k_minhash_key(const int *__restrict__ cand, long long stride,
                                                        const long long *__restrict__ ncand, int nq,
-                                                       unsigned *__restrict__ key) {
-    __shared__ unsigned wmin[RR_NT / 32];
+                                                       unsigned long long *__restrict__ key) {
+    __shared__ unsigned wmin[2][RR_NT / 32];
     const int q = blockIdx.x;
     const long long n = ncand[q] < stride ? ncand[q] : stride;
     const int *c = cand + (long long)q * stride;
-    unsigned m = 0xFFFFFFFFu;
+    unsigned m1 = 0xFFFFFFFFu, m2 = 0xFFFFFFFFu;
     for (long long i = threadIdx.x; i < n; i += RR_NT) {
-        const unsigned h = ((unsigned)c[i] * 2654435761u) >> 8;
-        m = h < m ? h : m;
+        const unsigned h1 = ((unsigned)c[i] * 2654435761u) >> 8, h2 = ((unsigned)c[i] * 2246822519u) >> 8;
+        m1 = h1 < m1 ? h1 : m1;
+        m2 = h2 < m2 ? h2 : m2;
     }
-    m = __reduce_min_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+    m1 = __reduce_min_sync(0xffffffffu, m1);
+    m2 = __reduce_min_sync(0xffffffffu, m2);
+    if ((threadIdx.x & 31) == 0) {
+        wmin[0][threadIdx.x >> 5] = m1;
+        wmin[1][threadIdx.x >> 5] = m2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned b = wmin[0];
-        for (int w = 1; w < RR_NT / 32; ++w) b = wmin[w] < b ? wmin[w] : b;
-        b = b > 0x1FFFFu ? 0x1FFFFu : b;
-        key[q] = (b << 15) | (unsigned)q;
+        unsigned a = wmin[0][0], b = wmin[1][0];
+        for (int w = 1; w < RR_NT / 32; ++w) {
+            a = wmin[0][w] < a ? wmin[0][w] : a;
+            b = wmin[1][w] < b ? wmin[1][w] : b;
+        }
+        a = a > 0xFFFFFu ? 0xFFFFFu : a;
+        b = b > 0xFFFFFu ? 0xFFFFFu : b;
+        key[q] = ((unsigned long long)a << 34) | ((unsigned long long)b << 14) | (unsigned long long)q;
     }
 }
 
-// One CTA: bitonic sort of the nq (<= 32768) keys; qord = their low 15 bits.
-__global__ void __launch_bounds__(1024) k_sort_queries(const unsigned *__restrict__ key, int nq, int *__restrict__ qord) {
-    extern __shared__ unsigned sk[];
+// One CTA: bitonic sort of the nq (<= SCH_MAXQ) keys; qord = their low 14 bits.
+__global__ void __launch_bounds__(1024) k_sort_queries(const unsigned long long *__restrict__ key, int nq,
+                                                       int *__restrict__ qord) {
+    extern __shared__ unsigned long long sk[];
     int n2 = 1;
     while (n2 < nq) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += 1024) sk[i] = i < nq ? key[i] : 0xFFFFFFFFu;
+    for (int i = threadIdx.x; i < n2; i += 1024) sk[i] = i < nq ? key[i] : ~0ull;
     __syncthreads();
     for (int size = 2; size <= n2; size <<= 1) {
         for (int st = size >> 1; st > 0; st >>= 1) {
@@ -1205,14 +1217,14 @@ __global__ void __launch_bounds__(1024) k_sort_queries(const unsigned *__restric
                 const int j = i ^ st;
                 if (j > i) {
                     const bool up = (i & size) == 0;
-                    const unsigned a = sk[i], b = sk[j];
+                    const unsigned long long a = sk[i], b = sk[j];
                     if ((a > b) == up) { sk[i] = b; sk[j] = a; }
                 }
             }
             __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < nq; i += 1024) qord[i] = (int)(sk[i] & 0x7FFFu);
+    for (int i = threadIdx.x; i < nq; i += 1024) qord[i] = (int)(sk[i] & 0x3FFFull);
 }
 
 // pos[q][r] = first list position with id >= r GS_SPAN (r = 0..R).
@@ -1855,7 +1867,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     if (cap > (1LL << 31) - 1) return CRISP_OK;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += (b + 255) / 256 * 256; return o; };
-    const size_t o_cnt = take(3 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned) * nq),
+    const size_t o_cnt = take(3 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
                  o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)cap),
                  o_mask = take(sizeof(unsigned) * (size_t)cap), o_pb = take(sizeof(int) * (size_t)cap),
@@ -1864,7 +1876,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
     GUnion u;
     u.counts = (unsigned long long *)(buf + o_cnt);
-    unsigned *key = (unsigned *)(buf + o_key);
+    unsigned long long *key = (unsigned long long *)(buf + o_key);
     u.qord = (int *)(buf + o_qord);
     u.pos = (int *)(buf + o_pos);
     u.items = (int2 *)(buf + o_items);
@@ -1885,9 +1897,9 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
         int n2 = 1;
         while (n2 < nq) n2 <<= 1;
         e = cudaFuncSetAttribute(k_sort_queries, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(unsigned) * n2));
+                                 (int)(sizeof(unsigned long long) * n2));
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
-        k_sort_queries<<<1, 1024, sizeof(unsigned) * n2, st>>>(key, nq, (int *)u.qord);
+        k_sort_queries<<<1, 1024, sizeof(unsigned long long) * n2, st>>>(key, nq, (int *)u.qord);
         CRISP_COUNT_LAUNCH();
         const long long npos = (long long)nq * (R + 1);
         k_sched_pos<<<(unsigned)((npos + 255) / 256), 256, 0, st>>>(cand, (long long)stride,
