@@ -220,28 +220,26 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
     float c_first = 0.0f, c_last = 0.0f;
     int *out = act + ((long long)q * M + m) * K2;
     while (got < budget) {
-        float bc = FLT_MAX;
-        int bi = INT_MAX;
-        bool have = false;
+        // the frontier's smallest (cost, row): costs are sums of squares (>= +0),
+        // so their bit patterns order like the values and two warp minima find
+        // it (no frontier row: key 0xFFFFFFFF, above every finite cost)
+        unsigned key = 0xFFFFFFFFu;
+        int row = INT_MAX;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             int i = lane + 32 * r;
             if (i < K) {
                 int j = rowlen[i];
                 if (j < K && (i == 0 || rowlen[i - 1] > j)) {
-                    float c = s1[i] + s2[j];
-                    if (!have || c < bc || (c == bc && i < bi)) { bc = c; bi = i; have = true; }
+                    const unsigned kb = __float_as_uint(s1[i] + s2[j]);
+                    if (kb < key) { key = kb; row = i; }       // rows rise with r: ties keep the lower
                 }
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            float oc = __shfl_xor_sync(0xffffffffu, bc, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            bool oh = __shfl_xor_sync(0xffffffffu, (int)have, o) != 0;
-            if (oh && (!have || oc < bc || (oc == bc && oi < bi))) { bc = oc; bi = oi; have = true; }
-        }
-        if (!have) break;
+        const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+        if (kmin == 0xFFFFFFFFu) break;
+        const int bi = __reduce_min_sync(0xffffffffu, key == kmin ? row : INT_MAX);
+        const float bc = __uint_as_float(kmin);
         int j = rowlen[bi];
         int cell = p1[bi] * K + p2[j];
         if (count == 0) c_first = bc;
