@@ -49,6 +49,14 @@ def workload_name(args):
 DEFAULT_POINT = dict(mode=0, rho=0.03, alpha=0.3)
 
 
+def max_sm_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -372,6 +380,17 @@ def run_crisp(args):
                 "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "stage_ms": {n: round(v, 4) for n, v in shares.items()},
                 "algorithmic_bytes_per_launch": dbytes}
+    if stage[dom]["kernel"].startswith("k_gscore"):
+        # the same kernel against the FP32 SIMT arithmetic it runs: per candidate a
+        # subtraction and an FMA per padded dim (3 flops); peak from unit counts and
+        # the maximum SM clock (SMs x 128 FP32 lanes x 2 flops per FMA)
+        n_cand = dbytes / (4 * info.Dp + 4)
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sm_count * 128 * 2 * max_sm_mhz() * 1e6 / 1e12
+        alu_ach = 3 * info.Dp * n_cand / (dms / 1e3) / 1e12
+        roofline["alu"] = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                           "frac": alu_ach / alu_peak,
+                           "peak_kind": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x {max_sm_mhz():.0f} MHz"}
     step_bytes = sum(v["bytes"] for v in stage.values())
     roofline_bf16 = None
     if sl_stage:
