@@ -449,7 +449,12 @@ crisp_status crisp_count_cut(const crisp_index *index, const int32_t *act, const
 /* Q6 (§4.3.2 Stage 3, phi = 0): exact CR32 distance from each query row of Qr
  * (device [nq][Dp]) to each of its candidates, then the k smallest by
  * (distance, id).  cand/ncand as written by crisp_count_cut (ascending ids).
- * ids: device [nq][k] int64, sqdist: device [nq][k] float32, padded -1/+inf. */
+ * ids: device [nq][k] int64, sqdist: device [nq][k] float32, padded -1/+inf.
+ * Batches of 1,024 to 16,384 queries with cand_stride >= 2,048 and Dp <= 1,024
+ * are scored in groups of 16 queries that read each shared candidate row once
+ * (queries held in tensor memory); other batches stream (query, candidate)
+ * pairs.  Both give the same bits: every distance is the CR32 order of its own
+ * (query, row) pair. */
 crisp_status crisp_rerank(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
                           int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
                           void *stream);
