@@ -49,6 +49,17 @@ def workload_name(args):
 DEFAULT_POINT = dict(mode=0, rho=0.03, alpha=0.3)
 
 
+def job_rate(torch, dist, dev, local_ms, units):
+    """Whole-job rate over replicas: the slowest rank's time (max over ranks)
+    and all ranks' units divided by it.  dist is torch.distributed or None."""
+    total_ms = float(local_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return total_ms, units / (total_ms / 1e3)
+
+
 def max_sm_mhz():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -351,16 +362,11 @@ def run_crisp(args):
         dist.barrier()
     clk = clocks.stop() if rank == 0 else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms, qps = job_rate(torch, dist, dev, sum(step_ms), world * nq * args.steps)
     rec = recall_at_k(torch, X, Q, ids, gdk)
     rec_sub = recall_at_k(torch, X, Q[:2000], ids[:2000], gdk[:2000])
     d2_err = d2_error(torch, X, Q, ids, d2)
     stats = st.cpu().numpy()
-    qps = world * nq * args.steps / (total_ms / 1e3)
 
     # ---- stage-timed pass through the step entry points (same kernels, same launch shapes)
     stage = stage_pass(torch, crisp, ix, info, Q, point, k, args.steps, stream, flush)
@@ -443,7 +449,7 @@ def run_crisp(args):
         t = time.perf_counter()
         crisp.crisp_search_host(ix, Qh, nq, sp, ih, dh, None, stream)
         e2e_t.append(time.perf_counter() - t)
-    e2e_qps = world * nq * len(e2e_t) / sum(e2e_t)
+    _, e2e_qps = job_rate(torch, dist, dev, 1e3 * sum(e2e_t), world * nq * len(e2e_t))
 
     # ---- CPU oracle baseline (rank 0, one GPU only)
     cpu = None
