@@ -1544,7 +1544,7 @@ __device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int d = c * 128 + 4 * lane;
-        // a plain load: the other groups score the same rows next (range-major items)
+        // a plain load: the other groups score the same rows next (range-block-major items)
         v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
     }
 }
