@@ -769,7 +769,7 @@ def run_ablation(args):
 
 def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     """Time each kernel of the search path with CUDA events on the launching stream,
-    and count the algorithmic bytes each launch must move (DESIGN: per-stage units)."""
+    and count the algorithmic bytes each launch must move (the per-stage units of each kernel)."""
     nq, Dp, M, K = Q.shape[0], info.Dp, info.M, info.K
     dev = Q.device
     tau = crisp.tau(point["alpha"], M)

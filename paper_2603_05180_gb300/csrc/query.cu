@@ -2269,9 +2269,10 @@ extern "C" crisp_status crisp_rerank_noalloc(const crisp_index *ix, const float 
     CRISP_REQUIRE(k >= 1 && k <= CRISP_KOUT_MAX, "crisp_rerank_noalloc: k outside [1, 256]");
     CRISP_REQUIRE(cand_stride >= 1, "crisp_rerank_noalloc: cand_stride < 1");
     CRISP_REQUIRE(nq == 0 || (cand && ncand && ids && sqdist), "crisp_rerank_noalloc: null pointer");
-    CRISP_REQUIRE((int64_t)nq * cand_stride <= (int64_t)CRISP_RERANK_NOALLOC_MAX,
-                  "crisp_rerank_noalloc: nq * cand_stride = %lld exceeds the fixed scratch of %d floats",
-                  (long long)nq * cand_stride, CRISP_RERANK_NOALLOC_MAX);
+    // compared without forming nq * cand_stride, which could overflow
+    CRISP_REQUIRE(cand_stride <= (int64_t)CRISP_RERANK_NOALLOC_MAX / (nq > 0 ? nq : 1),
+                  "crisp_rerank_noalloc: nq * cand_stride (%d x %lld) exceeds the fixed scratch of %d floats", nq,
+                  (long long)cand_stride, CRISP_RERANK_NOALLOC_MAX);
     if (nq == 0) return CRISP_OK;
     float *dbuf = nullptr;
     s = noalloc_scratch(&dbuf);

@@ -210,3 +210,54 @@ def test_full_size_build_and_search_properties():
     crisp.crisp_search(ix, Q[:500].contiguous(), 500,
                        crisp.search_params(k=10, **{k: v for k, v in bench.DEFAULT_POINT.items()}), ids_s, d2_s)
     assert torch.equal(ids_s, ids[:500]) and torch.equal(d2_s, d2[:500])
+
+
+@pytest.mark.slow
+def test_full_size_steps_equal_the_oracle():
+    """The benchmark's workload (1M x 960, M = 20) on an index the oracle built
+    from the same rows and draws: a 2,000-query batch (large enough for the
+    grouped re-rank) through the library's steps, and for 200 sampled queries
+    the visited cells, candidate lists, their scores and the re-ranked top-10
+    equal the oracle's, element by element."""
+    import bench
+
+    N, D, M, nq = 1_000_000, 960, 20, 2000
+    X, Q = synthetic.powerlaw(N, D, nq, device="cuda")
+    Xh, Qh = X.cpu().numpy(), Q.cpu().numpy()
+    del X
+    ix_o = oracle.build_index(Xh, M=M, draws=synthetic.method_draws(N, D, M, 50))
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    pt = bench.DEFAULT_POINT
+    p = oracle.SearchParams(k=10, mode=pt["mode"], rho=pt["rho"], alpha=pt["alpha"])
+    K2 = ix_o.K * ix_o.K
+    Qr = torch.empty((nq, ix_o.Dp), dtype=torch.float32, device=DEV)
+    crisp.crisp_rotate_rows(Q, nq, D, D, dev(ix_o.R32), Qr, ix_o.Dp)
+    act = torch.empty((nq, M, K2), dtype=torch.int32, device=DEV)
+    nact = torch.empty((nq, M), dtype=torch.int32, device=DEV)
+    bud = oracle.budget(p.rho, N)
+    crisp.crisp_activate(ix, Qr, nq, 0, 10, bud, act, nact)
+    stride = 200_000
+    cand = torch.empty((nq, stride), dtype=torch.int32, device=DEV)
+    ncand = torch.empty((nq,), dtype=torch.int64, device=DEV)
+    score = torch.empty((nq, stride), dtype=torch.uint8, device=DEV)
+    crisp.crisp_count_cut(ix, act, nact, nq, oracle.tau(p.alpha, M), 10, 0, cand, stride, ncand, score)
+    ids = torch.empty((nq, 10), dtype=torch.int64, device=DEV)
+    d2 = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    crisp.crisp_rerank(ix, Qr, nq, cand, stride, ncand, 10, ids, d2)
+    qr_g = Qr.cpu().numpy()
+    nact_g, n_g, gi, gd = nact.cpu().numpy(), ncand.cpu().numpy(), ids.cpu().numpy(), d2.cpu().numpy()
+    assert int(n_g.max()) < stride
+    sample = synthetic.subsample_queries(nq, 200, seed=1)
+    for q in sample:
+        det = oracle.query_detail(ix_o, Qh[q], p)
+        assert np.array_equal(qr_g[q], det["qr"]), q
+        a = act[q].cpu().numpy()
+        for m in range(M):
+            cells, w, _ = det["acts"][m]
+            assert nact_g[q, m] == len(cells) and np.array_equal(a[m, :len(cells)] & 0xFFFF, cells), (q, m)
+        C = det["C"]
+        assert n_g[q] == C.size and np.array_equal(cand[q, :C.size].cpu().numpy(), C), q
+        assert np.array_equal(score[q, :C.size].cpu().numpy(), det["V"][C]), q
+        oi, od = oracle.rerank(ix_o, det["qr"], C, 10)
+        assert np.array_equal(gi[q], oi) and np.array_equal(gd[q], od), q
+    ix.free()

@@ -76,3 +76,13 @@ def test_oracle_blob_header_matches_documented_layout():
         pos = (pos + s + 255) // 256 * 256
     assert len(b) == pos
     assert np.isclose(struct.unpack_from("<d", b, 72)[0], ix.cev)
+
+
+def test_binding_constants_match_the_header():
+    """Constants the binding restates must equal the header's #define values."""
+    import paper_2603_05180_gb300 as crisp
+
+    src = open(os.path.join(ROOT, "include", "crisp.h")).read()
+    m = re.search(r"#define\s+CRISP_RERANK_NOALLOC_MAX\s+\(([^)]*)\)", src)
+    assert m, "CRISP_RERANK_NOALLOC_MAX not found in include/crisp.h"
+    assert eval(m.group(1), {"__builtins__": {}}) == crisp.CRISP_RERANK_NOALLOC_MAX

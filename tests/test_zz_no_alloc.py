@@ -30,8 +30,9 @@ import paper_2603_05180_gb300 as crisp  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
-def _candidates(ix_o, ix, Q, rho, alpha, k):
-    """Rotated queries and their candidate lists from the library's own steps."""
+def _candidates(ix_o, ix, Q, rho, alpha, k, stride=None, cap=0):
+    """Rotated queries and their candidate lists from the library's own steps
+    (at most `cap` candidates a query when cap > 0)."""
     nq, M, K2, Dp = Q.shape[0], ix_o.M, ix_o.K * ix_o.K, ix_o.Dp
     Qd = torch.from_numpy(Q).to(DEV)
     Qr = torch.empty((nq, Dp), dtype=torch.float32, device=DEV)
@@ -39,10 +40,10 @@ def _candidates(ix_o, ix, Q, rho, alpha, k):
     act = torch.empty((nq, M, K2), dtype=torch.int32, device=DEV)
     nact = torch.empty((nq, M), dtype=torch.int32, device=DEV)
     crisp.crisp_activate(ix, Qr, nq, 0, k, crisp.budget(rho, ix_o.N), act, nact)
-    stride = ix_o.N
+    stride = stride or ix_o.N
     cand = torch.empty((nq, stride), dtype=torch.int32, device=DEV)
     ncand = torch.empty((nq,), dtype=torch.int64, device=DEV)
-    crisp.crisp_count_cut(ix, act, nact, nq, crisp.tau(alpha, M), k, 0, cand, stride, ncand)
+    crisp.crisp_count_cut(ix, act, nact, nq, crisp.tau(alpha, M), k, cap, cand, stride, ncand)
     return Qr, cand, stride, ncand
 
 
@@ -68,6 +69,32 @@ def test_rerank_noalloc_matches_rerank_on_two_calls_in_a_row():
     ix.free()
 
 
+def test_rerank_noalloc_matches_the_grouped_rerank_of_a_large_batch():
+    """1,024 queries with lists of up to 2,048 candidates: crisp_rerank scores
+    this batch in query groups that share row reads, the no-allocation entry
+    point streams every (query, candidate) pair; both must give the same bits,
+    on two calls in a row."""
+    X, Q = synthetic.gmm(N=20000, D=256, nq=2048, seed=4)
+    ix_o = oracle.build_index(X, M=8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=4))
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    stride = 2048
+    for Qc, k in ((Q[:1024], 10), (Q[1024:], 30)):
+        Qr, cand, _, ncand = _candidates(ix_o, ix, Qc, 0.05, 0.25, k, stride=stride, cap=stride)
+        nq = Qc.shape[0]
+        assert nq * stride <= crisp.CRISP_RERANK_NOALLOC_MAX
+        assert int(ncand.max()) > 1024
+        ref_i = torch.empty((nq, k), dtype=torch.int64, device=DEV)
+        ref_d = torch.empty((nq, k), dtype=torch.float32, device=DEV)
+        crisp.crisp_rerank(ix, Qr, nq, cand, stride, ncand, k, ref_i, ref_d)
+        got_i = torch.full((nq, k), -7, dtype=torch.int64, device=DEV)
+        got_d = torch.full((nq, k), -7.0, dtype=torch.float32, device=DEV)
+        crisp.crisp_rerank_noalloc(ix, Qr, nq, cand, stride, ncand, k, got_i, got_d)
+        torch.cuda.synchronize()
+        assert torch.equal(got_i, ref_i)
+        assert torch.equal(got_d, ref_d)
+    ix.free()
+
+
 def test_rerank_noalloc_rejects_sizes_beyond_its_scratch():
     X, Q = synthetic.small_gaussian(300, 64, 4, seed=9)
     ix_o = oracle.build_index(X, M=2, K=8, draws=synthetic.method_draws(300, 64, 2, 8, seed=9, kmeans_train=300))
@@ -81,5 +108,11 @@ def test_rerank_noalloc_rejects_sizes_beyond_its_scratch():
                                    torch.zeros(4, dtype=torch.int64, device=DEV), 5, ids, d2)
     assert e.value.status == crisp.CRISP_EINVAL
     assert "exceeds the fixed scratch" in str(e.value)
+    assert bool((ids == -7).all()) and bool((d2 == -7.0).all())
+    # a stride so large that nq * stride would wrap a 64-bit integer
+    with pytest.raises(crisp.CrispError) as e:
+        crisp.crisp_rerank_noalloc(ix, torch.zeros((4, 64), device=DEV), 4, dummy, (1 << 62) + 1,
+                                   torch.zeros(4, dtype=torch.int64, device=DEV), 5, ids, d2)
+    assert e.value.status == crisp.CRISP_EINVAL
     assert bool((ids == -7).all()) and bool((d2 == -7.0).all())
     ix.free()
