@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcrisp_gb300.so")
-SOURCES = ["api.cu", "query.cu", "verify.cu", "build.cu", "learned.cu", "server.cu", "tc.cu"]
+SOURCES = ["api.cu", "query.cu", "verify.cu", "build.cu", "learned.cu", "server.cu", "tc.cu", "rerank_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -129,6 +129,7 @@ static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->Xb);
     cudaFree(ix->X8);
     cudaFree(ix->S8);
+    cudaFree(ix->xn2);
     cudaFree(ix->mlp);
 }
 
@@ -155,6 +156,7 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
         {(void **)&ix->Xr, sizeof(float) * (size_t)ix->N * ix->Dp},
         {(void **)&ix->codes, sizeof(uint32_t) * (size_t)ix->N * (ix->Dp / 32)},
         {(void **)&ix->R32, ix->rotated ? sizeof(float) * (size_t)ix->D * ix->D : 0},
+        {(void **)&ix->xn2, sizeof(float) * (size_t)ix->N},
     };
     ix->bytes = 0;
     for (auto &a : arrs) {
@@ -168,6 +170,7 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
 // Derived tables: per-tile positions inside every cell list, largest cell.
 crisp_status crisp_finish_index(crisp_index *ix, cudaStream_t st) {
     crisp_status s = launch_tile_offsets(ix, st);
+    if (!s) s = launch_row_norms(ix, st);
     if (s) return s;
     const int64_t K2 = (int64_t)ix->K * ix->K;
     std::vector<int32_t> off((size_t)ix->M * (K2 + 1));

@@ -34,6 +34,7 @@ struct crisp_index {
     uint16_t *Xb = nullptr;        // [N][Dp] BF16 bits (optional)
     uint8_t *X8 = nullptr;         // [N][Dp] FP8 E4M3 codes (optional)
     float *S8 = nullptr;           // [N] FP8 row scales (optional)
+    float *xn2 = nullptr;          // [N] |x|^2 of the stored rows, FP64 sum rounded to FP32
     float *mlp = nullptr;          // learned-depth model (F = 2M + 68 -> H -> H -> 2), optional
     int32_t mlp_H = 0;
     int device = 0;
@@ -53,6 +54,7 @@ struct IxView {
     const uint16_t *Xb;
     const uint8_t *X8;
     const float *S8;
+    const float *xn2;
 };
 
 static inline IxView ix_view(const crisp_index *ix) {
@@ -61,6 +63,7 @@ static inline IxView ix_view(const crisp_index *ix) {
     v.cent = ix->cent; v.offsets = ix->offsets; v.ids = ix->ids; v.tile_off = ix->tile_off;
     v.Xr = ix->Xr; v.codes = ix->codes;
     v.Xb = ix->Xb; v.X8 = ix->X8; v.S8 = ix->S8;
+    v.xn2 = ix->xn2;
     return v;
 }
 
@@ -105,6 +108,7 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
 crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
                              cudaStream_t st);
 crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);
+crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st);
 crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
                                 int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
                                 crisp_query_stats *stats, cudaStream_t st);

@@ -3,17 +3,17 @@
 //   k_rotate        Q1       y = x R, FP32, each output an fmaf chain over d in order
 //   k_activate      Q2 + Q3  half distances, sorted lists, multi-sequence cell walk
 //   k_count_cut     Q4 + Q5  collision counting in shared-memory id tiles + threshold cut
-//   k_dist_flat     Q6       exact CR32 distances of all (query, candidate) pairs, persistent
-//                            (batches under 1,024 queries)
-//   k_minhash_key, k_sort_queries, k_sched_pos, k_gunion
-//                   Q6 / F2  large batches: MinHash query groups, and per (group, id
-//                            range) the rows some member needs
-//   k_gscore_tm     Q6       large batches: each such row read once and scored in FP32
-//                            against its members, queries in tensor memory
-//   k_select_rows   Q6       per query: radix select + bitonic top-k of those distances
+//   k_dist_flat     Q6       exact CR32 distances of (query, candidate) pairs, persistent
+//                            (small batches, and the candidates the tensor-core re-rank of
+//                            rerank_tc.cu keeps for the exact measure)
+//   k_minhash_key, k_sort_queries, k_sched_pos
+//                   Q6 / F2  large batches: MinHash query order, list position of each id range
+//   k_bound_select  Q6       per query: the candidates whose distance bound can reach the top-k
+//   k_select_rows   Q6       per query: radix select + bitonic top-k of the exact distances
+//   k_gunion        F2       large batches: per (query group, id range) the rows some member needs
 //   k_score_flat    F2       BF16 / FP8 E4M3 coarse CR32 scores, persistent (small batches)
-//   k_gscore        F2       the same coarse scores for large batches, grouped like
-//                            k_gscore_tm
+//   k_gscore        F2       the same coarse scores for large batches: each row read once per
+//                            group and scored against its members, queries in tensor memory
 //   k_short_select  F2       per query: the shortlist of the best coarse scores
 #include <float.h>
 #include <limits.h>
@@ -282,6 +282,20 @@ __global__ void k_tile_off(IxView ix, int *__restrict__ tile_off) {
         else hi = mid;
     }
     tile_off[gid] = lo;
+}
+
+// |x|^2 of every stored row: FP64 sum of squares rounded once to FP32 (the
+// row norms of the tensor-core re-rank's distance expansion).
+__global__ void k_row_norms(const float *__restrict__ Xr, long long N, int Dp, float *__restrict__ xn2) {
+    const long long n = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;
+    const float *x = Xr + n * Dp;
+    double s = 0.0;
+    for (int d = lane; d < Dp; d += 32) s += (double)x[d] * (double)x[d];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xn2[n] = (float)s;
 }
 
 // ================================================== Q4 + Q5 count and cut
@@ -1152,7 +1166,7 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
 // of their candidate sets and cut into groups (of GT_G, at most GS_G); the id
 // space into ranges of GS_SPAN ids.  k_gunion lists, for each (group, range),
 // the rows some member needs, with the member mask and where each (row, member)
-// distance goes in that member's list.  The scorers (k_gscore_tm, k_gscore)
+// distance goes in that member's list.  The coarse scorers (k_gscore)
 // then read each listed row once and score it against every member that needs
 // it.  The per-(row, query) arithmetic is the streaming kernels' CR32 order, and
 // every distance lands in its own slot, so results do not depend on grouping.
@@ -1413,10 +1427,8 @@ __global__ void __launch_bounds__(GU_NT) k_gunion(const int *__restrict__ cand, 
 //  - BF16 / E4M3 rows (k_gscore): lane l holds the row's 32-dim block l, widened
 //    (dequantised) to FP32 once per row, so the CR32 lane partials and their xor
 //    tree ((a0+a4)+(a2+a6))+((a1+a5)+(a3+a7)) stay in registers.
-//  - FP32 rows (k_gscore_tm): warp layout (coalesced row loads), partials
-//    transposed through shared memory (below).
-// Either way each pair ends with the sum of block `lane` in every lane, and the
-// block sums are added in block order by the batched gather.
+// Each pair ends with the sum of block `lane` in every lane, and the block sums
+// are added in block order by the batched gather.
 // Packed FP32 pairs (sm_100 family): each half is one IEEE round-to-nearest
 // subtraction or addition, exactly the scalar instruction's result.
 __device__ __forceinline__ float2 sub2(float a0, float a1, float b0, float b1) {
@@ -1496,23 +1508,14 @@ __device__ __forceinline__ void widen_e4m3(const uint4 (&v)[8], float sc, float 
 constexpr int GB_K = 16;
 constexpr int GB_LD = 33;
 // id ranges per scoring item (one query load per item): the CTAs in flight share
-// one block of ranges, which must stay in L2 (FP32 rows: 63 MB at D = 960)
-constexpr int GT_RB = 4;            // FP32 (k_gscore_tm)
-constexpr int GS_RB = 8;            // BF16 / E4M3 (k_gscore)
-// per-warp shared scratch: the gather rows; k_gscore_tm adds its CR32 partials
-template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD + (PREC == 0 ? 256 : 0); }
+// one block of ranges, which must stay in L2
+constexpr int GS_RB = 8;
+// per-warp shared scratch: the gather rows
+template <int PREC> __host__ __device__ constexpr int gw_floats() { return GB_K * GB_LD; }
 
-// ------------------------------ FP32 grouped scorer, queries in tensor memory
-// Warp layout for FP32 rows: lane l holds dims 128 c + 4 l .. + 3 (coalesced
-// 16-byte loads), i.e. CR32 lane partial l & 7 of block 4 c + (l >> 3).  The
-// group's queries sit in TMEM, so the per-pair query reads leave the L1 /
-// shared-memory pipe that bounds the scorer: member j of the group occupies
-// columns [32 j, 32 j + 32) of every lane quarter, lane l holding dims
-// 128 c + 4 l + k at column 32 j + 4 c + k.  16 members x 32 columns fill the
-// 512 columns of one CTA.  The partials are transposed through the warp's
-// shared scratch tp[256]: they land at tp[8 block + partial], and lane b reads
-// block b's eight partials (halves swapped on lanes with bit 2 set, so a
-// quarter-warp touches 32 distinct banks) and adds them in the xor-tree order.
+// Group layout in tensor memory: member j of a group of GT_G = 16 occupies
+// columns [32 j, 32 j + 32) of every lane quarter; 16 members x 32 columns fill
+// the 512 columns of one CTA.
 
 constexpr int GT_G = 16;
 constexpr int GT_COLS = 512;
@@ -1538,172 +1541,6 @@ __device__ __forceinline__ void tm_st16(uint32_t taddr, const uint32_t (&r)[16])
 
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void row_load_w(uint4 (&v)[8], const IxView &ix, long long id, int Dp) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int d = c * 128 + 4 * lane;
-        // a plain load: the other groups score the same rows next (range-block-major items)
-        v[c] = d < Dp ? __ldg(reinterpret_cast<const uint4 *>(ix.Xr + id * Dp + d)) : make_uint4(0, 0, 0, 0);
-    }
-}
-
-// CR32 block sum of block `lane` for the row in v (warp layout) against the
-// member whose query starts at TMEM address tq.
-__device__ __forceinline__ float row_cr32_tm(const uint4 (&v)[8], uint32_t tq, float *tp) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t q[16];
-        tm_ld16(tq + 16 * h, q);
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            const int c = 4 * h + cc;
-            const float2 t01 = sub2(__uint_as_float(v[c].x), __uint_as_float(v[c].y), __uint_as_float(q[4 * cc]),
-                                    __uint_as_float(q[4 * cc + 1]));
-            const float2 t23 = sub2(__uint_as_float(v[c].z), __uint_as_float(v[c].w), __uint_as_float(q[4 * cc + 2]),
-                                    __uint_as_float(q[4 * cc + 3]));
-            float x = 0.0f;
-            x = fmaf(t01.x, t01.x, x);
-            x = fmaf(t01.y, t01.y, x);
-            x = fmaf(t23.x, t23.x, x);
-            x = fmaf(t23.y, t23.y, x);
-            tp[32 * c + lane] = x;             // past Dp: row and query are 0, so x = +0
-        }
-    }
-    __syncwarp();
-    const int sw = (lane >> 2) & 1;
-    const float4 h0 = reinterpret_cast<const float4 *>(tp)[2 * lane + sw];
-    const float4 h1 = reinterpret_cast<const float4 *>(tp)[2 * lane + (sw ^ 1)];
-    // ((h0.x + h1.x) + (h0.z + h1.z)) + ((h0.y + h1.y) + (h0.w + h1.w))
-    const float2 sxy = add2(h0.x, h0.y, h1.x, h1.y), szw = add2(h0.z, h0.w, h1.z, h1.w);
-    const float2 t = add2(sxy.x, sxy.y, szw.x, szw.y);
-    return t.x + t.y;
-}
-
-__global__ void __launch_bounds__(GK_NT, 1) k_gscore_tm(IxView ix, const float *__restrict__ Qr, long long stride,
-                                                       GUnion u, float *__restrict__ dbuf) {
-    constexpr int NW = GK_NT / 32;
-    extern __shared__ __align__(16) float gsm[];          // gw_floats<0>() per warp
-    __shared__ long long s_it;
-    __shared__ int s_mem[GT_G];
-    __shared__ uint32_t s_tmem;
-    const int Dp = ix.Dp, nb = Dp >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *tp = gsm + (size_t)warp * gw_floats<0>();
-    float *gb = tp + 256;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(GT_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tm_fence_before();
-    __syncthreads();
-    tm_fence_after();
-    const uint32_t tq0 = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16);    // this warp's lane quarter
-    const int ngroups = (u.nq + GT_G - 1) / GT_G;
-    const int nrb = (u.R + GT_RB - 1) / GT_RB;
-    const long long items = (long long)ngroups * nrb;
-    int cur_g = -1;
-    int npend = 0, pj = 0, ppos = 0;
-    auto push = [&](float bs, int j, int slot) {
-        gb[npend * GB_LD + lane] = bs;
-        if (lane == npend) {
-            pj = j;
-            ppos = u.pair_pos[slot];
-        }
-        __syncwarp();
-        if (++npend == GB_K) {
-            if (lane < npend) {
-                const float *row = gb + lane * GB_LD;
-                float acc = 0.0f;
-                for (int b = 0; b < nb; ++b) acc = acc + row[b];
-                dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
-            }
-            __syncwarp();
-            npend = 0;
-        }
-    };
-    for (;;) {
-        if (threadIdx.x == 0) s_it = (long long)atomicAdd(&u.counts[2], 1ull);
-        tm_fence_before();
-        __syncthreads();
-        tm_fence_after();
-        const long long it = s_it;
-        if (it >= items) break;
-        // items are (block of GT_RB ranges, group), range-block-major: one query
-        // load per block, and the CTAs in flight share GT_RB ranges of rows in L2
-        const int g = (int)(it % ngroups), rb = (int)(it / ngroups);
-        const int gsize = (g + 1) * GT_G <= u.nq ? GT_G : u.nq - g * GT_G;
-        if (g != cur_g) {
-            if (threadIdx.x < gsize) s_mem[threadIdx.x] = u.qord[g * GT_G + threadIdx.x];
-            __syncthreads();
-            // the warps of each lane quarter write that quarter's copy (members
-            // past the group's end are zero and never read)
-            for (int j = warp >> 2; j < GT_G; j += NW / 4) {
-                const float *qrow = Qr + (long long)(j < gsize ? s_mem[j] : 0) * Dp;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t q[16];
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        const int d = (4 * h + cc) * 128 + 4 * lane;
-                        const uint4 x = j < gsize && d < Dp ? __ldg(reinterpret_cast<const uint4 *>(qrow + d))
-                                                            : make_uint4(0, 0, 0, 0);
-                        q[4 * cc] = x.x;
-                        q[4 * cc + 1] = x.y;
-                        q[4 * cc + 2] = x.z;
-                        q[4 * cc + 3] = x.w;
-                    }
-                    __syncwarp();
-                    tm_st16(tq0 + 32 * j + 16 * h, q);
-                }
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            cur_g = g;
-            tm_fence_before();
-            __syncthreads();
-            tm_fence_after();
-        }
-        const int r_end = (rb + 1) * GT_RB < u.R ? (rb + 1) * GT_RB : u.R;
-        for (int r = rb * GT_RB; r < r_end; ++r) {      // no barrier between the block's ranges
-            const int2 itm = u.items[(long long)g * u.R + r];
-            const int e0 = itm.x, ne = itm.y;
-            uint4 v[8];
-            // the next row's id is loaded a step ahead, so a row costs one L2 round trip
-            int id_next = warp < ne ? u.ent_row[e0 + warp] : 0;
-            for (int e = warp; e < ne; e += NW) {
-                const int id = id_next;
-                if (e + NW < ne) id_next = u.ent_row[e0 + e + NW];
-                row_load_w(v, ix, (long long)id, Dp);
-                const unsigned m0 = u.ent_mask[e0 + e];
-                const int pb = u.ent_pb[e0 + e];
-                unsigned m = m0;
-                for (int i = 0; m; ++i) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    __syncwarp();
-                    push(row_cr32_tm(v, tq0 + 32 * j, tp), j, pb + i);
-                }
-            }
-        }
-        if (lane < npend) {
-            const float *row = gb + lane * GB_LD;
-            float acc = 0.0f;
-            for (int b = 0; b < nb; ++b) acc = acc + row[b];
-            dbuf[(long long)s_mem[pj] * stride + ppos] = acc;
-        }
-        __syncwarp();
-        npend = 0;
-    }
-    tm_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tm_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(GT_COLS) : "memory");
-    }
-}
 
 // BF16 / E4M3 rows, lane per block, the group's 16 queries in TMEM laid out the
 // same way (member j at columns [32 j, 32 j + 32), lane l holding dims
@@ -1910,15 +1747,9 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // one CTA per SM (its registers fill the SM), so its 512 TMEM columns are always free
         const size_t smem = sizeof(float) * (size_t)(GK_NT / 32) * gw_floats<PREC>();
-        if constexpr (PREC == 0) {
-            e = cudaFuncSetAttribute(k_gscore_tm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
-            k_gscore_tm<<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
-        } else {
-            e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
-            k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
-        }
+        e = cudaFuncSetAttribute(k_gscore<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        k_gscore<PREC><<<sms, GK_NT, smem, st>>>(ix_view(ix), Qr, (long long)stride, u, dbuf);
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "grouped scoring", __FILE__, __LINE__); break; }
@@ -1927,6 +1758,33 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     crisp_scratch_free(buf, st);
     return s;
 }
+
+}  // namespace
+
+// Query groups of a large batch for the tensor-core re-rank: the MinHash order
+// of the queries (qord), and pos[q][r], the first list position of query q with
+// id >= r GS_SPAN (r = 0..R).  key is scratch [nq].
+crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
+                                   unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    CRISP_REQUIRE(nq <= SCH_MAXQ, "group order: at most %d queries", SCH_MAXQ);
+    k_minhash_key<<<nq, RR_NT, 0, st>>>(cand, (long long)stride, (const long long *)ncand, nq, key);
+    CRISP_COUNT_LAUNCH();
+    int n2 = 1;
+    while (n2 < nq) n2 <<= 1;
+    CRISP_CK(cudaFuncSetAttribute(k_sort_queries, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(unsigned long long) * n2)));
+    k_sort_queries<<<1, 1024, sizeof(unsigned long long) * n2, st>>>(key, nq, qord);
+    CRISP_COUNT_LAUNCH();
+    const long long npos = (long long)nq * (R + 1);
+    k_sched_pos<<<(unsigned)((npos + 255) / 256), 256, 0, st>>>(cand, (long long)stride, (const long long *)ncand,
+                                                                nq, R, pos);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+namespace {
 
 // The S_keep best (score, list position) of each query's scored candidates, in
 // list (ascending id) order: the shortlist for the FP32 re-rank.
@@ -1970,6 +1828,60 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
     }
 }
 
+// Re-measure set of the tensor-core re-rank.  ub / lb hold, for every listed
+// candidate, an upper and a lower bound of its CR32 distance.  With U the kk-th
+// smallest upper bound, every candidate whose lower bound is <= U is written (in
+// list order, so ascending id) to rc, their number to nr.  A candidate left out
+// has CR32 distance >= its lower bound > U >= the kk-th smallest CR32 distance,
+// so it cannot be among the kk nearest by (distance, id); the exact re-rank of
+// rc alone therefore gives the top-kk of the whole list.
+// If the scorer reported a failure (*err != 0) its bounds cannot be trusted
+// and every candidate is kept, so the result is still exact.
+__global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__restrict__ cand, long long stride,
+                                                        const long long *__restrict__ ncand, int kk,
+                                                        const float *__restrict__ ub, const float *__restrict__ lb,
+                                                        const unsigned *__restrict__ err, int *__restrict__ rc,
+                                                        long long *__restrict__ nr) {
+    __shared__ TopkShared S;
+    const int q = blockIdx.x, tid = threadIdx.x;
+    const long long n = ncand[q] < stride ? ncand[q] : stride;
+    const int *candq = cand + (long long)q * stride;
+    int *rcq = rc + (long long)q * stride;
+    if (n <= kk || (err && *err != 0u)) {
+        for (long long i = tid; i < n; i += RR_NT) rcq[i] = candq[i];
+        if (tid == 0) nr[q] = n;
+        return;
+    }
+    unsigned prefix;
+    int need;
+    radix_kth(ub + (long long)q * stride, n, kk, S, &prefix, &need);
+    const float U = __uint_as_float(prefix);
+    const float *lq = lb + (long long)q * stride;
+    long long run = 0;
+    for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {
+        float lv[SEL_U];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const long long i = c00 + (long long)u * RR_NT + tid;
+            lv[u] = i < n ? lq[i] : INFINITY;
+            any = any || lv[u] <= U;
+        }
+        if (!__syncthreads_or(any)) continue;       // most chunks hold nothing to re-measure
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const long long i = c00 + (long long)u * RR_NT + tid;
+            const int sel = lv[u] <= U;
+            if (!__syncthreads_or(sel)) continue;
+            long long tot;
+            const long long off = block_excl_scan<RR_NT>(sel, S.scan_ws, &tot);
+            if (sel) rcq[run + off] = candq[i];
+            run += tot;
+        }
+    }
+    if (tid == 0) nr[q] = run;
+}
+
 __global__ void k_stats(int nq, const long long *ncand, const int *how, const long long *retrieved, int M,
                         const long long *nver, const long long *nfull, int tau, crisp_query_stats *st) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2007,6 +1919,14 @@ crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, 
 crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st) {
     long long total = (long long)ix->M * ix->K * ix->K * (ix->T + 1);
     k_tile_off<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ix_view(ix), ix->tile_off);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st) {
+    if (ix->N <= 0) return CRISP_OK;
+    k_row_norms<<<(unsigned)((ix->N + 7) / 8), 256, 0, st>>>(ix->Xr, (long long)ix->N, ix->Dp, ix->xn2);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -2063,25 +1983,33 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
     return CRISP_OK;
 }
 
+crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids,
+                                 float *d2, cudaStream_t st, bool *done);
+
+// Large batches (1,024 queries or more with long lists) take the tensor-core
+// path of rerank_tc.cu (bounded TF32 scores, exact CR32 re-measure of the
+// candidates that can reach the top-k); the rest stream every (query,
+// candidate) pair.  Both give the top-k of the exact CR32 distances.
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
                               cudaStream_t st, bool no_alloc = false, bool may_group = true) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
-    bool grouped = false;
     if (!no_alloc && may_group) {
-        crisp_status gs = run_grouped<0>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
-        if (gs) return gs;
+        bool done = false;
+        crisp_status ts = crisp_run_rerank_tc(ix, Qr, nq, cand, stride, ncand, k, dbuf, ids, d2, st, &done);
+        if (ts || done) return ts;
     }
     long long *off = nullptr;           // no_alloc: a fixed number of items per query, no offsets
-    if (!grouped && !no_alloc) {
+    if (!no_alloc) {
         CRISP_CK(crisp_scratch_alloc((void **)&off, sizeof(long long) * ((size_t)nq + 1), st));
         k_chunk_offsets<<<1, RR_NT, 0, st>>>((const long long *)ncand, (long long)stride, nq, RF_CH, off);
         CRISP_COUNT_LAUNCH();
     }
     if (smem > 48 * 1024)
         CRISP_CK(cudaFuncSetAttribute(k_dist_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (!grouped) {
+    {
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -2096,6 +2024,17 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
                                         (long long *)ids, d2);
     CRISP_COUNT_LAUNCH();
     if (off) crisp_scratch_free(off, st);
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
+                                    const float *ub, const float *lb, const unsigned *err, int32_t *rc, int64_t *nr,
+                                    cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, ub, lb, err, rc,
+                                         (long long *)nr);
+    CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }

@@ -1,0 +1,773 @@
+// Exact re-rank of large batches on the tcgen05 tensor cores (§4.3.2 Stage 3,
+// the O(|C| D) verification the paper names as the dominant query cost, §4.4).
+//
+// The candidate lists of a large batch overlap: on the 1M-row workload a row is
+// a candidate of about 200 of 10,000 queries.  The queries are ordered by the
+// MinHash of their candidate sets and cut into groups of TG = 64; the id space
+// into ranges of TSPAN ids.  For every (group, range) k_union lists the rows
+// some member needs, with a 64-bit member mask and each (row, member) pair's
+// slot in that member's list.  Then:
+//
+//   k_rerank_tc   each listed row is fetched once per group (16-byte cp.async
+//                 copies straight into the 128-byte swizzled operand layout) and
+//                 multiplied against the group's 64 queries (one TMA tile) on the
+//                 tensor cores: dot = x . q in one TF32 pass, FP32 accumulation in
+//                 tensor memory.  The epilogue forms the expansion
+//                 d~ = |x|^2 + |q|^2 - 2 dot and, from a proven error bound E,
+//                 an upper and a lower bound of the pair's CR32 distance.
+//   k_bound_select (query.cu) per query: U = the k-th smallest upper bound;
+//                 every candidate whose lower bound is <= U is kept.
+//   k_dist_flat + k_select_rows (query.cu): the kept candidates are measured
+//                 exactly in the CR32 order and the top-k is taken from them.
+//
+// No candidate outside the kept set can be among the k nearest (its CR32
+// distance exceeds U, which is at least the k-th smallest CR32 distance), and
+// every kept distance is the CR32 value itself, so the result is bit-for-bit
+// the one of measuring every candidate exactly.
+//
+// Error bound of d~ against the exact real distance d of the FP32 rows:
+//  - TF32 keeps 10 mantissa bits, so each operand is within 2^-10 of itself
+//    (relative, truncation or rounding) and each product within
+//    (2^-9 + 2^-20) |x_i q_i|; summed, |dot~ - x.q| <= (2^-9 + 2^-20) S with
+//    S = sum |x_i q_i| <= |x| |q| (Cauchy-Schwarz);
+//  - the tensor core's FP32 accumulation over Dp / 8 steps is charged
+//    (Dp / 8 + 1) 2^-20 S, several times the rounding of an FP32 sum;
+//  - |x|^2 and |q|^2 are FP64 sums rounded once, and d~ takes three FP32
+//    operations: all within 2^-19 (|x|^2 + |q|^2);
+// so |d~ - d| <= E = c1 |x| |q| + c2 (|x|^2 + |q|^2), c1 = 2 (2^-9 + 2^-20 +
+// (Dp / 8 + 1) 2^-20) 1.01, c2 = 2^-19.  The CR32 value d32 of the same pair
+// (zero-padded blocks of 32 dims, a subtraction, a 4-term fma chain, a 3-level
+// tree and Dp / 32 block additions per term) is within g d of d, with
+// g = (Dp / 32 + 12) 2^-23 + 2^-20 (twice the first-order summation bound).
+// Hence d32 lies in [d~ - E', d~ + E'] with E' = E + g (|d~| + E).
+//
+// Every mbarrier wait is bounded in time; a wait that gives up records an
+// error word and the kernel winds down (waiting, bounded, for its copies and
+// MMAs in flight, then freeing its tensor memory).  The bound selection reads
+// the word and then keeps every candidate, so the result stays exact.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+#include "ptx.cuh"
+
+bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows);
+crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
+                                   unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
+crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
+                                    const float *ub, const float *lb, const unsigned *err, int32_t *rc, int64_t *nr,
+                                    cudaStream_t st);
+crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                              int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
+                              cudaStream_t st, bool no_alloc, bool may_group);
+
+namespace {
+
+constexpr int TG = 64;              // queries per group: N of the MMA
+constexpr int TSPAN = 4096;         // ids per range (the ordering's range size)
+constexpr int TU_NT = 256;          // k_union threads
+constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
+constexpr int TR_NS = 4;            // shared-memory stages, one 32-float k-block of a tile each
+constexpr int TR_NB = 4;            // tensor-memory accumulator buffers of 128 columns
+constexpr int TR_LT = 128;          // copy threads (warps 4-7)
+constexpr int TR_NT = 320;          // warps 0-3 epilogue, 4-7 copies, 8 tile preparation, 9 MMA issue
+constexpr int TR_RB = 4;            // id ranges per work item
+constexpr int TR_PMAX = 2048;       // (row, member) pairs of a tile whose list positions are staged in shared memory
+constexpr uint32_t TR_A_BYTES = 128 * 128;                     // 128 rows x one k-block
+constexpr uint32_t TR_B_BYTES = TG * 128;                      // 64 queries x one k-block
+constexpr uint32_t TR_STAGE = 2 * TR_A_BYTES + TR_B_BYTES;     // 40 KB
+
+__device__ unsigned int g_tr_error;   // first failing wait: 1 + its site code
+
+__device__ __forceinline__ void tr_error(unsigned site) { atomicCAS(&g_tr_error, 0u, 1u + site); }
+
+// Group-ordered copy of the queries: slot s = g TG + j holds query qord[s]
+// (zero rows past nq), with |q|^2 (FP64 sum rounded to FP32) and |q|.  One warp
+// per slot.
+__global__ void k_group_queries(const float *__restrict__ Qr, int nq, int Dp, const int *__restrict__ qord,
+                                int nslots, float *__restrict__ Qg, int *__restrict__ gq, float *__restrict__ gn2,
+                                float *__restrict__ gn1) {
+    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (slot >= nslots) return;
+    const int q = slot < nq ? qord[slot] : -1;
+    double s = 0.0;
+    for (int d = lane; d < Dp; d += 32) {
+        const float v = q >= 0 ? Qr[(long long)q * Dp + d] : 0.0f;
+        Qg[(long long)slot * Dp + d] = v;
+        s += (double)v * (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        gq[slot] = q;
+        gn2[slot] = (float)s;
+        gn1[slot] = (float)sqrt(s);
+    }
+}
+
+struct TUnion {
+    const int *gq;                  // [ngroups * TG] query of each group slot, -1 past nq
+    const int *pos;                 // [nq][R + 1] first list position with id >= r TSPAN
+    int *ent_row;                   // [ecap] row id
+    unsigned long long *ent_mask;   // [ecap] members that need the row
+    int *ent_pb;                    // [ecap] first pair slot of the row
+    float *ent_nx;                  // [ecap] |x|^2 of the row
+    const float *xn2;               // [N] row norms of the index
+    int *pair_pos;                  // [pcap] list position of each (row, member) pair, members in bit order
+    int2 *items;                    // [ngroups][R] (first entry, entries)
+    unsigned long long *counts;     // [0] entries, [1] pairs, [2] scoring item counter
+    long long ecap, pcap;
+    int R;
+};
+
+// Exclusive scan of one value per thread over the block (NT threads); the
+// block total goes to *total.  ws holds NT / 32 + 1 values.
+template <int NT>
+__device__ __forceinline__ long long tr_block_scan(long long v, long long *ws, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < NT / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < NT / 32) ws[lane] = t;
+        if (lane == NT / 32 - 1) ws[NT / 32] = t;
+    }
+    __syncthreads();
+    const long long excl = x - v + (warp > 0 ? ws[warp - 1] : 0);
+    *total = ws[NT / 32];
+    __syncthreads();
+    return excl;
+}
+
+// One block per (range r, group g): the rows of the range that some member of
+// the group needs, their member masks, and the slot of every (row, member)
+// pair.  Entry order inside a (group, range) is arbitrary: every pair has its
+// own slot, so nothing downstream depends on it.
+__global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, long long stride, TUnion u) {
+    extern __shared__ __align__(16) unsigned long long usm[];
+    unsigned long long *mask = usm;                      // [TSPAN]
+    int *pbl = reinterpret_cast<int *>(usm + TSPAN);    // [TSPAN] pair base of each row, within the block
+    __shared__ int s_q[TG], s_base[TG], s_cnt[TG], s_off[TG + 1];
+    __shared__ long long scan_ws[TU_NT / 32 + 1];
+    __shared__ long long s_eb, s_pb;
+    const int r = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+    if (tid < TG) {
+        const int q = u.gq[g * TG + tid];
+        int a = 0, b = 0;
+        if (q >= 0) {
+            const long long row = (long long)q * (u.R + 1) + r;
+            a = u.pos[row];
+            b = u.pos[row + 1];
+        }
+        s_q[tid] = q < 0 ? 0 : q;
+        s_base[tid] = a;
+        s_cnt[tid] = b - a;
+    }
+    for (int o = tid; o < TSPAN; o += TU_NT) mask[o] = 0ull;
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int j = 0; j < TG; ++j) {
+            s_off[j] = acc;
+            acc += s_cnt[j];
+        }
+        s_off[TG] = acc;
+    }
+    __syncthreads();
+    const int np = s_off[TG];
+    const long long lo_id = (long long)r * TSPAN;
+    for (int e = tid; e < np; e += TU_NT) {
+        int lo = 0, hi = TG - 1;                 // member j with s_off[j] <= e < s_off[j + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + (e - s_off[lo])];
+        atomicOr(&mask[id - lo_id], 1ull << lo);
+    }
+    __syncthreads();
+    // thread t owns the ids t, t + TU_NT, ... (conflict-free reads); one packed
+    // scan (pairs high, rows low) places every thread's rows and pairs
+    constexpr int PER = TSPAN / TU_NT;
+    int rows = 0, pairs = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int c = __popcll(mask[tid + k * TU_NT]);
+        pairs += c;
+        rows += c > 0 ? 1 : 0;
+    }
+    long long tot;
+    const long long ex = tr_block_scan<TU_NT>(((long long)pairs << 32) | rows, scan_ws, &tot);
+    if (tid == 0) {
+        const long long ne = tot & 0xFFFFFFFFll;
+        s_eb = (long long)atomicAdd(&u.counts[0], (unsigned long long)ne);
+        s_pb = (long long)atomicAdd(&u.counts[1], (unsigned long long)np);
+        const bool fits = s_eb + ne <= u.ecap && s_pb + np <= u.pcap;
+        u.items[(long long)g * u.R + r] = make_int2(fits ? (int)s_eb : 0, fits ? (int)ne : 0);
+        if (!fits) {
+            tr_error(10);       // never expected (the capacities bound every list); the selection then keeps all
+            s_eb = -1;
+        }
+    }
+    __syncthreads();
+    if (s_eb < 0) return;
+    int er = (int)(ex & 0xFFFFFFFFll), pr = (int)(ex >> 32);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int o = tid + k * TU_NT;
+        const unsigned long long m = mask[o];
+        if (m) {
+            const long long ei = s_eb + er;
+            u.ent_row[ei] = (int)(lo_id + o);
+            u.ent_mask[ei] = m;
+            u.ent_pb[ei] = (int)(s_pb + pr);
+            u.ent_nx[ei] = u.xn2[lo_id + o];
+            pbl[o] = pr;
+            ++er;
+            pr += __popcll(m);
+        }
+    }
+    __syncthreads();
+    // pair slots: member j of row o goes to slot base(o) + (members of o below j)
+    for (int e = tid; e < np; e += TU_NT) {
+        int lo = 0, hi = TG - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int t = e - s_off[lo];
+        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + t];
+        const int o = id - (int)lo_id;
+        const long long slot = s_pb + pbl[o] + __popcll(mask[o] & ((1ull << lo) - 1ull));
+        u.pair_pos[slot] = s_base[lo] + t;
+    }
+}
+
+struct TileMeta {
+    int g;                          // query group of the tile
+    int count;                      // rows in use (< 0: no more tiles)
+    int rid[TR_ROWS];               // per row: row id (rows past count repeat row 0)
+    unsigned long long mask[TR_ROWS];   // per row: members that need it
+    int pb[TR_ROWS];                // per row: first pair slot
+    int off[TR_ROWS];               // per row: its first pair in spos
+    float nx[TR_ROWS], rx[TR_ROWS]; // per row: |x|^2, |x|
+    int spos[TR_PMAX];              // list positions of the tile's first TR_PMAX pairs, rows in order
+    int gq[TG];                     // per member: query number (-1 past nq)
+    float gn2[TG], gn1[TG];         // per member: |q|^2, |q|
+};
+
+struct TrArgs {
+    int nk;                         // 32-float k-blocks per row (Dp / 32)
+    int Dp, ngroups, R;
+    long long items;                // ngroups * ceil(R / TR_RB)
+    long long stride;               // candidate list stride of ub / lb
+    const float *Xr;                // [N][Dp] stored rows
+    const int *gq;
+    const float *gn2, *gn1;         // per group slot: |q|^2, |q|
+    const int *ent_row;
+    const unsigned long long *ent_mask;
+    const int *ent_pb;
+    const float *ent_nx;
+    const int *pair_pos;
+    const int2 *items_arr;          // [ngroups][R]
+    unsigned long long *counter;    // work-item counter
+    float *ub, *lb;                 // [nq][stride] bounds of each pair's CR32 distance
+    float c1, c2, gam;              // error-bound constants (file comment)
+};
+
+constexpr int TR_MAXSEG = TR_RB;    // a tile holds consecutive entries of at most TR_RB ranges
+constexpr int TR_NBAR = 3 * TR_NS + 4 * TR_NB + 1;
+__host__ __device__ constexpr size_t tr_smem_bytes() {
+    return 1024 + (size_t)TR_NS * TR_STAGE + sizeof(TileMeta) * TR_NB + sizeof(int) * (TR_ROWS + 2 * TR_MAXSEG) +
+           sizeof(uint64_t) * TR_NBAR + 32;
+}
+
+__device__ __forceinline__ void copy_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TR_LT) : "memory"); }
+
+// Barrier of the copy threads that also returns, to every one of them, whether
+// any of them passed true (decisions that must be the same for the whole group).
+__device__ __forceinline__ bool copy_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(TR_LT)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Arrive on the mbarrier once every cp.async this thread has issued so far has
+// landed (the barrier's count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: one CTA per SM (its shared memory fills the SM, so its 512
+// tensor-memory columns are always free).  Work items are (block of TR_RB id
+// ranges, group), range-block-major, so the CTAs in flight fetch rows of the
+// same ranges for different groups and most fetches hit L2.  Roles:
+//  - tile preparation (warp 8): cuts each item's rows into tiles of up to 256
+//    and stages every tile's per-row data and the list positions of its pairs
+//    (consecutive union entries own consecutive pair slots, so a tile's
+//    positions are at most TR_MAXSEG contiguous runs), up to TR_NB tiles ahead;
+//  - copies (warps 4-7): every 32-float k-block of the tile's 256 rows into a
+//    stage with 16-byte cp.async (thread t moves chunk t & 7 of rows t / 8 +
+//    16 i; the 128-byte swizzled layout puts chunk c of row r at c ^ (r & 7)),
+//    and the group's 64 query rows by one TMA tile load;
+//  - MMA issue (warp 9, one thread): per k-block 2 x 4 MMAs (M = 128, N = 64,
+//    K = 8) into the tile's two accumulators;
+//  - epilogue (warps 0-3, one TMEM lane quarter each): per row and member pair
+//    the bounds of the CR32 distance, written to the member's list slot.
+__global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ CUtensorMap tmQ, TrArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzled tiles need 1024-byte alignment
+    uint8_t *stages = sm;
+    TileMeta *meta = reinterpret_cast<TileMeta *>(sm + (size_t)TR_NS * TR_STAGE);
+    int *sent = reinterpret_cast<int *>(meta + TR_NB);      // preparation scratch: entry of each tile row
+    int *sseg = sent + TR_ROWS;                             // preparation scratch: (first row, rows) per segment
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sseg + 2 * TR_MAXSEG);
+    const uint32_t full0 = smem_addr(bars), qfull0 = full0 + 8u * TR_NS, empty0 = qfull0 + 8u * TR_NS,
+                   mfull0 = empty0 + 8u * TR_NS, mempty0 = mfull0 + 8u * TR_NB, afull0 = mempty0 + 8u * TR_NB,
+                   aempty0 = afull0 + 8u * TR_NB, done = aempty0 + 8u * TR_NB;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + TR_NBAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TR_NS; ++i) {
+            mbar_init(full0 + 8u * i, TR_LT);   // one cp.async arrival per copy thread
+            mbar_init(qfull0 + 8u * i, 1);      // the query tile (TMA, counted in bytes)
+            mbar_init(empty0 + 8u * i, 1);      // the stage's MMAs have completed
+        }
+        for (int i = 0; i < TR_NB; ++i) {
+            mbar_init(mfull0 + 8u * i, 1);      // a tile's per-row data is staged
+            mbar_init(mempty0 + 8u * i, 4);     // the four epilogue warps are done with it
+            mbar_init(afull0 + 8u * i, 1);      // the tile's MMAs have completed
+            mbar_init(aempty0 + 8u * i, 4);     // the epilogue warps have read the accumulators
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(4 * 128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    long long issued = 0;           // copy threads: k-blocks issued
+
+    // lane 0 waits, the warp follows its verdict (warp-uniform control flow)
+    auto warp_wait = [&](uint32_t bar, uint32_t parity, unsigned site) -> bool {
+        int ok = 1;
+        if (lane == 0) {
+            ok = mbar_wait(bar, parity) ? 1 : 0;
+            if (!ok) {
+                tr_error(site);
+                *abort_flag = 1;
+            }
+        }
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+
+    if (warp == 8) {
+        // ---------------------------------------------------- tile preparation
+        int t = 0, b = 0, fill = 0, nseg = 0;
+        auto emit = [&](int g) -> bool {
+            if (t >= TR_NB && !warp_wait(mempty0 + 8u * b, (uint32_t)((t / TR_NB) - 1) & 1u, 0)) return false;
+            TileMeta &mt = meta[b];
+            const int count = fill;
+            const int id0 = a.ent_row[sent[0]];
+            for (int r = lane; r < TR_ROWS; r += 32) {
+                if (r < count) {
+                    const int e = sent[r];
+                    const float nx = a.ent_nx[e];
+                    mt.rid[r] = a.ent_row[e];
+                    mt.mask[r] = a.ent_mask[e];
+                    mt.pb[r] = a.ent_pb[e];
+                    mt.nx[r] = nx;
+                    mt.rx[r] = sqrtf(nx);
+                } else {
+                    mt.rid[r] = id0;        // padding rows repeat a real row; their results are not used
+                }
+            }
+            for (int j = lane; j < TG; j += 32) {
+                mt.gq[j] = a.gq[g * TG + j];
+                mt.gn2[j] = a.gn2[g * TG + j];
+                mt.gn1[j] = a.gn1[g * TG + j];
+            }
+            __syncwarp();
+            // pairs: segment by segment (consecutive entries of one range), each a
+            // contiguous run of slots starting at the pair base of its first row
+            int base = 0;
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int r0 = sseg[2 * sg], n = sseg[2 * sg + 1];
+                const int pb0 = mt.pb[r0], len = mt.pb[r0 + n - 1] + __popcll(mt.mask[r0 + n - 1]) - pb0;
+                for (int r = r0 + lane; r < r0 + n; r += 32) mt.off[r] = base + mt.pb[r] - pb0;
+                const int lim = base + len < TR_PMAX ? len : TR_PMAX - base;
+                for (int p = lane; p < lim; p += 32) mt.spos[base + p] = a.pair_pos[pb0 + p];
+                base += len;
+                if (base > TR_PMAX) base = TR_PMAX + 1;   // the rest read their positions from global memory
+            }
+            if (lane == 0) {
+                mt.g = g;
+                mt.count = count;
+            }
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(mfull0 + 8u * b);
+            ++t;
+            b = t % TR_NB;
+            fill = 0;
+            nseg = 0;
+            return true;
+        };
+        bool ok = true;
+        for (;;) {
+            unsigned long long it = 0;
+            if (lane == 0) it = atomicAdd(a.counter, 1ull);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if ((long long)it >= a.items || __shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+            const int g = (int)(it % (unsigned long long)a.ngroups), rb = (int)(it / (unsigned long long)a.ngroups);
+            const int r_end = (rb + 1) * TR_RB < a.R ? (rb + 1) * TR_RB : a.R;
+            for (int r = rb * TR_RB; r < r_end && ok; ++r) {
+                const int2 itm = a.items_arr[(long long)g * a.R + r];
+                for (int got = 0; got < itm.y;) {
+                    const int take = TR_ROWS - fill < itm.y - got ? TR_ROWS - fill : itm.y - got;
+                    for (int i = lane; i < take; i += 32) sent[fill + i] = itm.x + got + i;
+                    if (lane == 0) {
+                        sseg[2 * nseg] = fill;
+                        sseg[2 * nseg + 1] = take;
+                    }
+                    ++nseg;
+                    fill += take;
+                    got += take;
+                    __syncwarp();
+                    if (fill == TR_ROWS && !(ok = emit(g))) break;
+                }
+            }
+            if (!ok) break;
+            if (fill > 0 && !(ok = emit(g))) break;
+        }
+        // no more tiles (after an abort the other roles stop by themselves)
+        if (ok && !__shfl_sync(0xffffffffu, *abort_flag, 0) &&
+            (t < TR_NB || warp_wait(mempty0 + 8u * b, (uint32_t)((t / TR_NB) - 1) & 1u, 0))) {
+            if (lane == 0) {
+                meta[b].count = -1;
+                __threadfence_block();
+                mbar_arrive(mfull0 + 8u * b);
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // -------------------------------------------------------------- copies
+        const int lt = threadIdx.x - 128;
+        // one thread waits; the group goes on only if that wait succeeded and no
+        // other role has given up (the same verdict for every copy thread)
+        auto group_wait = [&](uint32_t bar, uint32_t parity, unsigned site) -> bool {
+            bool fail = false;
+            if (lt == 0 && !mbar_wait(bar, parity)) {
+                tr_error(site);
+                *abort_flag = 1;
+                fail = true;
+            }
+            return !copy_any(fail || *abort_flag != 0);
+        };
+        const int c = lt & 7, r0 = lt >> 3;
+        const uint32_t swz = (uint32_t)((c ^ (r0 & 7)) << 4);
+        for (int t = 0;; ++t) {
+            const int b = t % TR_NB;
+            if (!group_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 1)) break;
+            const TileMeta &mt = meta[b];
+            if (mt.count < 0) break;
+            const int g = mt.g;
+            int id[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) id[i] = mt.rid[r0 + 16 * i];
+            bool ok = true;
+            for (int kc = 0; kc < a.nk; ++kc, ++issued) {
+                const int s = (int)(issued % TR_NS);
+                if (issued >= TR_NS && !group_wait(empty0 + 8u * s, (uint32_t)((issued / TR_NS) - 1) & 1u, 2)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t sa = smem_addr(stages + (size_t)s * TR_STAGE);
+                if (lt == 0) {
+                    mbar_expect_tx(qfull0 + 8u * s, TR_B_BYTES);
+                    tma_load_2d(sa + 2 * TR_A_BYTES, &tmQ, 32 * kc, TG * g, qfull0 + 8u * s);
+                }
+                const float *col = a.Xr + 32 * kc + 4 * c;
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    cp_async16(sa + (uint32_t)((r0 + 16 * i) * 128) + swz, col + (long long)id[i] * a.Dp);
+                cp_async_arrive(full0 + 8u * s);
+            }
+            if (!ok) break;
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = tf32_idesc(TG, 128);
+            long long c = 0;
+            for (int t = 0;; ++t) {
+                const int b = t % TR_NB;
+                if (!mbar_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u)) {
+                    tr_error(3);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (meta[b].count < 0 || *abort_flag) break;
+                if (t >= TR_NB && !mbar_wait(aempty0 + 8u * b, (uint32_t)((t / TR_NB) - 1) & 1u)) {
+                    tr_error(4);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d0 = tmem + 128u * b, d1 = d0 + 64u;
+                bool bad = false;
+                for (int kc = 0; kc < a.nk; ++kc, ++c) {
+                    const int s = (int)(c % TR_NS);
+                    const uint32_t ph = (uint32_t)(c / TR_NS) & 1u;
+                    if (!mbar_wait(full0 + 8u * s, ph) || !mbar_wait(qfull0 + 8u * s, ph)) {
+                        bad = true;
+                        break;
+                    }
+                    // the rows were written through the generic proxy (cp.async); the MMA reads them
+                    // through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tc_fence_after();
+                    const uint32_t sa = smem_addr(stages + (size_t)s * TR_STAGE), sq = sa + 2 * TR_A_BYTES;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {       // UMMA K = 8 floats = 32 bytes
+                        const uint32_t o = 32u * j, acc = (kc | j) != 0;
+                        mma_tf32(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
+                        mma_tf32(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                    }
+                    mma_commit(empty0 + 8u * s);
+                }
+                if (bad) {
+                    tr_error(5);
+                    *abort_flag = 1;
+                    break;
+                }
+                mma_commit(afull0 + 8u * b);
+            }
+            mma_commit(done);       // completes once every MMA issued above has
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int qd = warp;                          // the TMEM lane quarter this warp may read
+        for (int t = 0;; ++t) {
+            const int b = t % TR_NB;
+            if (!warp_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 6)) break;
+            const TileMeta &mt = meta[b];
+            const int count = mt.count;
+            if (count < 0) break;
+            if (!warp_wait(afull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 7)) break;
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 128u * b;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int row = 32 * qd + lane + 128 * h;
+                const bool valid = row < count;
+                const unsigned long long m = valid ? mt.mask[row] : 0ull;
+                const int pb = valid ? mt.pb[row] : 0, po = valid ? mt.off[row] : 0;
+                const float nx = valid ? mt.nx[row] : 0.0f, rx = valid ? mt.rx[row] : 0.0f;
+#pragma unroll 1
+                for (int cb = 0; cb < TG / 16; ++cb) {
+                    uint32_t v[16];
+                    tmem_ld16(ta + 64u * h + 16u * cb, v);     // warp-collective: every lane takes part
+                    const unsigned sub = (unsigned)(m >> (16 * cb)) & 0xFFFFu;
+                    const int rank0 = __popcll(m & ((1ull << (16 * cb)) - 1ull));
+                    int pos[16];
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {      // list positions for members 16 cb + jj
+                        const int rk = rank0 + __popc(sub & ((1u << jj) - 1u));
+                        pos[jj] = !((sub >> jj) & 1u) ? 0 : po + rk < TR_PMAX ? mt.spos[po + rk] : a.pair_pos[pb + rk];
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        if ((sub >> jj) & 1u) {
+                            const int j = 16 * cb + jj;
+                            const float ss = nx + mt.gn2[j];
+                            const float dt = ss - 2.0f * __uint_as_float(v[jj]);
+                            const float E = a.c1 * (mt.gn1[j] * rx) + a.c2 * ss;
+                            const float E2 = E + a.gam * (fabsf(dt) + E);
+                            const long long o = (long long)mt.gq[j] * a.stride + pos[jj];
+                            a.ub[o] = fmaxf(dt + E2, 0.0f);
+                            a.lb[o] = dt - E2;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(aempty0 + 8u * b);
+                mbar_arrive(mempty0 + 8u * b);
+            }
+        }
+    }
+
+    // ---------------------------------------------------------------- teardown
+    if (warp == 9 && lane == 0 && !mbar_wait(done, 0)) tr_error(8);
+    if (warp >= 4 && warp < 8) {
+        // every copy still in flight lands before the CTA's shared memory goes away
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (threadIdx.x == 128)
+            for (long long c = issued - TR_NS < 0 ? 0 : issued - TR_NS; c < issued; ++c)
+                if (!mbar_wait(qfull0 + 8u * (c % TR_NS), (uint32_t)(c / TR_NS) & 1u)) tr_error(9);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * 128) : "memory");
+    }
+}
+
+}  // namespace
+
+// Tensor-core re-rank of a batch of 1,024 to CRISP_GROUP_MAXQ queries whose
+// candidate lists may hold 2,048 or more ids; *done = false (nothing run) for
+// other batches, which the caller streams.  dbuf: [nq][stride] floats of scratch.
+crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids,
+                                 float *d2, cudaStream_t st, bool *done) {
+    *done = false;
+    if (nq < 1024 || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
+    const int Dp = ix->Dp;
+    const int R = (int)((ix->N + TSPAN - 1) / TSPAN);
+    const int ngroups = (nq + TG - 1) / TG, nslots = ngroups * TG;
+    const long long pcap = (long long)nq * std::min<int64_t>(stride, ix->N);
+    const long long ecap = std::min<long long>(pcap, (long long)ngroups * R * TSPAN);
+    if (pcap > 0x7FFFFFFFLL) return CRISP_OK;        // pair slots are 32-bit
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
+                 o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
+                 o_gq = take(sizeof(int) * nslots), o_gn2 = take(sizeof(float) * nslots),
+                 o_gn1 = take(sizeof(float) * nslots), o_qg = take(sizeof(float) * (size_t)nslots * Dp),
+                 o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)ecap),
+                 o_mask = take(sizeof(unsigned long long) * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
+                 o_enx = take(sizeof(float) * (size_t)ecap),
+                 o_pp = take(sizeof(int) * (size_t)pcap), o_lb = take(sizeof(float) * (size_t)nq * stride),
+                 o_rc = take(sizeof(int) * (size_t)nq * stride), o_nr = take(sizeof(int64_t) * nq);
+    uint8_t *buf = nullptr;
+    CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
+    unsigned long long *counts = (unsigned long long *)(buf + o_cnt);
+    int *qord = (int *)(buf + o_qord), *pos = (int *)(buf + o_pos), *gq = (int *)(buf + o_gq);
+    float *gn2 = (float *)(buf + o_gn2), *gn1 = (float *)(buf + o_gn1), *Qg = (float *)(buf + o_qg);
+    float *lb = (float *)(buf + o_lb);
+    int32_t *rc = (int32_t *)(buf + o_rc);
+    int64_t *nr = (int64_t *)(buf + o_nr);
+    TUnion u;
+    u.gq = gq;
+    u.pos = pos;
+    u.ent_row = (int *)(buf + o_row);
+    u.ent_mask = (unsigned long long *)(buf + o_mask);
+    u.ent_pb = (int *)(buf + o_pb);
+    u.ent_nx = (float *)(buf + o_enx);
+    u.xn2 = ix->xn2;
+    u.pair_pos = (int *)(buf + o_pp);
+    u.items = (int2 *)(buf + o_items);
+    u.counts = counts;
+    u.ecap = ecap;
+    u.pcap = pcap;
+    u.R = R;
+    crisp_status s = CRISP_OK;
+    do {
+        cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__); break; }
+        unsigned *err_word = nullptr;
+        e = cudaGetSymbolAddress((void **)&err_word, g_tr_error);
+        if (e == cudaSuccess) e = cudaMemsetAsync(err_word, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "error word", __FILE__, __LINE__); break; }
+        s = crisp_run_group_order(cand, stride, ncand, nq, R, (unsigned long long *)(buf + o_key), qord, pos, st);
+        if (s) break;
+        k_group_queries<<<(nslots + 7) / 8, 256, 0, st>>>(Qr, nq, Dp, qord, nslots, Qg, gq, gn2, gn1);
+        CRISP_COUNT_LAUNCH();
+        const size_t usmem = sizeof(unsigned long long) * TSPAN + sizeof(int) * TSPAN;
+        e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        k_union<<<dim3(R, ngroups), TU_NT, usmem, st>>>(cand, (long long)stride, u);
+        CRISP_COUNT_LAUNCH();
+        CUtensorMap mq;
+        if (!crisp_make_map_f32(&mq, Qg, nslots, Dp, Dp, TG)) {
+            crisp_set_error("tensor-core re-rank: tensor map encoding failed");
+            s = CRISP_ECUDA;
+            break;
+        }
+        TrArgs ta;
+        ta.nk = Dp / 32;
+        ta.Dp = Dp;
+        ta.Xr = ix->Xr;
+        ta.ngroups = ngroups;
+        ta.R = R;
+        ta.items = (long long)ngroups * ((R + TR_RB - 1) / TR_RB);
+        ta.stride = stride;
+        ta.gq = gq;
+        ta.gn2 = gn2;
+        ta.gn1 = gn1;
+        ta.ent_row = u.ent_row;
+        ta.ent_mask = u.ent_mask;
+        ta.ent_pb = u.ent_pb;
+        ta.ent_nx = u.ent_nx;
+        ta.pair_pos = u.pair_pos;
+        ta.items_arr = u.items;
+        ta.counter = counts + 2;
+        ta.ub = dbuf;
+        ta.lb = lb;
+        const double eps_acc = (Dp / 8 + 1) * std::ldexp(1.0, -20);
+        ta.c1 = (float)(2.0 * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + eps_acc) * 1.01);
+        ta.c2 = (float)std::ldexp(1.0, -19);
+        ta.gam = (float)((Dp / 32 + 12) * std::ldexp(1.0, -23) + std::ldexp(1.0, -20));
+        const size_t smem = tr_smem_bytes();
+        e = cudaFuncSetAttribute(k_rerank_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_rerank_tc<<<sms, TR_NT, smem, st>>>(mq, ta);
+        CRISP_COUNT_LAUNCH();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rerank_tc", __FILE__, __LINE__); break; }
+        s = crisp_run_bound_select(nq, cand, stride, ncand, k, dbuf, lb, err_word, rc, nr, st);
+        if (s) break;
+        // the kept candidates, measured exactly (streaming CR32) -> top-k
+        s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false);
+        if (s) break;
+        *done = true;
+    } while (0);
+    crisp_scratch_free(buf, st);
+    return s;
+}

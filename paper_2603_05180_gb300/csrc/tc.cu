@@ -34,49 +34,6 @@ constexpr int TC_TMEM_COLS = 256;
 
 __device__ unsigned int g_tc_error;   // first failing wait: 1 + its site code
 
-// Shared-memory matrix descriptor of a K-major operand in the 128-byte
-// swizzled layout: 8-row groups of 128-byte rows, groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFF)      // start address
-           | ((uint64_t)1 << 16)                 // leading byte offset (unused for this layout)
-           | ((uint64_t)(1024 >> 4) << 32)       // stride byte offset: next 8-row group
-           | ((uint64_t)1 << 46)                 // descriptor version
-           | ((uint64_t)2 << 61);                // layout: 128-byte swizzle
-}
-
-// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Warp-collective: the warp is reconverged first (.sync.aligned needs every lane).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    __syncwarp();
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
 __device__ __forceinline__ void record_error(unsigned int site) { atomicCAS(&g_tc_error, 0u, 1u + site); }
 
 struct RotArgs {
@@ -145,7 +102,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_rotate_tc(const __grid_constant__ 
     if (tid == 0)
         for (; issued < 2 && issued < nk; ++issued) issue(issued);
 
-    const uint32_t idesc = tf32_idesc(a.BN);
+    const uint32_t idesc = tf32_idesc(a.BN, TC_BM);
     int consumed = 0;
     for (int kb = 0; kb < nk; ++kb) {
         const int s = kb & 1;
@@ -280,6 +237,16 @@ bool make_map(CUtensorMap *m, const float *base, long long rows, int cols, int l
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+}  // namespace
+
+// 2-D FP32 tensor map for other translation units (box 32 floats x box_rows,
+// 128-byte swizzle): the tensor-core re-rank fetches its rows and queries with it.
+bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows) {
+    return make_map(m, base, rows, cols, ld, box_rows);
+}
+
+namespace {
 
 size_t rot_smem(int BN) { return 1024 + 2 * (2 * (size_t)TC_BM * 128 + 2 * (size_t)BN * 128) + 64; }
 
@@ -460,7 +427,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
             issue(issued);
         }
     } else if (tid == 32) {
-        const uint32_t idesc = tf32_idesc(AS_KPAD);
+        const uint32_t idesc = tf32_idesc(AS_KPAD, TC_BM);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb & 1;
             if (!mbar_wait(full0 + 8u * s, (uint32_t)(kb >> 1) & 1u)) {
