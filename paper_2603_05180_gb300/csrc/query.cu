@@ -775,10 +775,12 @@ struct TopkShared {
     int need;
 };
 
-// Block-wide radix select over the FP32 keys dist[0..n) (non-negative, so
-// their bit patterns order like the values): the key of the kk-th smallest
-// (*prefix) and how many entries equal to it are among the kk smallest (*need).
-__device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S, unsigned *out_prefix, int *out_need) {
+// Block-wide radix select over the FP32 keys dist[i * ks], i in [0, n)
+// (non-negative, so their bit patterns order like the values): the key of the
+// kk-th smallest (*prefix) and how many entries equal to it are among the kk
+// smallest (*need).
+__device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S, unsigned *out_prefix, int *out_need,
+                          int ks = 1) {
     const int tid = threadIdx.x;
     unsigned prefix = 0, mask = 0;
     int need = kk;
@@ -793,7 +795,7 @@ __device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S
 #pragma unroll
             for (int u = 0; u < SEL_U; ++u) {
                 const long long i = i0 + (long long)u * RR_NT + tid;
-                key[u] = i < n ? __float_as_uint(distq[i]) : 0u;
+                key[u] = i < n ? __float_as_uint(distq[i * ks]) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < SEL_U; ++u) {
@@ -1828,8 +1830,8 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
     }
 }
 
-// Re-measure set of the tensor-core re-rank.  ub / lb hold, for every listed
-// candidate, an upper and a lower bound of its CR32 distance.  With U the kk-th
+// Re-measure set of the tensor-core re-rank.  ulb holds, for every listed
+// candidate, an upper and a lower bound of its CR32 distance (x, y).  With U the kk-th
 // smallest upper bound, every candidate whose lower bound is <= U is written (in
 // list order, so ascending id) to rc, their number to nr.  A candidate left out
 // has CR32 distance >= its lower bound > U >= the kk-th smallest CR32 distance,
@@ -1839,7 +1841,7 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
 // and every candidate is kept, so the result is still exact.
 __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__restrict__ cand, long long stride,
                                                         const long long *__restrict__ ncand, int kk,
-                                                        const float *__restrict__ ub, const float *__restrict__ lb,
+                                                        const float2 *__restrict__ ulb,
                                                         const unsigned *__restrict__ err, int *__restrict__ rc,
                                                         long long *__restrict__ nr) {
     __shared__ TopkShared S;
@@ -1854,9 +1856,10 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
     }
     unsigned prefix;
     int need;
-    radix_kth(ub + (long long)q * stride, n, kk, S, &prefix, &need);
+    const float *uq = reinterpret_cast<const float *>(ulb + (long long)q * stride);
+    radix_kth(uq, n, kk, S, &prefix, &need, 2);
     const float U = __uint_as_float(prefix);
-    const float *lq = lb + (long long)q * stride;
+    const float *lq = uq + 1;
     long long run = 0;
     for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {
         float lv[SEL_U];
@@ -1864,7 +1867,7 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
 #pragma unroll
         for (int u = 0; u < SEL_U; ++u) {
             const long long i = c00 + (long long)u * RR_NT + tid;
-            lv[u] = i < n ? lq[i] : INFINITY;
+            lv[u] = i < n ? lq[2 * i] : INFINITY;
             any = any || lv[u] <= U;
         }
         if (!__syncthreads_or(any)) continue;       // most chunks hold nothing to re-measure
@@ -2029,10 +2032,9 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 }
 
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const float *ub, const float *lb, const unsigned *err, int32_t *rc, int64_t *nr,
-                                    cudaStream_t st) {
+                                    const float2 *ulb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
-    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, ub, lb, err, rc,
+    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, ulb, err, rc,
                                          (long long *)nr);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();

@@ -57,8 +57,7 @@ bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int c
 crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                    unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const float *ub, const float *lb, const unsigned *err, int32_t *rc, int64_t *nr,
-                                    cudaStream_t st);
+                                    const float2 *ulb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
                               cudaStream_t st, bool no_alloc, bool may_group);
@@ -69,15 +68,31 @@ constexpr int TG = 64;              // queries per group: N of the MMA
 constexpr int TSPAN = 4096;         // ids per range (the ordering's range size)
 constexpr int TU_NT = 256;          // k_union threads
 constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
-constexpr int TR_NS = 4;            // shared-memory stages, one 32-float k-block of a tile each
+// Stage geometry (tunable at compile time): TR_NS stages of TR_KB 32-float
+// k-blocks of a tile each, TR_NB accumulator buffers, TR_RB id ranges per item.
+#ifndef CRISP_TR_NS
+#define CRISP_TR_NS 4
+#endif
+#ifndef CRISP_TR_KB
+#define CRISP_TR_KB 1
+#endif
+#ifndef CRISP_TR_RB
+#define CRISP_TR_RB 4
+#endif
+#ifndef CRISP_TR_PMAX
+#define CRISP_TR_PMAX 2048
+#endif
+constexpr int TR_NS = CRISP_TR_NS;  // shared-memory stages
+constexpr int TR_KB = CRISP_TR_KB;  // 32-float k-blocks of the tile's rows and queries per stage
 constexpr int TR_NB = 4;            // tensor-memory accumulator buffers of 128 columns
-constexpr int TR_LT = 128;          // copy threads (warps 4-7)
-constexpr int TR_NT = 320;          // warps 0-3 epilogue, 4-7 copies, 8 tile preparation, 9 MMA issue
-constexpr int TR_RB = 4;            // id ranges per work item
-constexpr int TR_PMAX = 2048;       // (row, member) pairs of a tile whose list positions are staged in shared memory
+constexpr int TR_LT = 128;          // copy threads (warps 8-11)
+constexpr int TR_NT = 448;          // warps 0-7 epilogue, 8-11 copies, 12 tile preparation, 13 MMA issue
+constexpr int TR_WC = 8, TR_WP = 12, TR_WM = 13;   // first copy warp, preparation warp, MMA warp
+constexpr int TR_RB = CRISP_TR_RB;  // id ranges per work item
+constexpr int TR_PMAX = CRISP_TR_PMAX;   // (row, member) pairs of a tile whose list positions are staged in shared memory
 constexpr uint32_t TR_A_BYTES = 128 * 128;                     // 128 rows x one k-block
 constexpr uint32_t TR_B_BYTES = TG * 128;                      // 64 queries x one k-block
-constexpr uint32_t TR_STAGE = 2 * TR_A_BYTES + TR_B_BYTES;     // 40 KB
+constexpr uint32_t TR_STAGE = TR_KB * (2 * TR_A_BYTES + TR_B_BYTES);   // rows of both halves, then the queries
 
 __device__ unsigned int g_tr_error;   // first failing wait: 1 + its site code
 
@@ -265,7 +280,7 @@ struct TileMeta {
     unsigned long long mask[TR_ROWS];   // per row: members that need it
     int pb[TR_ROWS];                // per row: first pair slot
     int off[TR_ROWS];               // per row: its first pair in spos
-    float nx[TR_ROWS], rx[TR_ROWS]; // per row: |x|^2, |x|
+    float nx[TR_ROWS];              // per row: |x|^2
     int spos[TR_PMAX];              // list positions of the tile's first TR_PMAX pairs, rows in order
     int gq[TG];                     // per member: query number (-1 past nq)
     float gn2[TG], gn1[TG];         // per member: |q|^2, |q|
@@ -286,33 +301,27 @@ struct TrArgs {
     const int *pair_pos;
     const int2 *items_arr;          // [ngroups][R]
     unsigned long long *counter;    // work-item counter
-    float *ub, *lb;                 // [nq][stride] bounds of each pair's CR32 distance
+    float2 *ulb;                    // [nq][stride] (upper, lower) bound of each pair's CR32 distance
     float c1, c2, gam;              // error-bound constants (file comment)
 };
 
 constexpr int TR_MAXSEG = TR_RB;    // a tile holds consecutive entries of at most TR_RB ranges
 constexpr int TR_NBAR = 3 * TR_NS + 4 * TR_NB + 1;
 __host__ __device__ constexpr size_t tr_smem_bytes() {
-    return 1024 + (size_t)TR_NS * TR_STAGE + sizeof(TileMeta) * TR_NB + sizeof(int) * (TR_ROWS + 2 * TR_MAXSEG) +
+    return 1024 + (size_t)TR_NS * TR_STAGE + sizeof(TileMeta) * TR_NB + sizeof(int) * 4 * TR_MAXSEG +
            sizeof(uint64_t) * TR_NBAR + 32;
-}
-
-__device__ __forceinline__ void copy_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TR_LT) : "memory"); }
-
-// Barrier of the copy threads that also returns, to every one of them, whether
-// any of them passed true (decisions that must be the same for the whole group).
-__device__ __forceinline__ bool copy_any(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(TR_LT)
-        : "memory");
-    return r != 0;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
 
 // Arrive on the mbarrier once every cp.async this thread has issued so far has
@@ -325,27 +334,27 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
 // tensor-memory columns are always free).  Work items are (block of TR_RB id
 // ranges, group), range-block-major, so the CTAs in flight fetch rows of the
 // same ranges for different groups and most fetches hit L2.  Roles:
-//  - tile preparation (warp 8): cuts each item's rows into tiles of up to 256
+//  - tile preparation (warp 12): cuts each item's rows into tiles of up to 256
 //    and stages every tile's per-row data and the list positions of its pairs
 //    (consecutive union entries own consecutive pair slots, so a tile's
 //    positions are at most TR_MAXSEG contiguous runs), up to TR_NB tiles ahead;
-//  - copies (warps 4-7): every 32-float k-block of the tile's 256 rows into a
-//    stage with 16-byte cp.async (thread t moves chunk t & 7 of rows t / 8 +
+//  - copies (warps 8-11): the tile's 256 rows, TR_KB 32-float k-blocks a
+//    stage, with 16-byte cp.async (thread t moves chunk t & 7 of rows t / 8 +
 //    16 i; the 128-byte swizzled layout puts chunk c of row r at c ^ (r & 7)),
-//    and the group's 64 query rows by one TMA tile load;
-//  - MMA issue (warp 9, one thread): per k-block 2 x 4 MMAs (M = 128, N = 64,
+//    and the group's 64 query rows by one TMA tile load per k-block;
+//  - MMA issue (warp 13, one thread): per k-block 2 x 4 MMAs (M = 128, N = 64,
 //    K = 8) into the tile's two accumulators;
-//  - epilogue (warps 0-3, one TMEM lane quarter each): per row and member pair
-//    the bounds of the CR32 distance, written to the member's list slot.
+//  - epilogue (warps 0-7, a TMEM lane quarter and one of the two accumulators
+//    each): per row and member pair the bounds of the CR32 distance, written to
+//    the member's list slot.
 __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ CUtensorMap tmQ, TrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
     uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzled tiles need 1024-byte alignment
     uint8_t *stages = sm;
     TileMeta *meta = reinterpret_cast<TileMeta *>(sm + (size_t)TR_NS * TR_STAGE);
-    int *sent = reinterpret_cast<int *>(meta + TR_NB);      // preparation scratch: entry of each tile row
-    int *sseg = sent + TR_ROWS;                             // preparation scratch: (first row, rows) per segment
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sseg + 2 * TR_MAXSEG);
+    int *sseg = reinterpret_cast<int *>(meta + TR_NB);      // preparation scratch: (first row, rows, first entry) per segment
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sseg + 4 * TR_MAXSEG);
     const uint32_t full0 = smem_addr(bars), qfull0 = full0 + 8u * TR_NS, empty0 = qfull0 + 8u * TR_NS,
                    mfull0 = empty0 + 8u * TR_NS, mempty0 = mfull0 + 8u * TR_NB, afull0 = mempty0 + 8u * TR_NB,
                    aempty0 = afull0 + 8u * TR_NB, done = aempty0 + 8u * TR_NB;
@@ -361,16 +370,16 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
         }
         for (int i = 0; i < TR_NB; ++i) {
             mbar_init(mfull0 + 8u * i, 1);      // a tile's per-row data is staged
-            mbar_init(mempty0 + 8u * i, 4);     // the four epilogue warps are done with it
+            mbar_init(mempty0 + 8u * i, 8);     // the eight epilogue warps are done with it
             mbar_init(afull0 + 8u * i, 1);      // the tile's MMAs have completed
-            mbar_init(aempty0 + 8u * i, 4);     // the epilogue warps have read the accumulators
+            mbar_init(aempty0 + 8u * i, 8);     // the epilogue warps have read the accumulators
         }
         mbar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == TR_WM) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                      "r"(4 * 128)
                      : "memory");
@@ -395,45 +404,46 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
         return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
 
-    if (warp == 8) {
+    if (warp == TR_WP) {
         // ---------------------------------------------------- tile preparation
         int t = 0, b = 0, fill = 0, nseg = 0;
         auto emit = [&](int g) -> bool {
             if (t >= TR_NB && !warp_wait(mempty0 + 8u * b, (uint32_t)((t / TR_NB) - 1) & 1u, 0)) return false;
             TileMeta &mt = meta[b];
             const int count = fill;
-            const int id0 = a.ent_row[sent[0]];
-            for (int r = lane; r < TR_ROWS; r += 32) {
-                if (r < count) {
-                    const int e = sent[r];
-                    const float nx = a.ent_nx[e];
-                    mt.rid[r] = a.ent_row[e];
-                    mt.mask[r] = a.ent_mask[e];
-                    mt.pb[r] = a.ent_pb[e];
-                    mt.nx[r] = nx;
-                    mt.rx[r] = sqrtf(nx);
-                } else {
-                    mt.rid[r] = id0;        // padding rows repeat a real row; their results are not used
+            // the tile's rows are consecutive union entries, segment by segment, so
+            // their data are contiguous runs of the entry arrays: fetched with
+            // asynchronous copies, one wait for all of them
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int r0 = sseg[3 * sg], n = sseg[3 * sg + 1], e0 = sseg[3 * sg + 2];
+                for (int i = lane; i < n; i += 32) {
+                    cp_async4(smem_addr(&mt.rid[r0 + i]), a.ent_row + e0 + i);
+                    cp_async8(smem_addr(&mt.mask[r0 + i]), a.ent_mask + e0 + i);
+                    cp_async4(smem_addr(&mt.pb[r0 + i]), a.ent_pb + e0 + i);
+                    cp_async4(smem_addr(&mt.nx[r0 + i]), a.ent_nx + e0 + i);
                 }
             }
             for (int j = lane; j < TG; j += 32) {
-                mt.gq[j] = a.gq[g * TG + j];
-                mt.gn2[j] = a.gn2[g * TG + j];
-                mt.gn1[j] = a.gn1[g * TG + j];
+                cp_async4(smem_addr(&mt.gq[j]), a.gq + g * TG + j);
+                cp_async4(smem_addr(&mt.gn2[j]), a.gn2 + g * TG + j);
+                cp_async4(smem_addr(&mt.gn1[j]), a.gn1 + g * TG + j);
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
-            // pairs: segment by segment (consecutive entries of one range), each a
-            // contiguous run of slots starting at the pair base of its first row
+            for (int r = count + lane; r < TR_ROWS; r += 32) mt.rid[r] = mt.rid[0];   // padding rows repeat row 0
+            // pairs: each segment's slots are one contiguous run starting at the
+            // pair base of its first row
             int base = 0;
             for (int sg = 0; sg < nseg; ++sg) {
-                const int r0 = sseg[2 * sg], n = sseg[2 * sg + 1];
+                const int r0 = sseg[3 * sg], n = sseg[3 * sg + 1];
                 const int pb0 = mt.pb[r0], len = mt.pb[r0 + n - 1] + __popcll(mt.mask[r0 + n - 1]) - pb0;
                 for (int r = r0 + lane; r < r0 + n; r += 32) mt.off[r] = base + mt.pb[r] - pb0;
                 const int lim = base + len < TR_PMAX ? len : TR_PMAX - base;
-                for (int p = lane; p < lim; p += 32) mt.spos[base + p] = a.pair_pos[pb0 + p];
+                for (int p = lane; p < lim; p += 32) cp_async4(smem_addr(&mt.spos[base + p]), a.pair_pos + pb0 + p);
                 base += len;
                 if (base > TR_PMAX) base = TR_PMAX + 1;   // the rest read their positions from global memory
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             if (lane == 0) {
                 mt.g = g;
                 mt.count = count;
@@ -459,10 +469,10 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                 const int2 itm = a.items_arr[(long long)g * a.R + r];
                 for (int got = 0; got < itm.y;) {
                     const int take = TR_ROWS - fill < itm.y - got ? TR_ROWS - fill : itm.y - got;
-                    for (int i = lane; i < take; i += 32) sent[fill + i] = itm.x + got + i;
                     if (lane == 0) {
-                        sseg[2 * nseg] = fill;
-                        sseg[2 * nseg + 1] = take;
+                        sseg[3 * nseg] = fill;
+                        sseg[3 * nseg + 1] = take;
+                        sseg[3 * nseg + 2] = itm.x + got;
                     }
                     ++nseg;
                     fill += take;
@@ -483,25 +493,17 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                 mbar_arrive(mfull0 + 8u * b);
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp >= TR_WC && warp < TR_WC + TR_LT / 32) {
         // -------------------------------------------------------------- copies
-        const int lt = threadIdx.x - 128;
-        // one thread waits; the group goes on only if that wait succeeded and no
-        // other role has given up (the same verdict for every copy thread)
-        auto group_wait = [&](uint32_t bar, uint32_t parity, unsigned site) -> bool {
-            bool fail = false;
-            if (lt == 0 && !mbar_wait(bar, parity)) {
-                tr_error(site);
-                *abort_flag = 1;
-                fail = true;
-            }
-            return !copy_any(fail || *abort_flag != 0);
-        };
+        // each copy warp waits by itself (lane 0 polls, the warp follows); the
+        // stage completes once all 128 copy threads' copies have landed
+        const int lt = threadIdx.x - 32 * TR_WC;
         const int c = lt & 7, r0 = lt >> 3;
         const uint32_t swz = (uint32_t)((c ^ (r0 & 7)) << 4);
+        const int nst = (a.nk + TR_KB - 1) / TR_KB;      // stages per tile
         for (int t = 0;; ++t) {
             const int b = t % TR_NB;
-            if (!group_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 1)) break;
+            if (!warp_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 1)) break;
             const TileMeta &mt = meta[b];
             if (mt.count < 0) break;
             const int g = mt.g;
@@ -509,26 +511,30 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
 #pragma unroll
             for (int i = 0; i < 16; ++i) id[i] = mt.rid[r0 + 16 * i];
             bool ok = true;
-            for (int kc = 0; kc < a.nk; ++kc, ++issued) {
+            for (int si = 0; si < nst; ++si, ++issued) {
                 const int s = (int)(issued % TR_NS);
-                if (issued >= TR_NS && !group_wait(empty0 + 8u * s, (uint32_t)((issued / TR_NS) - 1) & 1u, 2)) {
+                if (issued >= TR_NS && !warp_wait(empty0 + 8u * s, (uint32_t)((issued / TR_NS) - 1) & 1u, 2)) {
                     ok = false;
                     break;
                 }
-                const uint32_t sa = smem_addr(stages + (size_t)s * TR_STAGE);
+                const int k0 = si * TR_KB, nkb = a.nk - k0 < TR_KB ? a.nk - k0 : TR_KB;
+                const uint32_t sa = smem_addr(stages + (size_t)s * TR_STAGE), sq = sa + TR_KB * 2 * TR_A_BYTES;
                 if (lt == 0) {
-                    mbar_expect_tx(qfull0 + 8u * s, TR_B_BYTES);
-                    tma_load_2d(sa + 2 * TR_A_BYTES, &tmQ, 32 * kc, TG * g, qfull0 + 8u * s);
+                    mbar_expect_tx(qfull0 + 8u * s, (uint32_t)nkb * TR_B_BYTES);
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_2d(sq + (uint32_t)kb * TR_B_BYTES, &tmQ, 32 * (k0 + kb), TG * g, qfull0 + 8u * s);
                 }
-                const float *col = a.Xr + 32 * kc + 4 * c;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const float *col = a.Xr + 32 * (k0 + kb) + 4 * c;
+                    const uint32_t da = sa + (uint32_t)kb * 2 * TR_A_BYTES + swz;
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    cp_async16(sa + (uint32_t)((r0 + 16 * i) * 128) + swz, col + (long long)id[i] * a.Dp);
+                    for (int i = 0; i < 16; ++i) cp_async16(da + (uint32_t)((r0 + 16 * i) * 128), col + (long long)id[i] * a.Dp);
+                }
                 cp_async_arrive(full0 + 8u * s);
             }
             if (!ok) break;
         }
-    } else if (warp == 9) {
+    } else if (warp == TR_WM) {
         // ------------------------------------------------------------- MMA issue
         if (lane == 0) {
             const uint32_t idesc = tf32_idesc(TG, 128);
@@ -549,7 +555,8 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                 tc_fence_after();
                 const uint32_t d0 = tmem + 128u * b, d1 = d0 + 64u;
                 bool bad = false;
-                for (int kc = 0; kc < a.nk; ++kc, ++c) {
+                const int nst = (a.nk + TR_KB - 1) / TR_KB;
+                for (int si = 0; si < nst; ++si, ++c) {
                     const int s = (int)(c % TR_NS);
                     const uint32_t ph = (uint32_t)(c / TR_NS) & 1u;
                     if (!mbar_wait(full0 + 8u * s, ph) || !mbar_wait(qfull0 + 8u * s, ph)) {
@@ -560,12 +567,16 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                     // through the async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc_fence_after();
-                    const uint32_t sa = smem_addr(stages + (size_t)s * TR_STAGE), sq = sa + 2 * TR_A_BYTES;
+                    const int k0 = si * TR_KB, nkb = a.nk - k0 < TR_KB ? a.nk - k0 : TR_KB;
+                    const uint32_t sa0 = smem_addr(stages + (size_t)s * TR_STAGE), sq0 = sa0 + TR_KB * 2 * TR_A_BYTES;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t sa = sa0 + (uint32_t)kb * 2 * TR_A_BYTES, sq = sq0 + (uint32_t)kb * TR_B_BYTES;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {       // UMMA K = 8 floats = 32 bytes
-                        const uint32_t o = 32u * j, acc = (kc | j) != 0;
-                        mma_tf32(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
-                        mma_tf32(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                        for (int j = 0; j < 4; ++j) {   // UMMA K = 8 floats = 32 bytes
+                            const uint32_t o = 32u * j, acc = (k0 + kb + j) != 0;
+                            mma_tf32(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
+                            mma_tf32(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                        }
                     }
                     mma_commit(empty0 + 8u * s);
                 }
@@ -581,7 +592,9 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int qd = warp;                          // the TMEM lane quarter this warp may read
+        // warps w and w + 4 read TMEM lane quarter w & 3; warp w < 4 takes the
+        // tile's first accumulator (rows 0-127), w >= 4 the second
+        const int qd = warp & 3, h = warp >> 2;
         for (int t = 0;; ++t) {
             const int b = t % TR_NB;
             if (!warp_wait(mfull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 6)) break;
@@ -590,38 +603,33 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
             if (count < 0) break;
             if (!warp_wait(afull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 7)) break;
             tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 128u * b;
+            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 128u * b + 64u * h;
+            const int row = 32 * qd + lane + 128 * h;
+            const bool valid = row < count;
+            const unsigned long long m = valid ? mt.mask[row] : 0ull;
+            const int pb = valid ? mt.pb[row] : 0, po = valid ? mt.off[row] : 0;
+            const float nx = valid ? mt.nx[row] : 0.0f, c1rx = a.c1 * sqrtf(nx);
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int row = 32 * qd + lane + 128 * h;
-                const bool valid = row < count;
-                const unsigned long long m = valid ? mt.mask[row] : 0ull;
-                const int pb = valid ? mt.pb[row] : 0, po = valid ? mt.off[row] : 0;
-                const float nx = valid ? mt.nx[row] : 0.0f, rx = valid ? mt.rx[row] : 0.0f;
-#pragma unroll 1
-                for (int cb = 0; cb < TG / 16; ++cb) {
-                    uint32_t v[16];
-                    tmem_ld16(ta + 64u * h + 16u * cb, v);     // warp-collective: every lane takes part
-                    const unsigned sub = (unsigned)(m >> (16 * cb)) & 0xFFFFu;
-                    const int rank0 = __popcll(m & ((1ull << (16 * cb)) - 1ull));
-                    int pos[16];
+            for (int cb = 0; cb < TG / 16; ++cb) {
+                uint32_t v[16];
+                tmem_ld16(ta + 16u * cb, v);               // warp-collective: every lane takes part
+                const unsigned sub = (unsigned)(m >> (16 * cb)) & 0xFFFFu;
+                const int rank0 = __popcll(m & ((1ull << (16 * cb)) - 1ull));
+                int pos[16];
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {      // list positions for members 16 cb + jj
-                        const int rk = rank0 + __popc(sub & ((1u << jj) - 1u));
-                        pos[jj] = !((sub >> jj) & 1u) ? 0 : po + rk < TR_PMAX ? mt.spos[po + rk] : a.pair_pos[pb + rk];
-                    }
+                for (int jj = 0; jj < 16; ++jj) {          // list positions for members 16 cb + jj
+                    const int rk = rank0 + __popc(sub & ((1u << jj) - 1u));
+                    pos[jj] = !((sub >> jj) & 1u) ? 0 : po + rk < TR_PMAX ? mt.spos[po + rk] : a.pair_pos[pb + rk];
+                }
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        if ((sub >> jj) & 1u) {
-                            const int j = 16 * cb + jj;
-                            const float ss = nx + mt.gn2[j];
-                            const float dt = ss - 2.0f * __uint_as_float(v[jj]);
-                            const float E = a.c1 * (mt.gn1[j] * rx) + a.c2 * ss;
-                            const float E2 = E + a.gam * (fabsf(dt) + E);
-                            const long long o = (long long)mt.gq[j] * a.stride + pos[jj];
-                            a.ub[o] = fmaxf(dt + E2, 0.0f);
-                            a.lb[o] = dt - E2;
-                        }
+                for (int jj = 0; jj < 16; ++jj) {
+                    if ((sub >> jj) & 1u) {
+                        const int j = 16 * cb + jj;
+                        const float ss = nx + mt.gn2[j];
+                        const float dt = ss - 2.0f * __uint_as_float(v[jj]);
+                        const float E = mt.gn1[j] * c1rx + a.c2 * ss;
+                        const float E2 = E + a.gam * (fabsf(dt) + E);
+                        a.ulb[(long long)mt.gq[j] * a.stride + pos[jj]] = make_float2(fmaxf(dt + E2, 0.0f), dt - E2);
                     }
                 }
             }
@@ -635,17 +643,17 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
     }
 
     // ---------------------------------------------------------------- teardown
-    if (warp == 9 && lane == 0 && !mbar_wait(done, 0)) tr_error(8);
-    if (warp >= 4 && warp < 8) {
+    if (warp == TR_WM && lane == 0 && !mbar_wait(done, 0)) tr_error(8);
+    if (warp >= TR_WC && warp < TR_WC + TR_LT / 32) {
         // every copy still in flight lands before the CTA's shared memory goes away
         asm volatile("cp.async.wait_all;" ::: "memory");
-        if (threadIdx.x == 128)
+        if (threadIdx.x == 32 * TR_WC)
             for (long long c = issued - TR_NS < 0 ? 0 : issued - TR_NS; c < issued; ++c)
                 if (!mbar_wait(qfull0 + 8u * (c % TR_NS), (uint32_t)(c / TR_NS) & 1u)) tr_error(9);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == TR_WM) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * 128) : "memory");
     }
@@ -680,14 +688,14 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)ecap),
                  o_mask = take(sizeof(unsigned long long) * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
                  o_enx = take(sizeof(float) * (size_t)ecap),
-                 o_pp = take(sizeof(int) * (size_t)pcap), o_lb = take(sizeof(float) * (size_t)nq * stride),
+                 o_pp = take(sizeof(int) * (size_t)pcap), o_ulb = take(sizeof(float2) * (size_t)nq * stride),
                  o_rc = take(sizeof(int) * (size_t)nq * stride), o_nr = take(sizeof(int64_t) * nq);
     uint8_t *buf = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
     unsigned long long *counts = (unsigned long long *)(buf + o_cnt);
     int *qord = (int *)(buf + o_qord), *pos = (int *)(buf + o_pos), *gq = (int *)(buf + o_gq);
     float *gn2 = (float *)(buf + o_gn2), *gn1 = (float *)(buf + o_gn1), *Qg = (float *)(buf + o_qg);
-    float *lb = (float *)(buf + o_lb);
+    float2 *ulb = (float2 *)(buf + o_ulb);
     int32_t *rc = (int32_t *)(buf + o_rc);
     int64_t *nr = (int64_t *)(buf + o_nr);
     TUnion u;
@@ -745,8 +753,7 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
         ta.pair_pos = u.pair_pos;
         ta.items_arr = u.items;
         ta.counter = counts + 2;
-        ta.ub = dbuf;
-        ta.lb = lb;
+        ta.ulb = ulb;
         const double eps_acc = (Dp / 8 + 1) * std::ldexp(1.0, -20);
         ta.c1 = (float)(2.0 * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + eps_acc) * 1.01);
         ta.c2 = (float)std::ldexp(1.0, -19);
@@ -761,7 +768,7 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rerank_tc", __FILE__, __LINE__); break; }
-        s = crisp_run_bound_select(nq, cand, stride, ncand, k, dbuf, lb, err_word, rc, nr, st);
+        s = crisp_run_bound_select(nq, cand, stride, ncand, k, ulb, err_word, rc, nr, st);
         if (s) break;
         // the kept candidates, measured exactly (streaming CR32) -> top-k
         s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false);
