@@ -170,16 +170,27 @@ uint64_t crisp_kernel_launches(void);
 
 /* ================================================================ search */
 
-/* Answer nq queries (Algorithm 1).  Q: device [nq][D] float32 in the original
- * space (rotated inside when the index is rotated).  ids: device [nq][k] int64,
- * sqdist: device [nq][k] float32, both ascending by (distance, id) and padded
- * with -1 / +inf when fewer than k points qualify.  stats: device [nq] or NULL.
+/* Answer nq queries (Algorithm 1; the problem of §3 "Exact and Approximate
+ * Similarity Search": the k nearest rows of X to each query under L2).
+ * Q: device [nq][D] float32 in the original space (rotated inside when the
+ * index is rotated).  params: host array of p_count parameter sets, p_count = 1
+ * (one set for every query) or nq (set i for query i: each query may have its
+ * own k, mode, rho, alpha, precision, ...; queries are run class by class and
+ * their results put back in place).  ids: device [nq][kmax] int64, sqdist:
+ * device [nq][kmax] float32; row i holds query i's k_i neighbours ascending by
+ * (distance, id), padded with -1 / +inf past k_i or when fewer than k_i points
+ * qualify; kmax >= every k_i (kmax <= 0: the largest k_i).  stats: device [nq]
+ * or NULL.  A query's result does not depend on the other queries of the batch.
  * Scratch comes from a stream-ordered memory pool the library keeps per device
  * (it holds its memory between calls; crisp_search_scratch_bytes tells how much).
- * EINVAL: k outside [1, 256] or > N, rho outside (0, 1], alpha outside [0, 1],
- * mode outside {0, 1, 2}, 0 < max_candidates < k, nq < 0, precision outside
- * {0, 1, 2} or used outside Guaranteed mode, shortlist < k, or a precision
- * whose row copy the index lacks; mode 2 without a model or a BF16 copy.
+ * With p_count = nq the call waits for its small host-to-device copy of the
+ * per-query parameters before it returns.
+ * EINVAL (nothing written): p_count not 1 or nq, kmax < some k_i, or a
+ * parameter set with k outside [1, 256] or > N, rho outside (0, 1], alpha
+ * outside [0, 1], mode outside {0, 1, 2}, 0 < max_candidates < k, nq < 0,
+ * precision outside {0, 1, 2} or used outside Guaranteed mode, shortlist < k,
+ * or a precision whose row copy the index lacks; mode 2 without a model or a
+ * BF16 copy.
  *
  * Mode 2 (Learned, the engine's F1 extension; the paper's patience and
  * ordering are what it replaces, §4.3.2 Stage 3): after the Guaranteed cut, a
@@ -189,23 +200,33 @@ uint64_t crisp_kernel_launches(void);
  * re-rank of the shortlist gives the top-k.  Depth = ceil(2^(j/4)), j =
  * ceil(4 (prediction + margin)), clamped to [k, |C|] and [k, depth_V]. */
 crisp_status crisp_search(const crisp_index *index, const float *Q, int32_t nq, const crisp_search_params *params,
-                          int64_t *ids, float *sqdist, crisp_query_stats *stats, void *stream);
+                          int32_t p_count, int64_t *ids, float *sqdist, int32_t kmax, crisp_query_stats *stats,
+                          void *stream);
 
-/* As crisp_search, with HOST buffers (Q [nq][D], ids [nq][k], sqdist [nq][k],
- * stats [nq] or NULL): copies in, searches, copies out, and synchronises. */
+/* As crisp_search, with HOST buffers (Q [nq][D], ids [nq][kmax], sqdist
+ * [nq][kmax], stats [nq] or NULL): copies in, searches, copies out, and
+ * synchronises. */
 crisp_status crisp_search_host(const crisp_index *index, const float *Q, int32_t nq,
-                               const crisp_search_params *params, int64_t *ids, float *sqdist,
-                               crisp_query_stats *stats, void *stream);
+                               const crisp_search_params *params, int32_t p_count, int64_t *ids, float *sqdist,
+                               int32_t kmax, crisp_query_stats *stats, void *stream);
 
-/* Device bytes of scratch crisp_search needs for nq queries (for admission). */
+/* Device bytes of scratch crisp_search needs for nq queries with these
+ * parameter sets (p_count = 1 or nq; for admission). */
 crisp_status crisp_search_scratch_bytes(const crisp_index *index, int32_t nq, const crisp_search_params *params,
-                                        size_t *bytes);
+                                        int32_t p_count, size_t *bytes);
+
+/* The library's readings of the paper's parameters (Theorem 1: tau = alpha M;
+ * Algorithm 1: the per-subspace retrieval budget): tau = ceil(alpha M - 1e-9),
+ * budget = max(1, ceil(rho N - 1e-9)). */
+int32_t crisp_search_tau(double alpha, int32_t M);
+int64_t crisp_search_budget(double rho, int64_t N);
 
 /* =========================================== serving (continuous batching)
  * A request server over one index: requests (one query each, any search
- * parameters) arrive from any thread; a dispatcher thread batches waiting
- * requests with equal parameters (oldest first, up to max_batch), admits a
- * batch when one of `streams` stream slots is free and its search scratch
+ * parameters) arrive from any thread; a dispatcher thread batches the waiting
+ * requests oldest first (up to max_batch, whatever their k and mode: one
+ * crisp_search with per-query parameters), admits a batch when one of
+ * `streams` stream slots is free and its search scratch
  * (crisp_search_scratch_bytes) fits within scratch_budget next to the batches
  * already on the GPU, and runs copy-in, crisp_search and copy-out on that
  * slot's stream.  Batches on different slots overlap on the GPU.  A request's

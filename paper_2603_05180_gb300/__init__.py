@@ -79,9 +79,11 @@ _SIGS = {
     "crisp_quantize_bf16": [_P, _I64, _I32, _P, _P],
     "crisp_quantize_e4m3": [_P, _I64, _I32, _P, _P, _P],
     "crisp_shortlist": [_P, _P, _I32, _P, _I64, _P, _I32, _I32, _P, _I64, _P, _P],
-    "crisp_search": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
-    "crisp_search_host": [_P, _P, _I32, C.POINTER(SearchParams), _P, _P, _P, _P],
-    "crisp_search_scratch_bytes": [_P, _I32, C.POINTER(SearchParams), C.POINTER(_S)],
+    "crisp_search": [_P, _P, _I32, _P, _I32, _P, _P, _I32, _P, _P],
+    "crisp_search_host": [_P, _P, _I32, _P, _I32, _P, _P, _I32, _P, _P],
+    "crisp_search_scratch_bytes": [_P, _I32, _P, _I32, C.POINTER(_S)],
+    "crisp_search_tau": [_D, _I32],
+    "crisp_search_budget": [_D, _I64],
     "crisp_covariance": [_P, _I64, _I32, _I32, _P, _I64, _P, _P],
     "crisp_eigvalsh": [_P, _I32, _P, _P],
     "crisp_cev": [_P, _I64, _I32, _I32, _P, _I64, C.POINTER(_D), _P],
@@ -135,6 +137,8 @@ def lib():
         L.crisp_free.restype = None
         L.crisp_last_error.argtypes = []
         L.crisp_last_error.restype = C.c_char_p
+        L.crisp_search_tau.restype = C.c_int32
+        L.crisp_search_budget.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -250,19 +254,40 @@ def crisp_shortlist(index, Qr, nq, cand, cand_stride, ncand, precision, S, out, 
           out_stride, _ptr(nout), _stream(stream))
 
 
-def crisp_search(index, Q, nq, params: SearchParams, ids, sqdist, stats=None, stream=None):
-    _call("crisp_search", index, _ptr(Q), nq, C.byref(params), _ptr(ids), _ptr(sqdist), _ptr(stats), _stream(stream))
+def _param_array(params):
+    """One SearchParams (shared by every query) or a sequence of them (one per query)."""
+    if isinstance(params, SearchParams):
+        return (SearchParams * 1)(params), 1, params.k
+    arr = (SearchParams * len(params))(*params)
+    return arr, len(params), max((p.k for p in params), default=1)
 
 
-def crisp_search_host(index, Q, nq, params: SearchParams, ids, sqdist, stats=None, stream=None):
-    _call("crisp_search_host", index, _ptr(Q), nq, C.byref(params), _ptr(ids), _ptr(sqdist), _ptr(stats),
-          _stream(stream))
+def _kmax(ids, kbig, kmax):
+    if kmax is not None:
+        return int(kmax)
+    shape = getattr(ids, "shape", None)
+    return int(shape[1]) if shape is not None and len(shape) == 2 else kbig
 
 
-def crisp_search_scratch_bytes(index, nq, params: SearchParams) -> int:
-    n = C.c_size_t(0)
-    _call("crisp_search_scratch_bytes", index, nq, C.byref(params), C.byref(n))
-    return n.value
+def crisp_search(index, Q, nq, params, ids, sqdist, stats=None, stream=None, kmax=None):
+    """params: one SearchParams for every query, or one per query (p_count = nq);
+    ids / sqdist rows of kmax entries (default: their second dimension)."""
+    arr, n, kbig = _param_array(params)
+    _call("crisp_search", index, _ptr(Q), nq, C.cast(arr, C.c_void_p), n, _ptr(ids), _ptr(sqdist),
+          _kmax(ids, kbig, kmax), _ptr(stats), _stream(stream))
+
+
+def crisp_search_host(index, Q, nq, params, ids, sqdist, stats=None, stream=None, kmax=None):
+    arr, n, kbig = _param_array(params)
+    _call("crisp_search_host", index, _ptr(Q), nq, C.cast(arr, C.c_void_p), n, _ptr(ids), _ptr(sqdist),
+          _kmax(ids, kbig, kmax), _ptr(stats), _stream(stream))
+
+
+def crisp_search_scratch_bytes(index, nq, params) -> int:
+    arr, n, _ = _param_array(params)
+    out = C.c_size_t(0)
+    _call("crisp_search_scratch_bytes", index, nq, C.cast(arr, C.c_void_p), n, C.byref(out))
+    return int(out.value)
 
 
 def crisp_covariance(X, N, D, ldx, rows, S, cov, stream=None):
@@ -346,18 +371,18 @@ def crisp_verify_opt(index, Qr, nq, cand, cand_stride, ncand, k, eps0, patience,
 
 
 # ------------------------------------------------------------ conveniences
-def tau(alpha: float, M: int) -> int:
-    """tau = ceil(alpha M - 1e-9) (the library's reading of Theorem 1's tau = alpha M)."""
-    import math
-
-    return int(math.ceil(alpha * M - 1e-9))
+def crisp_search_tau(alpha: float, M: int) -> int:
+    """The library's tau for a minimum collision fraction alpha (Theorem 1's tau = alpha M)."""
+    return int(lib().crisp_search_tau(float(alpha), int(M)))
 
 
-def budget(rho: float, N: int) -> int:
-    """max(1, ceil(rho N - 1e-9)) ids per subspace (Algorithm 1's budget)."""
-    import math
+def crisp_search_budget(rho: float, N: int) -> int:
+    """The library's per-subspace retrieval budget for coverage rho (Algorithm 1)."""
+    return int(lib().crisp_search_budget(float(rho), int(N)))
 
-    return max(1, int(math.ceil(rho * N - 1e-9)))
+
+tau = crisp_search_tau
+budget = crisp_search_budget
 
 
 def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.1, max_candidates=0, precision=0,

@@ -11,31 +11,32 @@
 
 #include "internal.cuh"
 
-// launchers defined in query.cu / verify.cu
+// launchers defined in query.cu / verify.cu / learned.cu
 crisp_status crisp_run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
                                 int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st,
-                                float *cost_first, float *cost_last);
+                                float *cost_first, float *cost_last, const QParam *qp = nullptr);
 crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
                                  int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t stride, int64_t *ncand,
-                                 uint8_t *score, int32_t *how, cudaStream_t st);
+                                 uint8_t *score, int32_t *how, cudaStream_t st, const QParam *qp = nullptr);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st, bool no_alloc = false, bool may_group = true);
+                              cudaStream_t st, bool no_alloc = false, bool may_group = true,
+                              const QParam *qp = nullptr, int32_t ko = 0);
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
-                                 const int64_t *S_per_query);
+                                 const int64_t *S_per_query, const QParam *qp = nullptr);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
                                   int32_t order, int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const QParam *qp, int32_t ko);
 
 crisp_status crisp_run_features(const crisp_index *ix, const int32_t *cand, int64_t stride, const int64_t *ncand,
                                 const uint8_t *score, const float *cfirst, const float *clast, int32_t nq, int32_t k,
-                                int32_t tau, float *feats, cudaStream_t st);
+                                int32_t tau, float *feats, cudaStream_t st, const QParam *qp = nullptr);
 crisp_status crisp_run_mlp_depth(const crisp_index *ix, const float *feats, int32_t nq, const int64_t *ncand,
                                  int64_t stride, int32_t k, float mV, float mS, int64_t *dV, int64_t *dS,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const QParam *qp = nullptr);
 crisp_status crisp_run_select_score(const int32_t *cand, int64_t stride, const int64_t *ncand, const uint8_t *score,
                                     const int64_t *depth, int32_t nq, int32_t *out, int64_t *nout, cudaStream_t st);
 crisp_status crisp_run_labels_v(const int32_t *cand, int64_t stride, const int64_t *ncand, const uint8_t *score,
@@ -43,6 +44,10 @@ crisp_status crisp_run_labels_v(const int32_t *cand, int64_t stride, const int64
 crisp_status crisp_run_labels_s(const int32_t *P, int64_t stride, const int64_t *nP, const float *dist,
                                 const int64_t *top, int32_t k, int32_t nq, int64_t *dS, cudaStream_t st);
 crisp_status crisp_run_log2_targets(const int64_t *dV, const int64_t *dS, int32_t nq, int64_t *labels, float *targets,
+                                    cudaStream_t st);
+crisp_status launch_gather_rows(const float *Q, int32_t D, const int32_t *perm, int32_t n, float *Y, cudaStream_t st);
+crisp_status launch_scatter_results(const int64_t *ids_t, const float *d2_t, const crisp_query_stats *st_t, int32_t ko,
+                                    const int32_t *perm, int32_t n, int64_t *ids, float *d2, crisp_query_stats *stats,
                                     cudaStream_t st);
 
 // ------------------------------------------------------------ scratch pool
@@ -288,17 +293,16 @@ extern "C" crisp_status crisp_index_import(const void *host_buf, size_t bytes, v
 }
 
 // --------------------------------------------------------------- search
-struct SearchPlan {
-    int32_t tau, phi, k, prec, S;
-    bool learned;
-    int64_t budget, cap, stride;
-    int32_t chunk;
-    size_t per_query;
-};
+extern "C" int32_t crisp_search_tau(double alpha, int32_t M) { return crisp_tau(alpha, M); }
+extern "C" int64_t crisp_search_budget(double rho, int64_t N) { return crisp_budget(rho, N); }
 
-static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_search_params *p, SearchPlan *pl) {
-    CRISP_REQUIRE(ix && p, "crisp_search: null index or params");
-    CRISP_REQUIRE(nq >= 0, "crisp_search: nq < 0");
+// Stage-3 class of a parameter set: Guaranteed with FP32 re-rank (0), with
+// BF16 (1) or FP8 (2) coarse scores, Optimized (3), Learned (4).
+static int stage_class(const crisp_search_params *p) { return p->mode == 1 ? 3 : p->mode == 2 ? 4 : p->precision; }
+
+// Validate one parameter set; derive what the kernels read and the candidate
+// list bound of a query using it.
+static crisp_status check_params(const crisp_index *ix, const crisp_search_params *p, QParam *qp, int64_t *bound) {
     CRISP_REQUIRE(p->k >= 1 && p->k <= CRISP_KOUT_MAX && p->k <= ix->N, "crisp_search: k = %d outside [1, min(256, N)]",
                   p->k);
     CRISP_REQUIRE(p->mode >= 0 && p->mode <= 2, "crisp_search: mode must be 0, 1 or 2");
@@ -319,32 +323,89 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
         CRISP_REQUIRE(p->precision != 1 || ix->Xb, "crisp_search: the index has no BF16 copy (crisp_index_add_copies)");
         CRISP_REQUIRE(p->precision != 2 || ix->X8, "crisp_search: the index has no FP8 copy (crisp_index_add_copies)");
     }
-    if (ix->M > 127) { crisp_set_error("crisp_search: M > 127 is not supported"); return CRISP_EUNSUPPORTED; }
-    pl->tau = crisp_tau(p->alpha, ix->M);
-    pl->budget = crisp_budget(p->rho, ix->N);
-    pl->phi = p->mode == 1 ? 1 : 0;
-    pl->learned = p->mode == 2;
-    pl->k = p->k;
-    pl->cap = p->max_candidates;
-    pl->prec = p->precision;
-    pl->S = p->precision > 0 ? p->shortlist : 0;
+    qp->k = p->k;
+    qp->phi = p->mode == 1 ? 1 : 0;
+    qp->tau = crisp_tau(p->alpha, ix->M);
+    qp->order = p->verify_order;
+    qp->budget = crisp_budget(p->rho, ix->N);
+    qp->patience = p->patience_factor > 0 ? (int64_t)p->patience_factor * p->k : 0;
+    qp->eps0 = p->eps0;
+    qp->mV = p->depth_margin;
+    qp->mS = p->short_margin;
+    qp->S = p->precision > 0 ? p->shortlist : 0;
     // Every candidate needs V >= tau and the scores sum to at most w * (ids
     // retrieved), each subspace retrieving fewer than budget + largest cell:
     // |C| <= w M (budget + max_cell) / tau; the fallback returns at most k.
-    int64_t bound = ix->N;
-    if (pl->tau > 0) {
-        int64_t w = p->mode == 1 ? 2 : 1;
-        int64_t votes = w * (int64_t)ix->M * (pl->budget + ix->max_cell);
-        bound = std::min<int64_t>(ix->N, std::max<int64_t>((votes + pl->tau - 1) / pl->tau, p->k));
+    int64_t b = ix->N;
+    if (qp->tau > 0) {
+        const int64_t w = p->mode == 1 ? 2 : 1;
+        const int64_t votes = w * (int64_t)ix->M * (qp->budget + ix->max_cell);
+        b = std::min<int64_t>(ix->N, std::max<int64_t>((votes + qp->tau - 1) / qp->tau, p->k));
     }
-    pl->stride = p->max_candidates > 0 ? std::min<int64_t>(p->max_candidates, bound) : bound;
-    if (pl->cap > pl->stride) pl->cap = 0;   // the cap can never bind
-    pl->stride = std::max<int64_t>(pl->stride, 1);
+    if (p->max_candidates > 0) b = std::min<int64_t>(p->max_candidates, b);
+    qp->cap = p->max_candidates > b ? 0 : p->max_candidates;   // a cap at or above the bound never binds
+    *bound = std::max<int64_t>(b, 1);
+    return CRISP_OK;
+}
+
+struct SearchPlan {
+    bool shared;            // one parameter set for every query
+    QParam q0;              // the shared set (shared)
+    int cls0;               // its class (shared)
+    int64_t stride;         // candidate list stride: the largest bound
+    int32_t kmax;           // output row length
+    int32_t Smax;           // largest shortlist of a coarse-scored query
+    bool any_learned;
+    int32_t chunk;
+    size_t per_query;
+    std::vector<QParam> qp; // per query, in the original order (not shared)
+    std::vector<int> cls;   // per query (not shared)
+};
+
+static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_search_params *p, int32_t p_count,
+                                int32_t kmax, SearchPlan *pl) {
+    CRISP_REQUIRE(ix && p, "crisp_search: null index or params");
+    CRISP_REQUIRE(nq >= 0, "crisp_search: nq < 0");
+    CRISP_REQUIRE(p_count == 1 || p_count == nq, "crisp_search: p_count must be 1 or nq (%d), not %d", nq, p_count);
+    if (ix->M > 127) { crisp_set_error("crisp_search: M > 127 is not supported"); return CRISP_EUNSUPPORTED; }
+    pl->shared = p_count == 1;
+    pl->stride = 1;
+    pl->Smax = 0;
+    pl->any_learned = false;
+    int32_t kbig = 0;
+    if (!pl->shared) {
+        pl->qp.resize((size_t)nq);
+        pl->cls.resize((size_t)nq);
+    }
+    for (int32_t i = 0; i < p_count; ++i) {
+        QParam q;
+        int64_t b;
+        crisp_status s = check_params(ix, &p[i], &q, &b);
+        if (s) return s;
+        pl->stride = std::max(pl->stride, b);
+        pl->Smax = std::max(pl->Smax, q.S);
+        pl->any_learned = pl->any_learned || p[i].mode == 2;
+        kbig = std::max(kbig, q.k);
+        if (pl->shared) {
+            pl->q0 = q;
+            pl->cls0 = stage_class(&p[i]);
+        } else {
+            pl->qp[i] = q;
+            pl->cls[i] = stage_class(&p[i]);
+        }
+    }
+    pl->kmax = kmax <= 0 ? kbig : kmax;
+    CRISP_REQUIRE(pl->kmax >= kbig, "crisp_search: kmax = %d < the largest k (%d)", kmax, kbig);
     const int64_t K2 = (int64_t)ix->K * ix->K;
-    pl->per_query = sizeof(float) * ix->Dp + sizeof(int32_t) * ix->M * K2 + sizeof(int32_t) * ix->M +
-                    sizeof(int64_t) * ix->M + sizeof(int32_t) * pl->stride * 2 + sizeof(int32_t) * pl->S + 64;
-    if (pl->learned)   // scores, traversal costs, features, selected list
-        pl->per_query += pl->stride + sizeof(float) * (2 * ix->M + 2 * ix->M + 68) + sizeof(int32_t) * pl->stride + 64;
+    const int64_t st = pl->stride;
+    pl->per_query = sizeof(float) * ix->Dp + sizeof(float) * ix->D + sizeof(int32_t) * ix->M * K2 +
+                    sizeof(int32_t) * ix->M + sizeof(int64_t) * ix->M + sizeof(int32_t) * st * 2 +
+                    sizeof(int32_t) * pl->Smax + sizeof(QParam) + (sizeof(int64_t) + sizeof(float)) * pl->kmax +
+                    sizeof(crisp_query_stats) + 64;
+    if (pl->any_learned)   // scores, traversal costs, features, selected list
+        pl->per_query += st + sizeof(float) * (2 * ix->M + 2 * ix->M + 68) + sizeof(int32_t) * st + 64;
+    // batches of 1,024 queries or more re-rank on the tensor cores, with bounds, kept lists and pair slots
+    pl->per_query += sizeof(float) * 2 * st + sizeof(int32_t) * st + sizeof(int32_t) * st;
     size_t budget_bytes = (size_t)16 << 30;
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
@@ -354,9 +415,9 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
 }
 
 extern "C" crisp_status crisp_search_scratch_bytes(const crisp_index *ix, int32_t nq, const crisp_search_params *p,
-                                                   size_t *bytes) {
+                                                   int32_t p_count, size_t *bytes) {
     SearchPlan pl;
-    crisp_status s = plan_search(ix, nq, p, &pl);
+    crisp_status s = plan_search(ix, nq, p, p_count, 0, &pl);
     if (s) return s;
     CRISP_REQUIRE(bytes, "crisp_search_scratch_bytes: null output");
     *bytes = pl.per_query * (size_t)pl.chunk;
@@ -371,29 +432,46 @@ static T *carve(uint8_t *&p, size_t n) {
 }
 
 static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t nq, const crisp_search_params *p,
-                                  int64_t *ids, float *d2, crisp_query_stats *stats, cudaStream_t st) {
+                                  int32_t p_count, int64_t *ids, float *d2, int32_t kmax, crisp_query_stats *stats,
+                                  cudaStream_t st) {
     SearchPlan pl;
-    crisp_status s = plan_search(ix, nq, p, &pl);
+    crisp_status s = plan_search(ix, nq, p, p_count, kmax, &pl);
     if (s) return s;
     if (nq == 0) return CRISP_OK;
     CRISP_REQUIRE(Q && ids && d2, "crisp_search: null pointer");
     const int64_t K2 = (int64_t)ix->K * ix->K;
-    const int32_t C = pl.chunk, M = ix->M;
-    size_t total = 0;
-    {
-        size_t parts[] = {sizeof(float) * (size_t)C * ix->Dp, sizeof(int32_t) * (size_t)C * M * K2,
-                          sizeof(int32_t) * (size_t)C * M, sizeof(int64_t) * (size_t)C * M,
-                          sizeof(int32_t) * (size_t)C * pl.stride, sizeof(float) * (size_t)C * pl.stride,
-                          sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C, sizeof(int64_t) * (size_t)C,
-                          sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C * pl.S,
-                          sizeof(int64_t) * (size_t)C,
-                          pl.learned ? (size_t)C * pl.stride : 0, pl.learned ? sizeof(float) * (size_t)C * M : 0,
-                          pl.learned ? sizeof(float) * (size_t)C * M : 0,
-                          pl.learned ? sizeof(float) * (size_t)C * (2 * M + 68) : 0, sizeof(int64_t) * (size_t)C,
-                          sizeof(int64_t) * (size_t)C, pl.learned ? sizeof(int32_t) * (size_t)C * pl.stride : 0,
-                          sizeof(int64_t) * (size_t)C};
-        for (size_t x : parts) total += (x + 255) / 256 * 256;
+    const int32_t C = pl.chunk, M = ix->M, KO = pl.kmax, F = 2 * M + 68;
+    const int64_t ST = pl.stride;
+    // per-query batches run class by class: the queries are ordered by class
+    // (stably), searched in that order, and their results put back in place
+    std::vector<int32_t> perm;
+    std::vector<int> pcls;            // class of each position of the ordered batch
+    bool mixed = false;
+    if (!pl.shared) {
+        perm.resize((size_t)nq);
+        for (int32_t i = 0; i < nq; ++i) perm[i] = i;
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return pl.cls[x] < pl.cls[y]; });
+        pcls.resize((size_t)nq);
+        for (int32_t i = 0; i < nq; ++i) {
+            pcls[i] = pl.cls[perm[i]];
+            mixed = mixed || perm[i] != i;
+        }
     }
+    const bool learned = pl.any_learned;
+    std::vector<size_t> parts = {
+        sizeof(float) * (size_t)C * ix->Dp, sizeof(int32_t) * (size_t)C * M * K2, sizeof(int32_t) * (size_t)C * M,
+        sizeof(int64_t) * (size_t)C * M, sizeof(int32_t) * (size_t)C * ST, sizeof(float) * (size_t)C * ST,
+        sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C, sizeof(int64_t) * (size_t)C,
+        sizeof(int64_t) * (size_t)C, sizeof(int32_t) * (size_t)C * std::max(pl.Smax, 1), sizeof(int64_t) * (size_t)C,
+        learned ? (size_t)C * ST : 0, learned ? sizeof(float) * (size_t)C * M : 0,
+        learned ? sizeof(float) * (size_t)C * M : 0, learned ? sizeof(float) * (size_t)C * F : 0,
+        sizeof(int64_t) * (size_t)C, sizeof(int64_t) * (size_t)C, learned ? sizeof(int32_t) * (size_t)C * ST : 0,
+        sizeof(int64_t) * (size_t)C,
+        pl.shared ? 0 : sizeof(QParam) * (size_t)nq, pl.shared ? 0 : sizeof(int32_t) * (size_t)nq,
+        mixed ? sizeof(float) * (size_t)C * ix->D : 0, mixed ? sizeof(int64_t) * (size_t)C * KO : 0,
+        mixed ? sizeof(float) * (size_t)C * KO : 0, mixed && stats ? sizeof(crisp_query_stats) * (size_t)C : 0};
+    size_t total = 0;
+    for (size_t x : parts) total += (x + 255) / 256 * 256;
     uint8_t *base = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&base, total, st));
     uint8_t *cur = base;
@@ -401,93 +479,146 @@ static crisp_status search_device(const crisp_index *ix, const float *Q, int32_t
     int32_t *act = carve<int32_t>(cur, (size_t)C * M * K2);
     int32_t *nact = carve<int32_t>(cur, (size_t)C * M);
     int64_t *retr = carve<int64_t>(cur, (size_t)C * M);
-    int32_t *cand = carve<int32_t>(cur, (size_t)C * pl.stride);
-    float *dist = carve<float>(cur, (size_t)C * pl.stride);
+    int32_t *cand = carve<int32_t>(cur, (size_t)C * ST);
+    float *dist = carve<float>(cur, (size_t)C * ST);
     int64_t *ncand = carve<int64_t>(cur, C);
     int32_t *how = carve<int32_t>(cur, C);
     int64_t *nver = carve<int64_t>(cur, C);
     int64_t *nfull = carve<int64_t>(cur, C);
-    int32_t *shortl = carve<int32_t>(cur, (size_t)C * pl.S);
+    const int32_t SM = std::max(pl.Smax, 1);
+    int32_t *shortl = carve<int32_t>(cur, (size_t)C * SM);
     int64_t *nshort = carve<int64_t>(cur, C);
-    uint8_t *score = pl.learned ? carve<uint8_t>(cur, (size_t)C * pl.stride) : nullptr;
-    float *cfirst = pl.learned ? carve<float>(cur, (size_t)C * M) : nullptr;
-    float *clast = pl.learned ? carve<float>(cur, (size_t)C * M) : nullptr;
-    float *feats = pl.learned ? carve<float>(cur, (size_t)C * (2 * M + 68)) : nullptr;
-    int64_t *dV = pl.learned ? carve<int64_t>(cur, C) : nullptr;
-    int64_t *dS = pl.learned ? carve<int64_t>(cur, C) : nullptr;
-    int32_t *selV = pl.learned ? carve<int32_t>(cur, (size_t)C * pl.stride) : nullptr;
-    int64_t *nsel = pl.learned ? carve<int64_t>(cur, C) : nullptr;
+    uint8_t *score = learned ? carve<uint8_t>(cur, (size_t)C * ST) : nullptr;
+    float *cfirst = learned ? carve<float>(cur, (size_t)C * M) : nullptr;
+    float *clast = learned ? carve<float>(cur, (size_t)C * M) : nullptr;
+    float *feats = learned ? carve<float>(cur, (size_t)C * F) : nullptr;
+    int64_t *dV = carve<int64_t>(cur, C);
+    int64_t *dS = carve<int64_t>(cur, C);
+    int32_t *selV = learned ? carve<int32_t>(cur, (size_t)C * ST) : nullptr;
+    int64_t *nsel = carve<int64_t>(cur, C);
+    QParam *qp_d = pl.shared ? nullptr : carve<QParam>(cur, (size_t)nq);
+    int32_t *perm_d = pl.shared ? nullptr : carve<int32_t>(cur, (size_t)nq);
+    float *Qg = mixed ? carve<float>(cur, (size_t)C * ix->D) : nullptr;
+    int64_t *ids_t = mixed ? carve<int64_t>(cur, (size_t)C * KO) : nullptr;
+    float *d2_t = mixed ? carve<float>(cur, (size_t)C * KO) : nullptr;
+    crisp_query_stats *st_t = mixed && stats ? carve<crisp_query_stats>(cur, C) : nullptr;
+    std::vector<QParam> qp_perm;
+    if (!pl.shared) {
+        qp_perm.resize((size_t)nq);
+        for (int32_t i = 0; i < nq; ++i) qp_perm[i] = pl.qp[perm[i]];
+        cudaError_t e = cudaMemcpyAsync(qp_d, qp_perm.data(), sizeof(QParam) * nq, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(perm_d, perm.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st);
+        // the host vectors are read by the copies: wait for them before returning
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = crisp_cuda_fail(e, "per-query parameters", __FILE__, __LINE__);
+    }
+    const QParam &q0 = pl.q0;   // scalars of the shared case (per-query batches read qp instead)
     for (int32_t c0 = 0; c0 < nq && s == CRISP_OK; c0 += C) {
-        int32_t nc = std::min(C, nq - c0);
+        const int32_t nc = std::min(C, nq - c0);
+        const QParam *qpc = pl.shared ? nullptr : qp_d + c0;
         const float *Qc = Q + (int64_t)c0 * ix->D;
-        if (ix->rotated) s = crisp_rotate_rows(Qc, nc, ix->D, ix->D, ix->R32, Qr, ix->Dp, st);
-        else s = launch_pad_rows(Qc, nc, ix->D, ix->D, Qr, ix->Dp, st);
-        if (!s) s = crisp_run_activate(ix, Qr, nc, pl.phi, pl.k, pl.budget, act, nact, retr, st, cfirst, clast);
-        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, pl.k, pl.cap, cand, pl.stride, ncand, score, how, st);
-        int64_t *ids_c = ids + (int64_t)c0 * pl.k;
-        float *d2_c = d2 + (int64_t)c0 * pl.k;
-        if (!s && pl.learned) {
-            // F1: features -> MLP depths -> score prefix -> BF16 shortlist -> FP32 re-rank
-            s = crisp_run_features(ix, cand, pl.stride, ncand, score, cfirst, clast, nc, pl.k, pl.tau, feats, st);
-            if (!s) s = crisp_run_mlp_depth(ix, feats, nc, ncand, pl.stride, pl.k, p->depth_margin, p->short_margin, dV,
-                                            dS, st);
-            if (!s) s = crisp_run_select_score(cand, pl.stride, ncand, score, dV, nc, selV, nsel, st);
-            if (!s) s = crisp_run_shortlist(ix, Qr, nc, selV, pl.stride, nsel, 1, 1, dist, cand, pl.stride, nshort, st,
-                                            dS);
-            // shortlists are short whatever the list stride: stream them per query
-            if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, nshort, pl.k, dist, ids_c, d2_c, st, false, false);
-            if (!s && stats)
-                s = launch_write_stats(nc, ncand, how, retr, M, nsel, nshort, pl.tau, stats + c0, st);
-        } else if (!s && p->mode == 0 && pl.prec > 0) {
-            // F2: coarse-score every candidate on the low-precision rows, then the
-            // FP32 re-rank of the shortlist
-            s = crisp_run_shortlist(ix, Qr, nc, cand, pl.stride, ncand, pl.prec, pl.S, dist, shortl, pl.S, nshort, st,
-                                    nullptr);
-            if (!s) s = crisp_run_rerank(ix, Qr, nc, shortl, pl.S, nshort, pl.k, dist, ids_c, d2_c, st);
-            if (!s && stats)
-                s = launch_write_stats(nc, ncand, how, retr, M, ncand, nshort, pl.tau, stats + c0, st);
-        } else if (!s && p->mode == 0) {
-            s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, ncand, pl.k, dist, ids_c, d2_c, st);
-            if (!s && stats)
-                s = launch_write_stats(nc, ncand, how, retr, M, nullptr, nullptr, pl.tau, stats + c0, st);
-        } else if (!s) {
-            int64_t P = p->patience_factor > 0 ? (int64_t)p->patience_factor * pl.k : 0;
-            s = crisp_run_verify_opt(ix, Qr, nc, cand, pl.stride, ncand, pl.k, p->eps0, P, p->verify_order, ids_c,
-                                     d2_c, nver, nfull, nullptr, st);
-            if (!s && stats) s = launch_write_stats(nc, ncand, how, retr, M, nver, nfull, pl.tau, stats + c0, st);
+        if (mixed) {
+            s = launch_gather_rows(Q, ix->D, perm_d + c0, nc, Qg, st);
+            Qc = Qg;
         }
+        if (!s) {
+            if (ix->rotated) s = crisp_rotate_rows(Qc, nc, ix->D, ix->D, ix->R32, Qr, ix->Dp, st);
+            else s = launch_pad_rows(Qc, nc, ix->D, ix->D, Qr, ix->Dp, st);
+        }
+        if (!s) s = crisp_run_activate(ix, Qr, nc, q0.phi, q0.k, q0.budget, act, nact, retr, st, cfirst, clast, qpc);
+        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, q0.tau, q0.k, q0.cap, cand, ST, ncand, score, how, st, qpc);
+        int64_t *ids_o = mixed ? ids_t : ids + (int64_t)c0 * KO;
+        float *d2_o = mixed ? d2_t : d2 + (int64_t)c0 * KO;
+        crisp_query_stats *st_o = stats ? (mixed ? st_t : stats + c0) : nullptr;
+        // stage 3, one run per class segment of the chunk
+        for (int32_t a = 0; a < nc && s == CRISP_OK;) {
+            const int cls = pl.shared ? pl.cls0 : pcls[c0 + a];
+            int32_t b = a + 1;
+            if (pl.shared) b = nc;
+            else while (b < nc && pcls[c0 + b] == cls) ++b;
+            const int32_t n = b - a;
+            const QParam *qa = qpc ? qpc + a : nullptr;
+            const float *Qra = Qr + (int64_t)a * ix->Dp;
+            const int32_t *ca = cand + (int64_t)a * ST;
+            const int64_t *na = ncand + a;
+            float *da = dist + (int64_t)a * ST;
+            int64_t *io = ids_o + (int64_t)a * KO;
+            float *dout = d2_o + (int64_t)a * KO;
+            crisp_query_stats *so = st_o ? st_o + a : nullptr;
+            if (cls == 4) {
+                // F1: features -> MLP depths -> score prefix -> BF16 shortlist -> FP32 re-rank
+                const uint8_t *sa = score + (int64_t)a * ST;
+                s = crisp_run_features(ix, ca, ST, na, sa, cfirst + (int64_t)a * M, clast + (int64_t)a * M, n, q0.k,
+                                       q0.tau, feats + (int64_t)a * F, st, qa);
+                if (!s) s = crisp_run_mlp_depth(ix, feats + (int64_t)a * F, n, na, ST, q0.k, q0.mV, q0.mS, dV + a,
+                                                dS + a, st, qa);
+                if (!s) s = crisp_run_select_score(ca, ST, na, sa, dV + a, n, selV + (int64_t)a * ST, nsel + a, st);
+                if (!s) s = crisp_run_shortlist(ix, Qra, n, selV + (int64_t)a * ST, ST, nsel + a, 1, 1, da,
+                                                cand + (int64_t)a * ST, ST, nshort + a, st, dS + a, nullptr);
+                // shortlists are short whatever the list stride: stream them per query
+                if (!s) s = crisp_run_rerank(ix, Qra, n, cand + (int64_t)a * ST, ST, nshort + a, q0.k, da, io, dout,
+                                             st, false, false, qa, KO);
+                if (!s && so)
+                    s = launch_write_stats(n, na, how + a, retr + (int64_t)a * M, M, nsel + a, nshort + a, q0.tau, so,
+                                           st, qa);
+            } else if (cls == 1 || cls == 2) {
+                // F2: coarse-score every candidate on the low-precision rows, then the
+                // FP32 re-rank of the shortlist
+                int32_t *sa = shortl + (int64_t)a * SM;
+                s = crisp_run_shortlist(ix, Qra, n, ca, ST, na, cls, q0.S, da, sa, SM, nshort + a, st, nullptr, qa);
+                if (!s) s = crisp_run_rerank(ix, Qra, n, sa, SM, nshort + a, q0.k, da, io, dout, st, false, true, qa, KO);
+                if (!s && so)
+                    s = launch_write_stats(n, na, how + a, retr + (int64_t)a * M, M, na, nshort + a, q0.tau, so, st, qa);
+            } else if (cls == 0) {
+                s = crisp_run_rerank(ix, Qra, n, ca, ST, na, q0.k, da, io, dout, st, false, true, qa, KO);
+                if (!s && so)
+                    s = launch_write_stats(n, na, how + a, retr + (int64_t)a * M, M, nullptr, nullptr, q0.tau, so, st,
+                                           qa);
+            } else {
+                s = crisp_run_verify_opt(ix, Qra, n, ca, ST, na, q0.k, q0.eps0, q0.patience, q0.order, io, dout,
+                                         nver + a, nfull + a, nullptr, st, qa, KO);
+                if (!s && so)
+                    s = launch_write_stats(n, na, how + a, retr + (int64_t)a * M, M, nver + a, nfull + a, q0.tau, so,
+                                           st, qa);
+            }
+            a = b;
+        }
+        if (!s && mixed)
+            s = launch_scatter_results(ids_t, d2_t, st_t, KO, perm_d + c0, nc, ids, d2, stats, st);
     }
     crisp_scratch_free(base, st);
     return s;
 }
 
 extern "C" crisp_status crisp_search(const crisp_index *ix, const float *Q, int32_t nq, const crisp_search_params *p,
-                                     int64_t *ids, float *sqdist, crisp_query_stats *stats, void *stream) {
-    return search_device(ix, Q, nq, p, ids, sqdist, stats, as_stream(stream));
+                                     int32_t p_count, int64_t *ids, float *sqdist, int32_t kmax,
+                                     crisp_query_stats *stats, void *stream) {
+    return search_device(ix, Q, nq, p, p_count, ids, sqdist, kmax, stats, as_stream(stream));
 }
 
 extern "C" crisp_status crisp_search_host(const crisp_index *ix, const float *Q, int32_t nq,
-                                          const crisp_search_params *p, int64_t *ids, float *sqdist,
-                                          crisp_query_stats *stats, void *stream) {
+                                          const crisp_search_params *p, int32_t p_count, int64_t *ids, float *sqdist,
+                                          int32_t kmax, crisp_query_stats *stats, void *stream) {
     SearchPlan pl;
-    crisp_status s = plan_search(ix, nq, p, &pl);
+    crisp_status s = plan_search(ix, nq, p, p_count, kmax, &pl);
     if (s) return s;
     if (nq == 0) return CRISP_OK;
     CRISP_REQUIRE(Q && ids && sqdist, "crisp_search_host: null pointer");
     cudaStream_t st = as_stream(stream);
-    size_t qb = sizeof(float) * (size_t)nq * ix->D, ib = sizeof(int64_t) * (size_t)nq * p->k,
-           db = sizeof(float) * (size_t)nq * p->k, sb = stats ? sizeof(crisp_query_stats) * (size_t)nq : 0;
+    const int32_t KO = pl.kmax;
+    size_t qb = sizeof(float) * (size_t)nq * ix->D, ib = sizeof(int64_t) * (size_t)nq * KO,
+           db = sizeof(float) * (size_t)nq * KO, sb = stats ? sizeof(crisp_query_stats) * (size_t)nq : 0;
     uint8_t *buf = nullptr;
     size_t tot = (qb + 255) / 256 * 256 + (ib + 255) / 256 * 256 + (db + 255) / 256 * 256 + (sb + 255) / 256 * 256;
     CRISP_CK(crisp_scratch_alloc((void **)&buf, tot, st));
     uint8_t *cur = buf;
     float *dQ = carve<float>(cur, (size_t)nq * ix->D);
-    int64_t *dI = carve<int64_t>(cur, (size_t)nq * p->k);
-    float *dD = carve<float>(cur, (size_t)nq * p->k);
+    int64_t *dI = carve<int64_t>(cur, (size_t)nq * KO);
+    float *dD = carve<float>(cur, (size_t)nq * KO);
     crisp_query_stats *dS = stats ? carve<crisp_query_stats>(cur, nq) : nullptr;
     cudaError_t e = cudaMemcpyAsync(dQ, Q, qb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) s = crisp_cuda_fail(e, "cudaMemcpyAsync(Q)", __FILE__, __LINE__);
-    if (!s) s = search_device(ix, dQ, nq, p, dI, dD, dS, st);
+    if (!s) s = search_device(ix, dQ, nq, p, p_count, dI, dD, KO, dS, st);
     if (!s) {
         e = cudaMemcpyAsync(ids, dI, ib, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sqdist, dD, db, cudaMemcpyDeviceToHost, st);
@@ -510,13 +641,14 @@ extern "C" crisp_status crisp_learned_data(const crisp_index *ix, const float *Q
     g.mode = 0;
     g.precision = 0;
     SearchPlan pl;
-    crisp_status s = plan_search(ix, nq, &g, &pl);
+    crisp_status s = plan_search(ix, nq, &g, 1, 0, &pl);
     if (s) return s;
+    const QParam &q0 = pl.q0;
     if (nq == 0) return CRISP_OK;
     CRISP_REQUIRE(Q && features && labels, "crisp_learned_data: null pointer");
     cudaStream_t st = as_stream(stream);
     const int64_t K2 = (int64_t)ix->K * ix->K;
-    const int32_t M = ix->M, F = 2 * M + 68, k = pl.k;
+    const int32_t M = ix->M, F = 2 * M + 68, k = q0.k;
     int64_t per = pl.per_query + pl.stride * 5 + sizeof(float) * (4 * M + 2 * k) + 256;
     int32_t C = (int32_t)std::max<int64_t>(1, std::min<int64_t>(pl.chunk, ((int64_t)16 << 30) / per));
     C = std::min(C, nq);
@@ -555,16 +687,16 @@ extern "C" crisp_status crisp_learned_data(const crisp_index *ix, const float *Q
         const float *Qc = Q + (int64_t)c0 * ix->D;
         if (ix->rotated) s = crisp_rotate_rows(Qc, nc, ix->D, ix->D, ix->R32, Qr, ix->Dp, st);
         else s = launch_pad_rows(Qc, nc, ix->D, ix->D, Qr, ix->Dp, st);
-        if (!s) s = crisp_run_activate(ix, Qr, nc, 0, k, pl.budget, act, nact, retr, st, cfirst, clast);
-        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, pl.tau, k, pl.cap, cand, pl.stride, ncand, score, how, st);
-        if (!s) s = crisp_run_features(ix, cand, pl.stride, ncand, score, cfirst, clast, nc, k, pl.tau,
+        if (!s) s = crisp_run_activate(ix, Qr, nc, 0, k, q0.budget, act, nact, retr, st, cfirst, clast);
+        if (!s) s = crisp_run_count_cut(ix, act, nact, nc, q0.tau, k, q0.cap, cand, pl.stride, ncand, score, how, st);
+        if (!s) s = crisp_run_features(ix, cand, pl.stride, ncand, score, cfirst, clast, nc, k, q0.tau,
                                        features + (int64_t)c0 * F, st);
         if (!s) s = crisp_run_rerank(ix, Qr, nc, cand, pl.stride, ncand, k, dist, top, topd, st);
         if (!s) s = crisp_run_labels_v(cand, pl.stride, ncand, score, top, k, nc, dV, st);
         if (!s) s = crisp_run_select_score(cand, pl.stride, ncand, score, dV, nc, selV, nsel, st);
         // coarse distances of the whole prefix (keep all of it), then the coarse label
         if (!s) s = crisp_run_shortlist(ix, Qr, nc, selV, pl.stride, nsel, 1, 1, dist, cand, pl.stride, nshort, st,
-                                        nsel);
+                                        nsel, nullptr);
         if (!s) s = crisp_run_labels_s(selV, pl.stride, nsel, dist, top, k, nc, dS, st);
         if (!s) s = crisp_run_log2_targets(dV, dS, nc, labels + 2 * (int64_t)c0,
                                            targets ? targets + 2 * (int64_t)c0 : nullptr, st);

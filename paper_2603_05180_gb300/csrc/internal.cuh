@@ -67,6 +67,22 @@ static inline IxView ix_view(const crisp_index *ix) {
     return v;
 }
 
+// Search parameters of one query as the kernels read them (per-query batches:
+// crisp_search with p_count = nq).  Kernels given a null QParam array use their
+// scalar arguments for every query.
+struct QParam {
+    int32_t k;          // neighbours (k_size)
+    int32_t phi;        // 1: rank weights of Optimized mode
+    int32_t tau;        // collision threshold
+    int32_t order;      // Optimized verification order (0 Hamming, 1 id)
+    int64_t budget;     // ids retrieved per subspace
+    int64_t cap;        // candidate cap (0: none)
+    int64_t patience;   // Optimized: P = patience_factor k (0: never stop)
+    float eps0;         // Optimized: ADSampling margin
+    float mV, mS;       // Learned: depth margins
+    int32_t S;          // coarse scoring: shortlist size
+};
+
 // ------------------------------------------------------- launch accounting
 extern std::atomic<unsigned long long> g_crisp_launches;
 #define CRISP_COUNT_LAUNCH() g_crisp_launches.fetch_add(1, std::memory_order_relaxed)
@@ -111,4 +127,4 @@ crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);
 crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st);
 crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
                                 int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
-                                crisp_query_stats *stats, cudaStream_t st);
+                                crisp_query_stats *stats, cudaStream_t st, const QParam *qp = nullptr);

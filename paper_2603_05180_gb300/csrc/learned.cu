@@ -125,9 +125,13 @@ __global__ void __launch_bounds__(LF_NT) k_features(const int *__restrict__ cand
                                                     const long long *__restrict__ ncand,
                                                     const uint8_t *__restrict__ score, const float *__restrict__ cfirst,
                                                     const float *__restrict__ clast, int M, long long N, int kk, int tau,
-                                                    float *__restrict__ feats) {
+                                                    const QParam *__restrict__ qp, float *__restrict__ feats) {
     __shared__ unsigned hist[64];
     const int q = blockIdx.x, F = 2 * M + 68;
+    if (qp) {                           // per-query parameters
+        kk = qp[q].k;
+        tau = qp[q].tau;
+    }
     long long n = ncand[q];
     if (n > stride) n = stride;
     for (int i = threadIdx.x; i < 64; i += LF_NT) hist[i] = 0;
@@ -166,8 +170,8 @@ template <bool DEPTH>
 __global__ void __launch_bounds__(MI_NT) k_mlp_infer(const float *__restrict__ P, int F, int H, int O,
                                                      const float *__restrict__ X, long long B, float *__restrict__ Y,
                                                      const long long *__restrict__ ncand, long long stride, int kk,
-                                                     float mV, float mS, long long *__restrict__ dV,
-                                                     long long *__restrict__ dS) {
+                                                     float mV, float mS, const QParam *__restrict__ qp,
+                                                     long long *__restrict__ dV, long long *__restrict__ dS) {
     extern __shared__ float sm[];
     float *x = sm;                      // [QPB][F]
     float *h1 = x + MI_QPB * F;         // [QPB][H]
@@ -219,6 +223,11 @@ __global__ void __launch_bounds__(MI_NT) k_mlp_infer(const float *__restrict__ P
     __syncthreads();
     if (DEPTH && threadIdx.x < nb) {
         long long q = q0 + threadIdx.x;
+        if (qp) {                       // per-query parameters
+            kk = qp[q].k;
+            mV = qp[q].mV;
+            mS = qp[q].mS;
+        }
         long long n = ncand[q] < stride ? ncand[q] : stride;
         long long v = depth_q(y[threadIdx.x][0], mV, kk, n > kk ? n : kk);
         if (v > n) v = n;
@@ -560,10 +569,10 @@ MlpWork carve_work(float *base, int H, int O, long long B) {
 // ================================================================== launchers
 crisp_status crisp_run_features(const crisp_index *ix, const int32_t *cand, int64_t stride, const int64_t *ncand,
                                 const uint8_t *score, const float *cfirst, const float *clast, int32_t nq, int32_t k,
-                                int32_t tau, float *feats, cudaStream_t st) {
+                                int32_t tau, float *feats, cudaStream_t st, const QParam *qp) {
     if (nq <= 0) return CRISP_OK;
     k_features<<<nq, LF_NT, 0, st>>>(cand, (long long)stride, (const long long *)ncand, score, cfirst, clast, ix->M,
-                                     (long long)ix->N, k, tau, feats);
+                                     (long long)ix->N, k, tau, qp, feats);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -573,14 +582,14 @@ static size_t infer_smem(int F, int H) { return sizeof(float) * (size_t)MI_QPB *
 
 crisp_status crisp_run_mlp_depth(const crisp_index *ix, const float *feats, int32_t nq, const int64_t *ncand,
                                  int64_t stride, int32_t k, float mV, float mS, int64_t *dV, int64_t *dS,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const QParam *qp) {
     if (nq <= 0) return CRISP_OK;
     int F = 2 * ix->M + 68, H = ix->mlp_H;
     size_t smem = infer_smem(F, H);
     CRISP_CK(cudaFuncSetAttribute(k_mlp_infer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_mlp_infer<true><<<(nq + MI_QPB - 1) / MI_QPB, MI_NT, smem, st>>>(
-        ix->mlp, F, H, 2, feats, nq, nullptr, (const long long *)ncand, (long long)stride, k, mV, mS, (long long *)dV,
-        (long long *)dS);
+        ix->mlp, F, H, 2, feats, nq, nullptr, (const long long *)ncand, (long long)stride, k, mV, mS, qp,
+        (long long *)dV, (long long *)dS);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -653,7 +662,7 @@ extern "C" crisp_status crisp_mlp_infer(const float *params, int32_t F, int32_t 
     CRISP_REQUIRE(smem <= 220 * 1024, "crisp_mlp_infer: F + 2H too large for shared memory");
     CRISP_CK(cudaFuncSetAttribute(k_mlp_infer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_mlp_infer<false><<<(unsigned)((B + MI_QPB - 1) / MI_QPB), MI_NT, smem, as_stream(stream)>>>(
-        params, F, H, O, X, (long long)B, Y, nullptr, 0, 0, 0.0f, 0.0f, nullptr, nullptr);
+        params, F, H, O, X, (long long)B, Y, nullptr, 0, 0, 0.0f, 0.0f, nullptr, nullptr, nullptr);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;

@@ -137,7 +137,8 @@ constexpr int ACT_WARPS = 8;
 constexpr int ACT_WARP_WORDS_FIXED = 7 * 64;
 
 __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const float *__restrict__ Qr, int nq, int phi,
-                                                             int kk, long long budget, int *__restrict__ act,
+                                                             int kk, long long budget, const QParam *__restrict__ qp,
+                                                             int *__restrict__ act,
                                                              int *__restrict__ nact, long long *__restrict__ retrieved,
                                                              float *__restrict__ sorted_out, int *__restrict__ perm_out,
                                                              float *__restrict__ cost_first, float *__restrict__ cost_last) {
@@ -162,6 +163,11 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.x * ACT_WARPS + warp;
     if (q >= nq) return;
+    if (qp) {                           // per-query parameters
+        phi = qp[q].phi;
+        kk = qp[q].k;
+        budget = qp[q].budget;
+    }
     float *qs = wbase + warp * (2 * H + ACT_WARP_WORDS_FIXED);
     float *dl = qs + 2 * H, *dr = dl + 64, *s1 = dr + 64, *s2 = s1 + 64;
     int *p1 = reinterpret_cast<int *>(s2 + 64), *p2 = p1 + 64, *rowlen = p2 + 64;
@@ -662,12 +668,18 @@ __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t 
 
 __global__ void __launch_bounds__(CNT_NT, 3) k_count_cut(IxView ix, const int *__restrict__ act,
                                                       const int *__restrict__ nact, int nq, int tau, int kk,
-                                                      long long cap, int *__restrict__ cand, long long stride,
+                                                      long long cap, const QParam *__restrict__ qp,
+                                                      int *__restrict__ cand, long long stride,
                                                       long long *__restrict__ ncand, uint8_t *__restrict__ score,
                                                       int *__restrict__ how) {
     extern __shared__ __align__(16) uint32_t cnt[];
     __shared__ CountShared S;
     const int q = blockIdx.x, M = ix.M, K2 = ix.K * ix.K;
+    if (qp) {                           // per-query parameters
+        tau = qp[q].tau;
+        kk = qp[q].k;
+        cap = qp[q].cap;
+    }
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int m = 0; m < M; ++m) {
@@ -1794,9 +1806,11 @@ __global__ void __launch_bounds__(RR_NT) k_short_select(int nq, const int *__res
                                                         const long long *__restrict__ ncand, int S_keep,
                                                         const float *__restrict__ dbuf, int *__restrict__ out,
                                                         long long out_stride, long long *__restrict__ nout,
-                                                        const long long *__restrict__ S_per_query) {
+                                                        const long long *__restrict__ S_per_query,
+                                                        const QParam *__restrict__ qp) {
     __shared__ TopkShared S;
     const int q = blockIdx.x;
+    if (qp) S_keep = qp[q].S;
     const long long n = ncand[q] < stride ? ncand[q] : stride;
     const int *candq = cand + (long long)q * stride;
     const float *distq = dbuf + (long long)q * stride;
@@ -1815,18 +1829,22 @@ __global__ void __launch_bounds__(RR_NT) k_short_select(int nq, const int *__res
     if (threadIdx.x == 0) nout[q] = kept;
 }
 
+// Top-kk of each query's list into rows of ko >= kk entries (the rest padded
+// -1 / +inf); with per-query parameters kk is the query's own k.
 __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__restrict__ cand, long long stride,
                                                        const long long *__restrict__ ncand, int kk,
+                                                       const QParam *__restrict__ qp, int ko,
                                                        const float *__restrict__ dbuf, long long *__restrict__ out_ids,
                                                        float *__restrict__ out_d) {
     __shared__ TopkShared S;
     const int q = blockIdx.x;
+    if (qp) kk = qp[q].k;
     long long n = ncand[q] < stride ? ncand[q] : stride;
     int nsel = select_topk(dbuf + (long long)q * stride, cand + (long long)q * stride, n, kk, S);
-    for (int r = threadIdx.x; r < kk; r += RR_NT) {
-        bool ok = r < nsel;
-        out_ids[(long long)q * kk + r] = ok ? (long long)S.sid[r] : -1LL;
-        out_d[(long long)q * kk + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
+    for (int r = threadIdx.x; r < ko; r += RR_NT) {
+        bool ok = r < nsel && r < kk;
+        out_ids[(long long)q * ko + r] = ok ? (long long)S.sid[r] : -1LL;
+        out_d[(long long)q * ko + r] = ok ? __uint_as_float(S.skey[r]) : INFINITY;
     }
 }
 
@@ -1841,11 +1859,12 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
 // and every candidate is kept, so the result is still exact.
 __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__restrict__ cand, long long stride,
                                                         const long long *__restrict__ ncand, int kk,
-                                                        const float2 *__restrict__ ulb,
+                                                        const QParam *__restrict__ qp, const float2 *__restrict__ ulb,
                                                         const unsigned *__restrict__ err, int *__restrict__ rc,
                                                         long long *__restrict__ nr) {
     __shared__ TopkShared S;
     const int q = blockIdx.x, tid = threadIdx.x;
+    if (qp) kk = qp[q].k;
     const long long n = ncand[q] < stride ? ncand[q] : stride;
     const int *candq = cand + (long long)q * stride;
     int *rcq = rc + (long long)q * stride;
@@ -1886,9 +1905,11 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
 }
 
 __global__ void k_stats(int nq, const long long *ncand, const int *how, const long long *retrieved, int M,
-                        const long long *nver, const long long *nfull, int tau, crisp_query_stats *st) {
+                        const long long *nver, const long long *nfull, int tau, const QParam *qp,
+                        crisp_query_stats *st) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
+    if (qp) tau = qp[q].tau;
     crisp_query_stats s;
     s.n_candidates = ncand[q];
     long long r = 0;
@@ -1905,9 +1926,55 @@ __global__ void k_stats(int nq, const long long *ncand, const int *how, const lo
     st[q] = s;
 }
 
+// Row i of Q[perm[i]] into Y (per-query batches ordered by parameter class).
+__global__ void k_gather_rows(const float *__restrict__ Q, int D, const int *__restrict__ perm, int n,
+                              float *__restrict__ Y) {
+    const long long tot = (long long)n * D;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / D;
+        Y[e] = Q[(long long)perm[i] * D + (e - i * D)];
+    }
+}
+
+// Result row i (and its stats) to row perm[i] of the caller's arrays.
+__global__ void k_scatter_results(const long long *__restrict__ ids_t, const float *__restrict__ d2_t,
+                                  const crisp_query_stats *__restrict__ st_t, int ko, const int *__restrict__ perm,
+                                  int n, long long *__restrict__ ids, float *__restrict__ d2,
+                                  crisp_query_stats *__restrict__ stats) {
+    const long long tot = (long long)n * ko;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / ko, c = e - i * ko, o = (long long)perm[i] * ko + c;
+        ids[o] = ids_t[e];
+        d2[o] = d2_t[e];
+        if (stats && c == 0) stats[perm[i]] = st_t[i];
+    }
+}
+
 }  // namespace
 
 // ============================================================ launchers
+crisp_status launch_gather_rows(const float *Q, int32_t D, const int32_t *perm, int32_t n, float *Y, cudaStream_t st) {
+    if (n <= 0) return CRISP_OK;
+    const long long tot = (long long)n * D;
+    const int blocks = (int)((tot + 255) / 256 < 152 * 32 ? (tot + 255) / 256 : 152 * 32);
+    k_gather_rows<<<blocks, 256, 0, st>>>(Q, D, perm, n, Y);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
+crisp_status launch_scatter_results(const int64_t *ids_t, const float *d2_t, const crisp_query_stats *st_t, int32_t ko,
+                                    const int32_t *perm, int32_t n, int64_t *ids, float *d2, crisp_query_stats *stats,
+                                    cudaStream_t st) {
+    if (n <= 0) return CRISP_OK;
+    const long long tot = (long long)n * ko;
+    const int blocks = (int)((tot + 255) / 256 < 152 * 32 ? (tot + 255) / 256 : 152 * 32);
+    k_scatter_results<<<blocks, 256, 0, st>>>((const long long *)ids_t, d2_t, st_t, ko, perm, n, (long long *)ids, d2,
+                                              stats);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
 crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
                              cudaStream_t st) {
     if (N <= 0) return CRISP_OK;
@@ -1937,10 +2004,10 @@ crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st) {
 
 crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
                                 int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
-                                crisp_query_stats *stats, cudaStream_t st) {
+                                crisp_query_stats *stats, cudaStream_t st, const QParam *qp) {
     if (nq <= 0 || !stats) return CRISP_OK;
     k_stats<<<(nq + 255) / 256, 256, 0, st>>>(nq, (const long long *)ncand, how, (const long long *)retrieved, M,
-                                              (const long long *)nver, (const long long *)nfull, tau, stats);
+                                              (const long long *)nver, (const long long *)nfull, tau, qp, stats);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -1954,12 +2021,12 @@ static size_t activate_smem(const crisp_index *ix) {
 static crisp_status run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
                                  int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, float *sorted,
                                  int32_t *perm, cudaStream_t st, float *cost_first = nullptr,
-                                 float *cost_last = nullptr) {
+                                 float *cost_last = nullptr, const QParam *qp = nullptr) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = activate_smem(ix);
     CRISP_CK(cudaFuncSetAttribute(k_activate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((nq + ACT_WARPS - 1) / ACT_WARPS, ix->M);
-    k_activate<<<grid, ACT_WARPS * 32, smem, st>>>(ix_view(ix), Qr, nq, phi, k, (long long)budget, act, nact,
+    k_activate<<<grid, ACT_WARPS * 32, smem, st>>>(ix_view(ix), Qr, nq, phi, k, (long long)budget, qp, act, nact,
                                                    (long long *)retrieved, sorted, perm, cost_first, cost_last);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
@@ -1968,18 +2035,19 @@ static crisp_status run_activate(const crisp_index *ix, const float *Qr, int32_t
 
 crisp_status crisp_run_activate(const crisp_index *ix, const float *Qr, int32_t nq, int32_t phi, int32_t k,
                                 int64_t budget, int32_t *act, int32_t *nact, int64_t *retrieved, cudaStream_t st,
-                                float *cost_first, float *cost_last) {
-    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, st, cost_first, cost_last);
+                                float *cost_first, float *cost_last, const QParam *qp) {
+    return run_activate(ix, Qr, nq, phi, k, budget, act, nact, retrieved, nullptr, nullptr, st, cost_first, cost_last,
+                        qp);
 }
 
 crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, const int32_t *nact, int32_t nq,
                                  int32_t tau, int32_t k, int64_t cap, int32_t *cand, int64_t stride, int64_t *ncand,
-                                 uint8_t *score, int32_t *how, cudaStream_t st) {
+                                 uint8_t *score, int32_t *how, cudaStream_t st, const QParam *qp) {
     if (nq <= 0) return CRISP_OK;
     CRISP_REQUIRE((int64_t)ix->M * ix->N < ((int64_t)1 << 31), "count: M * N must stay below 2^31");
     size_t smem = CRISP_TILE;
     CRISP_CK(cudaFuncSetAttribute(k_count_cut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_count_cut<<<nq, CNT_NT, smem, st>>>(ix_view(ix), act, nact, nq, tau, k, (long long)cap, cand,
+    k_count_cut<<<nq, CNT_NT, smem, st>>>(ix_view(ix), act, nact, nq, tau, k, (long long)cap, qp, cand,
                                          (long long)stride, (long long *)ncand, score, how);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
@@ -1987,8 +2055,8 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
 }
 
 crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
-                                 int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids,
-                                 float *d2, cudaStream_t st, bool *done);
+                                 int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
+                                 float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done);
 
 // Large batches (1,024 queries or more with long lists) take the tensor-core
 // path of rerank_tc.cu (bounded TF32 scores, exact CR32 re-measure of the
@@ -1996,12 +2064,14 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
 // candidate) pair.  Both give the top-k of the exact CR32 distances.
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st, bool no_alloc = false, bool may_group = true) {
+                              cudaStream_t st, bool no_alloc = false, bool may_group = true,
+                              const QParam *qp = nullptr, int32_t ko = 0) {
     if (nq <= 0) return CRISP_OK;
+    if (ko <= 0) ko = k;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
     if (!no_alloc && may_group) {
         bool done = false;
-        crisp_status ts = crisp_run_rerank_tc(ix, Qr, nq, cand, stride, ncand, k, dbuf, ids, d2, st, &done);
+        crisp_status ts = crisp_run_rerank_tc(ix, Qr, nq, cand, stride, ncand, k, qp, ko, dbuf, ids, d2, st, &done);
         if (ts || done) return ts;
     }
     long long *off = nullptr;           // no_alloc: a fixed number of items per query, no offsets
@@ -2023,7 +2093,7 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
                                                (const long long *)ncand, off, dbuf);
         CRISP_COUNT_LAUNCH();
     }
-    k_select_rows<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, dbuf,
+    k_select_rows<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, qp, ko, dbuf,
                                         (long long *)ids, d2);
     CRISP_COUNT_LAUNCH();
     if (off) crisp_scratch_free(off, st);
@@ -2032,9 +2102,10 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 }
 
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const float2 *ulb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st) {
+                                    const QParam *qp, const float2 *ulb, const unsigned *err, int32_t *rc,
+                                    int64_t *nr, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
-    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, ulb, err, rc,
+    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, qp, ulb, err, rc,
                                          (long long *)nr);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
@@ -2044,7 +2115,7 @@ crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t str
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
-                                 const int64_t *S_per_query) {
+                                 const int64_t *S_per_query, const QParam *qp) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
     bool grouped = false;
@@ -2056,7 +2127,7 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
     if (grouped) {
         k_short_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, S, dbuf, out,
                                              (long long)out_stride, (long long *)nout,
-                                             (const long long *)S_per_query);
+                                             (const long long *)S_per_query, qp);
         CRISP_COUNT_LAUNCH();
         CRISP_CK_LAUNCH();
         return CRISP_OK;
@@ -2083,7 +2154,7 @@ crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t
     }
     CRISP_COUNT_LAUNCH();
     k_short_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, S, dbuf, out,
-                                         (long long)out_stride, (long long *)nout, (const long long *)S_per_query);
+                                         (long long)out_stride, (long long *)nout, (const long long *)S_per_query, qp);
     CRISP_COUNT_LAUNCH();
     crisp_scratch_free(off, st);
     CRISP_CK_LAUNCH();
@@ -2157,7 +2228,7 @@ extern "C" crisp_status crisp_count_cut(const crisp_index *ix, const int32_t *ac
     CRISP_REQUIRE(cand_stride >= 1, "crisp_count_cut: cand_stride < 1");
     CRISP_REQUIRE(nq == 0 || (nact && cand && ncand), "crisp_count_cut: null pointer");
     return crisp_run_count_cut(ix, act, nact, nq, tau, k, cap, cand, cand_stride, ncand, score, how,
-                               as_stream(stream));
+                               as_stream(stream), nullptr);
 }
 
 extern "C" crisp_status crisp_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
@@ -2236,7 +2307,7 @@ extern "C" crisp_status crisp_shortlist(const crisp_index *ix, const float *Qr, 
     float *dbuf = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
     s = crisp_run_shortlist(ix, Qr, nq, cand, cand_stride, ncand, precision, S, dbuf, out, out_stride, nout, st,
-                            nullptr);
+                            nullptr, nullptr);
     crisp_scratch_free(dbuf, st);
     return s;
 }

@@ -57,10 +57,11 @@ bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int c
 crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                    unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const float2 *ulb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
+                                    const QParam *qp, const float2 *ulb, const unsigned *err, int32_t *rc,
+                                    int64_t *nr, cudaStream_t st);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
-                              cudaStream_t st, bool no_alloc, bool may_group);
+                              cudaStream_t st, bool no_alloc, bool may_group, const QParam *qp, int32_t ko);
 
 namespace {
 
@@ -665,8 +666,8 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
 // candidate lists may hold 2,048 or more ids; *done = false (nothing run) for
 // other batches, which the caller streams.  dbuf: [nq][stride] floats of scratch.
 crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
-                                 int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids,
-                                 float *d2, cudaStream_t st, bool *done) {
+                                 int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
+                                 float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done) {
     *done = false;
     if (nq < 1024 || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
     const int Dp = ix->Dp;
@@ -768,10 +769,10 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rerank_tc", __FILE__, __LINE__); break; }
-        s = crisp_run_bound_select(nq, cand, stride, ncand, k, ulb, err_word, rc, nr, st);
+        s = crisp_run_bound_select(nq, cand, stride, ncand, k, qp, ulb, err_word, rc, nr, st);
         if (s) break;
         // the kept candidates, measured exactly (streaming CR32) -> top-k
-        s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false);
+        s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false, qp, ko);
         if (s) break;
         *done = true;
     } while (0);

@@ -1,9 +1,10 @@
 // Continuous-batching query server over one index (the engine's serving
 // extension; the paper has no serving loop).  Host runtime in C++: requests arrive one at a
-// time from any thread; a dispatcher thread groups waiting requests with equal
-// search parameters into batches, admits a batch when a stream slot is free and
-// the search's scratch fits the memory budget, and runs copy-in, crisp_search and
-// copy-out on that slot's stream.  Batches on different slots overlap on the
+// time from any thread; a dispatcher thread takes the oldest waiting requests as
+// one batch whatever their parameters (one crisp_search with per-query
+// parameters), admits it when a stream slot is free and the search's scratch
+// fits the memory budget, and runs copy-in, crisp_search and copy-out on that
+// slot's stream.  Batches on different slots overlap on the
 // GPU; completions are found by polling each slot's event.  Every request keeps
 // its arrival and completion time, from which p50 / p99 latency follow.
 #include <math.h>
@@ -41,7 +42,7 @@ struct Slot {
     cudaEvent_t event = nullptr;
     bool busy = false;
     std::vector<uint64_t> tickets;
-    int32_t k = 0;
+    int32_t ko = 0;                 // result row length of the batch (its largest k)
     size_t scratch = 0;
     float *hQ = nullptr, *hD = nullptr, *dQ = nullptr, *dD = nullptr;
     int64_t *hI = nullptr, *dI = nullptr;
@@ -50,19 +51,12 @@ struct Slot {
 
 }  // namespace
 
-// Waiting requests of one parameter set, oldest first (tickets increase with
-// arrival, so the oldest waiting request overall heads one of these queues).
-struct ParamClass {
-    crisp_search_params p;
-    std::deque<uint64_t> q;
-};
-
 struct crisp_server {
     const crisp_index *ix = nullptr;
     crisp_server_params prm{};
     int device = 0;
     std::vector<Slot> slots;
-    std::vector<ParamClass> classes;
+    std::deque<uint64_t> waiting;   // waiting requests, oldest first
     size_t n_waiting = 0;
     std::unordered_map<uint64_t, Req> reqs;
     std::mutex mu;
@@ -107,8 +101,8 @@ static bool reap(crisp_server *sv) {
                 sv->failed++;
                 continue;
             }
-            r.ids.assign(s.hI + i * s.k, s.hI + (i + 1) * s.k);
-            r.d2.assign(s.hD + i * s.k, s.hD + (i + 1) * s.k);
+            r.ids.assign(s.hI + i * s.ko, s.hI + i * s.ko + r.p.k);
+            r.d2.assign(s.hD + i * s.ko, s.hD + i * s.ko + r.p.k);
             r.st = s.hS[i];
             r.state = 2;
             r.t_done = now;
@@ -124,8 +118,8 @@ static bool reap(crisp_server *sv) {
     return any;
 }
 
-// Admit the oldest waiting request and the next waiting requests with the same
-// parameters (arrival order, up to max_batch) onto a free slot.
+// Admit the oldest waiting requests (arrival order, up to max_batch, any mix of
+// parameters) onto a free slot.
 static bool admit(crisp_server *sv) {
     if (sv->n_waiting == 0) return false;
     Slot *free_slot = nullptr;
@@ -135,16 +129,18 @@ static bool admit(crisp_server *sv) {
         any_busy |= s.busy;
     }
     if (!free_slot) return false;
-    ParamClass *pc = nullptr;
-    for (ParamClass &c : sv->classes)
-        if (!c.q.empty() && (!pc || c.q.front() < pc->q.front())) pc = &c;
-    const crisp_search_params key = pc->p;
-    const int32_t n = (int32_t)std::min<size_t>(pc->q.size(), (size_t)sv->prm.max_batch);
+    const int32_t n = (int32_t)std::min<size_t>(sv->waiting.size(), (size_t)sv->prm.max_batch);
+    std::vector<crisp_search_params> prm((size_t)n);
+    int32_t ko = 1;
+    for (int32_t i = 0; i < n; ++i) {
+        prm[i] = sv->reqs[sv->waiting[i]].p;
+        ko = std::max(ko, prm[i].k);
+    }
     size_t need = 0;
-    crisp_status st = crisp_search_scratch_bytes(sv->ix, n, &key, &need);
+    crisp_status st = crisp_search_scratch_bytes(sv->ix, n, prm.data(), n, &need);
     if (st == CRISP_OK && any_busy && sv->scratch_in_use + need > (size_t)sv->prm.scratch_budget) return false;
-    std::vector<uint64_t> batch(pc->q.begin(), pc->q.begin() + n);
-    pc->q.erase(pc->q.begin(), pc->q.begin() + n);    // the requests leave the waiting queue either way
+    std::vector<uint64_t> batch(sv->waiting.begin(), sv->waiting.begin() + n);
+    sv->waiting.erase(sv->waiting.begin(), sv->waiting.begin() + n);   // the requests leave the queue either way
     sv->n_waiting -= (size_t)n;
     Slot &s = *free_slot;
     const int32_t D = sv->ix->D;
@@ -152,12 +148,12 @@ static bool admit(crisp_server *sv) {
     cudaError_t e = cudaSuccess;
     if (st == CRISP_OK) {
         e = cudaMemcpyAsync(s.dQ, s.hQ, sizeof(float) * (size_t)n * D, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) st = crisp_search(sv->ix, s.dQ, n, &key, s.dI, s.dD, s.dS, s.stream);
+        if (e == cudaSuccess) st = crisp_search(sv->ix, s.dQ, n, prm.data(), n, s.dI, s.dD, ko, s.dS, s.stream);
         else st = CRISP_ECUDA;
     }
     if (st == CRISP_OK) {
-        e = cudaMemcpyAsync(s.hI, s.dI, sizeof(int64_t) * (size_t)n * key.k, cudaMemcpyDeviceToHost, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.hD, s.dD, sizeof(float) * (size_t)n * key.k, cudaMemcpyDeviceToHost, s.stream);
+        e = cudaMemcpyAsync(s.hI, s.dI, sizeof(int64_t) * (size_t)n * ko, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.hD, s.dD, sizeof(float) * (size_t)n * ko, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.hS, s.dS, sizeof(crisp_query_stats) * n, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.event, s.stream);
         if (e != cudaSuccess) st = CRISP_ECUDA;
@@ -177,7 +173,7 @@ static bool admit(crisp_server *sv) {
     for (uint64_t t : batch) sv->reqs[t].state = 1;
     s.busy = true;
     s.tickets = batch;
-    s.k = key.k;
+    s.ko = ko;
     s.scratch = need;
     sv->scratch_in_use += need;
     sv->scratch_peak = std::max(sv->scratch_peak, sv->scratch_in_use);
@@ -240,13 +236,10 @@ extern "C" crisp_status crisp_server_create(const crisp_index *ix, const crisp_s
     return CRISP_OK;
 }
 
-// The parameter struct has no padding, so equal parameters are equal bytes.
-static_assert(sizeof(crisp_search_params) == 64, "crisp_search_params has padding");
-
 static crisp_status submit_at(crisp_server *sv, const float *q, const crisp_search_params *p, Clock::time_point t_arrive,
                               uint64_t *ticket) {
     size_t probe = 0;
-    crisp_status st = crisp_search_scratch_bytes(sv->ix, 1, p, &probe);   // validates the parameters
+    crisp_status st = crisp_search_scratch_bytes(sv->ix, 1, p, 1, &probe);   // validates the parameters
     if (st) return st;
     Req r;
     r.q.assign(q, q + sv->ix->D);
@@ -255,16 +248,9 @@ static crisp_status submit_at(crisp_server *sv, const float *q, const crisp_sear
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         CRISP_REQUIRE(!sv->stop, "crisp_server_submit: server is stopping");
-        ParamClass *pc = nullptr;
-        for (ParamClass &c : sv->classes)
-            if (memcmp(&c.p, p, sizeof *p) == 0) pc = &c;
-        if (!pc) {
-            sv->classes.push_back(ParamClass{*p, {}});
-            pc = &sv->classes.back();
-        }
         *ticket = sv->next_ticket++;
         sv->reqs.emplace(*ticket, std::move(r));
-        pc->q.push_back(*ticket);
+        sv->waiting.push_back(*ticket);
         sv->n_waiting++;
         sv->submitted++;
     }

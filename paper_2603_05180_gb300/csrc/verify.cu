@@ -62,13 +62,20 @@ __device__ __forceinline__ int first_prune(const float *cs, const float *ft, int
 __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__restrict__ Qr, int nq,
                                                       const int *__restrict__ cand, long long stride,
                                                       const long long *__restrict__ ncand, int kk, float eps0,
-                                                      long long patience, int order, int cap_keys,
+                                                      long long patience, int order, const QParam *__restrict__ qp,
+                                                      int ko, int cap_keys,
                                                       long long *__restrict__ out_ids, float *__restrict__ out_d,
                                                       long long *__restrict__ out_nver, long long *__restrict__ out_nfull,
                                                       long long *__restrict__ out_nblk) {
     extern __shared__ __align__(16) float smv[];
     __shared__ VoShared S;
     const int q = blockIdx.x, tid = threadIdx.x;
+    if (qp) {                           // per-query parameters
+        kk = qp[q].k;
+        eps0 = qp[q].eps0;
+        patience = qp[q].patience;
+        order = qp[q].order;
+    }
     const int Dp = ix.Dp, nb = Dp / 32, W = Dp / 32, D = ix.D;
     float *qs = smv;                                        // [Dp]
     float *ft = qs + Dp;                                    // [nb]
@@ -241,10 +248,10 @@ __global__ void __launch_bounds__(VO_NT) k_verify_opt(IxView ix, const float *__
         }
         __syncthreads();
     }
-    for (int r = tid; r < kk; r += VO_NT) {
-        bool ok = r < S.tk_n;
-        out_ids[(long long)q * kk + r] = ok ? (long long)S.tk_id[r] : -1LL;
-        out_d[(long long)q * kk + r] = ok ? S.tk_d[r] : INFINITY;
+    for (int r = tid; r < ko; r += VO_NT) {          // rows of ko >= kk entries, padded -1 / +inf
+        bool ok = r < S.tk_n && r < kk;
+        out_ids[(long long)q * ko + r] = ok ? (long long)S.tk_id[r] : -1LL;
+        out_d[(long long)q * ko + r] = ok ? S.tk_d[r] : INFINITY;
     }
     if (tid == 0) {
         if (out_nver) out_nver[q] = S.processed;
@@ -270,8 +277,9 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
                                   int32_t order,
                                   int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const QParam *qp, int32_t ko) {
     if (nq <= 0) return CRISP_OK;
+    if (ko <= 0) ko = k;
     int64_t cap = stride;
     if (cap > CRISP_OPT_MAX_CAND) {
         // only the real candidate counts matter: read them back (one small copy)
@@ -293,7 +301,7 @@ crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_
     size_t smem = vo_smem(ix, cap_keys);
     CRISP_CK(cudaFuncSetAttribute(k_verify_opt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_verify_opt<<<nq, VO_NT, smem, st>>>(ix_view(ix), Qr, nq, cand, (long long)stride, (const long long *)ncand, k,
-                                          eps0, (long long)patience, order, cap_keys, (long long *)ids, d2,
+                                          eps0, (long long)patience, order, qp, ko, cap_keys, (long long *)ids, d2,
                                           (long long *)nver, (long long *)nfull, (long long *)nblk);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
@@ -310,5 +318,5 @@ extern "C" crisp_status crisp_verify_opt(const crisp_index *ix, const float *Qr,
     CRISP_REQUIRE(cand_stride >= 1, "crisp_verify_opt: cand_stride < 1");
     CRISP_REQUIRE(order == 0 || order == 1, "crisp_verify_opt: order must be 0 (Hamming) or 1 (id)");
     return crisp_run_verify_opt(ix, Qr, nq, cand, cand_stride, ncand, k, eps0, patience, order, ids, sqdist, n_verified,
-                                n_full, n_blocks, as_stream(stream));
+                                n_full, n_blocks, as_stream(stream), nullptr, k);
 }

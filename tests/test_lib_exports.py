@@ -86,3 +86,18 @@ def test_binding_constants_match_the_header():
     m = re.search(r"#define\s+CRISP_RERANK_NOALLOC_MAX\s+\(([^)]*)\)", src)
     assert m, "CRISP_RERANK_NOALLOC_MAX not found in include/crisp.h"
     assert eval(m.group(1), {"__builtins__": {}}) == crisp.CRISP_RERANK_NOALLOC_MAX
+
+
+def test_library_readings_of_tau_and_budget_equal_the_oracle(libc):
+    """The binding takes tau and the budget from the library (no copy of the
+    arithmetic); they must equal the oracle's readings, including the exact
+    products such as 0.3 x 10 = 3 that a plain ceil would round up."""
+    import oracle
+    import paper_2603_05180_gb300 as crisp
+
+    for alpha in (0.0, 0.1, 0.125, 0.2, 0.25, 0.3, 0.5, 0.7, 1.0):
+        for M in (1, 8, 10, 16, 20, 32, 127):
+            assert crisp.tau(alpha, M) == oracle.tau(alpha, M), (alpha, M)
+    for rho in (1e-9, 0.001, 0.002, 0.01, 0.03, 0.06, 0.3, 1.0):
+        for N in (1, 300, 20000, 1_000_000, 5_000_000):
+            assert crisp.budget(rho, N) == oracle.budget(rho, N), (rho, N)
