@@ -77,6 +77,21 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+# nominal dense tensor rates per GPU (PFLOP/s): TF32 is this fraction of BF16
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    """TF32 tensor peak (TFLOP/s) for a kernel timed inside a long step: the
+    measured sustained BF16 GEMM rate times the nominal TF32 / BF16 ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * TF32_PER_BF16, "measured"
+    return 1700.0 * TF32_PER_BF16, "fallback"
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -372,31 +387,9 @@ def run_crisp(args):
     stage = stage_pass(torch, crisp, ix, info, Q, point, k, args.steps, stream, flush)
     sl_stage = stage.pop("shortlist_bf16", None)
     shares = {n: v["ms"] for n, v in stage.items()}
-    dom = max((n for n in stage if stage[n]["bytes"]), key=lambda n: stage[n]["ms"])
     traffic_key = {"N": N, "D": D, "nq": nq, "M": args.M, "rho": point["rho"], "alpha": point["alpha"]}
-    dbytes, dms = stage[dom]["bytes"], stage[dom]["ms"]
-    achieved = dbytes / (dms / 1e3) / 1e9
-    traffic = _ncu_traffic(dom, traffic_key)
-    roofline = {"kernel": stage[dom]["kernel"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "dram_gbs": traffic / (dms / 1e3) / 1e9 if traffic else None,
-                "note": ("algorithmic bytes count every (query, candidate) row read; the grouped kernel reads a row "
-                         "once for all queries of its group that need it, so DRAM traffic (ncu) is below them and "
-                         "frac can exceed 1") if stage[dom]["kernel"].startswith("k_gscore") else None,
-                "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "stage_ms": {n: round(v, 4) for n, v in shares.items()},
-                "algorithmic_bytes_per_launch": dbytes}
-    if stage[dom]["kernel"].startswith("k_gscore"):
-        # the same kernel against the FP32 SIMT arithmetic it runs: per candidate a
-        # subtraction and an FMA per padded dim (3 flops); peak from unit counts and
-        # the maximum SM clock (SMs x 128 FP32 lanes x 2 flops per FMA)
-        n_cand = dbytes / (4 * info.Dp + 4)
-        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        alu_peak = sm_count * 128 * 2 * max_sm_mhz() * 1e6 / 1e12
-        alu_ach = 3 * info.Dp * n_cand / (dms / 1e3) / 1e12
-        roofline["alu"] = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
-                           "frac": alu_ach / alu_peak,
-                           "peak_kind": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x {max_sm_mhz():.0f} MHz"}
+    roofline, rooflines = stage_rooflines(stage, info, peak, peak_kind, traffic_key)
+    roofline["stage_ms"] = {n: round(v, 4) for n, v in shares.items()}
     step_bytes = sum(v["bytes"] for v in stage.values())
     roofline_bf16 = None
     if sl_stage:
@@ -429,6 +422,19 @@ def run_crisp(args):
     learned = None
     if not args.no_learned:
         learned = learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed, qps, world, dev)
+
+    # ---- both modes at k = 10 and k = 100 on the same index
+    modes = None
+    if not args.no_modes:
+        modes = modes_leg(torch, crisp, ix, X, Q, args, dev)
+
+    # ---- the vMF (D = 3072) and low-rank (D = 4096) configurations, each on its own index
+    big = {}
+    if world == 1:
+        if not args.no_vmf:
+            big["vmf_3072"] = vmf_leg(args, torch, crisp, synthetic, dev, flush, stream)
+        if not args.no_lowrank:
+            big["lowrank_4096"] = lowrank_leg(args, torch, crisp, synthetic, dev, flush, stream)
 
     # ---- continuous-batching serving (its own 5M x 1024 index)
     serving = None
@@ -473,13 +479,16 @@ def run_crisp(args):
                            "index_rotated": bool(info.rotated), "cev": info.cev, "build_s": round(build_s, 3)},
                 "recall_at_10": rec, "sqdist_error": d2_err,
                 "step_p50_ms": statistics.median(step_ms), "step_p99_ms": float(np.percentile(step_ms, 99)),
-                "hbm_frac_step": step_bytes / (total_ms / args.steps / 1e3) / 1e9 / peak,
+                "query_bytes_rate_vs_hbm": step_bytes / (total_ms / args.steps / 1e3) / 1e9 / peak,
+                "query_bytes_note": "per-query algorithmic bytes of every stage (each candidate row counted once per "
+                                    "query) over the step time, against the HBM copy peak: a reuse figure, not an "
+                                    "HBM fraction (rows shared by a query group are fetched once)",
                 "candidates_mean": float(stats[:, 0].mean()), "full_distances_mean": float(stats[:, 2].mean()),
-                "roofline": roofline, "roofline_bf16": roofline_bf16, "cpu_baseline": cpu,
+                "roofline": roofline, "rooflines": rooflines, "roofline_bf16": roofline_bf16, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
                         "d2h_bytes_per_step": nq * k * 12},
                 "gpu_launches": launches, "clocks": clk,
-                "coarse_scoring": variants, "learned_bf16": learned}
+                "coarse_scoring": variants, "learned_bf16": learned, "modes": modes, **big}
         if serving:
             ok = [r for r in serving["rates"] if r["achieved_qps"] >= 0.95 * r["offered_qps"]] or serving["rates"][:1]
             top = max(ok, key=lambda r: r["offered_qps"])
@@ -551,6 +560,241 @@ def learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed
             "epochs": args.epochs, "hidden": H, "features": F, "loss_first_epoch": losses[0],
             "loss_last_epoch": losses[-1], "label_seconds": round(t_data, 2), "train_seconds": round(t_train, 2),
             "val_recall_plain": r_plain, "val_recall_learned": best[2]}
+
+
+def _search_fn(torch, crisp, ix, dev):
+    """search(Qx, pt, out) -> None, and a timed(Qx, pt, steps) -> (qps, ms) helper for a leg's own index."""
+    def search(Qx, pt, ids, d2, st=None):
+        sp = crisp.search_params(k=pt["k"], mode=pt["mode"], rho=pt["rho"], alpha=pt["alpha"],
+                                 precision=pt.get("precision", 0), shortlist=pt.get("shortlist", 0),
+                                 depth_margin=pt.get("depth_margin", 0.0), short_margin=pt.get("short_margin", 0.0),
+                                 patience_factor=pt.get("patience_factor", 40),
+                                 max_candidates=pt.get("max_candidates", 0))
+        crisp.crisp_search(ix, Qx, Qx.shape[0], sp, ids, d2, st)
+
+    def timed(Qx, pt, ids, d2, steps, flush):
+        search(Qx, pt, ids, d2)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            search(Qx, pt, ids, d2)
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return Qx.shape[0] * steps / (tot / 1e3), tot / steps
+
+    return search, timed
+
+
+def _ladder(torch, X, Qv, gdv, search, pts, k, dev, target=0.955):
+    """Recall on the validation queries along a ladder of points; the fastest
+    reaching the target, else the one of highest recall."""
+    n = Qv.shape[0]
+    ids = torch.empty((n, k), dtype=torch.int64, device=dev)
+    d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
+    log, best = [], None
+    for pt in pts:
+        search(Qv, pt, ids, d2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        search(Qv, pt, ids, d2)
+        b.record()
+        torch.cuda.synchronize()
+        r = recall_at_k(torch, X, Qv, ids, gdv)
+        q = n / (a.elapsed_time(b) / 1e3)
+        log.append(dict(pt, recall=r, qps=q))
+        ok = r >= target
+        if best is None or (ok and (not best[2] or q > best[1])) or (not ok and not best[2] and r > best[3]):
+            best = (pt, q, ok, r)
+    return best[0], best[2], log
+
+
+def modes_leg(torch, crisp, ix, X, Q, args, dev):
+    """Guaranteed and Optimized modes at k = 10 and k = 100 on the headline
+    index (§4.3.2 Stages 2-3, §6.3): for each, the fastest point of a ladder
+    (coverage, threshold; for Optimized also the patience factor) whose
+    recall@k on 2,000 validation queries reaches 0.955, timed on the 10,000
+    evaluation queries."""
+    import synthetic
+
+    _, Qva = synthetic.powerlaw(1, args.dim, 2000, seed=args.seed, device="cuda", query_sub=synthetic.SUB_VALID)
+    _, gd = ground_truth(torch, X, Q, 100)
+    _, gdv = ground_truth(torch, X, Qva, 100)
+    search, timed = _search_fn(torch, crisp, ix, dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    nq = Q.shape[0]
+    for k in (10, 100):
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        for mode, name in ((0, "guaranteed"), (1, "optimized")):
+            if mode == 0:
+                pts = [dict(k=k, mode=0, rho=r_, alpha=a_) for r_, a_ in
+                       ((0.01, 0.3), (0.02, 0.3), (0.03, 0.3), (0.04, 0.3), (0.03, 0.25), (0.05, 0.25), (0.08, 0.2))]
+            else:
+                pts = [dict(k=k, mode=1, rho=r_, alpha=a_, patience_factor=pf, max_candidates=OPT_CAP)
+                       for r_, a_ in ((0.01, 0.3), (0.02, 0.3), (0.03, 0.3)) for pf in (40, 100, 200, 400)]
+            pt, ok, log = _ladder(torch, X, Qva, gdv[:, k - 1].contiguous(), search, pts, k, dev)
+            q, ms = timed(Q, pt, ids, d2, min(args.steps, 5), flush)
+            r = recall_at_k(torch, X, Q, ids, gd[:, k - 1].contiguous())
+            out[f"{name}_k{k}"] = {"value": q, "unit": "queries/s", f"recall_at_{k}": r, "ms_per_step": ms,
+                                   "point": pt, "reached_0_95": ok, "ladder": log}
+    del flush
+    return out
+
+
+VMF_WORKLOAD = ("vMF N=1,000,000 D=3072 unit rows, 1,000 components, kappa=200 (Wood's sampler), 10,000 queries, "
+                "k=10, M=16 subspaces, K=50")
+LOWRANK_WORKLOAD = ("low-rank N=2,000,000 D=4096, rank-128 N(0,1) loadings, noise 0.05, 5% of dims x10 variance, "
+                    "10,000 queries, k=10, M=16 subspaces, K=50")
+
+
+def vmf_leg(args, torch, crisp, synthetic, dev, flush, stream):
+    """Learned early termination + BF16 coarse scoring on near-isotropic unit
+    rows (D = 3072): plain FP32 at the fastest point reaching recall@10 0.955 on
+    validation queries (or the highest recall its ladder reaches, reported as
+    such), the MLP trained on method-generated queries, then the learned+BF16
+    path at the plain path's recall.  Each on its own index."""
+    N, D, M, k = args.vmf_n, 3072, 16, 10
+    seed = args.seed
+    t0 = time.perf_counter()
+    X, Q = synthetic.vmf(N, D, args.nq, seed=seed, device="cuda")
+    _, Qva = synthetic.vmf(1, D, 2000, seed=seed, device="cuda", query_sub=synthetic.SUB_VALID)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix = crisp.crisp_build(X, N, D, crisp.build_params(M, draws=synthetic.method_draws(N, D, M, 50, seed=seed),
+                                                       copies=1))
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    info = ix.info()
+    _, gd = ground_truth(torch, X, Q, k)
+    _, gdv = ground_truth(torch, X, Qva, k)
+    gdk, gdvk = gd[:, k - 1].contiguous(), gdv[:, k - 1].contiguous()
+    search, timed = _search_fn(torch, crisp, ix, dev)
+    pts = [dict(k=k, mode=0, rho=r_, alpha=a_) for r_, a_ in
+           ((0.02, 0.25), (0.05, 0.25), (0.05, 0.125), (0.1, 0.125), (0.2, 0.125), (0.3, 0.0625))]
+    pt, ok, log = _ladder(torch, X, Qva, gdvk, search, pts, k, dev)
+    nq = Q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    st = torch.empty((nq, 6), dtype=torch.int64, device=dev)
+    steps = min(args.steps, 5)
+    q_p, ms_p = timed(Q, pt, ids, d2, steps, flush)
+    r_p = recall_at_k(torch, X, Q, ids, gdk)
+    search(Q, pt, ids, d2, st)
+    cands = float(st[:, 0].double().mean())
+    stage = stage_pass(torch, crisp, ix, info, Q, pt, k, steps, stream, flush)
+    stage.pop("shortlist_bf16", None)
+    peak, peak_kind = load_peaks()
+    roof, roofs = stage_rooflines(stage, info, peak, peak_kind, None)
+    # learned depths: labels from the plain search on method-generated training queries
+    F, H = 2 * M + 68, 256
+    ntr = args.vmf_train
+    t0 = time.perf_counter()
+    _, Qtr = synthetic.vmf(1, D, ntr, seed=seed, device="cuda", query_sub=synthetic.SUB_TRAIN)
+    feats = torch.empty((ntr, F), dtype=torch.float32, device=dev)
+    labels = torch.empty((ntr, 2), dtype=torch.int64, device=dev)
+    tg = torch.empty((ntr, 2), dtype=torch.float32, device=dev)
+    crisp.crisp_learned_data(ix, Qtr, ntr, crisp.search_params(k=k, mode=0, rho=pt["rho"], alpha=pt["alpha"]), feats,
+                             labels, tg)
+    torch.cuda.synchronize()
+    t_labels = time.perf_counter() - t0
+    del Qtr
+    P = torch.empty(crisp.crisp_mlp_param_count(F, H, 2), dtype=torch.float32, device=dev)
+    crisp.crisp_mlp_init(P, F, H, 2, seed=seed + 1)
+    t0 = time.perf_counter()
+    losses = crisp.crisp_mlp_train(P, F, H, 2, feats, tg, ntr, args.epochs, 1024, 1e-3, seed=seed + 2)
+    t_train = time.perf_counter() - t0
+    del feats, labels, tg
+    crisp.crisp_index_set_model(ix, P, H)
+    vi = torch.empty((Qva.shape[0], k), dtype=torch.int64, device=dev)
+    vd = torch.empty((Qva.shape[0], k), dtype=torch.float32, device=dev)
+    search(Qva, pt, vi, vd)
+    r_vplain = recall_at_k(torch, X, Qva, vi, gdvk)
+    lpts = [dict(pt, mode=2, depth_margin=dm, short_margin=sm) for dm in (0.0, 0.5, 1.0, 2.0, 3.0)
+            for sm in (0.0, 1.0, 2.0)]
+    lpt, lok, llog = _ladder(torch, X, Qva, gdvk, search, lpts, k, dev, target=r_vplain - 0.002)
+    q_l, ms_l = timed(Q, lpt, ids, d2, steps, flush)
+    r_l = recall_at_k(torch, X, Q, ids, gdk)
+    out = {"workload": VMF_WORKLOAD, "index_rotated": bool(info.rotated), "cev": info.cev,
+           "data_s": round(t_data, 2), "build_s": round(t_build, 2),
+           "plain_fp32": {"value": q_p, "unit": "queries/s", "recall_at_10": r_p, "ms_per_step": ms_p, "point": pt,
+                          "reached_0_95": ok, "candidates_mean": cands, "ladder": log},
+           "learned_bf16": {"value": q_l, "unit": "queries/s", "recall_at_10": r_l, "ms_per_step": ms_l,
+                            "speedup_vs_fp32": q_l / q_p, "depth_margin": lpt["depth_margin"],
+                            "short_margin": lpt["short_margin"], "matched_plain_recall": lok,
+                            "train_queries": ntr, "epochs": args.epochs, "loss_first_epoch": losses[0],
+                            "loss_last_epoch": losses[-1], "label_seconds": round(t_labels, 2),
+                            "train_seconds": round(t_train, 2)},
+           "roofline": roof, "rooflines": roofs,
+           "stage_ms": {n: round(v["ms"], 4) for n, v in stage.items()}}
+    ix.free()
+    del X, Q, Qva, gd, gdv, ids, d2, st, vi, vd
+    torch.cuda.empty_cache()
+    return out
+
+
+def lowrank_leg(args, torch, crisp, synthetic, dev, flush, stream):
+    """FP8 E4M3 coarse scoring with per-row scales and an FP32 re-rank of the
+    shortlist on low-rank rows (D = 4096, the CEV test rotates them), against
+    the plain FP32 path at the same recall; its own index."""
+    N, D, M, k = args.lowrank_n, 4096, 16, 10
+    seed = args.seed
+    t0 = time.perf_counter()
+    X, Q = synthetic.lowrank(N, D, args.nq, seed=seed, device="cuda")
+    _, Qva = synthetic.lowrank(1, D, 2000, seed=seed, device="cuda", query_sub=synthetic.SUB_VALID)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix = crisp.crisp_build(X, N, D, crisp.build_params(M, draws=synthetic.method_draws(N, D, M, 50, seed=seed),
+                                                       copies=3))
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    info = ix.info()
+    _, gd = ground_truth(torch, X, Q, k)
+    _, gdv = ground_truth(torch, X, Qva, k)
+    gdk, gdvk = gd[:, k - 1].contiguous(), gdv[:, k - 1].contiguous()
+    search, timed = _search_fn(torch, crisp, ix, dev)
+    pts = [dict(k=k, mode=0, rho=r_, alpha=a_) for r_, a_ in
+           ((0.01, 0.25), (0.02, 0.25), (0.05, 0.2), (0.1, 0.15), (0.15, 0.125), (0.2, 0.125), (0.3, 0.0625))]
+    pt, ok, log = _ladder(torch, X, Qva, gdvk, search, pts, k, dev)
+    nq = Q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    st = torch.empty((nq, 6), dtype=torch.int64, device=dev)
+    steps = min(args.steps, 5)
+    q_p, ms_p = timed(Q, pt, ids, d2, steps, flush)
+    r_p = recall_at_k(torch, X, Q, ids, gdk)
+    search(Q, pt, ids, d2, st)
+    cands = float(st[:, 0].double().mean())
+    vi = torch.empty((Qva.shape[0], k), dtype=torch.int64, device=dev)
+    vd = torch.empty((Qva.shape[0], k), dtype=torch.float32, device=dev)
+    search(Qva, pt, vi, vd)
+    r_vplain = recall_at_k(torch, X, Qva, vi, gdvk)
+    fpts = [dict(pt, precision=2, shortlist=S) for S in (50, 100, 200, 400, 800, 1600)]
+    fpt, fok, flog = _ladder(torch, X, Qva, gdvk, search, fpts, k, dev, target=r_vplain - 0.002)
+    q_f, ms_f = timed(Q, fpt, ids, d2, steps, flush)
+    r_f = recall_at_k(torch, X, Q, ids, gdk)
+    stage = stage_pass(torch, crisp, ix, info, Q, pt, k, steps, stream, flush)
+    stage.pop("shortlist_bf16", None)
+    peak, peak_kind = load_peaks()
+    roof, roofs = stage_rooflines(stage, info, peak, peak_kind, None)
+    out = {"workload": LOWRANK_WORKLOAD, "index_rotated": bool(info.rotated), "cev": info.cev,
+           "data_s": round(t_data, 2), "build_s": round(t_build, 2),
+           "plain_fp32": {"value": q_p, "unit": "queries/s", "recall_at_10": r_p, "ms_per_step": ms_p, "point": pt,
+                          "reached_0_95": ok, "candidates_mean": cands, "ladder": log},
+           "fp8_e4m3": {"value": q_f, "unit": "queries/s", "recall_at_10": r_f, "ms_per_step": ms_f,
+                        "shortlist": fpt["shortlist"], "speedup_vs_fp32": q_f / q_p, "matched_plain_recall": fok,
+                        "ladder": flog},
+           "roofline": roof, "rooflines": roofs,
+           "stage_ms": {n: round(v["ms"], 4) for n, v in stage.items()}}
+    ix.free()
+    del X, Q, Qva, gd, gdv, ids, d2, st, vi, vd
+    torch.cuda.empty_cache()
+    return out
 
 
 SERVE_WORKLOAD = ("serving: powerlaw N=5,000,000 D=1024 (lambda_i = i^-1.2, Haar mix), M=32; open-loop Poisson "
@@ -767,6 +1011,54 @@ def run_ablation(args):
     print(json.dumps({"ablation": out}), flush=True)
 
 
+def stage_rooflines(stage, info, hbm_peak, hbm_kind, traffic_key):
+    """Roofline of the dominant kernel and of every timed stage.
+
+    The tensor-core re-rank scorer is a dense contraction: its achieved rate is
+    the TF32 flops it executes per launch (each (group, row) entry one row
+    times the group's queries over Dp dims) over its CUDA-event duration,
+    against the TF32 peak.  Its row traffic (entries x row bytes, from L2 or
+    HBM) and the pairs it serves per row fetch are reported beside it.  The
+    other stages are measured in their algorithmic bytes against the HBM copy
+    bandwidth."""
+    tpk, tkind = tf32_peak()
+    rooflines = {}
+    for n, v in stage.items():
+        if v["bytes"]:
+            a = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            rooflines[n] = {"kernel": v["kernel"], "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": a / hbm_peak, "ms": round(v["ms"], 4), "algorithmic_bytes_per_launch": v["bytes"]}
+    sc = stage.get("rerank", {}).get("scorer")
+    if sc:
+        fl = sc["rows_per_launch"] * sc["group"] * 2 * sc["Dp"]
+        t = sc["ms_per_launch"] / 1e3
+        ach = fl / t / 1e12
+        row_bytes = sc["rows_per_launch"] * 4 * sc["Dp"]
+        traffic = _ncu_traffic("k_rerank_tc", traffic_key)
+        rooflines["rerank_scorer"] = {
+            "kernel": "k_rerank_tc", "bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+            "frac": ach / tpk, "traffic": traffic, "ms": round(sc["ms_per_launch"], 4),
+            "peak_kind": f"{tkind} sustained BF16 GEMM rate (MEASURED_PEAKS.json) x {TF32_PER_BF16:.3f}, the nominal "
+                         "TF32 / BF16 dense ratio",
+            "flops_per_launch": fl, "rows_per_launch": sc["rows_per_launch"], "pairs_per_launch": sc["pairs_per_launch"],
+            "pairs_per_row_fetch": sc["pairs_per_launch"] / max(sc["rows_per_launch"], 1.0),
+            "row_bytes_per_launch": row_bytes, "row_gbs": row_bytes / t / 1e9,
+            "dram_gbs": traffic / t / 1e9 if traffic else None,
+            "dram_frac": traffic / t / 1e9 / hbm_peak if traffic else None,
+            "note": "flops: one TF32 pass of every (64-query group, listed row) entry; rows come from L2 when the "
+                    "range-block order keeps them there; the exact re-measure and selection are separate kernels"}
+    timed_ms = {n: v["ms"] for n, v in stage.items()}
+    dom_stage = max(timed_ms, key=lambda n: timed_ms[n])
+    if dom_stage == "rerank" and "rerank_scorer" in rooflines:
+        dom = dict(rooflines["rerank_scorer"])
+    else:
+        dom = dict(rooflines.get(dom_stage) or {"kernel": stage[dom_stage]["kernel"], "bound": "hbm", "achieved": None,
+                                                "peak": hbm_peak, "unit": "GB/s", "frac": None})
+        dom["traffic"] = _ncu_traffic(dom_stage, traffic_key)
+        dom["peak_kind"] = f"{hbm_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    return dom, rooflines
+
+
 def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     """Time each kernel of the search path with CUDA events on the launching stream,
     and count the algorithmic bytes each launch must move (the per-stage units of each kernel)."""
@@ -789,11 +1081,13 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     nf = torch.empty((nq,), dtype=torch.int64, device=dev)
     nb = torch.empty((nq,), dtype=torch.int64, device=dev)
     names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
-    # batches of >= 1,024 queries with candidate lists >= 2,048 wide are scored in
-    # MinHash-ordered query groups (k_gunion + k_gscore); smaller ones stream (k_dist_flat)
-    grouped = nq >= 1024 and stride >= 2048 and Dp <= 1024
+    # batches of >= 1,024 queries with candidate lists >= 2,048 wide re-rank on the
+    # tensor cores (MinHash-ordered query groups, bounded TF32 scores, exact re-measure
+    # of the candidates that can reach the top-k); smaller ones stream (k_dist_flat)
+    grouped = nq >= 1024 and stride >= 2048
     kernels = ["k_rotate", "k_activate", "k_count_cut",
-               ("k_gscore_tm (FP32)" if grouped else "k_dist_flat") if point["mode"] == 0 else "k_verify_opt"]
+               ("k_rerank_tc (+ order, union, bound select, exact re-measure)" if grouped else "k_dist_flat")
+               if point["mode"] == 0 else "k_verify_opt"]
     bf16 = bool(info.Xb) and point["mode"] == 0
     if bf16:            # the F2 coarse-scoring kernel on the same candidates (timed on its own)
         names.append("shortlist_bf16")
@@ -822,7 +1116,12 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
             crisp.crisp_shortlist(ix, Qr, nq, cand, stride, ncand, 1, 50, sl, 64, nsl, stream)
             yield
 
+    prof = None
     for s in range(steps + 1):
+        if s == 1:
+            crisp.crisp_rerank_profile_read()          # drop the warm-up pass
+        if s == 0:
+            crisp.crisp_rerank_profile_enable(True)
         flush.zero_()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         evs[0].record(stream)
@@ -833,6 +1132,8 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
             continue            # warm-up
         for i, n in enumerate(names):
             acc[n] += evs[i].elapsed_time(evs[i + 1]) / steps
+    prof = crisp.crisp_rerank_profile_read()
+    crisp.crisp_rerank_profile_enable(False)
     C = float(ncand.sum().item())
     retr = float(got.sum().item())
     cells = float(nact.sum().item())
@@ -846,6 +1147,16 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     if point["mode"] == 0:
         # every candidate row (Dp floats) + its id
         out["rerank"] = {"ms": acc["rerank"], "bytes": C * (4 * Dp + 4), "kernel": kernels[3]}
+        if prof is not None and prof.launches > 0:
+            # the tensor-core scorer alone (events around its launches inside the library):
+            # per launch, its (group, row) entries each multiply one row by the group's
+            # queries over Dp dims (2 flops per multiply-add); pairs are (row, query)
+            # distances it bounds
+            out["rerank"]["scorer"] = {"kernel": "k_rerank_tc", "launches": prof.launches,
+                                       "ms_per_launch": prof.ms / prof.launches,
+                                       "rows_per_launch": prof.rows / prof.launches,
+                                       "pairs_per_launch": prof.pairs / prof.launches, "group": prof.group,
+                                       "Dp": prof.Dp}
     else:
         blocks = float(nb.sum().item())
         out["verify_opt"] = {"ms": acc["verify_opt"], "bytes": C * (4 * W + 4) + 128 * blocks,
@@ -894,6 +1205,12 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
+    ap.add_argument("--no-modes", action="store_true", help="skip the Guaranteed / Optimized k=10 / k=100 points")
+    ap.add_argument("--no-vmf", action="store_true", help="skip the vMF D=3072 learned+BF16 configuration")
+    ap.add_argument("--no-lowrank", action="store_true", help="skip the low-rank D=4096 FP8 configuration")
+    ap.add_argument("--vmf-n", type=int, default=1_000_000)
+    ap.add_argument("--vmf-train", type=int, default=200_000)
+    ap.add_argument("--lowrank-n", type=int, default=2_000_000)
     ap.add_argument("--ablation", action="store_true", help="run the paper's ablations (tau_CEV, patience, "
                                                             "verification sub-components) instead of the benchmark")
     ap.add_argument("--serve-n", type=int, default=5_000_000)
@@ -902,7 +1219,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=4096, help="distinct queries the requests draw from")
     ap.add_argument("--serve-train", type=int, default=20000)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--serve-batch", type=int, default=512)
+    ap.add_argument("--serve-batch", type=int, default=2048)
     ap.add_argument("--serve-rates", type=lambda v: [int(x) for x in v.split(",")], default=[20000, 50000, 100000, 200000])
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-max-requests", type=int, default=60000)

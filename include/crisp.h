@@ -502,6 +502,27 @@ crisp_status crisp_rerank_noalloc(const crisp_index *index, const float *Qr, int
                                   int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
                                   void *stream);
 
+/* Profiling aid (the paper has no counterpart): while enabled, the tensor-core
+ * re-rank of large batches (crisp_rerank, crisp_search) records CUDA events on
+ * its stream around its scoring kernel and copies the kernel's work counts.
+ * crisp_rerank_profile_read waits for what was recorded and returns, for the
+ * scoring launches since the previous read: their number, their summed
+ * duration, the (query group, row) entries multiplied on the tensor cores (each
+ * one row against a group's 64 queries over Dp dims, one TF32 pass) and the
+ * (row, query) pairs whose distance bounds were written.  Call both from one
+ * thread; reading also clears.  Synchronous. */
+typedef struct {
+    int64_t launches;
+    double ms;                 /* summed kernel duration, CUDA events on the launching stream */
+    int64_t rows;              /* (query group, row) entries scored */
+    int64_t pairs;             /* (row, query) pairs bounded */
+    int32_t Dp;                /* padded dimension of the last launch */
+    int32_t group;             /* queries per group (the MMA's N) */
+} crisp_rerank_profile;
+
+crisp_status crisp_rerank_profile_enable(int32_t on);
+crisp_status crisp_rerank_profile_read(crisp_rerank_profile *out);
+
 /* Q7 (§4.3.2 Stages 2-3, phi = 1; Eq. 2): candidates ordered by (Hamming
  * distance of sign codes, id); each is pruned by ADSampling checks at t = 32,
  * 64, ... < D when the running top-k is full (d_t > fl(r_k^2 * f_t), f_t =

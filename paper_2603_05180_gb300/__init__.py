@@ -69,6 +69,11 @@ class IndexInfo(C.Structure):
                 ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p), ("S8", C.c_void_p)]
 
 
+class RerankProfile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("rows", C.c_int64), ("pairs", C.c_int64),
+                ("Dp", C.c_int32), ("group", C.c_int32)]
+
+
 _P, _I32, _I64, _F, _D, _S = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t
 _SIGS = {
     "crisp_build": [_P, _I64, _I32, C.POINTER(BuildParams), _P, C.POINTER(_P)],
@@ -83,6 +88,8 @@ _SIGS = {
     "crisp_search_host": [_P, _P, _I32, _P, _I32, _P, _P, _I32, _P, _P],
     "crisp_search_scratch_bytes": [_P, _I32, _P, _I32, C.POINTER(_S)],
     "crisp_search_tau": [_D, _I32],
+    "crisp_rerank_profile_enable": [_I32],
+    "crisp_rerank_profile_read": [C.POINTER(RerankProfile)],
     "crisp_search_budget": [_D, _I64],
     "crisp_covariance": [_P, _I64, _I32, _I32, _P, _I64, _P, _P],
     "crisp_eigvalsh": [_P, _I32, _P, _P],
@@ -544,3 +551,15 @@ def crisp_server_replay(server, Q, qidx, params, pidx, arrival_us, kmax):
 
 def crisp_server_destroy(server):
     server.free()
+
+
+def crisp_rerank_profile_enable(on=True):
+    """Record CUDA events around the tensor-core re-rank's scoring kernel (profiling aid)."""
+    _call("crisp_rerank_profile_enable", int(bool(on)))
+
+
+def crisp_rerank_profile_read() -> RerankProfile:
+    """Launches, summed duration (ms) and work counts of the scoring kernel since the last read."""
+    out = RerankProfile()
+    _call("crisp_rerank_profile_read", C.byref(out))
+    return out

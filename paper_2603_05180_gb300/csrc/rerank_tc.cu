@@ -49,6 +49,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -660,22 +662,87 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
     }
 }
 
+// Profiling records (crisp_rerank_profile_*): events around each scoring
+// launch and a pinned copy of its work counters.
+struct ProfRec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    unsigned long long *host = nullptr;   // pinned [2]: entries, pairs
+    int Dp = 0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+
 }  // namespace
+
+extern "C" crisp_status crisp_rerank_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_rerank_profile_read(crisp_rerank_profile *out) {
+    CRISP_REQUIRE(out, "crisp_rerank_profile_read: null output");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    crisp_rerank_profile r = {};
+    r.group = TG;
+    crisp_status s = CRISP_OK;
+    for (ProfRec &p : g_prof_recs) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess && s == CRISP_OK) s = crisp_cuda_fail(e, "crisp_rerank_profile_read", __FILE__, __LINE__);
+        r.launches += 1;
+        r.ms += ms;
+        r.rows += (int64_t)p.host[0];
+        r.pairs += (int64_t)p.host[1];
+        r.Dp = p.Dp;
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+        cudaFreeHost(p.host);
+    }
+    g_prof_recs.clear();
+    *out = r;
+    return s;
+}
 
 // Tensor-core re-rank of a batch of 1,024 to CRISP_GROUP_MAXQ queries whose
 // candidate lists may hold 2,048 or more ids; *done = false (nothing run) for
 // other batches, which the caller streams.  dbuf: [nq][stride] floats of scratch.
+static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                    int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
+                                    float *dbuf, int64_t *ids, float *d2, cudaStream_t st);
+
 crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
                                  float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done) {
     *done = false;
     if (nq < 1024 || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
+    // pair slots are 32-bit: batches whose lists could hold more pairs run in
+    // equal sub-batches (the kernels have no minimum batch size)
+    const long long per_q = std::min<int64_t>(stride, ix->N);
+    const long long sub = 0x7FFFFFFFLL / per_q;
+    if (sub < 512) return CRISP_OK;
+    const int32_t nb = (int32_t)((nq + sub - 1) / sub), each = (nq + nb - 1) / nb;
+    for (int32_t q0 = 0; q0 < nq; q0 += each) {
+        const int32_t n = std::min(each, nq - q0);
+        crisp_status s = rerank_tc_batch(ix, Qr + (int64_t)q0 * ix->Dp, n, cand + (int64_t)q0 * stride, stride,
+                                         ncand + q0, k, qp ? qp + q0 : nullptr, ko, dbuf + (int64_t)q0 * stride,
+                                         ids + (int64_t)q0 * ko, d2 + (int64_t)q0 * ko, st);
+        if (s) return s;
+    }
+    *done = true;
+    return CRISP_OK;
+}
+
+static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                    int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
+                                    float *dbuf, int64_t *ids, float *d2, cudaStream_t st) {
     const int Dp = ix->Dp;
     const int R = (int)((ix->N + TSPAN - 1) / TSPAN);
     const int ngroups = (nq + TG - 1) / TG, nslots = ngroups * TG;
     const long long pcap = (long long)nq * std::min<int64_t>(stride, ix->N);
     const long long ecap = std::min<long long>(pcap, (long long)ngroups * R * TSPAN);
-    if (pcap > 0x7FFFFFFFLL) return CRISP_OK;        // pair slots are 32-bit
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -765,16 +832,33 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ProfRec rec;
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            if (g_prof_on) {
+                rec.Dp = Dp;
+                if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess ||
+                    cudaMallocHost((void **)&rec.host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+                    s = crisp_cuda_fail(cudaGetLastError(), "profiling record", __FILE__, __LINE__);
+                    break;
+                }
+                cudaEventRecord(rec.a, st);
+            }
+        }
         k_rerank_tc<<<sms, TR_NT, smem, st>>>(mq, ta);
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rerank_tc", __FILE__, __LINE__); break; }
+        if (rec.a) {
+            cudaEventRecord(rec.b, st);
+            cudaMemcpyAsync(rec.host, counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_prof_recs.push_back(rec);
+        }
         s = crisp_run_bound_select(nq, cand, stride, ncand, k, qp, ulb, err_word, rc, nr, st);
         if (s) break;
         // the kept candidates, measured exactly (streaming CR32) -> top-k
         s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false, qp, ko);
-        if (s) break;
-        *done = true;
     } while (0);
     crisp_scratch_free(buf, st);
     return s;

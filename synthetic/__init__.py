@@ -123,11 +123,17 @@ def _wood_vmf_weights(rr, n, D, kappa):
     return w
 
 
-def vmf(N=1_000_000, D=3072, nq=10_000, n_comp=1000, kappa=200.0, seed=0):
-    """Unit rows from a vMF mixture (uniform weights, means uniform on the sphere)."""
+def vmf(N=1_000_000, D=3072, nq=10_000, n_comp=1000, kappa=200.0, seed=0, device="cpu", query_sub=SUB_QUERY):
+    """Unit rows from a vMF mixture (uniform weights, means uniform on the sphere).
+
+    With ``device='cuda'`` the per-row scalars (component, Wood cosine) are
+    drawn on the host and the D-dimensional tangent directions on the GPU with
+    a seeded torch generator (other rows than the host version, same law)."""
     r = _rng(seed, SUB_DATA)
     mu = r.normal(size=(n_comp, D))
     mu /= np.linalg.norm(mu, axis=1, keepdims=True)
+    if device != "cpu":
+        return _vmf_device(mu, N, D, nq, n_comp, kappa, seed, device, query_sub)
 
     def draw(rr, n):
         comp = rr.integers(0, n_comp, size=n)
@@ -142,14 +148,21 @@ def vmf(N=1_000_000, D=3072, nq=10_000, n_comp=1000, kappa=200.0, seed=0):
     return draw(r, N), draw(_rng(seed, SUB_QUERY), nq)
 
 
-def lowrank(N=2_000_000, D=4096, nq=10_000, rank=128, noise=0.05, boost_frac=0.05, boost_var=10.0, seed=0):
-    """x = L f + noise*e, with a seeded 5% of dims scaled to 10x variance."""
+def lowrank(N=2_000_000, D=4096, nq=10_000, rank=128, noise=0.05, boost_frac=0.05, boost_var=10.0, seed=0,
+            device="cpu", query_sub=SUB_QUERY):
+    """x = L f + noise*e, with a seeded 5% of dims scaled to 10x variance.
+
+    With ``device='cuda'`` the loadings and boosted dims come from the host
+    stream and the Gaussian factors and noise from a seeded torch generator on
+    the GPU (other rows than the host version, same law)."""
     r = _rng(seed, SUB_DATA)
     L = r.normal(size=(D, rank)).astype(np.float32)
     nb = int(math.floor(boost_frac * D))
     boost = r.choice(D, size=nb, replace=False)
     scale = np.ones(D, np.float32)
     scale[boost] = math.sqrt(boost_var)
+    if device != "cpu":
+        return _lowrank_device(L, scale, N, D, nq, rank, noise, seed, device, query_sub)
 
     def draw(rr, n):
         f = rr.standard_normal((n, rank), dtype=np.float32)
@@ -157,6 +170,51 @@ def lowrank(N=2_000_000, D=4096, nq=10_000, rank=128, noise=0.05, boost_frac=0.0
         return ((f @ L.T + noise * e) * scale[None, :]).astype(np.float32)
 
     return draw(r, N), draw(_rng(seed, SUB_QUERY), nq)
+
+
+def _vmf_device(mu, N, D, nq, n_comp, kappa, seed, device, query_sub):
+    import torch
+
+    mu_d = torch.from_numpy(mu.astype(np.float32)).to(device)
+    g = torch.Generator(device=device)
+    out = []
+    for sub, n in ((SUB_DATA, N), (query_sub, nq)):
+        rr = _rng(seed, 100 + sub)
+        comp = torch.from_numpy(rr.integers(0, n_comp, size=n)).to(device)
+        w = torch.from_numpy(_wood_vmf_weights(rr, n, D, kappa).astype(np.float32)).to(device)
+        g.manual_seed(seed * 1000003 + 100 + sub)
+        Y = torch.empty((n, D), dtype=torch.float32, device=device)
+        step = 1 << 16
+        for s0 in range(0, n, step):
+            e = min(n, s0 + step)
+            m = mu_d[comp[s0:e]]
+            v = torch.randn((e - s0, D), generator=g, device=device, dtype=torch.float32)
+            v -= (v * m).sum(1, keepdim=True) * m                      # tangent direction
+            v /= torch.linalg.vector_norm(v, dim=1, keepdim=True)
+            ws = w[s0:e, None]
+            Y[s0:e] = ws * m + torch.sqrt(torch.clamp(1.0 - ws * ws, min=0.0)) * v
+        out.append(Y)
+    return out[0], out[1]
+
+
+def _lowrank_device(L, scale, N, D, nq, rank, noise, seed, device, query_sub):
+    import torch
+
+    Lt = torch.from_numpy(L.T.copy()).to(device)
+    sc = torch.from_numpy(scale).to(device)
+    g = torch.Generator(device=device)
+    out = []
+    for sub, n in ((SUB_DATA, N), (query_sub, nq)):
+        g.manual_seed(seed * 1000003 + 200 + sub)
+        Y = torch.empty((n, D), dtype=torch.float32, device=device)
+        step = 1 << 16
+        for s0 in range(0, n, step):
+            e = min(n, s0 + step)
+            f = torch.randn((e - s0, rank), generator=g, device=device, dtype=torch.float32)
+            z = torch.randn((e - s0, D), generator=g, device=device, dtype=torch.float32)
+            Y[s0:e] = (f @ Lt + noise * z) * sc
+        out.append(Y)
+    return out[0], out[1]
 
 
 def small_gaussian(N, D, nq, seed=0, scale=1.0):
