@@ -3,7 +3,9 @@
 A plain, slow, obviously-correct restatement of what the GPU engine computes,
 written from the paper: the index build of §4.1-§4.2 (covariance and CEV test,
 random orthogonal rotation, IMI k-means per subspace half, cell assignment,
-CSR, sign codes) and the query pipeline of Algorithm 1 / §4.3 (partial
+CSR, sign codes), the two build extensions of §7 (block-wise rotation of the
+correlated blocks only, variance-aware subspace boundaries) and the query
+pipeline of Algorithm 1 / §4.3 (partial
 distances, multi-sequence traversal, collision counting, threshold cut with
 fallback, exact re-rank or Hamming-ordered ADSampling with patience).
 
@@ -47,7 +49,8 @@ class _OrIndex(C.Structure):
                 ("H", C.c_int32), ("rotated", C.c_int32), ("_pad", C.c_int32),
                 ("R32", C.c_void_p), ("cent", C.c_void_p), ("offsets", C.c_void_p), ("ids", C.c_void_p),
                 ("Xr", C.c_void_p), ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p),
-                ("S8", C.c_void_p), ("mlp", C.c_void_p), ("mlp_H", C.c_int32), ("_pad2", C.c_int32)]
+                ("S8", C.c_void_p), ("mlp", C.c_void_p), ("mlp_H", C.c_int32), ("_pad2", C.c_int32),
+                ("sub", C.c_void_p)]
 
 
 class _OrParams(C.Structure):
@@ -77,7 +80,7 @@ def _declare(L):
         "or_pad_rows": (None, [_P, _I64, _I32, _I32, _I32, _P]),
         "or_covariance": (None, [_P, _I64, _I32, _I32, _P, _I64, _P]),
         "or_kmeans": (None, [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P]),
-        "or_assign_cells": (None, [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P]),
+        "or_assign_cells": (None, [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
         "or_csr": (None, [_P, _I64, _I32, _P, _P]),
         "or_sign_codes": (None, [_P, _I64, _I32, _P]),
         "or_half_dists": (None, [_P, _P, _I32, _I32, _P, _P, _P]),
@@ -144,6 +147,64 @@ def padded_dim(D: int) -> int:
 
 def half_width_max(D: int, M: int) -> int:
     return max(max(subspace(D, M, m)[1:]) for m in range(M))
+
+
+def equal_bounds(D: int, M: int) -> np.ndarray:
+    """Boundaries of the equal split of §3: sub[m] = floor(mD/M), sub[M] = D."""
+    return np.array([subspace(D, M, m)[0] for m in range(M)] + [D], np.int32)
+
+
+def bounds_half_max(sub) -> int:
+    """Widest subspace half (the centroid row length H) for boundaries sub[0..M]."""
+    w = np.diff(np.asarray(sub, np.int64))
+    return int(np.max(w - w // 2))
+
+
+# ------------------------------------- §7 adaptive subspace decomposition
+def column_variance(X, rows) -> np.ndarray:
+    """Per-dimension sample variance of X[rows] over the first D columns, FP64,
+    mean-centred with 1/(S-1): the statistic the adaptive decomposition of §7
+    balances across subspaces.  X may carry padding columns past D (pass D)."""
+    Xs = np.asarray(X)[np.asarray(rows, np.int64)].astype(np.float64)
+    S = Xs.shape[0]
+    mean = Xs.sum(axis=0) / S
+    c = Xs - mean[None, :]
+    return (c * c).sum(axis=0) / (S - 1)
+
+
+SUB_MIN, SUB_MAX = 2, 256   # a subspace needs two non-empty halves of at most 128 dims
+
+
+def adaptive_bounds(var, M: int) -> np.ndarray:
+    """Variance-aware subspace boundaries (§7 Adaptive Subspace Decomposition).
+
+    Subspaces stay contiguous in dimension order and get (near) equal shares of
+    the total variance, so a high-variance region is split into narrow
+    subspaces and a low-variance region grouped into wide ones.  With the
+    cumulative variance V_j = var[0] + ... + var[j-1] (FP64, summed in order),
+    boundary m (0 < m < M) is the largest j with V_j <= m V_D / M, clamped so
+    that every subspace keeps between 2 and 256 dims.  Zero total variance
+    gives the equal split."""
+    var = [float(v) for v in var]
+    D = len(var)
+    cum = [0.0]
+    for v in var:
+        cum.append(cum[-1] + v)
+    tot = cum[D]
+    b = [0]
+    for m in range(1, M):
+        if tot > 0.0:
+            t = float(m) * tot / float(M)
+            j = 0
+            while j < D and cum[j + 1] <= t:
+                j += 1
+        else:
+            j = (m * D) // M
+        lo = max(b[-1] + SUB_MIN, D - SUB_MAX * (M - m))
+        hi = min(b[-1] + SUB_MAX, D - SUB_MIN * (M - m))
+        b.append(min(max(j, lo), hi))
+    b.append(D)
+    return np.array(b, np.int32)
 
 
 # ------------------------------------------------------------ FP32 orders
@@ -213,6 +274,38 @@ def rotation_from_gaussian(G: np.ndarray) -> np.ndarray:
     return Q * s[None, :]
 
 
+def rotation_blocks(D: int, b: int):
+    """Contiguous blocks of b dims, [jb, min((j+1)b, D)), the last one ragged."""
+    return [(lo, min(lo + b, D)) for lo in range(0, D, b)]
+
+
+def block_rotation(X, rows, G, b: int, tau_cev: float, rotate: int = -1):
+    """Block-wise variance redistribution (§7 Partial Variance Redistribution).
+
+    The dimensions are cut into contiguous blocks of b dims.  Each block takes
+    the §4.1 test on its own: its CEV is computed from the eigenvalues of the
+    sample covariance restricted to the block (top floor(0.2 w) of w), and a
+    block whose CEV exceeds tau_cev (every block for rotate = 1, none for 0) is
+    rotated by its own Haar rotation, R_B = rotation_from_gaussian(G_BB) with
+    G_BB the block's diagonal block of the Gaussian draws.  R is block-diagonal,
+    the identity outside rotated blocks, so X R costs O(N sum w^2) <= O(N D b).
+
+    Returns (R64 [D][D], [(lo, hi, cev, rotated) per block])."""
+    G = np.asarray(G, np.float64)
+    D = G.shape[0]
+    cov = covariance(X, rows)
+    R = np.eye(D)
+    info = []
+    for lo, hi in rotation_blocks(D, b):
+        ev = np.linalg.eigvalsh(cov[lo:hi, lo:hi])[::-1].copy()
+        c = cev_from_eigenvalues(ev)
+        rot = rotate == 1 or (rotate == -1 and c > tau_cev)
+        if rot:
+            R[lo:hi, lo:hi] = rotation_from_gaussian(G[lo:hi, lo:hi])
+        info.append((lo, hi, c, bool(rot)))
+    return R, info
+
+
 def rotate_rows(X, R32, Dp=None) -> np.ndarray:
     """X' = X R in FP32, each output an fmaf chain over d = 0..D-1 (Q1 / B2)."""
     X = _c(X, np.float32)
@@ -243,13 +336,15 @@ def kmeans(T, off, h, K, H, init, iters) -> np.ndarray:
     return Cc
 
 
-def assign_cells(Xr, D, M, K, H, cent) -> np.ndarray:
-    """u_m(x) = cL*K + cR for all rows and subspaces, [M][N] uint16 (§3, §4.2)."""
+def assign_cells(Xr, D, M, K, H, cent, sub=None) -> np.ndarray:
+    """u_m(x) = cL*K + cR for all rows and subspaces, [M][N] uint16 (§3, §4.2);
+    ``sub`` gives the subspace boundaries (None: the equal split)."""
     Xr = _c(Xr, np.float32)
     cent = _c(cent, np.float32)
     N, Dp = Xr.shape
     cells = np.empty((M, N), np.uint16)
-    lib().or_assign_cells(_p(Xr), N, D, Dp, M, K, H, _p(cent), _p(cells))
+    sb = _c(sub, np.int32) if sub is not None else None
+    lib().or_assign_cells(_p(Xr), N, D, Dp, M, K, H, _p(cent), _p(sb) if sb is not None else None, _p(cells))
     return cells
 
 
@@ -296,7 +391,12 @@ class Index:
     S8: np.ndarray | None = None          # [N] FP8 row scales
     mlp: np.ndarray | None = None         # learned depth model, packed FP32 parameters
     mlp_H: int = 0
+    sub: np.ndarray | None = None         # [M+1] subspace boundaries (None: the equal split)
+    blocks: list | None = None            # block-wise rotation: (lo, hi, cev, rotated) per block
     _st: _OrIndex | None = field(default=None, repr=False)
+
+    def bounds(self) -> np.ndarray:
+        return self.sub if self.sub is not None else equal_bounds(self.D, self.M)
 
     def set_model(self, params, H):
         self.mlp = np.ascontiguousarray(params, np.float32)
@@ -317,16 +417,22 @@ class Index:
             pv = lambda a: _p(a).value if a is not None else None
             self._st = _OrIndex(self.N, self.D, self.Dp, self.M, self.K, self.H, self.rotated, 0,
                                 pv(self.R32), pv(self.cent), pv(self.offsets), pv(self.ids), pv(self.Xr),
-                                pv(self.codes), pv(self.Xb), pv(self.X8), pv(self.S8), pv(self.mlp), self.mlp_H, 0)
+                                pv(self.codes), pv(self.Xb), pv(self.X8), pv(self.S8), pv(self.mlp), self.mlp_H, 0,
+                                pv(self.sub))
         return self._st
 
 
-def build_index(X, M, K=50, draws=None, tau_cev=0.85, rotate=-1, kmeans_iters=20, seed=0) -> Index:
+def build_index(X, M, K=50, draws=None, tau_cev=0.85, rotate=-1, kmeans_iters=20, seed=0, adaptive=0,
+                block_dims=0) -> Index:
     """The index build of §4.1-§4.2 in order: CEV test, optional rotation,
     k-means per subspace half, cell assignment, CSR per subspace, sign codes.
 
     ``draws`` holds the random numbers the build uses (synthetic.method_draws);
-    ``rotate`` is -1 (decide by CEV > tau_cev), 0 (never) or 1 (always)."""
+    ``rotate`` is -1 (decide by CEV > tau_cev), 0 (never) or 1 (always).
+    The two extensions of §7: ``block_dims`` = b > 0 replaces the global test
+    and rotation by the block-wise one (block_rotation); ``adaptive`` = 1 sets
+    the subspace boundaries by adaptive_bounds from the per-dimension variance
+    of the stored rows over the covariance sample (else the equal split)."""
     import synthetic
 
     X = _c(X, np.float32)
@@ -334,47 +440,63 @@ def build_index(X, M, K=50, draws=None, tau_cev=0.85, rotate=-1, kmeans_iters=20
     if draws is None:
         draws = synthetic.method_draws(N, D, M, K, seed)
     Dp = padded_dim(D)
-    H = half_width_max(D, M)
     cval, eig = cev(X, draws.cev_sample)
-    do_rot = (rotate == 1) or (rotate == -1 and cval > tau_cev)
-    R64 = R32 = None
+    blocks = None
+    if block_dims > 0:
+        R64, blocks = block_rotation(X, draws.cev_sample, draws.gaussian, block_dims, tau_cev, rotate)
+        do_rot = any(b[3] for b in blocks)
+        if not do_rot:
+            R64 = None
+    else:
+        do_rot = (rotate == 1) or (rotate == -1 and cval > tau_cev)
+        R64 = rotation_from_gaussian(draws.gaussian) if do_rot else None
+    R32 = None
     if do_rot:
-        R64 = rotation_from_gaussian(draws.gaussian)
         R32 = R64.astype(np.float32)
         Xr = rotate_rows(X, R32, Dp)
     else:
         Xr = pad_rows(X, Dp)
+    sub = adaptive_bounds(column_variance(Xr[:, :D], draws.cev_sample), M) if adaptive else equal_bounds(D, M)
+    H = bounds_half_max(sub)
     T = np.ascontiguousarray(Xr[draws.kmeans_sample])
     cent = np.zeros((M, 2, K, H), np.float32)
     for m in range(M):
-        lo, hl, hr = subspace(D, M, m)
+        lo, w = int(sub[m]), int(sub[m + 1] - sub[m])
+        hl, hr = w // 2, w - w // 2
         cent[m, 0] = kmeans(T, lo, hl, K, H, draws.kmeans_init[m, 0], kmeans_iters)
         cent[m, 1] = kmeans(T, lo + hl, hr, K, H, draws.kmeans_init[m, 1], kmeans_iters)
-    cells = assign_cells(Xr, D, M, K, H, cent)
+    cells = assign_cells(Xr, D, M, K, H, cent, sub)
     offsets = np.empty((M, K * K + 1), np.int32)
     ids = np.empty((M, N), np.int32)
     for m in range(M):
         offsets[m], ids[m] = csr(cells[m], K * K)
     codes = sign_codes(Xr)
-    return Index(N, D, Dp, M, K, H, int(do_rot), float(cval), R32, cent, offsets, ids, Xr, codes, cells, R64, eig)
+    ix = Index(N, D, Dp, M, K, H, int(do_rot), float(cval), R32, cent, offsets, ids, Xr, codes, cells, R64, eig)
+    if adaptive:
+        ix.sub = sub
+    ix.blocks = blocks
+    return ix
 
 
 # Index blob: a 256-byte header (magic "CRISPIX1", then int64 version, N, D,
 # Dp, M, K, H, rotated, and the CEV as a float64), then sections R32 (only if
 # rotated), cent, offsets, ids, Xr, codes, each starting at a multiple of 256.
+# Version 2 adds a last section, the int32 subspace boundaries [M+1], for an
+# index whose boundaries are not the equal split; version 1 has the equal split.
 BLOB_MAGIC = b"CRISPIX1"
-BLOB_VERSION = 1
 
 
 def export_blob(ix: Index) -> bytes:
+    sub = ix.bounds()
+    v2 = not np.array_equal(sub, equal_bounds(ix.D, ix.M))
     hdr = bytearray(256)
     hdr[0:8] = BLOB_MAGIC
-    struct.pack_into("<8q", hdr, 8, BLOB_VERSION, ix.N, ix.D, ix.Dp, ix.M, ix.K, ix.H, ix.rotated)
+    struct.pack_into("<8q", hdr, 8, 2 if v2 else 1, ix.N, ix.D, ix.Dp, ix.M, ix.K, ix.H, ix.rotated)
     struct.pack_into("<d", hdr, 72, ix.cev)
     parts = [bytes(hdr)]
     secs = ([ix.R32.astype(np.float32)] if ix.rotated else []) + [
         ix.cent.astype(np.float32), ix.offsets.astype(np.int32), ix.ids.astype(np.int32),
-        ix.Xr.astype(np.float32), ix.codes.astype(np.uint32)]
+        ix.Xr.astype(np.float32), ix.codes.astype(np.uint32)] + ([sub.astype(np.int32)] if v2 else [])
     pos = 256
     for a in secs:
         b = np.ascontiguousarray(a).tobytes()

@@ -45,6 +45,7 @@ typedef struct {
     const float *S8;         /* [N]           FP8 row scales, or NULL */
     const float *mlp;        /* learned depth model (F = 2M + 68 -> H -> H -> 2), or NULL */
     int32_t mlp_H, _pad2;
+    const int32_t *sub;      /* [M+1] subspace boundaries (adaptive decomposition), or NULL = equal split */
 } or_index;
 
 typedef struct {
@@ -72,6 +73,18 @@ void or_subspace(int D, int M, int m, int *lo, int *hl, int *hr) {
     int a = (int)(((int64_t)m * D) / M), b = (int)(((int64_t)(m + 1) * D) / M);
     int d = b - a;
     *lo = a;
+    *hl = d / 2;
+    *hr = d - d / 2;
+}
+
+/* Subspace m given explicit boundaries sub[0..M] (subspace m covers dims
+ * [sub[m], sub[m+1])), or the equal split of or_subspace when sub is NULL;
+ * halves as in or_subspace (the adaptive decomposition of §7 changes only
+ * where the subspaces start and end). */
+void or_subspace_b(const int32_t *sub, int D, int M, int m, int *lo, int *hl, int *hr) {
+    if (!sub) { or_subspace(D, M, m, lo, hl, hr); return; }
+    int d = sub[m + 1] - sub[m];
+    *lo = sub[m];
     *hl = d / 2;
     *hr = d - d / 2;
 }
@@ -214,12 +227,12 @@ void or_kmeans(const float *T, int64_t S, int ldt, int off, int h, int K, int H,
 /* Cell u_m(x) = Combine(argmin_left, argmin_right) = cL*K + cR for every row
  * and subspace (§3 u(x); §4.2 cells = K x K).  cells is [M][N]. */
 void or_assign_cells(const float *Xr, int64_t N, int D, int Dp, int M, int K, int H,
-                     const float *cent, uint16_t *cells) {
+                     const float *cent, const int32_t *sub, uint16_t *cells) {
 #pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < N; ++n) {
         for (int m = 0; m < M; ++m) {
             int lo, hl, hr;
-            or_subspace(D, M, m, &lo, &hl, &hr);
+            or_subspace_b(sub, D, M, m, &lo, &hl, &hr);
             const float *x = Xr + n * Dp + lo;
             const float *CL = cent + ((int64_t)m * 2 + 0) * K * H;
             const float *CR = cent + ((int64_t)m * 2 + 1) * K * H;
@@ -260,7 +273,7 @@ void or_sign_codes(const float *Xr, int64_t N, int Dp, uint32_t *codes) {
  * each sorted ascending with ties by centroid index. */
 void or_half_dists(const or_index *ix, const float *qr, int m, int half, float *dist, float *sorted, int32_t *perm) {
     int lo, hl, hr;
-    or_subspace(ix->D, ix->M, m, &lo, &hl, &hr);
+    or_subspace_b(ix->sub, ix->D, ix->M, m, &lo, &hl, &hr);
     int h = half ? hr : hl;
     const float *qh = qr + lo + (half ? hl : 0);
     const float *C = ix->cent + ((int64_t)m * 2 + half) * ix->K * ix->H;

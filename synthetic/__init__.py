@@ -20,6 +20,10 @@ benchmark configurations):
                   kappa=200, D=3072 (Simplewiki-shaped), Wood's (1994) sampler.
 * ``lowrank``   -- x = L f + 0.05 e, rank-128 N(0,1) loadings, with 5% of the
                   dimensions scaled to 10x variance, D=4096 (Trevi-shaped).
+* ``mixed``     -- a correlated block (the first dims, a Haar-mixed low-rank
+                  Gaussian) beside independent dims whose standard deviations
+                  decay geometrically: the mixed, skewed distribution that the
+                  block-wise rotation and adaptive subspace sizes (§7) target.
 
 The random numbers the *method* draws (the covariance sample of §4.1, the
 Gaussian matrix G of the rotation in §3, the k-means training sample and
@@ -215,6 +219,35 @@ def _lowrank_device(L, scale, N, D, nq, rank, noise, seed, device, query_sub):
             Y[s0:e] = (f @ Lt + noise * z) * sc
         out.append(Y)
     return out[0], out[1]
+
+
+def mixed(N=200_000, D=960, nq=1_000, corr_dims=192, rank=8, skew=8.0, noise=0.05, seed=0):
+    """Rows with a correlated block and a skewed independent part.
+
+    Dims [0, corr_dims): U_b (F z) + noise e, F a rank-``rank`` N(0,1) loading
+    matrix and U_b a Haar mix of the block, so the block's spectrum is
+    concentrated (block CEV near 1).  Dims [corr_dims, D): independent
+    N(0, s_d^2) with s_d falling geometrically from ``skew`` to 1 across the
+    part (variance skewed towards its first dims, no correlation)."""
+    r = _rng(seed, SUB_DATA)
+    F = r.standard_normal((corr_dims, rank))
+    U = haar_orthogonal(corr_dims, seed * 7919 + 17)
+    L = U @ F
+    rest = D - corr_dims
+    s = skew ** (1.0 - np.arange(rest) / max(rest - 1, 1))
+
+    def draw(rr, n):
+        out = np.empty((n, D), np.float32)
+        for a in range(0, n, 65536):
+            b = min(n, a + 65536)
+            z = rr.standard_normal((b - a, rank))
+            out[a:b, :corr_dims] = z @ L.T + noise * rr.standard_normal((b - a, corr_dims))
+            out[a:b, corr_dims:] = s[None, :] * rr.standard_normal((b - a, rest))
+        return out
+
+    X = draw(r, N)
+    Q = draw(_rng(seed, SUB_QUERY), nq)
+    return X, Q
 
 
 def small_gaussian(N, D, nq, seed=0, scale=1.0):
