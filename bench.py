@@ -932,8 +932,10 @@ def run_ablation(args):
     QPS with the rotation forced off and on, then what each tau_CEV would
     choose; (2) the patience factor of the Optimized mode (20 / 40 / 60);
     (3) the verification sub-components: full (Hamming order + ADSampling),
-    exact L2 (ADSampling off, eps0 = inf) and id order (Hamming re-ranking off).
-    Prints one JSON line."""
+    exact L2 (ADSampling off, eps0 = inf) and id order (Hamming re-ranking off);
+    (4) the two build extensions of §7 (block-wise rotation, variance-aware
+    subspace sizes) against the equal split with and without the global
+    rotation, on skewed mixed data.  Prints one JSON line."""
     import torch
 
     import paper_2603_05180_gb300 as crisp
@@ -1006,8 +1008,39 @@ def run_ablation(args):
                 k=10, mode=1, rho=rho, alpha=0.3, max_candidates=OPT_CAP, **kw), 10)))
     out["subcomponents"] = {"point": "Optimized, k=10, alpha=0.3, patience 40 k, 2,000 queries, 1M x 960",
                             "points": sub}
+    ix.free()
+    del X, Q
+    torch.cuda.empty_cache()
+    # (4) §7 extensions on the mixed workload (a correlated 192-dim block beside
+    # 768 independent dims with standard deviations 8 .. 1)
+    N, D, M = 1_000_000, 960, 20
+    Xh, Qh = synthetic.mixed(N, D, 2000, corr_dims=192, rank=8, skew=8.0)
+    X, Q = torch.from_numpy(Xh).to(dev), torch.from_numpy(Qh).to(dev)
+    del Xh, Qh
+    _, gd = ground_truth(torch, X, Q, 10)
+    draws = synthetic.method_draws(N, D, M, 50)
+    ext = []
+    for name, kw in (("equal split, no rotation", dict(rotate=0)), ("equal split, global rotation", dict(rotate=1)),
+                     ("equal split, block-wise rotation (192-dim blocks)", dict(rotate=-1, block_dims=192)),
+                     ("variance-aware subspaces, no rotation", dict(rotate=0, adaptive=1)),
+                     ("variance-aware subspaces, block-wise rotation", dict(rotate=-1, block_dims=192, adaptive=1))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = crisp.crisp_build(X, N, D, crisp.build_params(M, draws=draws, **kw))
+        build_s = time.perf_counter() - t0
+        info = ix.info()
+        w = np.diff(crisp.crisp_index_get_bounds(ix))
+        ext.append(dict(config=name, build_s=build_s, rotated=int(info.rotated), rotated_blocks=int(info.rotated_blocks),
+                        subspace_dims_min=int(w.min()), subspace_dims_max=int(w.max()),
+                        points=[dict(rho=rho, **measure(ix, X, Q, gd, crisp.search_params(k=10, rho=rho, alpha=0.25),
+                                                        10)) for rho in (0.01, 0.02, 0.05)]))
+        ix.free()
+    out["extensions"] = {"point": "Guaranteed, k=10, alpha=0.25, 2,000 queries, mixed 1M x 960, M=20",
+                         "configs": ext}
     out["workloads"] = {"tau_cev": "gmm, powerlaw, vmf (200 components, kappa 200), lowrank (rank 128, 5% x10)",
-                        "patience_subcomponents": "powerlaw 1M x 960, M=20"}
+                        "patience_subcomponents": "powerlaw 1M x 960, M=20",
+                        "extensions": "mixed 1M x 960: rank-8 correlated block of 192 dims + 768 independent "
+                                      "dims, std 8 .. 1"}
     print(json.dumps({"ablation": out}), flush=True)
 
 

@@ -76,6 +76,18 @@ typedef struct {
     int64_t kmeans_sample_n;
     const int32_t *kmeans_init;   /* host [M][2][K] positions in the k-means sample, or NULL */
     uint32_t copies;              /* low-precision row copies to keep: bit 0 BF16, bit 1 FP8 E4M3 */
+    int32_t adaptive;             /* §7 Adaptive Subspace Decomposition: 0 equal split of §3; 1
+                                     contiguous subspaces of near-equal variance shares
+                                     (crisp_adaptive_bounds of the stored rows' per-dimension
+                                     variances over the covariance sample; needs D <= 256 M) */
+    int32_t block_dims;           /* §7 Partial Variance Redistribution: 0 the global test and
+                                     rotation of §4.1; b > 0 (a multiple of 4) cuts the dims into
+                                     contiguous blocks [jb, min((j+1)b, D)), tests each block's own
+                                     CEV (of its block of the sample covariance) against tau_cev
+                                     (rotate = 1: every block, 0: none) and rotates each chosen
+                                     block B by the orthogonal factor of the QR of G's diagonal
+                                     block G_BB (sign-fixed as in §3); R is block-diagonal, the
+                                     identity elsewhere, and the rows cost O(N sum w^2) */
 } crisp_build_params;
 
 /* Search parameters (Algorithm 1, §4.3, Table 1). */
@@ -128,15 +140,21 @@ typedef struct {
     const uint16_t *Xb;        /* [N][Dp] BF16 bits, or NULL */
     const uint8_t *X8;         /* [N][Dp] FP8 E4M3 codes, or NULL */
     const float *S8;           /* [N] FP8 row scales, or NULL */
+    const int32_t *sub;        /* [M+1] subspace boundaries: subspace m is [sub[m], sub[m+1]) */
+    int32_t block_dims;        /* build's block width (0: global rotation test) */
+    int32_t rotated_blocks;    /* blocks the block-wise test rotated */
 } crisp_index_info;
 
 /* ================================================================ index */
 
 /* Build the index of §4.1-§4.2 from X (device [N][D] float32, caller-owned,
  * copied): spectral check, rotation when CEV > tau_cev (the library keeps the
- * rotated copy and R), k-means per subspace half, cells, CSR, sign codes.
- * Synchronises `stream` before returning.  *out receives a new index.
- * EINVAL: N < 2, D < 2, M outside [1, D/2], K outside [2, 64], K > N. */
+ * rotated copy and R), k-means per subspace half, cells, CSR, sign codes;
+ * with params->block_dims or params->adaptive, the §7 extensions described
+ * beside those fields.  Synchronises `stream` before returning.  *out receives
+ * a new index.  EINVAL: N < 2, D < 2, M outside [1, D/2], K outside [2, 64],
+ * K > N, block_dims not a multiple of 4.  EUNSUPPORTED: a subspace half wider
+ * than 128 dims (equal split), or D > 256 M with adaptive = 1. */
 crisp_status crisp_build(const float *X, int64_t N, int32_t D, const crisp_build_params *params,
                          void *stream, crisp_index **out);
 
@@ -145,9 +163,11 @@ void crisp_free(crisp_index *index);
 
 /* Serialise an index into a host buffer.  With host_buf == NULL only the size
  * is written to *bytes.  Format: a 256-byte header (magic "CRISPIX1", then
- * int64 version=1, N, D, Dp, M, K, H, rotated, float64 CEV at byte 72), then
+ * int64 version, N, D, Dp, M, K, H, rotated, float64 CEV at byte 72), then
  * the arrays R32 (only if rotated), cent, offsets, ids, Xr, codes of
- * crisp_index_info, each starting at a multiple of 256 bytes.  Synchronous. */
+ * crisp_index_info, each starting at a multiple of 256 bytes.  Version 1
+ * has the equal split of §3; version 2 (other boundaries) adds a last
+ * section, the int32 boundaries sub[M+1].  Synchronous. */
 crisp_status crisp_index_export(const crisp_index *index, void *host_buf, size_t *bytes);
 
 /* Create an index from a blob in the export format (host memory), e.g. one
@@ -155,6 +175,9 @@ crisp_status crisp_index_export(const crisp_index *index, void *host_buf, size_t
 crisp_status crisp_index_import(const void *host_buf, size_t bytes, void *stream, crisp_index **out);
 
 crisp_status crisp_index_get_info(const crisp_index *index, crisp_index_info *out);
+
+/* The index's subspace boundaries into host memory (bounds: host [M+1] int32). */
+crisp_status crisp_index_get_bounds(const crisp_index *index, int32_t *bounds);
 
 /* Add low-precision copies of the stored rows to an index (bit 0: BF16, bit 1:
  * FP8 E4M3), as crisp_quantize_bf16 / crisp_quantize_e4m3 define them.  Copies
@@ -349,6 +372,21 @@ crisp_status crisp_eigvalsh(double *A, int32_t D, double *eig, void *stream);
 crisp_status crisp_cev(const float *X, int64_t N, int32_t D, int32_t ldx, const int64_t *rows, int64_t S,
                        double *cev, void *stream);
 
+/* §7 Adaptive Subspace Decomposition: per-dimension sample variance, FP64,
+ * mean-centred, divided by S-1, of the rows X[rows[s]] (X device [N][ldx]
+ * float32, rows device [S] int64 < N) into var (device [D] float64). */
+crisp_status crisp_column_variance(const float *X, int64_t N, int32_t D, int32_t ldx, const int64_t *rows,
+                                   int64_t S, double *var, void *stream);
+
+/* §7 Adaptive Subspace Decomposition (host arithmetic): boundaries (host
+ * [M+1] int32) of M contiguous subspaces with near-equal shares of the total
+ * variance (var: host [D] float64).  With V_j = var[0] + ... + var[j-1]
+ * (FP64, in order), boundary m is the last j with V_j <= m V_D / M, held to
+ * [b_{m-1} + 2, b_{m-1} + 256] and to what leaves every later subspace 2..256
+ * dims; zero total variance gives the equal split.  EINVAL unless
+ * 2M <= D <= 256 M. */
+crisp_status crisp_adaptive_bounds(const double *var, int32_t D, int32_t M, int32_t *bounds);
+
 /* B2 (§3 Randomized Orthogonal Rotation): R = Q diag(sign(diag R')) where
  * G = Q R' is the Householder QR of G (device [D][D] float64, row-major,
  * not modified).  R: device [D][D] float64. */
@@ -385,9 +423,11 @@ crisp_status crisp_kmeans(const float *T, int64_t S, int32_t ldt, int32_t off, i
 
 /* B3 (§3 u(x)): cells[m][n] = argmin_left*K + argmin_right of row n of Xr
  * (device [N][Dp]) in subspace m, SEQ distances, ties to the lowest index.
- * cent: device [M][2][K][H]; cells: device [M][N] uint16. */
+ * sub: host [M+1] subspace boundaries (NULL: the equal split floor(mD/M));
+ * cent: device [M][2][K][H]; cells: device [M][N] uint16.  EINVAL: a
+ * subspace outside 2..256 dims or a half wider than H. */
 crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                int32_t H, const float *cent, uint16_t *cells, void *stream);
+                                int32_t H, const int32_t *sub, const float *cent, uint16_t *cells, void *stream);
 
 /* B3 on the tensor cores (tcgen05, TF32 pipe), same result as
  * crisp_assign_cells bit for bit: the tensor cores score every centroid
@@ -397,7 +437,8 @@ crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t D
  * Dp a multiple of 32 (rows are fetched by TMA); K <= 64.  Synchronous on the
  * stream: ECUDA if a pipeline wait of the kernel timed out. */
 crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                   int32_t H, const float *cent, uint16_t *cells, void *stream);
+                                   int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
+                                   void *stream);
 
 /* B4 (§4.2 CSR): for one subspace, Offsets (device [K2+1] int32) and ids
  * (device [N] int32): ids grouped by ascending cell, ascending inside a cell.

@@ -15,6 +15,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcrisp_gb300.so")
 _lib = None
@@ -35,7 +37,7 @@ class BuildParams(C.Structure):
                 ("kmeans_iters", C.c_int32), ("kmeans_train", C.c_int64), ("seed", C.c_uint64),
                 ("cev_sample", C.c_void_p), ("cev_sample_n", C.c_int64), ("gaussian", C.c_void_p),
                 ("kmeans_sample", C.c_void_p), ("kmeans_sample_n", C.c_int64), ("kmeans_init", C.c_void_p),
-                ("copies", C.c_uint32)]
+                ("copies", C.c_uint32), ("adaptive", C.c_int32), ("block_dims", C.c_int32)]
 
 
 class SearchParams(C.Structure):
@@ -66,7 +68,8 @@ class IndexInfo(C.Structure):
                 ("H", C.c_int32), ("rotated", C.c_int32), ("cev", C.c_double), ("max_cell", C.c_int32),
                 ("id_tile_log2", C.c_int32), ("device_bytes", C.c_int64), ("R32", C.c_void_p),
                 ("cent", C.c_void_p), ("offsets", C.c_void_p), ("ids", C.c_void_p), ("Xr", C.c_void_p),
-                ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p), ("S8", C.c_void_p)]
+                ("codes", C.c_void_p), ("Xb", C.c_void_p), ("X8", C.c_void_p), ("S8", C.c_void_p),
+                ("sub", C.c_void_p), ("block_dims", C.c_int32), ("rotated_blocks", C.c_int32)]
 
 
 class RerankProfile(C.Structure):
@@ -80,6 +83,7 @@ _SIGS = {
     "crisp_index_export": [_P, _P, C.POINTER(_S)],
     "crisp_index_import": [_P, _S, _P, C.POINTER(_P)],
     "crisp_index_get_info": [_P, C.POINTER(IndexInfo)],
+    "crisp_index_get_bounds": [_P, _P],
     "crisp_index_add_copies": [_P, C.c_uint32, _P],
     "crisp_quantize_bf16": [_P, _I64, _I32, _P, _P],
     "crisp_quantize_e4m3": [_P, _I64, _I32, _P, _P, _P],
@@ -98,8 +102,10 @@ _SIGS = {
     "crisp_rotate_rows": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
     "crisp_rotate_rows_tc": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
     "crisp_kmeans": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P, _P],
-    "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
-    "crisp_assign_cells_tc": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
+    "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
+    "crisp_assign_cells_tc": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
+    "crisp_column_variance": [_P, _I64, _I32, _I32, _P, _I64, _P, _P],
+    "crisp_adaptive_bounds": [_P, _I32, _I32, _P],
     "crisp_csr_build": [_P, _I64, _I32, _P, _P, _P],
     "crisp_sign_codes": [_P, _I64, _I32, _P, _P],
     "crisp_half_dists": [_P, _P, _I32, _P, _P, _P],
@@ -243,6 +249,13 @@ def crisp_index_get_info(index: Index) -> IndexInfo:
     return info
 
 
+def crisp_index_get_bounds(index: Index) -> np.ndarray:
+    """Subspace boundaries [M+1] of an index (host int32)."""
+    out = np.empty(crisp_index_get_info(index).M + 1, np.int32)
+    _call("crisp_index_get_bounds", index, _ptr(out))
+    return out
+
+
 def crisp_index_add_copies(index, copies, stream=None):
     """Add BF16 (bit 0) and/or FP8 E4M3 (bit 1) copies of the stored rows."""
     _call("crisp_index_add_copies", index, copies, _stream(stream))
@@ -327,12 +340,31 @@ def crisp_kmeans(T, S, ldt, off, h, K, H, init, iters, Cout, stream=None):
     _call("crisp_kmeans", _ptr(T), S, ldt, off, h, K, H, _ptr(init), iters, _ptr(Cout), _stream(stream))
 
 
-def crisp_assign_cells(Xr, N, D, Dp, M, K, H, cent, cells, stream=None):
-    _call("crisp_assign_cells", _ptr(Xr), N, D, Dp, M, K, H, _ptr(cent), _ptr(cells), _stream(stream))
+def _host_i32(a):
+    return None if a is None else np.ascontiguousarray(np.asarray(a), dtype=np.int32)
 
 
-def crisp_assign_cells_tc(Xr, N, D, Dp, M, K, H, cent, cells, stream=None):
-    _call("crisp_assign_cells_tc", _ptr(Xr), N, D, Dp, M, K, H, _ptr(cent), _ptr(cells), _stream(stream))
+def crisp_assign_cells(Xr, N, D, Dp, M, K, H, cent, cells, stream=None, sub=None):
+    """``sub``: host subspace boundaries [M+1] (None: the equal split)."""
+    sb = _host_i32(sub)
+    _call("crisp_assign_cells", _ptr(Xr), N, D, Dp, M, K, H, _ptr(sb), _ptr(cent), _ptr(cells), _stream(stream))
+
+
+def crisp_assign_cells_tc(Xr, N, D, Dp, M, K, H, cent, cells, stream=None, sub=None):
+    sb = _host_i32(sub)
+    _call("crisp_assign_cells_tc", _ptr(Xr), N, D, Dp, M, K, H, _ptr(sb), _ptr(cent), _ptr(cells), _stream(stream))
+
+
+def crisp_column_variance(X, N, D, ldx, rows, S, var, stream=None):
+    _call("crisp_column_variance", _ptr(X), N, D, ldx, _ptr(rows), S, _ptr(var), _stream(stream))
+
+
+def crisp_adaptive_bounds(var, M) -> np.ndarray:
+    """Variance-aware boundaries [M+1] from host per-dimension variances."""
+    v = np.ascontiguousarray(np.asarray(var), dtype=np.float64)
+    out = np.empty(M + 1, np.int32)
+    _call("crisp_adaptive_bounds", _ptr(v), v.size, M, _ptr(out))
+    return out
 
 
 def crisp_csr_build(cells, N, K2, offsets, ids, stream=None):
@@ -399,10 +431,11 @@ def search_params(k=10, mode=0, rho=0.01, alpha=0.3, patience_factor=40, eps0=2.
 
 
 def build_params(M, K=50, tau_cev=0.85, rotate=-1, kmeans_iters=20, kmeans_train=100000, seed=0, draws=None,
-                 copies=0):
+                 copies=0, adaptive=0, block_dims=0):
     """BuildParams; ``draws`` (host numpy arrays: cev_sample, gaussian,
     kmeans_sample, kmeans_init) are referenced by the returned struct."""
-    p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None, copies)
+    p = BuildParams(M, K, tau_cev, rotate, kmeans_iters, kmeans_train, seed, None, 0, None, None, 0, None, copies,
+                    adaptive, block_dims)
     p._draws = draws          # the struct holds raw pointers into these arrays: keep them alive with it
     if draws is not None:
         p.cev_sample = draws.cev_sample.ctypes.data

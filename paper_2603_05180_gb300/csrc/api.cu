@@ -122,6 +122,67 @@ void crisp_subspace(int32_t D, int32_t M, int32_t m, int32_t *lo, int32_t *hl, i
     *hr = d - d / 2;
 }
 
+std::vector<int32_t> crisp_equal_bounds(int32_t D, int32_t M) {
+    std::vector<int32_t> b((size_t)M + 1);
+    for (int32_t m = 0; m <= M; ++m) b[m] = (int32_t)(((int64_t)m * D) / M);
+    return b;
+}
+
+int32_t crisp_bounds_half_max(const int32_t *sub, int32_t M) {
+    int32_t h = 0;
+    for (int32_t m = 0; m < M; ++m) {
+        const int32_t w = sub[m + 1] - sub[m];
+        h = std::max(h, w - w / 2);
+    }
+    return h;
+}
+
+bool crisp_bounds_valid(const int32_t *sub, int32_t D, int32_t M, const char *who) {
+    if (!sub || sub[0] != 0 || sub[M] != D) {
+        crisp_set_error("%s: subspace boundaries must run from 0 to D = %d", who, D);
+        return false;
+    }
+    for (int32_t m = 0; m < M; ++m) {
+        const int32_t w = sub[m + 1] - sub[m];
+        if (w < 2 || w > 256) {
+            crisp_set_error("%s: subspace %d has %d dims (need 2..256)", who, m, w);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Variance-aware boundaries (§7 Adaptive Subspace Decomposition): contiguous
+// subspaces with near-equal shares of the total variance.  V_j is the running
+// FP64 sum of var[0..j-1]; boundary m is the last j with V_j <= m V_D / M,
+// then held to [b_{m-1} + 2, b_{m-1} + 256] and to what leaves every later
+// subspace 2..256 dims.  Zero total variance gives the equal split.
+extern "C" crisp_status crisp_adaptive_bounds(const double *var, int32_t D, int32_t M, int32_t *bounds) {
+    CRISP_REQUIRE(var && bounds, "crisp_adaptive_bounds: null pointer");
+    CRISP_REQUIRE(M >= 1 && 2 * (int64_t)M <= D && D <= 256 * (int64_t)M,
+                  "crisp_adaptive_bounds: need 2M <= D <= 256M (D = %d, M = %d)", D, M);
+    std::vector<double> V((size_t)D + 1, 0.0);
+    for (int32_t d = 0; d < D; ++d) V[d + 1] = V[d] + var[d];
+    const double tot = V[D];
+    bounds[0] = 0;
+    int32_t j = 0;
+    for (int32_t m = 1; m < M; ++m) {
+        int32_t want;
+        if (tot > 0.0) {
+            const double t = (double)m * tot / (double)M;
+            while (j < D && V[j + 1] <= t) ++j;   // targets grow with m: the scan resumes
+            want = j;
+        } else {
+            want = (int32_t)(((int64_t)m * D) / M);
+        }
+        const int32_t prev = bounds[m - 1];
+        const int32_t lo = std::max(prev + 2, D - 256 * (M - m)), hi = std::min(prev + 256, D - 2 * (M - m));
+        bounds[m] = std::min(std::max(want, lo), hi);
+    }
+    bounds[M] = D;
+    return CRISP_OK;
+}
+
 // ------------------------------------------------------------ lifetime
 static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->R32);
@@ -136,6 +197,7 @@ static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->S8);
     cudaFree(ix->xn2);
     cudaFree(ix->mlp);
+    cudaFree(ix->sub);
 }
 
 extern "C" void crisp_free(crisp_index *ix) {
@@ -149,12 +211,14 @@ extern "C" void crisp_free(crisp_index *ix) {
     delete ix;
 }
 
-// Allocate the arrays of an index whose sizes are already set.
+// Allocate the arrays of an index whose sizes are already set (the centroids
+// only once H is known: an index build with variance-aware boundaries sets H
+// after the rows are stored).
 crisp_status crisp_alloc_index(crisp_index *ix) {
     const int64_t K2 = (int64_t)ix->K * ix->K;
     ix->T = (int32_t)((ix->N + CRISP_TILE - 1) / CRISP_TILE);
     struct A { void **p; size_t n; } arrs[] = {
-        {(void **)&ix->cent, sizeof(float) * (size_t)ix->M * 2 * ix->K * ix->H},
+        {(void **)&ix->cent, sizeof(float) * (size_t)ix->M * 2 * ix->K * ix->H},   // 0 while H = 0
         {(void **)&ix->offsets, sizeof(int32_t) * (size_t)ix->M * (K2 + 1)},
         {(void **)&ix->ids, sizeof(int32_t) * (size_t)ix->M * ix->N},
         {(void **)&ix->tile_off, sizeof(int32_t) * (size_t)ix->M * K2 * (ix->T + 1)},
@@ -162,6 +226,7 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
         {(void **)&ix->codes, sizeof(uint32_t) * (size_t)ix->N * (ix->Dp / 32)},
         {(void **)&ix->R32, ix->rotated ? sizeof(float) * (size_t)ix->D * ix->D : 0},
         {(void **)&ix->xn2, sizeof(float) * (size_t)ix->N},
+        {(void **)&ix->sub, sizeof(int32_t) * ((size_t)ix->M + 1)},
     };
     ix->bytes = 0;
     for (auto &a : arrs) {
@@ -172,8 +237,12 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
     return CRISP_OK;
 }
 
-// Derived tables: per-tile positions inside every cell list, largest cell.
+// Derived tables: per-tile positions inside every cell list, largest cell;
+// the subspace boundaries (host copy, the equal split if unset) go to the device.
 crisp_status crisp_finish_index(crisp_index *ix, cudaStream_t st) {
+    if (ix->sub_h.empty()) ix->sub_h = crisp_equal_bounds(ix->D, ix->M);
+    CRISP_CK(cudaMemcpyAsync(ix->sub, ix->sub_h.data(), sizeof(int32_t) * ix->sub_h.size(), cudaMemcpyHostToDevice,
+                             st));
     crisp_status s = launch_tile_offsets(ix, st);
     if (!s) s = launch_row_norms(ix, st);
     if (s) return s;
@@ -197,6 +266,13 @@ extern "C" crisp_status crisp_index_get_info(const crisp_index *ix, crisp_index_
     o->R32 = ix->R32; o->cent = ix->cent; o->offsets = ix->offsets; o->ids = ix->ids; o->Xr = ix->Xr;
     o->codes = ix->codes;
     o->Xb = ix->Xb; o->X8 = ix->X8; o->S8 = ix->S8;
+    o->sub = ix->sub; o->block_dims = ix->block_dims; o->rotated_blocks = ix->rotated_blocks;
+    return CRISP_OK;
+}
+
+extern "C" crisp_status crisp_index_get_bounds(const crisp_index *ix, int32_t *bounds) {
+    CRISP_REQUIRE(ix && bounds, "crisp_index_get_bounds: null pointer");
+    std::copy(ix->sub_h.begin(), ix->sub_h.end(), bounds);
     return CRISP_OK;
 }
 
@@ -204,17 +280,19 @@ extern "C" crisp_status crisp_index_get_info(const crisp_index *ix, crisp_index_
 static const char kMagic[8] = {'C', 'R', 'I', 'S', 'P', 'I', 'X', '1'};
 
 struct BlobLayout {
-    size_t off[6], len[6], total;   // R32, cent, offsets, ids, Xr, codes
+    size_t off[7], len[7], total;   // R32, cent, offsets, ids, Xr, codes, boundaries (version 2)
 };
 
-static BlobLayout blob_layout(int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H, int32_t rot) {
+static BlobLayout blob_layout(int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H, int32_t rot,
+                              int64_t version) {
     BlobLayout L;
     size_t K2 = (size_t)K * K;
-    size_t lens[6] = {rot ? sizeof(float) * (size_t)D * D : 0, sizeof(float) * (size_t)M * 2 * K * H,
+    size_t lens[7] = {rot ? sizeof(float) * (size_t)D * D : 0, sizeof(float) * (size_t)M * 2 * K * H,
                       sizeof(int32_t) * (size_t)M * (K2 + 1), sizeof(int32_t) * (size_t)M * N,
-                      sizeof(float) * (size_t)N * Dp, sizeof(uint32_t) * (size_t)N * (Dp / 32)};
+                      sizeof(float) * (size_t)N * Dp, sizeof(uint32_t) * (size_t)N * (Dp / 32),
+                      version >= 2 ? sizeof(int32_t) * ((size_t)M + 1) : 0};
     size_t pos = 256;
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 7; ++i) {
         L.off[i] = pos;
         L.len[i] = lens[i];
         pos += lens[i];
@@ -226,13 +304,15 @@ static BlobLayout blob_layout(int64_t N, int32_t D, int32_t Dp, int32_t M, int32
 
 extern "C" crisp_status crisp_index_export(const crisp_index *ix, void *host_buf, size_t *bytes) {
     CRISP_REQUIRE(ix && bytes, "crisp_index_export: null pointer");
-    BlobLayout L = blob_layout(ix->N, ix->D, ix->Dp, ix->M, ix->K, ix->H, ix->rotated);
+    // version 1 holds the equal split; other boundaries need version 2
+    const int64_t version = ix->sub_h == crisp_equal_bounds(ix->D, ix->M) ? 1 : 2;
+    BlobLayout L = blob_layout(ix->N, ix->D, ix->Dp, ix->M, ix->K, ix->H, ix->rotated, version);
     if (!host_buf) { *bytes = L.total; return CRISP_OK; }
     CRISP_REQUIRE(*bytes >= L.total, "crisp_index_export: buffer of %zu bytes, need %zu", *bytes, L.total);
     uint8_t *b = (uint8_t *)host_buf;
     memset(b, 0, L.total);
     memcpy(b, kMagic, 8);
-    int64_t h[8] = {1, ix->N, ix->D, ix->Dp, ix->M, ix->K, ix->H, ix->rotated};
+    int64_t h[8] = {version, ix->N, ix->D, ix->Dp, ix->M, ix->K, ix->H, ix->rotated};
     memcpy(b + 8, h, sizeof h);
     memcpy(b + 72, &ix->cev, sizeof(double));
     const void *src[6] = {ix->R32, ix->cent, ix->offsets, ix->ids, ix->Xr, ix->codes};
@@ -242,6 +322,7 @@ extern "C" crisp_status crisp_index_export(const crisp_index *ix, void *host_buf
     CRISP_CK(cudaDeviceSynchronize());
     for (int i = 0; i < 6; ++i)
         if (L.len[i]) CRISP_CK(cudaMemcpy(b + L.off[i], src[i], L.len[i], cudaMemcpyDeviceToHost));
+    if (L.len[6]) memcpy(b + L.off[6], ix->sub_h.data(), L.len[6]);
     cudaSetDevice(cur);
     *bytes = L.total;
     return CRISP_OK;
@@ -255,23 +336,25 @@ extern "C" crisp_status crisp_index_import(const void *host_buf, size_t bytes, v
     memcpy(h, b + 8, sizeof h);
     double cev;
     memcpy(&cev, b + 72, sizeof cev);
-    CRISP_REQUIRE(h[0] == 1, "crisp_index_import: unsupported version %lld", (long long)h[0]);
+    CRISP_REQUIRE(h[0] == 1 || h[0] == 2, "crisp_index_import: unsupported version %lld", (long long)h[0]);
     int64_t N = h[1];
     int32_t D = (int32_t)h[2], Dp = (int32_t)h[3], M = (int32_t)h[4], K = (int32_t)h[5], H = (int32_t)h[6];
     int32_t rot = (int32_t)h[7];
     CRISP_REQUIRE(N >= 1 && N < (1LL << 31) && D >= 2 && Dp == (D + 31) / 32 * 32 && M >= 1 && 2 * M <= D,
                   "crisp_index_import: inconsistent header");
     CRISP_REQUIRE(K >= 2 && K <= CRISP_KMAX, "crisp_index_import: K = %d outside [2, %d]", K, CRISP_KMAX);
-    int32_t hmax = 0;
-    for (int32_t m = 0; m < M; ++m) {
-        int32_t lo, hl, hr;
-        crisp_subspace(D, M, m, &lo, &hl, &hr);
-        hmax = std::max(hmax, std::max(hl, hr));
-    }
-    CRISP_REQUIRE(H == hmax, "crisp_index_import: H = %d, expected %d", H, hmax);
-    BlobLayout L = blob_layout(N, D, Dp, M, K, H, rot);
+    BlobLayout L = blob_layout(N, D, Dp, M, K, H, rot, h[0]);
     CRISP_REQUIRE(bytes >= L.total, "crisp_index_import: blob of %zu bytes, need %zu", bytes, L.total);
+    std::vector<int32_t> sub = crisp_equal_bounds(D, M);
+    if (L.len[6]) {
+        memcpy(sub.data(), b + L.off[6], L.len[6]);
+        if (!crisp_bounds_valid(sub.data(), D, M, "crisp_index_import")) return CRISP_EINVAL;
+    }
+    const int32_t hmax = crisp_bounds_half_max(sub.data(), M);
+    CRISP_REQUIRE(H == hmax, "crisp_index_import: H = %d, expected %d", H, hmax);
+    CRISP_REQUIRE(H <= 128, "crisp_index_import: subspace halves wider than 128 dims");
     crisp_index *ix = new crisp_index();
+    ix->sub_h = sub;
     ix->N = N; ix->D = D; ix->Dp = Dp; ix->M = M; ix->K = K; ix->H = H; ix->rotated = rot != 0; ix->cev = cev;
     cudaGetDevice(&ix->device);
     cudaStream_t st = as_stream(stream);

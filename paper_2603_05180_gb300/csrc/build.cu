@@ -4,6 +4,8 @@
 //       k_house_* / k_sturm          Householder tridiagonalisation + Sturm bisection (eigenvalues)
 //   B2  k_qr_*                       Householder QR of G, explicit Q, sign fix -> R
 //       (the product X R runs in the rotation kernel of query.cu)
+//       k_eye / k_put_block          block-diagonal R of the block-wise rotation (§7)
+//   §7  k_col_var                    per-dimension variance for the adaptive boundaries
 //   B3  k_km_assign / k_km_update    batched Lloyd k-means over every subspace half
 //       k_assign_cells               u_m(x) = cL*K + cR for all rows
 //   B4  k_csr_*                      stable counting sort of ids by cell: Offsets + ids
@@ -32,6 +34,39 @@ __global__ void k_col_mean(const float *__restrict__ X, int D, int ldx, const lo
     double acc = 0.0;
     for (long long s = 0; s < S; ++s) acc += (double)X[rows[s] * ldx + d];
     mu[d] = acc / (double)S;
+}
+
+// var[d] = sum over the sample of (x_d - mu_d)^2 / (S - 1), FP64 (the statistic
+// the variance-aware boundaries of §7 balance).
+__global__ void k_col_var(const float *__restrict__ X, int D, int ldx, const long long *__restrict__ rows, long long S,
+                          const double *__restrict__ mu, double *__restrict__ var) {
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= D) return;
+    const double m = mu[d];
+    double acc = 0.0;
+    for (long long s = 0; s < S; ++s) {
+        const double c = (double)X[rows[s] * ldx + d] - m;
+        acc += c * c;
+    }
+    var[d] = acc / (double)(S - 1);
+}
+
+// R = I (D x D, FP32)
+__global__ void k_eye(float *__restrict__ R, int D) {
+    const long long n = (long long)D * D;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        R[e] = (e / D == e % D) ? 1.0f : 0.0f;
+}
+
+// R[lo + i][lo + j] = B[i][j] (FP64 -> FP32) for a w x w block; Bf gets the FP32 block too.
+__global__ void k_put_block(const double *__restrict__ B, int w, float *__restrict__ R, int D, int lo,
+                            float *__restrict__ Bf) {
+    const long long n = (long long)w * w;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)B[e];
+        Bf[e] = v;
+        R[(long long)(lo + e / w) * D + lo + e % w] = v;
+    }
 }
 
 // cov[i][j] for 64x64 output tiles above the diagonal; 256 threads, 4x4 each.
@@ -378,8 +413,9 @@ __global__ void k_gather_rows(const float *__restrict__ X, int ld, const long lo
 }
 
 // cells[m][n] for every row n (blockIdx.x) and subspace m (blockIdx.y)
-__global__ void __launch_bounds__(128) k_assign_cells(const float *__restrict__ Xr, long long N, int D, int Dp, int M,
-                                                      int K, int H, const float *__restrict__ cent,
+__global__ void __launch_bounds__(128) k_assign_cells(const float *__restrict__ Xr, long long N, int Dp, int K, int H,
+                                                      const int32_t *__restrict__ sub,
+                                                      const float *__restrict__ cent,
                                                       uint16_t *__restrict__ cells) {
     extern __shared__ float Cs[];   // [2][K][H]
     const int m = blockIdx.y;
@@ -388,7 +424,7 @@ __global__ void __launch_bounds__(128) k_assign_cells(const float *__restrict__ 
     __syncthreads();
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    int a = (int)(((long long)m * D) / M), b = (int)(((long long)(m + 1) * D) / M);
+    int a = sub[m], b = sub[m + 1];
     int hl = (b - a) / 2, hr = (b - a) - hl;
     int arg[2];
 #pragma unroll
@@ -556,6 +592,23 @@ extern "C" crisp_status crisp_covariance(const float *X, int64_t N, int32_t D, i
     return CRISP_OK;
 }
 
+extern "C" crisp_status crisp_column_variance(const float *X, int64_t N, int32_t D, int32_t ldx, const int64_t *rows,
+                                              int64_t S, double *var, void *stream) {
+    CRISP_REQUIRE(X && rows && var, "crisp_column_variance: null pointer");
+    CRISP_REQUIRE(S >= 2 && D >= 1 && ldx >= D && N >= 1, "crisp_column_variance: need S >= 2, D >= 1, ldx >= D");
+    cudaStream_t st = as_stream(stream);
+    double *mu = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&mu, sizeof(double) * D, st));
+    k_col_mean<<<grid1(D, 128), 128, 0, st>>>(X, D, ldx, (const long long *)rows, S, mu);
+    CRISP_COUNT_LAUNCH();
+    k_col_var<<<grid1(D, 128), 128, 0, st>>>(X, D, ldx, (const long long *)rows, S, mu, var);
+    CRISP_COUNT_LAUNCH();
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(mu, st);
+    if (e != cudaSuccess) return crisp_cuda_fail(e, "variance kernels", __FILE__, __LINE__);
+    return CRISP_OK;
+}
+
 extern "C" crisp_status crisp_eigvalsh(double *A, int32_t D, double *eig, void *stream) {
     CRISP_REQUIRE(A && eig && D >= 1, "crisp_eigvalsh: bad arguments");
     cudaStream_t st = as_stream(stream);
@@ -652,12 +705,13 @@ extern "C" crisp_status crisp_rotation_from_gaussian(const double *G, int32_t D,
     return CRISP_OK;
 }
 
-// tc_D > 0: the jobs are the 2M subspace halves of a D-dim index in order and T
-// has the index's row pitch, so the assignment step runs on the tensor cores
-// (same assignments as k_km_assign, see crisp_assign_cells_tc).
+// tc_D > 0: the jobs are the 2M subspace halves (boundaries tc_sub, host) of a
+// D-dim index in order and T has the index's row pitch, so the assignment step
+// runs on the tensor cores (same assignments as k_km_assign, see
+// crisp_assign_cells_tc).
 static crisp_status kmeans_batched(const float *T, int64_t S, int32_t ldt, const std::vector<KmJob> &jobs, int32_t K,
                                    int32_t H, const int32_t *init_dev, int32_t iters, float *C, cudaStream_t st,
-                                   int32_t tc_D = 0) {
+                                   int32_t tc_D = 0, const int32_t *tc_sub = nullptr) {
     int nj = (int)jobs.size();
     KmJob *djobs = nullptr;
     int *asg = nullptr;
@@ -669,7 +723,7 @@ static crisp_status kmeans_batched(const float *T, int64_t S, int32_t ldt, const
     CRISP_CK(cudaFuncSetAttribute(k_km_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int it = 0; it < iters; ++it) {
         if (tc_D > 0) {
-            crisp_status s = crisp_tc_assign(T, S, tc_D, ldt, nj / 2, K, H, C, nullptr, asg, st);
+            crisp_status s = crisp_tc_assign(T, S, tc_D, ldt, nj / 2, K, H, tc_sub, C, nullptr, asg, st);
             if (s) {
                 cudaFreeAsync(asg, st);
                 cudaFreeAsync(djobs, st);
@@ -699,16 +753,41 @@ extern "C" crisp_status crisp_kmeans(const float *T, int64_t S, int32_t ldt, int
     return kmeans_batched(T, S, ldt, jobs, K, H, init, iters, C, as_stream(stream));
 }
 
+// Host boundaries [M+1] (NULL: the equal split), checked and copied.
+static crisp_status host_bounds(const int32_t *sub, int32_t D, int32_t M, int32_t H, const char *who,
+                                std::vector<int32_t> &out) {
+    if (sub) out.assign(sub, sub + M + 1);
+    else out = crisp_equal_bounds(D, M);
+    if (sub && !crisp_bounds_valid(out.data(), D, M, who)) return CRISP_EINVAL;
+    if (crisp_bounds_half_max(out.data(), M) > H) {
+        crisp_set_error("%s: a subspace half is wider than H = %d", who, H);
+        return CRISP_EINVAL;
+    }
+    return CRISP_OK;
+}
+
 extern "C" crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                           int32_t H, const float *cent, uint16_t *cells, void *stream) {
+                                           int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
+                                           void *stream) {
     CRISP_REQUIRE(Xr && cent && cells, "crisp_assign_cells: null pointer");
-    CRISP_REQUIRE(K >= 2 && K <= CRISP_KMAX && M >= 1 && 2 * M <= D && Dp >= D && N >= 1,
+    CRISP_REQUIRE(K >= 2 && K <= CRISP_KMAX && M >= 1 && 2 * M <= D && Dp >= D && N >= 1 && H <= 128,
                   "crisp_assign_cells: bad sizes");
+    std::vector<int32_t> hb;
+    crisp_status s = host_bounds(sub, D, M, H, "crisp_assign_cells", hb);
+    if (s) return s;
     cudaStream_t st = as_stream(stream);
+    int32_t *db = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&db, sizeof(int32_t) * hb.size(), st));
+    cudaError_t e = cudaMemcpyAsync(db, hb.data(), sizeof(int32_t) * hb.size(), cudaMemcpyHostToDevice, st);
     size_t smem = sizeof(float) * 2 * (size_t)K * H;
-    CRISP_CK(cudaFuncSetAttribute(k_assign_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_assign_cells<<<dim3(grid1(N, 128), M), 128, smem, st>>>(Xr, N, D, Dp, M, K, H, cent, cells);
-    CRISP_CK_LAUNCH();
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_assign_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        k_assign_cells<<<dim3(grid1(N, 128), M), 128, smem, st>>>(Xr, N, Dp, K, H, db, cent, cells);
+        CRISP_COUNT_LAUNCH();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(db, st);
+    if (e != cudaSuccess) return crisp_cuda_fail(e, "k_assign_cells", __FILE__, __LINE__);
     return CRISP_OK;
 }
 
@@ -776,18 +855,19 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
     CRISP_REQUIRE(p->rotate >= -1 && p->rotate <= 1, "crisp_build: rotate must be -1, 0 or 1");
     CRISP_REQUIRE(p->kmeans_iters >= 0, "crisp_build: kmeans_iters < 0");
     CRISP_REQUIRE((p->copies & ~3u) == 0, "crisp_build: copies must be a mask of 1 (BF16) and 2 (FP8)");
+    CRISP_REQUIRE(p->adaptive == 0 || p->adaptive == 1, "crisp_build: adaptive must be 0 or 1");
+    CRISP_REQUIRE(p->block_dims >= 0 && p->block_dims % 4 == 0, "crisp_build: block_dims must be a multiple of 4");
     cudaStream_t st = as_stream(stream);
     const int32_t M = p->M, K = p->K;
+    if (p->adaptive && D > 256 * (int64_t)M) {
+        crisp_set_error("crisp_build: variance-aware boundaries need D <= 256 M");
+        return CRISP_EUNSUPPORTED;
+    }
     crisp_index *ix = new crisp_index();
     ix->N = N; ix->D = D; ix->Dp = (D + 31) / 32 * 32; ix->M = M; ix->K = K;
-    int32_t H = 0;
-    for (int32_t m = 0; m < M; ++m) {
-        int32_t lo, hl, hr;
-        crisp_subspace(D, M, m, &lo, &hl, &hr);
-        H = std::max(H, std::max(hl, hr));
-    }
-    ix->H = H;
-    if (H > 128) {
+    ix->block_dims = p->block_dims;
+    ix->sub_h = crisp_equal_bounds(D, M);
+    if (!p->adaptive && crisp_bounds_half_max(ix->sub_h.data(), M) > 128) {
         delete ix;
         crisp_set_error("crisp_build: subspace halves wider than 128 dims (raise M)");
         return CRISP_EUNSUPPORTED;
@@ -816,26 +896,43 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
             if (e_ != cudaSuccess) s = crisp_cuda_fail(e_, #x, __FILE__, __LINE__); \
         }                                                                       \
     } while (0)
-    // ---- B1: CEV on the covariance sample
+    // ---- B1: CEV on the covariance sample (and, block-wise, per block)
     int64_t *drows = nullptr;
     BCUDA(cudaMallocAsync((void **)&drows, sizeof(int64_t) * cs.size(), st));
     BCUDA(cudaMemcpyAsync(drows, cs.data(), sizeof(int64_t) * cs.size(), cudaMemcpyHostToDevice, st));
     double cev = 0.0;
     BSTEP(crisp_cev(X, N, D, D, drows, (int64_t)cs.size(), &cev, st));
-    if (drows) cudaFreeAsync(drows, st);
     ix->cev = cev;
-    ix->rotated = (p->rotate == 1) || (p->rotate == -1 && cev > p->tau_cev);
+    std::vector<std::pair<int32_t, int32_t>> rot_blocks;   // [lo, hi) of the blocks to rotate
+    if (p->block_dims > 0) {
+        // §7 block-wise redistribution: each block of block_dims dims takes the
+        // §4.1 test on its own covariance (the block of the sample covariance)
+        for (int32_t lo = 0; lo < D && s == CRISP_OK; lo += p->block_dims) {
+            const int32_t hi = std::min(D, lo + p->block_dims);
+            double cb = 0.0;
+            BSTEP(crisp_cev(X + lo, N, hi - lo, D, drows, (int64_t)cs.size(), &cb, st));
+            if (p->rotate == 1 || (p->rotate == -1 && cb > p->tau_cev)) rot_blocks.push_back({lo, hi});
+        }
+        ix->rotated = !rot_blocks.empty();
+        ix->rotated_blocks = (int32_t)rot_blocks.size();
+    } else {
+        ix->rotated = (p->rotate == 1) || (p->rotate == -1 && cev > p->tau_cev);
+    }
+    const int32_t H_eq = crisp_bounds_half_max(ix->sub_h.data(), M);
+    ix->H = p->adaptive ? 0 : H_eq;   // centroids are allocated once H is known
     BSTEP(crisp_alloc_index(ix));
     // ---- B2: rotation (R from the QR of G), X' = X R; else zero-padded copy
-    if (s == CRISP_OK && ix->rotated) {
-        std::vector<double> G;
-        const double *Gh = p->gaussian;
-        if (!Gh) {
-            G.resize((size_t)D * D);
-            std::normal_distribution<double> nd(0.0, 1.0);
-            for (auto &g : G) g = nd(rng);
-            Gh = G.data();
-        }
+    std::vector<double> G;
+    const double *Gh = p->gaussian;
+    if (s == CRISP_OK && ix->rotated && !Gh) {
+        G.resize((size_t)D * D);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        for (auto &g : G) g = nd(rng);
+        Gh = G.data();
+    }
+    // TMA reads of X need 16-byte aligned rows: other shapes go through a zero-padded copy
+    const bool x_aligned = ((uintptr_t)X % 16) == 0 && D % 4 == 0;
+    if (s == CRISP_OK && ix->rotated && p->block_dims == 0) {
         double *dG = nullptr;
         BCUDA(cudaMallocAsync((void **)&dG, sizeof(double) * 2 * (size_t)D * D, st));
         BCUDA(cudaMemcpyAsync(dG, Gh, sizeof(double) * (size_t)D * D, cudaMemcpyHostToDevice, st));
@@ -846,9 +943,8 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
         }
         BCUDA(cudaStreamSynchronize(st));   // G (host) must outlive its copy
         if (dG) cudaFreeAsync(dG, st);
-        // X' = X R on the tensor cores; TMA needs 16-byte aligned rows, so other
-        // shapes go through a zero-padded copy first
-        if (((uintptr_t)X % 16) == 0 && D % 4 == 0) {
+        // X' = X R on the tensor cores
+        if (x_aligned) {
             BSTEP(crisp_rotate_rows_tc(X, N, D, D, ix->R32, ix->Xr, ix->Dp, st));
         } else if (s == CRISP_OK) {
             float *Xp = nullptr;
@@ -857,9 +953,70 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
             BSTEP(crisp_rotate_rows_tc(Xp, N, D, ix->Dp, ix->R32, ix->Xr, ix->Dp, st));
             if (Xp) cudaFreeAsync(Xp, st);
         }
+    } else if (s == CRISP_OK && ix->rotated) {
+        // block-diagonal R: identity, then each rotated block's own rotation from
+        // its diagonal block of G; the stored rows are the padded copy with each
+        // rotated block's columns replaced by x_B R_B (O(N sum w^2) on the tensor cores)
+        k_eye<<<(unsigned)std::min<long long>(grid1((long long)D * D, 256), 152LL * 32), 256, 0, st>>>(ix->R32, D);
+        BCUDA(cudaGetLastError());
+        BSTEP(launch_pad_rows(X, N, D, D, ix->Xr, ix->Dp, st));
+        const float *src = X;
+        int32_t lds = D;
+        float *Xp = nullptr;
+        if (!x_aligned && s == CRISP_OK) {
+            BCUDA(cudaMallocAsync((void **)&Xp, sizeof(float) * (size_t)N * ix->Dp, st));
+            BSTEP(launch_pad_rows(X, N, D, D, Xp, ix->Dp, st));
+            src = Xp;
+            lds = ix->Dp;
+        }
+        int32_t wmax = 0;
+        for (auto &bk : rot_blocks) wmax = std::max(wmax, bk.second - bk.first);
+        double *dG = nullptr;
+        float *Bf = nullptr;
+        BCUDA(cudaMallocAsync((void **)&dG, sizeof(double) * 2 * (size_t)wmax * wmax, st));
+        BCUDA(cudaMallocAsync((void **)&Bf, sizeof(float) * (size_t)wmax * wmax, st));
+        std::vector<double> Gb((size_t)wmax * wmax);
+        for (auto &bk : rot_blocks) {
+            if (s != CRISP_OK) break;
+            const int32_t lo = bk.first, w = bk.second - bk.first;
+            for (int32_t i = 0; i < w; ++i)
+                for (int32_t j = 0; j < w; ++j) Gb[(size_t)i * w + j] = Gh[(size_t)(lo + i) * D + lo + j];
+            BCUDA(cudaMemcpyAsync(dG, Gb.data(), sizeof(double) * (size_t)w * w, cudaMemcpyHostToDevice, st));
+            BSTEP(crisp_rotation_from_gaussian(dG, w, dG + (size_t)w * w, st));
+            if (s == CRISP_OK) {
+                k_put_block<<<(unsigned)std::min<long long>(grid1((long long)w * w, 256), 152LL * 32), 256, 0, st>>>(
+                    dG + (size_t)w * w, w, ix->R32, D, lo, Bf);
+                BCUDA(cudaGetLastError());
+            }
+            BSTEP(crisp_rotate_rows_tc_cols(src + lo, N, w, lds, Bf, ix->Xr + lo, ix->Dp, w, st));
+            BCUDA(cudaStreamSynchronize(st));   // Gb and Bf are reused by the next block
+        }
+        if (dG) cudaFreeAsync(dG, st);
+        if (Bf) cudaFreeAsync(Bf, st);
+        if (Xp) cudaFreeAsync(Xp, st);
     } else if (s == CRISP_OK) {
         BSTEP(launch_pad_rows(X, N, D, D, ix->Xr, ix->Dp, st));
     }
+    // ---- §7 variance-aware subspace boundaries from the stored rows' variances
+    if (s == CRISP_OK && p->adaptive) {
+        double *dvar = nullptr;
+        std::vector<double> var(D);
+        BCUDA(cudaMallocAsync((void **)&dvar, sizeof(double) * D, st));
+        BSTEP(crisp_column_variance(ix->Xr, N, D, ix->Dp, drows, (int64_t)cs.size(), dvar, st));
+        BCUDA(cudaMemcpyAsync(var.data(), dvar, sizeof(double) * D, cudaMemcpyDeviceToHost, st));
+        BCUDA(cudaStreamSynchronize(st));
+        if (dvar) cudaFreeAsync(dvar, st);
+        BSTEP(crisp_adaptive_bounds(var.data(), D, M, ix->sub_h.data()));
+        if (s == CRISP_OK) {
+            ix->H = crisp_bounds_half_max(ix->sub_h.data(), M);
+            const size_t cb = sizeof(float) * (size_t)M * 2 * K * ix->H;
+            BCUDA(cudaMalloc((void **)&ix->cent, cb));
+            if (s == CRISP_OK) ix->bytes += (int64_t)cb;
+        }
+    }
+    if (drows) cudaFreeAsync(drows, st);
+    const int32_t H = ix->H;
+    const int32_t *sub = ix->sub_h.data();
     // ---- B3: k-means per subspace half on the training sample, then cells
     std::vector<int64_t> ks;
     if (p->kmeans_sample) ks.assign(p->kmeans_sample, p->kmeans_sample + p->kmeans_sample_n);
@@ -878,10 +1035,9 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
         if (s == CRISP_OK && (v < 0 || v >= TS)) { crisp_set_error("crisp_build: k-means init out of range"); s = CRISP_EINVAL; }
     std::vector<KmJob> jobs;
     for (int32_t m = 0; m < M; ++m) {
-        int32_t lo, hl, hr;
-        crisp_subspace(D, M, m, &lo, &hl, &hr);
+        const int32_t lo = sub[m], w = sub[m + 1] - sub[m], hl = w / 2;
         jobs.push_back({lo, hl});
-        jobs.push_back({lo + hl, hr});
+        jobs.push_back({lo + hl, w - hl});
     }
     if (s == CRISP_OK) {
         size_t tb = sizeof(float) * (size_t)TS * ix->Dp, rb = sizeof(int64_t) * (size_t)TS,
@@ -903,8 +1059,8 @@ extern "C" crisp_status crisp_build(const float *X, int64_t N, int32_t D, const 
         }
         // centroids are laid out [M][2][K][H] = jobs in order
         // Lloyd's assignment steps and the final cells on the tensor cores
-        BSTEP(kmeans_batched(T, TS, ix->Dp, jobs, K, H, dinit, p->kmeans_iters, ix->cent, st, D));
-        BSTEP(crisp_tc_assign(ix->Xr, N, D, ix->Dp, M, K, H, ix->cent, cells, nullptr, st));
+        BSTEP(kmeans_batched(T, TS, ix->Dp, jobs, K, H, dinit, p->kmeans_iters, ix->cent, st, D, sub));
+        BSTEP(crisp_tc_assign(ix->Xr, N, D, ix->Dp, M, K, H, sub, ix->cent, cells, nullptr, st));
         // ---- B4: CSR per subspace
         for (int32_t m = 0; m < M && s == CRISP_OK; ++m)
             BSTEP(crisp_csr_build(cells + (size_t)m * N, N, K * K, ix->offsets + (size_t)m * (K * K + 1),

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "crisp.h"
 
@@ -37,6 +38,10 @@ struct crisp_index {
     float *xn2 = nullptr;          // [N] |x|^2 of the stored rows, FP64 sum rounded to FP32
     float *mlp = nullptr;          // learned-depth model (F = 2M + 68 -> H -> H -> 2), optional
     int32_t mlp_H = 0;
+    int32_t *sub = nullptr;        // [M+1] subspace boundaries (device)
+    std::vector<int32_t> sub_h;    // the same boundaries on the host
+    int32_t block_dims = 0;        // block-wise rotation: block width (0: global test)
+    int32_t rotated_blocks = 0;    // blocks rotated by the block-wise test
     int device = 0;
     int64_t bytes = 0;
 };
@@ -55,6 +60,7 @@ struct IxView {
     const uint8_t *X8;
     const float *S8;
     const float *xn2;
+    const int32_t *sub;
 };
 
 static inline IxView ix_view(const crisp_index *ix) {
@@ -64,6 +70,7 @@ static inline IxView ix_view(const crisp_index *ix) {
     v.Xr = ix->Xr; v.codes = ix->codes;
     v.Xb = ix->Xb; v.X8 = ix->X8; v.S8 = ix->S8;
     v.xn2 = ix->xn2;
+    v.sub = ix->sub;
     return v;
 }
 
@@ -110,6 +117,12 @@ static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStre
 int32_t crisp_tau(double alpha, int32_t M);
 int64_t crisp_budget(double rho, int64_t N);
 void crisp_subspace(int32_t D, int32_t M, int32_t m, int32_t *lo, int32_t *hl, int32_t *hr);
+// Boundaries of the equal split, sub[m] = floor(mD/M), sub[M] = D.
+std::vector<int32_t> crisp_equal_bounds(int32_t D, int32_t M);
+// Widest half over the subspaces [sub[m], sub[m+1]) (half widths floor(w/2), w - floor(w/2)).
+int32_t crisp_bounds_half_max(const int32_t *sub, int32_t M);
+// False (with the error set) unless sub[0] = 0, sub[M] = D and every width is in [2, 256].
+bool crisp_bounds_valid(const int32_t *sub, int32_t D, int32_t M, const char *who);
 
 // ------------------------------------------ stream-ordered scratch memory
 // A memory pool per device that keeps its memory between calls.
@@ -119,8 +132,12 @@ void crisp_scratch_free(void *p, cudaStream_t st);
 // ------------------------------------------------ internal launchers
 // Tensor-core cell assignment (tc.cu): cells [M][N], or per-half centroid
 // indices asg [2M][N] when asg is not null.  Synchronous on st.
+// sub: host [M+1] subspace boundaries.
 crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
-                             const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st);
+                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st);
+// X' = X R on the tensor cores writing only Y[:, 0:ncols] (ncols <= D rounded up to 32).
+crisp_status crisp_rotate_rows_tc_cols(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                                       int32_t ldy, int32_t ncols, cudaStream_t st);
 crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, float *Y, int32_t ldy,
                              cudaStream_t st);
 crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);

@@ -27,8 +27,10 @@
 
 namespace {
 
-__device__ __forceinline__ void subspace_dev(int D, int M, int m, int *lo, int *hl, int *hr) {
-    int a = (int)(((long long)m * D) / M), b = (int)(((long long)(m + 1) * D) / M);
+// Subspace m covers dims [sub[m], sub[m+1]) (the index's boundaries: the equal
+// split or the variance-aware ones); halves floor(w/2) and w - floor(w/2).
+__device__ __forceinline__ void subspace_dev(const int32_t *__restrict__ sub, int m, int *lo, int *hl, int *hr) {
+    int a = sub[m], b = sub[m + 1];
     int d = b - a;
     *lo = a;
     *hl = d / 2;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) k_activate(IxView ix, const fl
     int *offs = reinterpret_cast<int *>(CtR + H * K);
     float *wbase = reinterpret_cast<float *>(offs + K2 + 1);
     int lo, hl, hr;
-    subspace_dev(ix.D, M, m, &lo, &hl, &hr);
+    subspace_dev(ix.sub, m, &lo, &hl, &hr);
     const float *cL = ix.cent + ((long long)m * 2 + 0) * K * H;
     const float *cR = ix.cent + ((long long)m * 2 + 1) * K * H;
     for (int e = threadIdx.x; e < K * H; e += blockDim.x) {

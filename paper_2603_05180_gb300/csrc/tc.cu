@@ -254,15 +254,22 @@ size_t rot_smem(int BN) { return 1024 + 2 * (2 * (size_t)TC_BM * 128 + 2 * (size
 
 extern "C" crisp_status crisp_rotate_rows_tc(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
                                              int32_t ldy, void *stream) {
+    return crisp_rotate_rows_tc_cols(X, N, D, ldx, R, Y, ldy, -1, as_stream(stream));
+}
+
+// ncols < 0: Y[:, 0:min(ldy, Dp)] with columns D.. zero; else Y[:, 0:ncols] only
+// (a block of columns inside a wider row).
+crisp_status crisp_rotate_rows_tc_cols(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
+                                       int32_t ldy, int32_t ncols_req, cudaStream_t st) {
     CRISP_REQUIRE(N >= 0 && D >= 1 && ldx >= D && ldy >= D, "crisp_rotate_rows_tc: bad sizes");
     CRISP_REQUIRE(N == 0 || (X && R && Y), "crisp_rotate_rows_tc: null pointer");
     CRISP_REQUIRE((const void *)X != (const void *)Y, "crisp_rotate_rows_tc: Y overlaps X");
     CRISP_REQUIRE(((uintptr_t)X % 16) == 0 && ((size_t)ldx * sizeof(float)) % 16 == 0,
                   "crisp_rotate_rows_tc: X must be 16-byte aligned with a row pitch of a multiple of 4 floats");
     if (N == 0) return CRISP_OK;
-    cudaStream_t st = as_stream(stream);
     const int Dp = (D + TC_BK - 1) / TC_BK * TC_BK;
-    const int ncols = ldy < Dp ? ldy : Dp;              // columns D..ncols-1 come out zero
+    const int ncols = ncols_req >= 0 ? std::min(ncols_req, ldy < Dp ? ldy : Dp)
+                                     : (ldy < Dp ? ldy : Dp);   // columns D..ncols-1 come out zero
     const int nt = (ncols + 255) / 256;
     const int BN = ((ncols + nt - 1) / nt + 15) / 16 * 16;
     float *bt = nullptr;
@@ -347,6 +354,7 @@ struct AsgArgs {
     long long N;
     int D, Dp, M, K, H, KB;
     const float *Xr;
+    const int32_t *sub;     // [M+1] subspace boundaries
     const float *cent;      // [M][2][K][H]
     const float *cn2;       // [M][2][64] |c|^2 (FP32)
     const float *cn;        // [M][2][64] |c|
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = (int)(blockIdx.x % (unsigned)a.M);
     const long long row0 = (long long)(blockIdx.x / (unsigned)a.M) * TC_BM;
-    const int lo = (int)(((long long)m * a.D) / a.M), hi_ = (int)(((long long)(m + 1) * a.D) / a.M);
+    const int lo = a.sub[m], hi_ = a.sub[m + 1];
     const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl, HS = hr;     // hr >= hl
     const int base = lo & ~(TC_BK - 1);
     const int nk = (hi_ - base + TC_BK - 1) / TC_BK;
@@ -551,8 +559,8 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
 // Bm [M][2][64][KB*32]: row c of half h holds centroid c at the Xr columns of
 // that half (relative to the subspace's 32-aligned base column), zeros
 // elsewhere; cn2 / cn: |c|^2 and |c| (zero rows past K).
-__global__ void k_asg_prep(const float *__restrict__ cent, int D, int M, int K, int H, int KB, float *__restrict__ Bm,
-                           float *__restrict__ cn2, float *__restrict__ cn) {
+__global__ void k_asg_prep(const float *__restrict__ cent, const int32_t *__restrict__ sub, int M, int K, int H, int KB,
+                           float *__restrict__ Bm, float *__restrict__ cn2, float *__restrict__ cn) {
     const int W = KB * TC_BK;
     const long long tot = (long long)M * 2 * AS_KPAD * W;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
@@ -560,7 +568,7 @@ __global__ void k_asg_prep(const float *__restrict__ cent, int D, int M, int K, 
         const int j = (int)(e % W);
         const long long rowi = e / W;
         const int c = (int)(rowi % AS_KPAD), half = (int)((rowi / AS_KPAD) % 2), m = (int)(rowi / (2 * AS_KPAD));
-        const int lo = (int)(((long long)m * D) / M), hi_ = (int)(((long long)(m + 1) * D) / M);
+        const int lo = sub[m], hi_ = sub[m + 1];
         const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl;
         const int start = lo + (half ? hl : 0) - (lo & ~(TC_BK - 1)), h = half ? hr : hl;
         float v = 0.0f;
@@ -582,27 +590,34 @@ __global__ void k_asg_prep(const float *__restrict__ cent, int D, int M, int K, 
 }  // namespace
 
 crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
-                             const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st) {
-    CRISP_REQUIRE(Xr && cent && (cells || asg), "crisp_assign_cells_tc: null pointer");
+                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st) {
+    CRISP_REQUIRE(Xr && sub && cent && (cells || asg), "crisp_assign_cells_tc: null pointer");
     CRISP_REQUIRE(K >= 2 && K <= AS_KPAD && M >= 1 && 2 * M <= D && Dp >= D && N >= 1 && H >= 1,
                   "crisp_assign_cells_tc: bad sizes");
     CRISP_REQUIRE(Dp % TC_BK == 0 && ((uintptr_t)Xr % 16) == 0,
                   "crisp_assign_cells_tc: Xr must be 16-byte aligned with Dp a multiple of 32");
-    int KB = 1;
+    CRISP_REQUIRE(crisp_bounds_valid(sub, D, M, "crisp_assign_cells_tc") && crisp_bounds_half_max(sub, M) <= H,
+                  "crisp_assign_cells_tc: subspace boundaries do not fit H = %d", H);
+    int KB = 1, HS = 1;
     for (int m = 0; m < M; ++m) {
-        const int lo = (int)(((long long)m * D) / M), hi_ = (int)(((long long)(m + 1) * D) / M);
+        const int lo = sub[m], hi_ = sub[m + 1];
         KB = std::max(KB, (hi_ - (lo & ~(TC_BK - 1)) + TC_BK - 1) / TC_BK);
+        HS = std::max(HS, (hi_ - lo) - (hi_ - lo) / 2);
     }
     const size_t bm_n = (size_t)M * 2 * AS_KPAD * KB * TC_BK, nn = (size_t)M * 2 * AS_KPAD;
     float *buf = nullptr;
-    CRISP_CK(cudaMallocAsync((void **)&buf, sizeof(float) * (bm_n + 2 * nn), st));
+    CRISP_CK(cudaMallocAsync((void **)&buf, sizeof(float) * (bm_n + 2 * nn) + sizeof(int32_t) * ((size_t)M + 1), st));
     float *Bm = buf, *cn2 = buf + bm_n, *cn = cn2 + nn;
+    int32_t *dsub = (int32_t *)(cn + nn);
+    const std::vector<int32_t> hsub(sub, sub + M + 1);   // pageable: the copy is staged before return
     crisp_status s = CRISP_OK;
     do {
-        k_asg_prep<<<(unsigned)std::min<size_t>((bm_n + 255) / 256, 4096), 256, 0, st>>>(cent, D, M, K, H, KB, Bm, cn2,
-                                                                                         cn);
+        cudaError_t e = cudaMemcpyAsync(dsub, hsub.data(), sizeof(int32_t) * hsub.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__); break; }
+        k_asg_prep<<<(unsigned)std::min<size_t>((bm_n + 255) / 256, 4096), 256, 0, st>>>(cent, dsub, M, K, H, KB, Bm,
+                                                                                         cn2, cn);
         CRISP_COUNT_LAUNCH();
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_asg_prep", __FILE__, __LINE__); break; }
         CUtensorMap mx, mb;
         if (!make_map(&mx, Xr, N, Dp, Dp, TC_BM) || !make_map(&mb, Bm, (long long)M * 2 * AS_KPAD, KB * TC_BK,
@@ -610,11 +625,6 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
             crisp_set_error("crisp_assign_cells_tc: tensor map encoding failed");
             s = CRISP_ECUDA;
             break;
-        }
-        int HS = 1;
-        for (int m = 0; m < M; ++m) {
-            const int w = (int)(((long long)(m + 1) * D) / M) - (int)(((long long)m * D) / M);
-            HS = std::max(HS, w - w / 2);
         }
         const size_t smem = asg_smem_bytes(K, HS);
         e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -628,7 +638,7 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
             s = CRISP_EINVAL;
             break;
         }
-        AsgArgs a{N, D, Dp, M, K, H, KB, Xr, cent, cn2, cn, cells, asg};
+        AsgArgs a{N, D, Dp, M, K, H, KB, Xr, dsub, cent, cn2, cn, cells, asg};
         k_assign_tc<<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mb, a);
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
@@ -647,7 +657,9 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
 }
 
 extern "C" crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                              int32_t H, const float *cent, uint16_t *cells, void *stream) {
-    CRISP_REQUIRE(cells, "crisp_assign_cells_tc: null pointer");
-    return crisp_tc_assign(Xr, N, D, Dp, M, K, H, cent, cells, nullptr, as_stream(stream));
+                                              int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
+                                              void *stream) {
+    CRISP_REQUIRE(cells && M >= 1, "crisp_assign_cells_tc: null pointer or M < 1");
+    const std::vector<int32_t> eq = crisp_equal_bounds(D, M);
+    return crisp_tc_assign(Xr, N, D, Dp, M, K, H, sub ? sub : eq.data(), cent, cells, nullptr, as_stream(stream));
 }

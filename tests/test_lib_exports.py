@@ -101,3 +101,23 @@ def test_library_readings_of_tau_and_budget_equal_the_oracle(libc):
     for rho in (1e-9, 0.001, 0.002, 0.01, 0.03, 0.06, 0.3, 1.0):
         for N in (1, 300, 20000, 1_000_000, 5_000_000):
             assert crisp.budget(rho, N) == oracle.budget(rho, N), (rho, N)
+
+
+def test_library_adaptive_bounds_equal_the_oracle(libc):
+    """The library's variance-aware boundaries (host arithmetic) equal the
+    oracle's reading on random, skewed, flat and zero variance profiles."""
+    import numpy as np
+
+    import oracle
+    import paper_2603_05180_gb300 as crisp
+
+    r = np.random.default_rng(8)
+    cases = [(np.ones(960), 20), (np.zeros(300), 7), ([0.0] * 15 + [100.0], 4), ([1.0] * 10 + [0.0] * 490, 2)]
+    for _ in range(150):
+        D = int(r.integers(8, 1500))
+        M = int(r.integers(max(1, -(-D // 256)), D // 2 + 1))
+        cases.append((r.exponential(1.0, D) ** r.uniform(0.3, 5.0), M))
+    for v, M in cases:
+        assert np.array_equal(crisp.crisp_adaptive_bounds(v, M), oracle.adaptive_bounds(v, M))
+    with pytest.raises(crisp.CrispError):
+        crisp.crisp_adaptive_bounds(np.ones(600), 2)      # D > 256 M
