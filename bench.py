@@ -81,15 +81,22 @@ def load_peaks():
 TF32_PER_BF16 = 1.1 / 2.25
 
 
-def tf32_peak():
-    """TF32 tensor peak (TFLOP/s) for a kernel timed inside a long step: the
-    measured sustained BF16 GEMM rate times the nominal TF32 / BF16 ratio."""
+def bf16_peak():
+    """BF16 tensor peak (TFLOP/s) for a kernel timed inside a long step: the
+    measured sustained BF16 GEMM rate."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * TF32_PER_BF16, "measured"
-    return 1700.0 * TF32_PER_BF16, "fallback"
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    return 1700.0, "fallback"
+
+
+def tf32_peak():
+    """TF32 tensor peak (TFLOP/s) for a kernel timed inside a long step: the
+    measured sustained BF16 GEMM rate times the nominal TF32 / BF16 ratio."""
+    b, kind = bf16_peak()
+    return b * TF32_PER_BF16, kind
 
 
 # ------------------------------------------------------------------ clocks
@@ -418,28 +425,56 @@ def run_crisp(args):
             variants[name] = {"precision": name, "shortlist": chosen["shortlist"], "value": q_v, "recall_at_10": r_v,
                               "ms_per_step": ms_v, "speedup_vs_fp32": q_v / qps * world}
 
+    leg_s = {}
+    # ---- the same step with the re-rank bounds from one TF32 pass over the FP32
+    # rows instead of one BF16 pass over the BF16 copy (identical results)
+    tf32_rows = None
+    if info.Xb:
+        t_leg = time.perf_counter()
+        os.environ["CRISP_RERANK_TF32"] = "1"
+        try:
+            q_t, r_t, ms_t = timed(point, args.steps)
+        finally:
+            del os.environ["CRISP_RERANK_TF32"]
+        tf32_rows = {"value": q_t, "recall_at_10": r_t, "ms_per_step": ms_t,
+                     "note": "re-rank bounds from one TF32 pass over the FP32 rows (CRISP_RERANK_TF32=1); the "
+                             "headline value takes them from one BF16 pass over the index's BF16 copy; both return "
+                             "the exact FP32 (CR32) top-k"}
+        leg_s["tf32_rows"] = time.perf_counter() - t_leg
+
     # ---- learned depths + BF16 (F1): train the model on queries of the same law
     learned = None
     if not args.no_learned:
+        t_leg = time.perf_counter()
         learned = learned_leg(torch, crisp, synthetic, ix, info, X, args, point, search, timed, qps, world, dev)
+        leg_s["learned"] = time.perf_counter() - t_leg
 
     # ---- both modes at k = 10 and k = 100 on the same index
     modes = None
     if not args.no_modes:
+        t_leg = time.perf_counter()
         modes = modes_leg(torch, crisp, ix, X, Q, args, dev)
+        leg_s["modes"] = time.perf_counter() - t_leg
 
-    # ---- the vMF (D = 3072) and low-rank (D = 4096) configurations, each on its own index
+    # ---- the vMF (D = 3072) and low-rank (D = 4096) configurations, each on its
+    # own index (with --full or their own flags: several minutes each)
     big = {}
     if world == 1:
-        if not args.no_vmf:
+        if args.vmf or (args.full and not args.no_vmf):
+            t_leg = time.perf_counter()
             big["vmf_3072"] = vmf_leg(args, torch, crisp, synthetic, dev, flush, stream)
-        if not args.no_lowrank:
+            leg_s["vmf_3072"] = time.perf_counter() - t_leg
+        if args.lowrank or (args.full and not args.no_lowrank):
+            t_leg = time.perf_counter()
             big["lowrank_4096"] = lowrank_leg(args, torch, crisp, synthetic, dev, flush, stream)
+            leg_s["lowrank_4096"] = time.perf_counter() - t_leg
 
-    # ---- continuous-batching serving (its own 5M x 1024 index)
+    # ---- continuous-batching serving (its own 5M x 1024 index; --full or --serve)
     serving = None
-    if not args.no_serve and world == 1:
+    if (args.serve or (args.full and not args.no_serve)) and world == 1:
+        t_leg = time.perf_counter()
         serving = serving_leg(args, torch, crisp, synthetic, dev)
+        leg_s["serving"] = time.perf_counter() - t_leg
 
     # ---- end to end through the host-buffer entry point
     Qh = torch.empty((nq, D), dtype=torch.float32, pin_memory=True)
@@ -488,7 +523,8 @@ def run_crisp(args):
                 "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": nq * D * 4,
                         "d2h_bytes_per_step": nq * k * 12},
                 "gpu_launches": launches, "clocks": clk,
-                "coarse_scoring": variants, "learned_bf16": learned, "modes": modes, **big}
+                "coarse_scoring": variants, "learned_bf16": learned, "modes": modes, "tf32_rows": tf32_rows,
+                "leg_seconds": leg_s, **big}
         if serving:
             ok = [r for r in serving["rates"] if r["achieved_qps"] >= 0.95 * r["offered_qps"]] or serving["rates"][:1]
             top = max(ok, key=lambda r: r["offered_qps"])
@@ -1048,13 +1084,13 @@ def stage_rooflines(stage, info, hbm_peak, hbm_kind, traffic_key):
     """Roofline of the dominant kernel and of every timed stage.
 
     The tensor-core re-rank scorer is a dense contraction: its achieved rate is
-    the TF32 flops it executes per launch (each (group, row) entry one row
-    times the group's queries over Dp dims) over its CUDA-event duration,
-    against the TF32 peak.  Its row traffic (entries x row bytes, from L2 or
-    HBM) and the pairs it serves per row fetch are reported beside it.  The
+    the flops it executes per launch (each (group, row) entry one row times the
+    group's queries over Dp dims) over its CUDA-event duration, against the
+    tensor peak of its pass: BF16 when it reads the index's BF16 copy, TF32
+    when it reads the FP32 rows.  Its row traffic (entries x row bytes, from L2
+    or HBM) and the pairs it serves per row fetch are reported beside it.  The
     other stages are measured in their algorithmic bytes against the HBM copy
     bandwidth."""
-    tpk, tkind = tf32_peak()
     rooflines = {}
     for n, v in stage.items():
         if v["bytes"]:
@@ -1063,23 +1099,28 @@ def stage_rooflines(stage, info, hbm_peak, hbm_kind, traffic_key):
                             "frac": a / hbm_peak, "ms": round(v["ms"], 4), "algorithmic_bytes_per_launch": v["bytes"]}
     sc = stage.get("rerank", {}).get("scorer")
     if sc:
+        bf = sc.get("elem_bytes", 4) == 2
+        tpk, tkind = bf16_peak() if bf else tf32_peak()
         fl = sc["rows_per_launch"] * sc["group"] * 2 * sc["Dp"]
         t = sc["ms_per_launch"] / 1e3
         ach = fl / t / 1e12
-        row_bytes = sc["rows_per_launch"] * 4 * sc["Dp"]
+        row_bytes = sc["rows_per_launch"] * sc.get("elem_bytes", 4) * sc["Dp"]
         traffic = _ncu_traffic("k_rerank_tc", traffic_key)
         rooflines["rerank_scorer"] = {
             "kernel": "k_rerank_tc", "bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
             "frac": ach / tpk, "traffic": traffic, "ms": round(sc["ms_per_launch"], 4),
-            "peak_kind": f"{tkind} sustained BF16 GEMM rate (MEASURED_PEAKS.json) x {TF32_PER_BF16:.3f}, the nominal "
-                         "TF32 / BF16 dense ratio",
+            "pass": "BF16 (the index's BF16 copy, queries rounded to BF16)" if bf else "TF32 (the FP32 rows)",
+            "peak_kind": (f"{tkind} sustained BF16 GEMM rate (MEASURED_PEAKS.json)" if bf else
+                          f"{tkind} sustained BF16 GEMM rate (MEASURED_PEAKS.json) x {TF32_PER_BF16:.3f}, the nominal "
+                          "TF32 / BF16 dense ratio"),
             "flops_per_launch": fl, "rows_per_launch": sc["rows_per_launch"], "pairs_per_launch": sc["pairs_per_launch"],
             "pairs_per_row_fetch": sc["pairs_per_launch"] / max(sc["rows_per_launch"], 1.0),
             "row_bytes_per_launch": row_bytes, "row_gbs": row_bytes / t / 1e9,
             "dram_gbs": traffic / t / 1e9 if traffic else None,
             "dram_frac": traffic / t / 1e9 / hbm_peak if traffic else None,
-            "note": "flops: one TF32 pass of every (64-query group, listed row) entry; rows come from L2 when the "
-                    "range-block order keeps them there; the exact re-measure and selection are separate kernels"}
+            "note": "flops: one pass of every (64-query group, listed row) entry; rows come from L2 when the "
+                    "range-block order keeps them there; the exact FP32 re-measure and selection are separate "
+                    "kernels"}
     timed_ms = {n: v["ms"] for n, v in stage.items()}
     dom_stage = max(timed_ms, key=lambda n: timed_ms[n])
     if dom_stage == "rerank" and "rerank_scorer" in rooflines:
@@ -1114,10 +1155,10 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     nf = torch.empty((nq,), dtype=torch.int64, device=dev)
     nb = torch.empty((nq,), dtype=torch.int64, device=dev)
     names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
-    # batches of >= 1,024 queries with candidate lists >= 2,048 wide re-rank on the
+    # batches of >= 256 queries with candidate lists >= 2,048 wide re-rank on the
     # tensor cores (MinHash-ordered query groups, bounded TF32 scores, exact re-measure
     # of the candidates that can reach the top-k); smaller ones stream (k_dist_flat)
-    grouped = nq >= 1024 and stride >= 2048
+    grouped = nq >= 256 and stride >= 2048
     kernels = ["k_rotate", "k_activate", "k_count_cut",
                ("k_rerank_tc (+ order, union, bound select, exact re-measure)" if grouped else "k_dist_flat")
                if point["mode"] == 0 else "k_verify_opt"]
@@ -1189,7 +1230,7 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
                                        "ms_per_launch": prof.ms / prof.launches,
                                        "rows_per_launch": prof.rows / prof.launches,
                                        "pairs_per_launch": prof.pairs / prof.launches, "group": prof.group,
-                                       "Dp": prof.Dp}
+                                       "Dp": prof.Dp, "elem_bytes": prof.elem_bytes}
     else:
         blocks = float(nb.sum().item())
         out["verify_opt"] = {"ms": acc["verify_opt"], "bytes": C * (4 * W + 4) + 128 * blocks,
@@ -1237,6 +1278,11 @@ def main():
     ap.add_argument("--train-queries", type=int, default=50000)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--full", action="store_true", help="also run the vMF D=3072, low-rank D=4096 and serving "
+                    "configurations (several minutes each)")
+    ap.add_argument("--vmf", action="store_true", help="run the vMF D=3072 learned+BF16 configuration")
+    ap.add_argument("--lowrank", action="store_true", help="run the low-rank D=4096 FP8 configuration")
+    ap.add_argument("--serve", action="store_true", help="run the continuous-batching serving configuration")
     ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
     ap.add_argument("--no-modes", action="store_true", help="skip the Guaranteed / Optimized k=10 / k=100 points")
     ap.add_argument("--no-vmf", action="store_true", help="skip the vMF D=3072 learned+BF16 configuration")

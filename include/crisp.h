@@ -513,11 +513,14 @@ crisp_status crisp_count_cut(const crisp_index *index, const int32_t *act, const
  * (device [nq][Dp]) to each of its candidates, then the k smallest by
  * (distance, id).  cand/ncand as written by crisp_count_cut (ascending ids).
  * ids: device [nq][k] int64, sqdist: device [nq][k] float32, padded -1/+inf.
- * Batches of 1,024 to 16,384 queries with cand_stride >= 2,048 and Dp <= 1,024
- * are scored in groups of 16 queries that read each shared candidate row once
- * (queries held in tensor memory); other batches stream (query, candidate)
- * pairs.  Both give the same bits: every distance is the CR32 order of its own
- * (query, row) pair. */
+ * Batches of 256 to 16,384 queries with cand_stride >= 2,048 are ordered by
+ * the MinHash of their candidate sets and scored in groups of 64 queries that
+ * fetch each shared candidate row once: one TF32 pass on the tensor cores
+ * gives every (query, candidate) pair an upper and a lower bound of its CR32
+ * distance, and only the candidates whose lower bound reaches the k-th
+ * smallest upper bound are measured exactly.  Other batches stream (query,
+ * candidate) pairs.  Both give the same bits: every returned distance is the
+ * CR32 value of its own (query, row) pair. */
 crisp_status crisp_rerank(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
                           int64_t cand_stride, const int64_t *ncand, int32_t k, int64_t *ids, float *sqdist,
                           void *stream);
@@ -549,9 +552,10 @@ crisp_status crisp_rerank_noalloc(const crisp_index *index, const float *Qr, int
  * crisp_rerank_profile_read waits for what was recorded and returns, for the
  * scoring launches since the previous read: their number, their summed
  * duration, the (query group, row) entries multiplied on the tensor cores (each
- * one row against a group's 64 queries over Dp dims, one TF32 pass) and the
- * (row, query) pairs whose distance bounds were written.  Call both from one
- * thread; reading also clears.  Synchronous. */
+ * one row against a group's 64 queries over Dp dims, one TF32 pass over the
+ * FP32 rows or one BF16 pass over the index's BF16 copy) and the (row, query)
+ * pairs whose distance bounds were written.  Call both from one thread;
+ * reading also clears.  Synchronous. */
 typedef struct {
     int64_t launches;
     double ms;                 /* summed kernel duration, CUDA events on the launching stream */
@@ -559,6 +563,8 @@ typedef struct {
     int64_t pairs;             /* (row, query) pairs bounded */
     int32_t Dp;                /* padded dimension of the last launch */
     int32_t group;             /* queries per group (the MMA's N) */
+    int32_t elem_bytes;        /* bytes per row element of the last launch: 4 (TF32 pass), 2 (BF16 pass) */
+    int32_t _pad;
 } crisp_rerank_profile;
 
 crisp_status crisp_rerank_profile_enable(int32_t on);

@@ -74,7 +74,7 @@ class IndexInfo(C.Structure):
 
 class RerankProfile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("rows", C.c_int64), ("pairs", C.c_int64),
-                ("Dp", C.c_int32), ("group", C.c_int32)]
+                ("Dp", C.c_int32), ("group", C.c_int32), ("elem_bytes", C.c_int32), ("_pad", C.c_int32)]
 
 
 _P, _I32, _I64, _F, _D, _S = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_size_t

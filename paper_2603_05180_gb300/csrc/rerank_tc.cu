@@ -11,10 +11,13 @@
 //   k_rerank_tc   each listed row is fetched once per group (16-byte cp.async
 //                 copies straight into the 128-byte swizzled operand layout) and
 //                 multiplied against the group's 64 queries (one TMA tile) on the
-//                 tensor cores: dot = x . q in one TF32 pass, FP32 accumulation in
-//                 tensor memory.  The epilogue forms the expansion
-//                 d~ = |x|^2 + |q|^2 - 2 dot and, from a proven error bound E,
-//                 an upper and a lower bound of the pair's CR32 distance.
+//                 tensor cores: dot = x . q in one TF32 pass over the FP32 rows,
+//                 or, when the index keeps its BF16 copy, in one BF16 pass over
+//                 that copy against the queries rounded to BF16 (half the bytes
+//                 per row), FP32 accumulation in tensor memory.  The epilogue
+//                 forms the expansion d~ = |x|^2 + |q|^2 - 2 dot (|x|^2 of the
+//                 FP32 row) and, from a proven error bound E, an upper and a
+//                 lower bound of the pair's CR32 distance.
 //   k_bound_select (query.cu) per query: U = the k-th smallest upper bound;
 //                 every candidate whose lower bound is <= U is kept.
 //   k_dist_flat + k_select_rows (query.cu): the kept candidates are measured
@@ -29,13 +32,21 @@
 //  - TF32 keeps 10 mantissa bits, so each operand is within 2^-10 of itself
 //    (relative, truncation or rounding) and each product within
 //    (2^-9 + 2^-20) |x_i q_i|; summed, |dot~ - x.q| <= (2^-9 + 2^-20) S with
-//    S = sum |x_i q_i| <= |x| |q| (Cauchy-Schwarz);
-//  - the tensor core's FP32 accumulation over Dp / 8 steps is charged
-//    (Dp / 8 + 1) 2^-20 S, several times the rounding of an FP32 sum;
+//    S = sum |x_i q_i| <= |x| |q| (Cauchy-Schwarz).  BF16 keeps 8 bits and
+//    both roundings are to nearest (2^-9 each), so each product is within
+//    (2^-8 + 2^-18) |x_i q_i| (the product of two BF16 values is exact in FP32);
+//  - the tensor core's FP32 accumulation: every MMA step adds its K products
+//    (K = 8 TF32, 16 BF16) to the running sum, charged (K + 1) 2^-22 S per
+//    step (K + 1 additions, each within 2^-23 of a magnitude <= 2 S), over
+//    Dp / K + 1 steps;
+//  - operands or products below the FP32 normal range may be flushed: at most
+//    2^-126 sqrt(Dp) (|x| + |q|) + Dp 2^-126, covered by c3 (|x| + |q|) + c4
+//    with c3 = 2^-110, c4 = 2^-100;
 //  - |x|^2 and |q|^2 are FP64 sums rounded once, and d~ takes three FP32
 //    operations: all within 2^-19 (|x|^2 + |q|^2);
-// so |d~ - d| <= E = c1 |x| |q| + c2 (|x|^2 + |q|^2), c1 = 2 (2^-9 + 2^-20 +
-// (Dp / 8 + 1) 2^-20) 1.01, c2 = 2^-19.  The CR32 value d32 of the same pair
+// so |d~ - d| <= E = c1 |x| |q| + c2 (|x|^2 + |q|^2) + c3 (|x| + |q|) + c4,
+// c1 = 2 (p + (Dp / K + 1)(K + 1) 2^-22) 1.01 with p = 2^-9 + 2^-20 (TF32) or
+// 2^-8 + 2^-18 (BF16), c2 = 2^-19.  The CR32 value d32 of the same pair
 // (zero-padded blocks of 32 dims, a subtraction, a 4-term fma chain, a 3-level
 // tree and Dp / 32 block additions per term) is within g d of d, with
 // g = (Dp / 32 + 12) 2^-23 + 2^-20 (twice the first-order summation bound).
@@ -52,9 +63,12 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 #include "ptx.cuh"
 
+bool crisp_make_map_bf16(CUtensorMap *m, const uint16_t *base, long long rows, int cols, int ld, int box_rows);
 bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows);
 crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                    unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
@@ -68,6 +82,7 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 namespace {
 
 constexpr int TG = 64;              // queries per group: N of the MMA
+constexpr int TR_MINQ = 256;        // smaller batches re-rank query by query
 constexpr int TSPAN = 4096;         // ids per range (the ordering's range size)
 constexpr int TU_NT = 256;          // k_union threads
 constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
@@ -104,9 +119,11 @@ __device__ __forceinline__ void tr_error(unsigned site) { atomicCAS(&g_tr_error,
 // Group-ordered copy of the queries: slot s = g TG + j holds query qord[s]
 // (zero rows past nq), with |q|^2 (FP64 sum rounded to FP32) and |q|.  One warp
 // per slot.
+// Qgb (when not null): the same rows rounded to BF16 (to nearest even), Dp64 =
+// Dp rounded up to 64 columns, zeros past Dp.
 __global__ void k_group_queries(const float *__restrict__ Qr, int nq, int Dp, const int *__restrict__ qord,
-                                int nslots, float *__restrict__ Qg, int *__restrict__ gq, float *__restrict__ gn2,
-                                float *__restrict__ gn1) {
+                                int nslots, float *__restrict__ Qg, uint16_t *__restrict__ Qgb, int Dp64,
+                                int *__restrict__ gq, float *__restrict__ gn2, float *__restrict__ gn1) {
     const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (slot >= nslots) return;
     const int q = slot < nq ? qord[slot] : -1;
@@ -116,6 +133,11 @@ __global__ void k_group_queries(const float *__restrict__ Qr, int nq, int Dp, co
         Qg[(long long)slot * Dp + d] = v;
         s += (double)v * (double)v;
     }
+    if (Qgb)
+        for (int d = lane; d < Dp64; d += 32) {
+            const float v = (q >= 0 && d < Dp) ? Qr[(long long)q * Dp + d] : 0.0f;
+            Qgb[(long long)slot * Dp64 + d] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        }
 #pragma unroll
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -290,11 +312,13 @@ struct TileMeta {
 };
 
 struct TrArgs {
-    int nk;                         // 32-float k-blocks per row (Dp / 32)
+    int nk;                         // 128-byte k-blocks per row (Dp / 32 FP32, ceil(Dp / 64) BF16)
     int Dp, ngroups, R;
+    int bf16;                       // 1: BF16 rows and queries (kind::f16), 0: FP32 rows (kind::tf32)
+    int row_bytes;                  // bytes of a stored row (Dp x 4 or Dp x 2)
     long long items;                // ngroups * ceil(R / TR_RB)
     long long stride;               // candidate list stride of ub / lb
-    const float *Xr;                // [N][Dp] stored rows
+    const uint8_t *X;               // [N][Dp] rows scored: the FP32 rows or their BF16 copy
     const int *gq;
     const float *gn2, *gn1;         // per group slot: |q|^2, |q|
     const int *ent_row;
@@ -305,7 +329,7 @@ struct TrArgs {
     const int2 *items_arr;          // [ngroups][R]
     unsigned long long *counter;    // work-item counter
     float2 *ulb;                    // [nq][stride] (upper, lower) bound of each pair's CR32 distance
-    float c1, c2, gam;              // error-bound constants (file comment)
+    float c1, c2, c3, c4, gam;      // error-bound constants (file comment)
 };
 
 constexpr int TR_MAXSEG = TR_RB;    // a tile holds consecutive entries of at most TR_RB ranges
@@ -315,8 +339,9 @@ __host__ __device__ constexpr size_t tr_smem_bytes() {
            sizeof(uint64_t) * TR_NBAR + 32;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// 16 bytes, of which the first n (0 or 16) come from src and the rest are zeros.
+__device__ __forceinline__ void cp_async16_n(uint32_t dst, const void *src, uint32_t n) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
@@ -525,13 +550,19 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                 if (lt == 0) {
                     mbar_expect_tx(qfull0 + 8u * s, (uint32_t)nkb * TR_B_BYTES);
                     for (int kb = 0; kb < nkb; ++kb)
-                        tma_load_2d(sq + (uint32_t)kb * TR_B_BYTES, &tmQ, 32 * (k0 + kb), TG * g, qfull0 + 8u * s);
+                        tma_load_2d(sq + (uint32_t)kb * TR_B_BYTES, &tmQ, (a.bf16 ? 64 : 32) * (k0 + kb), TG * g,
+                                    qfull0 + 8u * s);
                 }
                 for (int kb = 0; kb < nkb; ++kb) {
-                    const float *col = a.Xr + 32 * (k0 + kb) + 4 * c;
+                    // chunk c of the k-block: bytes 128 (k0 + kb) + 16 c of the row; a BF16
+                    // row of Dp = 64 j + 32 ends halfway through its last k-block (zeros after)
+                    const int cb = 128 * (k0 + kb) + 16 * c;
+                    const uint32_t n = cb < a.row_bytes ? 16u : 0u;
+                    const uint8_t *col = a.X + (n ? cb : 0);      // an empty copy still names its own row
                     const uint32_t da = sa + (uint32_t)kb * 2 * TR_A_BYTES + swz;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) cp_async16(da + (uint32_t)((r0 + 16 * i) * 128), col + (long long)id[i] * a.Dp);
+                    for (int i = 0; i < 16; ++i)
+                        cp_async16_n(da + (uint32_t)((r0 + 16 * i) * 128), col + (long long)id[i] * a.row_bytes, n);
                 }
                 cp_async_arrive(full0 + 8u * s);
             }
@@ -540,7 +571,8 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
     } else if (warp == TR_WM) {
         // ------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            const uint32_t idesc = tf32_idesc(TG, 128);
+            const bool bf = a.bf16 != 0;
+            const uint32_t idesc = bf ? bf16_idesc(TG, 128) : tf32_idesc(TG, 128);
             long long c = 0;
             for (int t = 0;; ++t) {
                 const int b = t % TR_NB;
@@ -574,11 +606,20 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                     const uint32_t sa0 = smem_addr(stages + (size_t)s * TR_STAGE), sq0 = sa0 + TR_KB * 2 * TR_A_BYTES;
                     for (int kb = 0; kb < nkb; ++kb) {
                         const uint32_t sa = sa0 + (uint32_t)kb * 2 * TR_A_BYTES, sq = sq0 + (uint32_t)kb * TR_B_BYTES;
+                        if (bf) {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {   // UMMA K = 8 floats = 32 bytes
-                            const uint32_t o = 32u * j, acc = (k0 + kb + j) != 0;
-                            mma_tf32(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
-                            mma_tf32(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                            for (int j = 0; j < 4; ++j) {   // UMMA K = 16 BF16 = 32 bytes
+                                const uint32_t o = 32u * j, acc = (k0 + kb + j) != 0;
+                                mma_bf16(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
+                                mma_bf16(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {   // UMMA K = 8 floats = 32 bytes
+                                const uint32_t o = 32u * j, acc = (k0 + kb + j) != 0;
+                                mma_tf32(d0, sw128_desc(sa + o), sw128_desc(sq + o), idesc, acc);
+                                mma_tf32(d1, sw128_desc(sa + TR_A_BYTES + o), sw128_desc(sq + o), idesc, acc);
+                            }
                         }
                     }
                     mma_commit(empty0 + 8u * s);
@@ -611,7 +652,7 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
             const bool valid = row < count;
             const unsigned long long m = valid ? mt.mask[row] : 0ull;
             const int pb = valid ? mt.pb[row] : 0, po = valid ? mt.off[row] : 0;
-            const float nx = valid ? mt.nx[row] : 0.0f, c1rx = a.c1 * sqrtf(nx);
+            const float nx = valid ? mt.nx[row] : 0.0f, rx = sqrtf(nx), c1rx = a.c1 * rx;
 #pragma unroll 1
             for (int cb = 0; cb < TG / 16; ++cb) {
                 uint32_t v[16];
@@ -630,7 +671,7 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                         const int j = 16 * cb + jj;
                         const float ss = nx + mt.gn2[j];
                         const float dt = ss - 2.0f * __uint_as_float(v[jj]);
-                        const float E = mt.gn1[j] * c1rx + a.c2 * ss;
+                        const float E = mt.gn1[j] * c1rx + a.c2 * ss + (a.c3 * (rx + mt.gn1[j]) + a.c4);
                         const float E2 = E + a.gam * (fabsf(dt) + E);
                         a.ulb[(long long)mt.gq[j] * a.stride + pos[jj]] = make_float2(fmaxf(dt + E2, 0.0f), dt - E2);
                     }
@@ -668,6 +709,7 @@ struct ProfRec {
     cudaEvent_t a = nullptr, b = nullptr;
     unsigned long long *host = nullptr;   // pinned [2]: entries, pairs
     int Dp = 0;
+    int elem_bytes = 4;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -697,6 +739,7 @@ extern "C" crisp_status crisp_rerank_profile_read(crisp_rerank_profile *out) {
         r.rows += (int64_t)p.host[0];
         r.pairs += (int64_t)p.host[1];
         r.Dp = p.Dp;
+        r.elem_bytes = p.elem_bytes;
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
         cudaFreeHost(p.host);
@@ -717,7 +760,7 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
                                  int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
                                  float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done) {
     *done = false;
-    if (nq < 1024 || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
+    if (nq < TR_MINQ || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
     // pair slots are 32-bit: batches whose lists could hold more pairs run in
     // equal sub-batches (the kernels have no minimum batch size)
     const long long per_q = std::min<int64_t>(stride, ix->N);
@@ -749,10 +792,16 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         off += (bytes + 255) / 256 * 256;
         return o;
     };
+    // the BF16 copy, when the index keeps one, halves the bytes of every row fetch
+    // (CRISP_RERANK_TF32=1 keeps the FP32 rows)
+    const char *force_tf32 = getenv("CRISP_RERANK_TF32");
+    const bool bf = ix->Xb != nullptr && !(force_tf32 && atoi(force_tf32) != 0);
+    const int Dp64 = (Dp + 63) / 64 * 64;
     const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
                  o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
                  o_gq = take(sizeof(int) * nslots), o_gn2 = take(sizeof(float) * nslots),
                  o_gn1 = take(sizeof(float) * nslots), o_qg = take(sizeof(float) * (size_t)nslots * Dp),
+                 o_qgb = take(bf ? sizeof(uint16_t) * (size_t)nslots * Dp64 : 0),
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)ecap),
                  o_mask = take(sizeof(unsigned long long) * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
                  o_enx = take(sizeof(float) * (size_t)ecap),
@@ -763,6 +812,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     unsigned long long *counts = (unsigned long long *)(buf + o_cnt);
     int *qord = (int *)(buf + o_qord), *pos = (int *)(buf + o_pos), *gq = (int *)(buf + o_gq);
     float *gn2 = (float *)(buf + o_gn2), *gn1 = (float *)(buf + o_gn1), *Qg = (float *)(buf + o_qg);
+    uint16_t *Qgb = bf ? (uint16_t *)(buf + o_qgb) : nullptr;
     float2 *ulb = (float2 *)(buf + o_ulb);
     int32_t *rc = (int32_t *)(buf + o_rc);
     int64_t *nr = (int64_t *)(buf + o_nr);
@@ -790,7 +840,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "error word", __FILE__, __LINE__); break; }
         s = crisp_run_group_order(cand, stride, ncand, nq, R, (unsigned long long *)(buf + o_key), qord, pos, st);
         if (s) break;
-        k_group_queries<<<(nslots + 7) / 8, 256, 0, st>>>(Qr, nq, Dp, qord, nslots, Qg, gq, gn2, gn1);
+        k_group_queries<<<(nslots + 7) / 8, 256, 0, st>>>(Qr, nq, Dp, qord, nslots, Qg, Qgb, Dp64, gq, gn2, gn1);
         CRISP_COUNT_LAUNCH();
         const size_t usmem = sizeof(unsigned long long) * TSPAN + sizeof(int) * TSPAN;
         e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
@@ -798,15 +848,17 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         k_union<<<dim3(R, ngroups), TU_NT, usmem, st>>>(cand, (long long)stride, u);
         CRISP_COUNT_LAUNCH();
         CUtensorMap mq;
-        if (!crisp_make_map_f32(&mq, Qg, nslots, Dp, Dp, TG)) {
+        if (bf ? !crisp_make_map_bf16(&mq, Qgb, nslots, Dp64, Dp64, TG) : !crisp_make_map_f32(&mq, Qg, nslots, Dp, Dp, TG)) {
             crisp_set_error("tensor-core re-rank: tensor map encoding failed");
             s = CRISP_ECUDA;
             break;
         }
         TrArgs ta;
-        ta.nk = Dp / 32;
+        ta.nk = bf ? Dp64 / 64 : Dp / 32;
         ta.Dp = Dp;
-        ta.Xr = ix->Xr;
+        ta.bf16 = bf ? 1 : 0;
+        ta.row_bytes = Dp * (bf ? 2 : 4);
+        ta.X = bf ? (const uint8_t *)ix->Xb : (const uint8_t *)ix->Xr;
         ta.ngroups = ngroups;
         ta.R = R;
         ta.items = (long long)ngroups * ((R + TR_RB - 1) / TR_RB);
@@ -822,9 +874,13 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         ta.items_arr = u.items;
         ta.counter = counts + 2;
         ta.ulb = ulb;
-        const double eps_acc = (Dp / 8 + 1) * std::ldexp(1.0, -20);
-        ta.c1 = (float)(2.0 * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + eps_acc) * 1.01);
+        const int K = bf ? 16 : 8;
+        const double eps_acc = (double)(Dp / K + 1) * (K + 1) * std::ldexp(1.0, -22);
+        const double eps_mul = bf ? std::ldexp(1.0, -8) + std::ldexp(1.0, -18) : std::ldexp(1.0, -9) + std::ldexp(1.0, -20);
+        ta.c1 = (float)(2.0 * (eps_mul + eps_acc) * 1.01);
         ta.c2 = (float)std::ldexp(1.0, -19);
+        ta.c3 = (float)std::ldexp(1.0, -110);
+        ta.c4 = (float)std::ldexp(1.0, -100);
         ta.gam = (float)((Dp / 32 + 12) * std::ldexp(1.0, -23) + std::ldexp(1.0, -20));
         const size_t smem = tr_smem_bytes();
         e = cudaFuncSetAttribute(k_rerank_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -837,6 +893,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
             std::lock_guard<std::mutex> lk(g_prof_mu);
             if (g_prof_on) {
                 rec.Dp = Dp;
+                rec.elem_bytes = bf ? 2 : 4;
                 if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess ||
                     cudaMallocHost((void **)&rec.host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
                     s = crisp_cuda_fail(cudaGetLastError(), "profiling record", __FILE__, __LINE__);

@@ -246,6 +246,20 @@ bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int c
     return make_map(m, base, rows, cols, ld, box_rows);
 }
 
+// 2-D BF16 tensor map over rows x cols (row pitch ld elements), box 64
+// elements (128 bytes) x box_rows, 128-byte swizzle, zero fill outside.
+bool crisp_make_map_bf16(CUtensorMap *m, const uint16_t *base, long long rows, int cols, int ld, int box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(uint16_t)};
+    cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 namespace {
 
 size_t rot_smem(int BN) { return 1024 + 2 * (2 * (size_t)TC_BM * 128 + 2 * (size_t)BN * 128) + 64; }

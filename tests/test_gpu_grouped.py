@@ -1,8 +1,10 @@
-"""Grouped scoring (batches of >= 1,024 queries) against the oracle at the shapes
-the scorers treat specially: D = 1024 (every 128-dim chunk of the FP32 warp
-layout and all 32 blocks in use), D = 100 and D = 33 (padded to 128 and 64, so
-the last blocks and chunks are padding), and batch sizes that leave a partial
-last query group (16 queries per FP32 group, 32 per BF16 / E4M3 group).
+"""Grouped scoring (large batches) against the oracle at the shapes the scorers
+treat specially: D = 1024 (every 128-dim chunk of the FP32 warp layout and all
+32 blocks in use), D = 100 and D = 33 (padded to 128 and 64, so the last blocks
+and chunks are padding), D = 96 (a BF16 row ends halfway through its last
+128-byte k-block of the tensor-core re-rank), and batch sizes that leave a
+partial last query group (64 queries per tensor-core group, 16 / 32 per group
+of the FP32 / BF16 shortlist scorers).
 
 The oracle builds the index and the GPU searches the imported blob.  For every
 sampled query the GPU's candidate list must equal the oracle's cut, and the
@@ -35,8 +37,9 @@ def empty(shape, dtype):
     return torch.empty(shape, dtype=dtype, device=DEV)
 
 
-@pytest.fixture(scope="module", params=[(6000, 1024, 1100, 4), (5000, 100, 1030, 5), (3000, 33, 1531, 3)],
-                ids=["D1024", "D100", "D33"])
+@pytest.fixture(scope="module", params=[(6000, 1024, 1100, 4), (5000, 100, 1030, 5), (3000, 33, 1531, 3),
+                                        (4000, 96, 600, 4)],
+                ids=["D1024", "D100", "D33", "D96"])
 def grouped_case(request):
     N, D, nq, M = request.param
     X, Q = synthetic.gmm(N=N, D=D, nq=nq, n_comp=30, rank=min(16, D), seed=D)
@@ -76,7 +79,13 @@ def _sample(nq, step):
 
 
 @pytest.mark.parametrize("k", [10, 100])
-def test_grouped_rerank_bitexact(grouped_case, k):
+@pytest.mark.parametrize("scorer", ["bf16", "tf32"])
+def test_grouped_rerank_bitexact(grouped_case, k, scorer, monkeypatch):
+    """The index keeps its BF16 copy, so the tensor-core bounds come from one
+    BF16 pass over it; CRISP_RERANK_TF32=1 takes one TF32 pass over the FP32
+    rows instead.  Either way every returned distance is exact (CR32)."""
+    if scorer == "tf32":
+        monkeypatch.setenv("CRISP_RERANK_TF32", "1")
     X, Q, ix_o, ix = grouped_case
     nq = Q.shape[0]
     Qr, cand, ncand = _candidates(ix_o, ix, Q, 0.05, 0.3, k)
