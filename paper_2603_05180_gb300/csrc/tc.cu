@@ -284,6 +284,7 @@ crisp_status crisp_rotate_rows_tc_cols(const float *X, int64_t N, int32_t D, int
     const int Dp = (D + TC_BK - 1) / TC_BK * TC_BK;
     const int ncols = ncols_req >= 0 ? std::min(ncols_req, ldy < Dp ? ldy : Dp)
                                      : (ldy < Dp ? ldy : Dp);   // columns D..ncols-1 come out zero
+    if (ncols <= 0) return CRISP_OK;
     const int nt = (ncols + 255) / 256;
     const int BN = ((ncols + nt - 1) / nt + 15) / 16 * 16;
     float *bt = nullptr;
@@ -326,7 +327,7 @@ crisp_status crisp_rotate_rows_tc_cols(const float *X, int64_t N, int32_t D, int
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_rotate_tc", __FILE__, __LINE__); break; }
-        if (ldy > ncols) {
+        if (ncols_req < 0 && ldy > ncols) {   // full rows: the columns past the output are zeroed
             e = cudaMemset2DAsync(Y + ncols, sizeof(float) * (size_t)ldy, 0, sizeof(float) * (size_t)(ldy - ncols),
                                   (size_t)N, st);
             if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemset2DAsync", __FILE__, __LINE__); break; }
