@@ -65,9 +65,10 @@ static cudaMemPool_t scratch_pool(int dev) {
         pp.location.type = cudaMemLocationTypeDevice;
         pp.location.id = dev;
         if (cudaMemPoolCreate(&g_pool[dev], &pp) != cudaSuccess) return nullptr;
-        // keep up to 16 GiB between calls (a serving loop's scratch stays resident);
-        // what a larger search took goes back to the device at its next synchronisation
-        uint64_t keep = (uint64_t)16 << 30;
+        // keep up to 64 GiB between calls (the largest default search scratch, so
+        // repeated searches do not map and unmap it); what a larger search took
+        // goes back to the device at its next synchronisation
+        uint64_t keep = (uint64_t)64 << 30;
         cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
         g_pool_ok[dev] = true;
     }
@@ -491,10 +492,12 @@ static crisp_status plan_search(const crisp_index *ix, int32_t nq, const crisp_s
         pl->per_query += st + sizeof(float) * (2 * ix->M + 2 * ix->M + 68) + sizeof(int32_t) * st + 64;
     // batches of 1,024 queries or more re-rank on the tensor cores, with bounds, kept lists and pair slots
     pl->per_query += sizeof(float) * 2 * st + sizeof(int32_t) * st + sizeof(int32_t) * st;
-    // default budget: half the device memory free now, at least 16 GiB (a
-    // chunk large enough to re-rank in query groups when candidate lists are long)
+    // default budget: half the device memory free now, between 16 and 64 GiB (a
+    // chunk large enough to re-rank in query groups when candidate lists are
+    // long, and no larger than what the scratch pool keeps between calls)
     size_t budget_bytes = (size_t)16 << 30, free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget_bytes = std::max(budget_bytes, free_b / 2);
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+        budget_bytes = std::min<size_t>(std::max(budget_bytes, free_b / 2), (size_t)64 << 30);
     else cudaGetLastError();
     if (const char *e = getenv("CRISP_SCRATCH_MB")) budget_bytes = (size_t)atoll(e) << 20;
     int64_t chunk = (int64_t)(budget_bytes / pl->per_query);
