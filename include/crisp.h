@@ -464,9 +464,13 @@ crisp_status crisp_quantize_e4m3(const float *Xr, int64_t N, int32_t Dp, uint8_t
  * exactly, or the E4M3 value times the row scale, precision 1 or 2), then the S
  * smallest by (distance, id), written in ascending id to out (device
  * [nq][out_stride] int32) with their number in nout (device [nq] int64).
- * cand/ncand as written by crisp_count_cut.  Large batches take the grouped
- * path described at crisp_rerank, with the same results.  EINVAL: the index
- * lacks the copy, S < 1, out_stride < S. */
+ * cand/ncand as written by crisp_count_cut.  Large batches of BF16 scoring
+ * take the tensor-core path described at crisp_rerank: one BF16 pass (the
+ * query rounded to BF16) bounds every coarse score, and only the candidates
+ * whose lower bound reaches the S-th smallest upper bound are scored exactly;
+ * large E4M3 batches are scored in groups of queries that read each shared row
+ * once.  Every path gives the same shortlist.  EINVAL: the index lacks the
+ * copy, S < 1, out_stride < S. */
 crisp_status crisp_shortlist(const crisp_index *index, const float *Qr, int32_t nq, const int32_t *cand,
                              int64_t cand_stride, const int64_t *ncand, int32_t precision, int32_t S, int32_t *out,
                              int64_t out_stride, int64_t *nout, void *stream);

@@ -25,7 +25,7 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
-                                 const int64_t *S_per_query, const QParam *qp = nullptr);
+                                 const int64_t *S_per_query, const QParam *qp = nullptr, bool may_group = true);
 crisp_status crisp_run_verify_opt(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                   int64_t stride, const int64_t *ncand, int32_t k, float eps0, int64_t patience,
                                   int32_t order, int64_t *ids, float *d2, int64_t *nver, int64_t *nfull, int64_t *nblk,
@@ -199,6 +199,7 @@ static void free_index_arrays(crisp_index *ix) {
     cudaFree(ix->X8);
     cudaFree(ix->S8);
     cudaFree(ix->xn2);
+    cudaFree(ix->xbn2);
     cudaFree(ix->mlp);
     cudaFree(ix->sub);
 }

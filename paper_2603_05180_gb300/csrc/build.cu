@@ -1112,6 +1112,10 @@ crisp_status crisp_make_copies(crisp_index *ix, uint32_t copies, cudaStream_t st
         ix->bytes += (int64_t)b;
         crisp_status s = crisp_quantize_bf16(ix->Xr, ix->N, ix->Dp, ix->Xb, st);
         if (s) return s;
+        CRISP_CK(cudaMalloc((void **)&ix->xbn2, sizeof(float) * (size_t)ix->N));
+        ix->bytes += (int64_t)(sizeof(float) * (size_t)ix->N);
+        s = launch_row_norms_bf16(ix, st);
+        if (s) return s;
     }
     if ((copies & 2u) && !ix->X8) {
         size_t b = (size_t)ix->N * ix->Dp, sb = sizeof(float) * (size_t)ix->N;

@@ -36,6 +36,7 @@ struct crisp_index {
     uint8_t *X8 = nullptr;         // [N][Dp] FP8 E4M3 codes (optional)
     float *S8 = nullptr;           // [N] FP8 row scales (optional)
     float *xn2 = nullptr;          // [N] |x|^2 of the stored rows, FP64 sum rounded to FP32
+    float *xbn2 = nullptr;         // [N] |xb|^2 of the BF16 copy (widened), FP64 sum rounded to FP32
     float *mlp = nullptr;          // learned-depth model (F = 2M + 68 -> H -> H -> 2), optional
     int32_t mlp_H = 0;
     int32_t *sub = nullptr;        // [M+1] subspace boundaries (device)
@@ -142,6 +143,7 @@ crisp_status launch_pad_rows(const float *X, int64_t N, int32_t D, int32_t ldx, 
                              cudaStream_t st);
 crisp_status launch_tile_offsets(crisp_index *ix, cudaStream_t st);
 crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st);
+crisp_status launch_row_norms_bf16(crisp_index *ix, cudaStream_t st);
 crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
                                 int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
                                 crisp_query_stats *stats, cudaStream_t st, const QParam *qp = nullptr);

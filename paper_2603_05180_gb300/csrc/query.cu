@@ -306,6 +306,22 @@ __global__ void k_row_norms(const float *__restrict__ Xr, long long N, int Dp, f
     if (lane == 0) xn2[n] = (float)s;
 }
 
+// |xb|^2 of the BF16 copy's rows, each value widened exactly to FP32.
+__global__ void k_row_norms_bf16(const uint16_t *__restrict__ Xb, long long N, int Dp, float *__restrict__ xn2) {
+    const long long n = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;
+    const uint16_t *x = Xb + n * Dp;
+    double s = 0.0;
+    for (int d = lane; d < Dp; d += 32) {
+        const double v = (double)__uint_as_float((unsigned)x[d] << 16);
+        s += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xn2[n] = (float)s;
+}
+
 // ================================================== Q4 + Q5 count and cut
 constexpr int CNT_NT = 512;
 
@@ -1859,14 +1875,19 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
 // rc alone therefore gives the top-kk of the whole list.
 // If the scorer reported a failure (*err != 0) its bounds cannot be trusted
 // and every candidate is kept, so the result is still exact.
+// Target per query: kq[q] if given, else the query's k (qfield 0) or
+// shortlist size S (qfield 1) from qp, else kk.
 __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__restrict__ cand, long long stride,
                                                         const long long *__restrict__ ncand, int kk,
-                                                        const QParam *__restrict__ qp, const float2 *__restrict__ ulb,
+                                                        const QParam *__restrict__ qp, int qfield,
+                                                        const long long *__restrict__ kq,
+                                                        const float2 *__restrict__ ulb,
                                                         const unsigned *__restrict__ err, int *__restrict__ rc,
                                                         long long *__restrict__ nr) {
     __shared__ TopkShared S;
     const int q = blockIdx.x, tid = threadIdx.x;
-    if (qp) kk = qp[q].k;
+    if (kq) kk = (int)(kq[q] < (long long)INT_MAX ? kq[q] : (long long)INT_MAX);
+    else if (qp) kk = qfield ? qp[q].S : qp[q].k;
     const long long n = ncand[q] < stride ? ncand[q] : stride;
     const int *candq = cand + (long long)q * stride;
     int *rcq = rc + (long long)q * stride;
@@ -2004,6 +2025,14 @@ crisp_status launch_row_norms(crisp_index *ix, cudaStream_t st) {
     return CRISP_OK;
 }
 
+crisp_status launch_row_norms_bf16(crisp_index *ix, cudaStream_t st) {
+    if (ix->N <= 0 || !ix->Xb || !ix->xbn2) return CRISP_OK;
+    k_row_norms_bf16<<<(unsigned)((ix->N + 7) / 8), 256, 0, st>>>(ix->Xb, (long long)ix->N, ix->Dp, ix->xbn2);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
+}
+
 crisp_status launch_write_stats(int32_t nq, const int64_t *ncand, const int32_t *how, const int64_t *retrieved,
                                 int32_t M, const int64_t *nver, const int64_t *nfull, int32_t tau,
                                 crisp_query_stats *stats, cudaStream_t st, const QParam *qp) {
@@ -2059,6 +2088,10 @@ crisp_status crisp_run_count_cut(const crisp_index *ix, const int32_t *act, cons
 crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
                                  float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done);
+crisp_status crisp_run_shortlist_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                    int64_t stride, const int64_t *ncand, int32_t S, const int64_t *S_per_query,
+                                    const QParam *qp, float *dbuf, int32_t *out, int64_t out_stride, int64_t *nout,
+                                    cudaStream_t st, bool *done);
 
 // Large batches (1,024 queries or more with long lists) take the tensor-core
 // path of rerank_tc.cu (bounded TF32 scores, exact CR32 re-measure of the
@@ -2104,11 +2137,11 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 }
 
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const QParam *qp, const float2 *ulb, const unsigned *err, int32_t *rc,
-                                    int64_t *nr, cudaStream_t st) {
+                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float2 *ulb,
+                                    const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
-    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, qp, ulb, err, rc,
-                                         (long long *)nr);
+    k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, qp, qfield,
+                                         (const long long *)kq, ulb, err, rc, (long long *)nr);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;
@@ -2117,11 +2150,19 @@ crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t str
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
-                                 const int64_t *S_per_query, const QParam *qp) {
+                                 const int64_t *S_per_query, const QParam *qp, bool may_group) {
     if (nq <= 0) return CRISP_OK;
     size_t smem = sizeof(float) * (size_t)ix->Dp;
     bool grouped = false;
-    {
+    if (may_group && precision == 1) {
+        // large batches: bounds from one BF16 tensor-core pass, exact scores of the
+        // candidates that can reach the shortlist only
+        bool done = false;
+        crisp_status ts = crisp_run_shortlist_tc(ix, Qr, nq, cand, stride, ncand, S, S_per_query, qp, dbuf, out,
+                                                 out_stride, nout, st, &done);
+        if (ts || done) return ts;
+    }
+    if (may_group) {
         crisp_status gs = precision == 1 ? run_grouped<1>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped)
                                          : run_grouped<2>(ix, Qr, nq, cand, stride, ncand, dbuf, st, &grouped);
         if (gs) return gs;
@@ -2309,7 +2350,7 @@ extern "C" crisp_status crisp_shortlist(const crisp_index *ix, const float *Qr, 
     float *dbuf = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&dbuf, sizeof(float) * (size_t)nq * cand_stride, st));
     s = crisp_run_shortlist(ix, Qr, nq, cand, cand_stride, ncand, precision, S, dbuf, out, out_stride, nout, st,
-                            nullptr, nullptr);
+                            nullptr, nullptr, true);
     crisp_scratch_free(dbuf, st);
     return s;
 }

@@ -23,6 +23,13 @@
 //   k_dist_flat + k_select_rows (query.cu): the kept candidates are measured
 //                 exactly in the CR32 order and the top-k is taken from them.
 //
+// The same machinery makes the BF16 coarse-score shortlists of large batches
+// (precision 1 and the learned path): the pass reads the BF16 copy against the
+// queries rounded to BF16, the bounds are of the coarse score (the CR32
+// distance of the FP32 query to the widened BF16 row, whose |xb|^2 the index
+// keeps), the selection keeps what can reach the S-th smallest upper bound, and
+// the kept candidates' coarse scores are computed exactly (k_score_flat).
+//
 // No candidate outside the kept set can be among the k nearest (its CR32
 // distance exceeds U, which is at least the k-th smallest CR32 distance), and
 // every kept distance is the CR32 value itself, so the result is bit-for-bit
@@ -35,6 +42,8 @@
 //    S = sum |x_i q_i| <= |x| |q| (Cauchy-Schwarz).  BF16 keeps 8 bits and
 //    both roundings are to nearest (2^-9 each), so each product is within
 //    (2^-8 + 2^-18) |x_i q_i| (the product of two BF16 values is exact in FP32);
+//    for a coarse score the row is the BF16 row itself and only the query is
+//    rounded: 2^-9 + 2^-18 (with margin);
 //  - the tensor core's FP32 accumulation: every MMA step adds its K products
 //    (K = 8 TF32, 16 BF16) to the running sum, charged (K + 1) 2^-22 S per
 //    step (K + 1 additions, each within 2^-23 of a magnitude <= 2 S), over
@@ -45,8 +54,8 @@
 //  - |x|^2 and |q|^2 are FP64 sums rounded once, and d~ takes three FP32
 //    operations: all within 2^-19 (|x|^2 + |q|^2);
 // so |d~ - d| <= E = c1 |x| |q| + c2 (|x|^2 + |q|^2) + c3 (|x| + |q|) + c4,
-// c1 = 2 (p + (Dp / K + 1)(K + 1) 2^-22) 1.01 with p = 2^-9 + 2^-20 (TF32) or
-// 2^-8 + 2^-18 (BF16), c2 = 2^-19.  The CR32 value d32 of the same pair
+// c1 = 2 (p + (Dp / K + 1)(K + 1) 2^-22) 1.01 with p = 2^-9 + 2^-20 (TF32),
+// 2^-8 + 2^-18 (BF16) or 2^-9 + 2^-18 (coarse), c2 = 2^-19.  The CR32 value d32 of the same pair
 // (zero-padded blocks of 32 dims, a subtraction, a 4-term fma chain, a 3-level
 // tree and Dp / 32 block additions per term) is within g d of d, with
 // g = (Dp / 32 + 12) 2^-23 + 2^-20 (twice the first-order summation bound).
@@ -73,8 +82,12 @@ bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int c
 crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                    unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const QParam *qp, const float2 *ulb, const unsigned *err, int32_t *rc,
-                                    int64_t *nr, cudaStream_t st);
+                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float2 *ulb,
+                                    const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
+crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
+                                 int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
+                                 const int64_t *S_per_query, const QParam *qp, bool may_group);
 crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                               int64_t stride, const int64_t *ncand, int32_t k, float *dbuf, int64_t *ids, float *d2,
                               cudaStream_t st, bool no_alloc, bool may_group, const QParam *qp, int32_t ko);
@@ -749,16 +762,33 @@ extern "C" crisp_status crisp_rerank_profile_read(crisp_rerank_profile *out) {
     return s;
 }
 
-// Tensor-core re-rank of a batch of 1,024 to CRISP_GROUP_MAXQ queries whose
-// candidate lists may hold 2,048 or more ids; *done = false (nothing run) for
-// other batches, which the caller streams.  dbuf: [nq][stride] floats of scratch.
-static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
-                                    int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
-                                    float *dbuf, int64_t *ids, float *d2, cudaStream_t st);
+// What a tensor-core batch computes after its bounds: the exact FP32 top-k
+// (ids, d2: [nq][ko]), or the shortlist of the S smallest BF16 coarse scores
+// (out: [nq][out_stride], nout) for the coarse-scoring and learned paths.
+struct TcTask {
+    bool coarse;
+    int32_t k;                      // exact: k; coarse: S (per query: S_per_query, else qp S)
+    const int64_t *S_per_query;
+    const QParam *qp;
+    int32_t ko;
+    int64_t *ids;
+    float *d2;
+    int32_t *out;
+    int64_t out_stride;
+    int64_t *nout;
+};
 
-crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
-                                 int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
-                                 float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done) {
+// One batch of TR_MINQ to CRISP_GROUP_MAXQ queries whose pairs fit 32-bit
+// slots.  dbuf: [nq][stride] floats of scratch.
+static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                    int64_t stride, const int64_t *ncand, const TcTask &task, float *dbuf,
+                                    cudaStream_t st);
+
+// Batches of TR_MINQ to CRISP_GROUP_MAXQ queries whose candidate lists may hold
+// 2,048 or more ids; *done = false (nothing run) for other batches, which the
+// caller streams.
+static crisp_status run_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand, int64_t stride,
+                           const int64_t *ncand, const TcTask &task, float *dbuf, cudaStream_t st, bool *done) {
     *done = false;
     if (nq < TR_MINQ || nq > CRISP_GROUP_MAXQ || stride < 2048) return CRISP_OK;
     // pair slots are 32-bit: batches whose lists could hold more pairs run in
@@ -769,18 +799,49 @@ crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t
     const int32_t nb = (int32_t)((nq + sub - 1) / sub), each = (nq + nb - 1) / nb;
     for (int32_t q0 = 0; q0 < nq; q0 += each) {
         const int32_t n = std::min(each, nq - q0);
+        TcTask t = task;
+        if (t.qp) t.qp += q0;
+        if (t.S_per_query) t.S_per_query += q0;
+        if (t.coarse) {
+            t.out += (int64_t)q0 * t.out_stride;
+            t.nout += q0;
+        } else {
+            t.ids += (int64_t)q0 * t.ko;
+            t.d2 += (int64_t)q0 * t.ko;
+        }
         crisp_status s = rerank_tc_batch(ix, Qr + (int64_t)q0 * ix->Dp, n, cand + (int64_t)q0 * stride, stride,
-                                         ncand + q0, k, qp ? qp + q0 : nullptr, ko, dbuf + (int64_t)q0 * stride,
-                                         ids + (int64_t)q0 * ko, d2 + (int64_t)q0 * ko, st);
+                                         ncand + q0, t, dbuf + (int64_t)q0 * stride, st);
         if (s) return s;
     }
     *done = true;
     return CRISP_OK;
 }
 
+crisp_status crisp_run_rerank_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                 int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
+                                 float *dbuf, int64_t *ids, float *d2, cudaStream_t st, bool *done) {
+    TcTask t{false, k, nullptr, qp, ko, ids, d2, nullptr, 0, nullptr};
+    return run_tc(ix, Qr, nq, cand, stride, ncand, t, dbuf, st, done);
+}
+
+// The BF16 coarse-score shortlist (precision 1, learned depths) of large
+// batches: one BF16 pass bounds every pair's coarse score (the CR32 distance
+// of the FP32 query to the widened BF16 row), the candidates whose lower bound
+// reaches the S-th smallest upper bound are scored exactly, and the S best by
+// (score, id) are kept, in ascending id.
+crisp_status crisp_run_shortlist_tc(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
+                                    int64_t stride, const int64_t *ncand, int32_t S, const int64_t *S_per_query,
+                                    const QParam *qp, float *dbuf, int32_t *out, int64_t out_stride, int64_t *nout,
+                                    cudaStream_t st, bool *done) {
+    *done = false;
+    if (!ix->Xb || !ix->xbn2) return CRISP_OK;
+    TcTask t{true, S, S_per_query, qp, 0, nullptr, nullptr, out, out_stride, nout};
+    return run_tc(ix, Qr, nq, cand, stride, ncand, t, dbuf, st, done);
+}
+
 static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
-                                    int64_t stride, const int64_t *ncand, int32_t k, const QParam *qp, int32_t ko,
-                                    float *dbuf, int64_t *ids, float *d2, cudaStream_t st) {
+                                    int64_t stride, const int64_t *ncand, const TcTask &task, float *dbuf,
+                                    cudaStream_t st) {
     const int Dp = ix->Dp;
     const int R = (int)((ix->N + TSPAN - 1) / TSPAN);
     const int ngroups = (nq + TG - 1) / TG, nslots = ngroups * TG;
@@ -795,7 +856,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     // the BF16 copy, when the index keeps one, halves the bytes of every row fetch
     // (CRISP_RERANK_TF32=1 keeps the FP32 rows)
     const char *force_tf32 = getenv("CRISP_RERANK_TF32");
-    const bool bf = ix->Xb != nullptr && !(force_tf32 && atoi(force_tf32) != 0);
+    const bool bf = task.coarse || (ix->Xb != nullptr && !(force_tf32 && atoi(force_tf32) != 0));
     const int Dp64 = (Dp + 63) / 64 * 64;
     const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
                  o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
@@ -823,7 +884,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     u.ent_mask = (unsigned long long *)(buf + o_mask);
     u.ent_pb = (int *)(buf + o_pb);
     u.ent_nx = (float *)(buf + o_enx);
-    u.xn2 = ix->xn2;
+    u.xn2 = task.coarse ? ix->xbn2 : ix->xn2;   // |x|^2 of the rows the exact value is measured on
     u.pair_pos = (int *)(buf + o_pp);
     u.items = (int2 *)(buf + o_items);
     u.counts = counts;
@@ -876,7 +937,10 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         ta.ulb = ulb;
         const int K = bf ? 16 : 8;
         const double eps_acc = (double)(Dp / K + 1) * (K + 1) * std::ldexp(1.0, -22);
-        const double eps_mul = bf ? std::ldexp(1.0, -8) + std::ldexp(1.0, -18) : std::ldexp(1.0, -9) + std::ldexp(1.0, -20);
+        // coarse scores are of the BF16 rows themselves: only the query is rounded
+        const double eps_mul = task.coarse ? std::ldexp(1.0, -9) + std::ldexp(1.0, -18)
+                               : bf        ? std::ldexp(1.0, -8) + std::ldexp(1.0, -18)
+                                           : std::ldexp(1.0, -9) + std::ldexp(1.0, -20);
         ta.c1 = (float)(2.0 * (eps_mul + eps_acc) * 1.01);
         ta.c2 = (float)std::ldexp(1.0, -19);
         ta.c3 = (float)std::ldexp(1.0, -110);
@@ -912,10 +976,15 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
             std::lock_guard<std::mutex> lk(g_prof_mu);
             g_prof_recs.push_back(rec);
         }
-        s = crisp_run_bound_select(nq, cand, stride, ncand, k, qp, ulb, err_word, rc, nr, st);
+        s = crisp_run_bound_select(nq, cand, stride, ncand, task.k, task.qp, task.coarse ? 1 : 0, task.S_per_query,
+                                   ulb, err_word, rc, nr, st);
         if (s) break;
-        // the kept candidates, measured exactly (streaming CR32) -> top-k
-        s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, k, dbuf, ids, d2, st, false, false, qp, ko);
+        if (task.coarse)   // the kept candidates' exact coarse scores (streaming) -> the S best
+            s = crisp_run_shortlist(ix, Qr, nq, rc, stride, nr, 1, task.k, dbuf, task.out, task.out_stride, task.nout,
+                                    st, task.S_per_query, task.qp, false);
+        else               // the kept candidates, measured exactly (streaming CR32) -> top-k
+            s = crisp_run_rerank(ix, Qr, nq, rc, stride, nr, task.k, dbuf, task.ids, task.d2, st, false, false,
+                                 task.qp, task.ko);
     } while (0);
     crisp_scratch_free(buf, st);
     return s;

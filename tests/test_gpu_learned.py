@@ -157,3 +157,47 @@ def test_trained_model_gain_over_plain():
     # learned+BF16 moves fewer row bytes than plain FP32 at equal recall, and never more than BF16 alone
     assert learned_bytes < 0.55 * plain_bytes
     assert learned_bytes <= bf16_bytes * 1.001
+
+
+@pytest.fixture(scope="module")
+def c1l_big():
+    """600 queries: the learned path's BF16 shortlists of a batch this large come
+    from the tensor-core bounds (one BF16 pass, per-query shortlist sizes)."""
+    X, Q = synthetic.gmm(N=20000, D=256, nq=600, seed=9)
+    ix_o = oracle.build_index(X, M=8, draws=synthetic.method_draws(20000, 256, 8, 50, seed=9)).add_copies(fp8=False)
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    crisp.crisp_index_add_copies(ix, 1)
+    return X, Q, ix_o, ix
+
+
+@pytest.mark.parametrize("margins", [(0.0, 0.0), (1.0, 2.0)])
+def test_learned_search_large_batch_bitexact(c1l_big, margins):
+    X, Q, ix_o, ix = c1l_big
+    F, H = 2 * ix_o.M + 68, 64
+    P = synthetic.mlp_weights(F, H, 2, seed=13, scale=1.0)
+    P[-2:] += np.float32(7.0)
+    ix_o.set_model(P, H)
+    crisp.crisp_index_set_model(ix, dev(P), H)
+    kw = dict(k=10, mode=2, rho=0.02, alpha=0.25, depth_margin=margins[0], short_margin=margins[1])
+    nq = Q.shape[0]
+    ids = torch.empty((nq, 10), dtype=torch.int64, device=DEV)
+    d2 = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    st = torch.empty((nq, 6), dtype=torch.int64, device=DEV)
+    crisp.crisp_search(ix, dev(Q), nq, crisp.search_params(**kw), ids, d2, st)
+    oi, od, ost, _ = oracle.search(ix_o, Q, oracle.SearchParams(**kw))
+    assert np.array_equal(ids.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+    s = st.cpu().numpy()
+    assert np.array_equal(s[:, 1], ost["n_verified"]) and np.array_equal(s[:, 2], ost["n_full"])
+
+
+@pytest.mark.parametrize("S", [12, 50])
+def test_coarse_search_large_batch_bitexact(c1l_big, S):
+    """Guaranteed mode with BF16 coarse scores on 600 queries (tensor-core bounds)."""
+    X, Q, ix_o, ix = c1l_big
+    kw = dict(k=10, mode=0, rho=0.03, alpha=0.25, precision=1, shortlist=S)
+    nq = Q.shape[0]
+    ids = torch.empty((nq, 10), dtype=torch.int64, device=DEV)
+    d2 = torch.empty((nq, 10), dtype=torch.float32, device=DEV)
+    crisp.crisp_search(ix, dev(Q), nq, crisp.search_params(**kw), ids, d2)
+    oi, od, _, _ = oracle.search(ix_o, Q, oracle.SearchParams(**kw))
+    assert np.array_equal(ids.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
