@@ -404,8 +404,8 @@ def run_crisp(args):
         roofline_bf16 = {"kernel": sl_stage["kernel"], "bound": "hbm", "achieved": a_bf, "peak": peak, "unit": "GB/s",
                          "frac": a_bf / peak, "traffic": _ncu_traffic("shortlist_bf16", traffic_key),
                          "ms": round(sl_stage["ms"], 4), "algorithmic_bytes_per_launch": sl_stage["bytes"],
-                         "note": "BF16 coarse scoring of the same candidates (the learned+BF16 path's dominant "
-                                 "kernel), shortlist of 50, timed on its own"}
+                         "note": "BF16 coarse scoring of the same candidates (the learned+BF16 path's shortlist "
+                                 "step), shortlist of 50, timed on its own"}
 
     # ---- coarse-scoring variants (BF16 / FP8 rows, FP32 re-rank of a shortlist)
     variants = {}
@@ -1105,7 +1105,7 @@ def stage_rooflines(stage, info, hbm_peak, hbm_kind, traffic_key):
         t = sc["ms_per_launch"] / 1e3
         ach = fl / t / 1e12
         row_bytes = sc["rows_per_launch"] * sc.get("elem_bytes", 4) * sc["Dp"]
-        traffic = _ncu_traffic("k_rerank_tc", traffic_key)
+        traffic = _ncu_traffic("k_rerank_tc", traffic_key) if bf else None   # captured for the BF16 pass
         rooflines["rerank_scorer"] = {
             "kernel": "k_rerank_tc", "bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
             "frac": ach / tpk, "traffic": traffic, "ms": round(sc["ms_per_launch"], 4),
@@ -1165,7 +1165,8 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     bf16 = bool(info.Xb) and point["mode"] == 0
     if bf16:            # the F2 coarse-scoring kernel on the same candidates (timed on its own)
         names.append("shortlist_bf16")
-        kernels.append("k_gscore<BF16>" if grouped else "k_score_flat<BF16>")
+        kernels.append("k_rerank_tc BF16 coarse bounds (+ order, union, bound select, exact scores of the kept)"
+                       if grouped else "k_score_flat<BF16>")
         sl = torch.empty((nq, 64), dtype=torch.int32, device=dev)
         nsl = torch.empty((nq,), dtype=torch.int64, device=dev)
     acc = {n: 0.0 for n in names}

@@ -324,6 +324,21 @@ __global__ void k_row_norms_bf16(const uint16_t *__restrict__ Xb, long long N, i
 
 // ================================================== Q4 + Q5 count and cut
 constexpr int CNT_NT = 512;
+// Tuning (compile time): CNT_U flat ids per lane in flight, CNT_MINB resident
+// CTAs per SM (the register budget), CNT_EC activated cells decoded once per
+// query into shared memory (0: decoded again for every tile).
+#ifndef CRISP_CNT_U
+#define CRISP_CNT_U 4
+#endif
+#ifndef CRISP_CNT_MINB
+#define CRISP_CNT_MINB 3
+#endif
+#ifndef CRISP_CNT_ECACHE
+#define CRISP_CNT_ECACHE 0
+#endif
+constexpr int CNT_U = CRISP_CNT_U;
+constexpr int CNT_MINB = CRISP_CNT_MINB;
+constexpr int CNT_EC = CRISP_CNT_ECACHE;
 
 struct CountShared {
     int base[129];
@@ -338,9 +353,8 @@ struct CountShared {
     int c_gd[CNT_NT + 1];       // id-array position of the cell's flat id 0: m N + first - c_pre
     int c_w[CNT_NT + 1];        // the cell's weight (entry CNT_NT: read by lanes past the end, unused)
     long long scan_ws[CNT_NT / 32 + 1];
+    int ecache[CNT_EC > 0 ? CNT_EC : 1];   // (m << 20) | (w << 16) | cell per activated cell, when E <= CNT_EC
 };
-
-constexpr int CNT_U = 4;   // flat ids per lane in flight
 
 // Count tile t of query q into the byte counters `cnt` (zeroed here): every id
 // of every activated cell that falls in the tile adds its cell's weight.  The
@@ -364,14 +378,21 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
         const int i = threadIdx.x;
         if (i < ne) {
             const int e = e0 + i;
-            int lo = 0, hi = M - 1;            // subspace m with base[m] <= e < base[m+1]
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (S.base[mid] <= e) lo = mid;
-                else hi = mid - 1;
+            int ent;
+            if (CNT_EC > 0 && E <= CNT_EC) {
+                const int pk = S.ecache[e];
+                m = pk >> 20;
+                ent = pk & 0xFFFFF;
+            } else {
+                int lo = 0, hi = M - 1;            // subspace m with base[m] <= e < base[m+1]
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (S.base[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                m = lo;
+                ent = actq[(long long)m * K2 + (e - S.base[m])];
             }
-            m = lo;
-            const int ent = actq[(long long)m * K2 + (e - S.base[m])];
             const int *to = ix.tile_off + ((long long)m * K2 + (ent & 0xFFFF)) * (T + 1) + t;
             beg = to[0];
             len = to[1] - beg;
@@ -684,7 +705,7 @@ __device__ long long emit_tile(const IxView &ix, CountShared &S, const uint32_t 
     return tot_sel;
 }
 
-__global__ void __launch_bounds__(CNT_NT, 3) k_count_cut(IxView ix, const int *__restrict__ act,
+__global__ void __launch_bounds__(CNT_NT, CNT_MINB) k_count_cut(IxView ix, const int *__restrict__ act,
                                                       const int *__restrict__ nact, int nq, int tau, int kk,
                                                       long long cap, const QParam *__restrict__ qp,
                                                       int *__restrict__ cand, long long stride,
@@ -709,6 +730,18 @@ __global__ void __launch_bounds__(CNT_NT, 3) k_count_cut(IxView ix, const int *_
     __syncthreads();
     const int E = S.base[M];
     const int *actq = act + (long long)q * M * K2;
+    if (CNT_EC > 0 && E <= CNT_EC) {
+        for (int e = threadIdx.x; e < E; e += CNT_NT) {
+            int lo = 0, hi = M - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (S.base[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            S.ecache[e] = (lo << 20) | actq[(long long)lo * K2 + (e - S.base[lo])];
+        }
+        __syncthreads();
+    }
     int *candq = cand + (long long)q * stride;
     uint8_t *scoreq = score ? score + (long long)q * stride : nullptr;
     const int T = ix.T;
