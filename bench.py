@@ -4,7 +4,8 @@
 Workload (the paper's datasets are not available; synthetic rows of the Gist
 shape stand in for them): N = 1,000,000 rows, D = 960, x = U diag(sqrt(l)) z
 with l_i = i^-1.2 and U Haar-orthogonal (the CEV test triggers the rotation);
-10,000 held-out queries from the same law; k = 10; M = 20 subspaces, K = 50.
+10,000 held-out queries from the same law; k = 10; M = 12 subspaces, K = 50
+(the fastest M of a sweep over 12..32 at recall@10 >= 0.95).
 
 A step is one crisp_search over the whole 10,000-query batch (Q1-Q7 of the
 engine), inputs already resident in HBM; L2 (129 MB) is flushed by a 512 MB
@@ -671,7 +672,8 @@ def modes_leg(torch, crisp, ix, X, Q, args, dev):
                        ((0.01, 0.3), (0.02, 0.3), (0.03, 0.3), (0.04, 0.3), (0.03, 0.25), (0.05, 0.25), (0.08, 0.2))]
             else:
                 pts = [dict(k=k, mode=1, rho=r_, alpha=a_, patience_factor=pf, max_candidates=OPT_CAP)
-                       for r_, a_ in ((0.01, 0.3), (0.02, 0.3), (0.03, 0.3)) for pf in (40, 100, 200, 400)]
+                       for r_, a_ in ((0.01, 0.3), (0.02, 0.3), (0.03, 0.3), (0.04, 0.3), (0.05, 0.25))
+                       for pf in (40, 100, 200, 400)]
             pt, ok, log = _ladder(torch, X, Qva, gdv[:, k - 1].contiguous(), search, pts, k, dev)
             q, ms = timed(Q, pt, ids, d2, min(args.steps, 5), flush)
             r = recall_at_k(torch, X, Q, ids, gd[:, k - 1].contiguous())
@@ -1267,7 +1269,7 @@ def main():
     ap.add_argument("--dim", type=int, default=960)
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--k", type=int, default=10)
-    ap.add_argument("--M", type=int, default=20)
+    ap.add_argument("--M", type=int, default=12)
     ap.add_argument("--mode", type=int, default=None)
     ap.add_argument("--rho", type=float, default=None)
     ap.add_argument("--alpha", type=float, default=None)

@@ -3,14 +3,14 @@
 //
 // The candidate lists of a large batch overlap: on the 1M-row workload a row is
 // a candidate of about 200 of 10,000 queries.  The queries are ordered by the
-// MinHash of their candidate sets and cut into groups of TG = 64; the id space
+// MinHash of their candidate sets and cut into groups of TG (64) queries; the id space
 // into ranges of TSPAN ids.  For every (group, range) k_union lists the rows
 // some member needs, with a 64-bit member mask and each (row, member) pair's
 // slot in that member's list.  Then:
 //
 //   k_rerank_tc   each listed row is fetched once per group (16-byte cp.async
 //                 copies straight into the 128-byte swizzled operand layout) and
-//                 multiplied against the group's 64 queries (one TMA tile) on the
+//                 multiplied against the group's queries (one TMA tile) on the
 //                 tensor cores: dot = x . q in one TF32 pass over the FP32 rows,
 //                 or, when the index keeps its BF16 copy, in one BF16 pass over
 //                 that copy against the queries rounded to BF16 (half the bytes
@@ -94,7 +94,14 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 
 namespace {
 
-constexpr int TG = 64;              // queries per group: N of the MMA
+// Queries per group (N of the MMA; 64 or 128): a group's member mask is TGW
+// 64-bit words.
+#ifndef CRISP_TR_TG
+#define CRISP_TR_TG 64
+#endif
+constexpr int TG = CRISP_TR_TG;
+constexpr int TGW = TG / 64;
+static_assert(TG == 64 || TG == 128, "query groups of 64 or 128");
 constexpr int TR_MINQ = 256;        // smaller batches re-rank query by query
 constexpr int TSPAN = 4096;         // ids per range (the ordering's range size)
 constexpr int TU_NT = 256;          // k_union threads
@@ -102,7 +109,7 @@ constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
 // Stage geometry (tunable at compile time): TR_NS stages of TR_KB 32-float
 // k-blocks of a tile each, TR_NB accumulator buffers, TR_RB id ranges per item.
 #ifndef CRISP_TR_NS
-#define CRISP_TR_NS 4
+#define CRISP_TR_NS (CRISP_TR_TG == 64 ? 4 : 3)
 #endif
 #ifndef CRISP_TR_KB
 #define CRISP_TR_KB 1
@@ -115,14 +122,14 @@ constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
 #endif
 constexpr int TR_NS = CRISP_TR_NS;  // shared-memory stages
 constexpr int TR_KB = CRISP_TR_KB;  // 32-float k-blocks of the tile's rows and queries per stage
-constexpr int TR_NB = 4;            // tensor-memory accumulator buffers of 128 columns
+constexpr int TR_NB = 512 / (2 * TG);   // tensor-memory accumulator buffers of 2 TG columns (512 in all)
 constexpr int TR_LT = 128;          // copy threads (warps 8-11)
 constexpr int TR_NT = 448;          // warps 0-7 epilogue, 8-11 copies, 12 tile preparation, 13 MMA issue
 constexpr int TR_WC = 8, TR_WP = 12, TR_WM = 13;   // first copy warp, preparation warp, MMA warp
 constexpr int TR_RB = CRISP_TR_RB;  // id ranges per work item
 constexpr int TR_PMAX = CRISP_TR_PMAX;   // (row, member) pairs of a tile whose list positions are staged in shared memory
 constexpr uint32_t TR_A_BYTES = 128 * 128;                     // 128 rows x one k-block
-constexpr uint32_t TR_B_BYTES = TG * 128;                      // 64 queries x one k-block
+constexpr uint32_t TR_B_BYTES = TG * 128;                      // the group's queries x one k-block
 constexpr uint32_t TR_STAGE = TR_KB * (2 * TR_A_BYTES + TR_B_BYTES);   // rows of both halves, then the queries
 
 __device__ unsigned int g_tr_error;   // first failing wait: 1 + its site code
@@ -164,7 +171,7 @@ struct TUnion {
     const int *gq;                  // [ngroups * TG] query of each group slot, -1 past nq
     const int *pos;                 // [nq][R + 1] first list position with id >= r TSPAN
     int *ent_row;                   // [ecap] row id
-    unsigned long long *ent_mask;   // [ecap] members that need the row
+    unsigned long long *ent_mask;   // [ecap][TGW] members that need the row
     int *ent_pb;                    // [ecap] first pair slot of the row
     float *ent_nx;                  // [ecap] |x|^2 of the row
     const float *xn2;               // [N] row norms of the index
@@ -211,8 +218,8 @@ __device__ __forceinline__ long long tr_block_scan(long long v, long long *ws, l
 // own slot, so nothing downstream depends on it.
 __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, long long stride, TUnion u) {
     extern __shared__ __align__(16) unsigned long long usm[];
-    unsigned long long *mask = usm;                      // [TSPAN]
-    int *pbl = reinterpret_cast<int *>(usm + TSPAN);    // [TSPAN] pair base of each row, within the block
+    unsigned long long *mask = usm;                      // [TSPAN][TGW]
+    int *pbl = reinterpret_cast<int *>(usm + TSPAN * TGW);   // [TSPAN] pair base of each row, within the block
     __shared__ int s_q[TG], s_base[TG], s_cnt[TG], s_off[TG + 1];
     __shared__ long long scan_ws[TU_NT / 32 + 1];
     __shared__ long long s_eb, s_pb;
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
         s_base[tid] = a;
         s_cnt[tid] = b - a;
     }
-    for (int o = tid; o < TSPAN; o += TU_NT) mask[o] = 0ull;
+    for (int o = tid; o < TSPAN * TGW; o += TU_NT) mask[o] = 0ull;
     __syncthreads();
     if (tid == 0) {
         int acc = 0;
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
             else hi = mid - 1;
         }
         const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + (e - s_off[lo])];
-        atomicOr(&mask[id - lo_id], 1ull << lo);
+        atomicOr(&mask[(id - lo_id) * TGW + (lo >> 6)], 1ull << (lo & 63));
     }
     __syncthreads();
     // thread t owns the ids t, t + TU_NT, ... (conflict-free reads); one packed
@@ -259,7 +266,9 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
     int rows = 0, pairs = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int c = __popcll(mask[tid + k * TU_NT]);
+        int c = 0;
+#pragma unroll
+        for (int w = 0; w < TGW; ++w) c += __popcll(mask[(tid + k * TU_NT) * TGW + w]);
         pairs += c;
         rows += c > 0 ? 1 : 0;
     }
@@ -282,16 +291,19 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int o = tid + k * TU_NT;
-        const unsigned long long m = mask[o];
-        if (m) {
+        int c = 0;
+#pragma unroll
+        for (int w = 0; w < TGW; ++w) c += __popcll(mask[o * TGW + w]);
+        if (c) {
             const long long ei = s_eb + er;
             u.ent_row[ei] = (int)(lo_id + o);
-            u.ent_mask[ei] = m;
+#pragma unroll
+            for (int w = 0; w < TGW; ++w) u.ent_mask[ei * TGW + w] = mask[o * TGW + w];
             u.ent_pb[ei] = (int)(s_pb + pr);
             u.ent_nx[ei] = u.xn2[lo_id + o];
             pbl[o] = pr;
             ++er;
-            pr += __popcll(m);
+            pr += c;
         }
     }
     __syncthreads();
@@ -306,7 +318,9 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
         const int t = e - s_off[lo];
         const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + t];
         const int o = id - (int)lo_id;
-        const long long slot = s_pb + pbl[o] + __popcll(mask[o] & ((1ull << lo) - 1ull));
+        int below = __popcll(mask[o * TGW + (lo >> 6)] & ((1ull << (lo & 63)) - 1ull));
+        if (TGW > 1 && lo >= 64) below += __popcll(mask[o * TGW]);
+        const long long slot = s_pb + pbl[o] + below;
         u.pair_pos[slot] = s_base[lo] + t;
     }
 }
@@ -315,7 +329,7 @@ struct TileMeta {
     int g;                          // query group of the tile
     int count;                      // rows in use (< 0: no more tiles)
     int rid[TR_ROWS];               // per row: row id (rows past count repeat row 0)
-    unsigned long long mask[TR_ROWS];   // per row: members that need it
+    unsigned long long mask[TR_ROWS][TGW];   // per row: members that need it
     int pb[TR_ROWS];                // per row: first pair slot
     int off[TR_ROWS];               // per row: its first pair in spos
     float nx[TR_ROWS];              // per row: |x|^2
@@ -351,6 +365,7 @@ __host__ __device__ constexpr size_t tr_smem_bytes() {
     return 1024 + (size_t)TR_NS * TR_STAGE + sizeof(TileMeta) * TR_NB + sizeof(int) * 4 * TR_MAXSEG +
            sizeof(uint64_t) * TR_NBAR + 32;
 }
+static_assert(tr_smem_bytes() <= 227 * 1024, "the stages and tile buffers must fit one CTA's shared memory");
 
 // 16 bytes, of which the first n (0 or 16) come from src and the rest are zeros.
 __device__ __forceinline__ void cp_async16_n(uint32_t dst, const void *src, uint32_t n) {
@@ -459,7 +474,9 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                 const int r0 = sseg[3 * sg], n = sseg[3 * sg + 1], e0 = sseg[3 * sg + 2];
                 for (int i = lane; i < n; i += 32) {
                     cp_async4(smem_addr(&mt.rid[r0 + i]), a.ent_row + e0 + i);
-                    cp_async8(smem_addr(&mt.mask[r0 + i]), a.ent_mask + e0 + i);
+#pragma unroll
+                    for (int w = 0; w < TGW; ++w)
+                        cp_async8(smem_addr(&mt.mask[r0 + i][w]), a.ent_mask + (long long)(e0 + i) * TGW + w);
                     cp_async4(smem_addr(&mt.pb[r0 + i]), a.ent_pb + e0 + i);
                     cp_async4(smem_addr(&mt.nx[r0 + i]), a.ent_nx + e0 + i);
                 }
@@ -477,7 +494,10 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
             int base = 0;
             for (int sg = 0; sg < nseg; ++sg) {
                 const int r0 = sseg[3 * sg], n = sseg[3 * sg + 1];
-                const int pb0 = mt.pb[r0], len = mt.pb[r0 + n - 1] + __popcll(mt.mask[r0 + n - 1]) - pb0;
+                int lastc = 0;
+#pragma unroll
+                for (int w = 0; w < TGW; ++w) lastc += __popcll(mt.mask[r0 + n - 1][w]);
+                const int pb0 = mt.pb[r0], len = mt.pb[r0 + n - 1] + lastc - pb0;
                 for (int r = r0 + lane; r < r0 + n; r += 32) mt.off[r] = base + mt.pb[r] - pb0;
                 const int lim = base + len < TR_PMAX ? len : TR_PMAX - base;
                 for (int p = lane; p < lim; p += 32) cp_async4(smem_addr(&mt.spos[base + p]), a.pair_pos + pb0 + p);
@@ -601,7 +621,7 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d0 = tmem + 128u * b, d1 = d0 + 64u;
+                const uint32_t d0 = tmem + (uint32_t)(2 * TG) * b, d1 = d0 + (uint32_t)TG;
                 bool bad = false;
                 const int nst = (a.nk + TR_KB - 1) / TR_KB;
                 for (int si = 0; si < nst; ++si, ++c) {
@@ -660,18 +680,23 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
             if (count < 0) break;
             if (!warp_wait(afull0 + 8u * b, (uint32_t)(t / TR_NB) & 1u, 7)) break;
             tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 128u * b + 64u * h;
+            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(2 * TG) * b + (uint32_t)TG * h;
             const int row = 32 * qd + lane + 128 * h;
             const bool valid = row < count;
-            const unsigned long long m = valid ? mt.mask[row] : 0ull;
+            unsigned long long mw[TGW];
+#pragma unroll
+            for (int w = 0; w < TGW; ++w) mw[w] = valid ? mt.mask[row][w] : 0ull;
             const int pb = valid ? mt.pb[row] : 0, po = valid ? mt.off[row] : 0;
             const float nx = valid ? mt.nx[row] : 0.0f, rx = sqrtf(nx), c1rx = a.c1 * rx;
 #pragma unroll 1
             for (int cb = 0; cb < TG / 16; ++cb) {
                 uint32_t v[16];
                 tmem_ld16(ta + 16u * cb, v);               // warp-collective: every lane takes part
-                const unsigned sub = (unsigned)(m >> (16 * cb)) & 0xFFFFu;
-                const int rank0 = __popcll(m & ((1ull << (16 * cb)) - 1ull));
+                const unsigned long long m = mw[cb >> 2];                  // the word holding members 16 cb ..
+                const int sh = 16 * (cb & 3);
+                const unsigned sub = (unsigned)(m >> sh) & 0xFFFFu;
+                int rank0 = __popcll(m & ((1ull << sh) - 1ull));
+                if (TGW > 1 && cb >= 4) rank0 += __popcll(mw[0]);
                 int pos[16];
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {          // list positions for members 16 cb + jj
@@ -864,7 +889,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
                  o_gn1 = take(sizeof(float) * nslots), o_qg = take(sizeof(float) * (size_t)nslots * Dp),
                  o_qgb = take(bf ? sizeof(uint16_t) * (size_t)nslots * Dp64 : 0),
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)ecap),
-                 o_mask = take(sizeof(unsigned long long) * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
+                 o_mask = take(sizeof(unsigned long long) * TGW * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
                  o_enx = take(sizeof(float) * (size_t)ecap),
                  o_pp = take(sizeof(int) * (size_t)pcap), o_ulb = take(sizeof(float2) * (size_t)nq * stride),
                  o_rc = take(sizeof(int) * (size_t)nq * stride), o_nr = take(sizeof(int64_t) * nq);
@@ -903,7 +928,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         if (s) break;
         k_group_queries<<<(nslots + 7) / 8, 256, 0, st>>>(Qr, nq, Dp, qord, nslots, Qg, Qgb, Dp64, gq, gn2, gn1);
         CRISP_COUNT_LAUNCH();
-        const size_t usmem = sizeof(unsigned long long) * TSPAN + sizeof(int) * TSPAN;
+        const size_t usmem = sizeof(unsigned long long) * TSPAN * TGW + sizeof(int) * TSPAN;
         e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
         k_union<<<dim3(R, ngroups), TU_NT, usmem, st>>>(cand, (long long)stride, u);
