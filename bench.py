@@ -1070,10 +1070,10 @@ def run_ablation(args):
         w = np.diff(crisp.crisp_index_get_bounds(ix))
         ext.append(dict(config=name, build_s=build_s, rotated=int(info.rotated), rotated_blocks=int(info.rotated_blocks),
                         subspace_dims_min=int(w.min()), subspace_dims_max=int(w.max()),
-                        points=[dict(rho=rho, **measure(ix, X, Q, gd, crisp.search_params(k=10, rho=rho, alpha=0.25),
-                                                        10)) for rho in (0.01, 0.02, 0.05)]))
+                        points=[dict(rho=rho, **measure(ix, X, Q, gd, crisp.search_params(k=10, rho=rho, alpha=0.15),
+                                                        10)) for rho in (0.05, 0.1, 0.2)]))
         ix.free()
-    out["extensions"] = {"point": "Guaranteed, k=10, alpha=0.25, 2,000 queries, mixed 1M x 960, M=20",
+    out["extensions"] = {"point": "Guaranteed, k=10, alpha=0.15, 2,000 queries, mixed 1M x 960, M=20",
                          "configs": ext}
     out["workloads"] = {"tau_cev": "gmm, powerlaw, vmf (200 components, kappa 200), lowrank (rank 128, 5% x10)",
                         "patience_subcomponents": "powerlaw 1M x 960, M=20",

@@ -836,6 +836,7 @@ struct TopkShared {
     int sid[CRISP_KOUT_MAX];
     unsigned prefix;
     int need;
+    unsigned count, fill;   // radix_kth_gather: keys in the selected bin; keys gathered
 };
 
 // Block-wide radix select over the FP32 keys dist[i * ks], i in [0, n)
@@ -888,6 +889,81 @@ __device__ void radix_kth(const float *distq, long long n, int kk, TopkShared &S
     }
     *out_prefix = prefix;
     *out_need = need;
+}
+
+// One radix pass: the histogram of digit (key >> shift) & 255 over the keys
+// whose bits under `mask` equal `prefix` (key(i) for i in [0, n)), then the
+// digit holding the need-th of them; updates prefix / need (block-uniform).
+template <class KeyAt>
+__device__ void radix_pass(KeyAt key_at, long long n, int shift, unsigned &mask, unsigned &prefix, int &need,
+                           TopkShared &S) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 256; i += RR_NT) S.hist[i] = 0;
+    __syncthreads();
+    for (long long i0 = 0; i0 < n; i0 += (long long)RR_NT * SEL_U) {
+        unsigned key[SEL_U];
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const long long i = i0 + (long long)u * RR_NT + tid;
+            key[u] = i < n ? key_at(i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const long long i = i0 + (long long)u * RR_NT + tid;
+            const bool hit = i < n && (key[u] & mask) == prefix;
+            const unsigned bin = hit ? (key[u] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (hit && (__ffs(peers) - 1) == (int)(tid & 31)) atomicAdd(&S.hist[bin], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned cum = 0;
+        int b = 0;
+        for (; b < 255; ++b) {
+            if (cum + S.hist[b] >= (unsigned)need) break;
+            cum += S.hist[b];
+        }
+        S.prefix = prefix | ((unsigned)b << shift);
+        S.need = need - (int)cum;
+        S.count = S.hist[b];
+    }
+    __syncthreads();
+    prefix = S.prefix;
+    need = S.need;
+    mask |= 255u << shift;
+    __syncthreads();
+}
+
+constexpr int BS_CAP = 2048;   // keys of the selected 16-bit prefix finished in shared memory
+
+// The key of the kk-th smallest of n non-negative FP32 keys (contiguous): the
+// two high digits are selected over the keys in global memory; the keys that
+// share the resulting 16-bit prefix are then gathered into shared memory (when
+// at most BS_CAP of them) and the two low digits are selected there.
+__device__ unsigned radix_kth_gather(const float *keys, long long n, int kk, TopkShared &S, unsigned *buf) {
+    unsigned prefix = 0, mask = 0;
+    int need = kk;
+    auto gk = [&](long long i) { return __float_as_uint(keys[i]); };
+    radix_pass(gk, n, 24, mask, prefix, need, S);
+    radix_pass(gk, n, 16, mask, prefix, need, S);
+    if (S.count > (unsigned)BS_CAP) {
+        radix_pass(gk, n, 8, mask, prefix, need, S);
+        radix_pass(gk, n, 0, mask, prefix, need, S);
+        return prefix;
+    }
+    if (threadIdx.x == 0) S.fill = 0;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < n; i += RR_NT) {
+        const unsigned k = gk(i);
+        if ((k & mask) == prefix) buf[atomicAdd(&S.fill, 1u)] = k;
+    }
+    __syncthreads();
+    const long long m = S.fill;
+    auto sk = [&](long long i) { return buf[i]; };
+    radix_pass(sk, m, 8, mask, prefix, need, S);
+    radix_pass(sk, m, 0, mask, prefix, need, S);
+    return prefix;
 }
 
 // Visit, in list order, the entries with key < prefix and the first `need`
@@ -1909,15 +1985,17 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
 // If the scorer reported a failure (*err != 0) its bounds cannot be trusted
 // and every candidate is kept, so the result is still exact.
 // Target per query: kq[q] if given, else the query's k (qfield 0) or
-// shortlist size S (qfield 1) from qp, else kk.
+// shortlist size S (qfield 1) from qp, else kk.  ub / lb: each pair's upper and
+// lower bound, at the candidate's list position.
 __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__restrict__ cand, long long stride,
                                                         const long long *__restrict__ ncand, int kk,
                                                         const QParam *__restrict__ qp, int qfield,
                                                         const long long *__restrict__ kq,
-                                                        const float2 *__restrict__ ulb,
+                                                        const float *__restrict__ ub, const float *__restrict__ lb,
                                                         const unsigned *__restrict__ err, int *__restrict__ rc,
                                                         long long *__restrict__ nr) {
     __shared__ TopkShared S;
+    __shared__ unsigned gbuf[BS_CAP];
     const int q = blockIdx.x, tid = threadIdx.x;
     if (kq) kk = (int)(kq[q] < (long long)INT_MAX ? kq[q] : (long long)INT_MAX);
     else if (qp) kk = qfield ? qp[q].S : qp[q].k;
@@ -1929,12 +2007,8 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
         if (tid == 0) nr[q] = n;
         return;
     }
-    unsigned prefix;
-    int need;
-    const float *uq = reinterpret_cast<const float *>(ulb + (long long)q * stride);
-    radix_kth(uq, n, kk, S, &prefix, &need, 2);
-    const float U = __uint_as_float(prefix);
-    const float *lq = uq + 1;
+    const float U = __uint_as_float(radix_kth_gather(ub + (long long)q * stride, n, kk, S, gbuf));
+    const float *lq = lb + (long long)q * stride;
     long long run = 0;
     for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {
         float lv[SEL_U];
@@ -1942,7 +2016,7 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
 #pragma unroll
         for (int u = 0; u < SEL_U; ++u) {
             const long long i = c00 + (long long)u * RR_NT + tid;
-            lv[u] = i < n ? lq[2 * i] : INFINITY;
+            lv[u] = i < n ? lq[i] : INFINITY;
             any = any || lv[u] <= U;
         }
         if (!__syncthreads_or(any)) continue;       // most chunks hold nothing to re-measure
@@ -2170,11 +2244,11 @@ crisp_status crisp_run_rerank(const crisp_index *ix, const float *Qr, int32_t nq
 }
 
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float2 *ulb,
-                                    const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st) {
+                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float *ub,
+                                    const float *lb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
     k_bound_select<<<nq, RR_NT, 0, st>>>(nq, cand, (long long)stride, (const long long *)ncand, k, qp, qfield,
-                                         (const long long *)kq, ulb, err, rc, (long long *)nr);
+                                         (const long long *)kq, ub, lb, err, rc, (long long *)nr);
     CRISP_COUNT_LAUNCH();
     CRISP_CK_LAUNCH();
     return CRISP_OK;

@@ -82,8 +82,8 @@ bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int c
 crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                    unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
-                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float2 *ulb,
-                                    const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
+                                    const QParam *qp, int32_t qfield, const int64_t *kq, const float *ub,
+                                    const float *lb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
 crisp_status crisp_run_shortlist(const crisp_index *ix, const float *Qr, int32_t nq, const int32_t *cand,
                                  int64_t stride, const int64_t *ncand, int32_t precision, int32_t S, float *dbuf,
                                  int32_t *out, int64_t out_stride, int64_t *nout, cudaStream_t st,
@@ -249,15 +249,12 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
     __syncthreads();
     const int np = s_off[TG];
     const long long lo_id = (long long)r * TSPAN;
-    for (int e = tid; e < np; e += TU_NT) {
-        int lo = 0, hi = TG - 1;                 // member j with s_off[j] <= e < s_off[j + 1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= e) lo = mid;
-            else hi = mid - 1;
-        }
-        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + (e - s_off[lo])];
-        atomicOr(&mask[(id - lo_id) * TGW + (lo >> 6)], 1ull << (lo & 63));
+    const int warp = tid >> 5, lane = tid & 31;
+    // a warp per member, lanes over the member's ids in the range (coalesced)
+    for (int j = warp; j < TG; j += TU_NT / 32) {
+        const int *cq = cand + (long long)s_q[j] * stride + s_base[j];
+        const unsigned long long bit = 1ull << (j & 63);
+        for (int t = lane; t < s_cnt[j]; t += 32) atomicOr(&mask[(cq[t] - lo_id) * TGW + (j >> 6)], bit);
     }
     __syncthreads();
     // thread t owns the ids t, t + TU_NT, ... (conflict-free reads); one packed
@@ -308,20 +305,15 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
     }
     __syncthreads();
     // pair slots: member j of row o goes to slot base(o) + (members of o below j)
-    for (int e = tid; e < np; e += TU_NT) {
-        int lo = 0, hi = TG - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= e) lo = mid;
-            else hi = mid - 1;
+    for (int j = warp; j < TG; j += TU_NT / 32) {
+        const int *cq = cand + (long long)s_q[j] * stride + s_base[j];
+        const unsigned long long lowbits = (1ull << (j & 63)) - 1ull;
+        for (int t = lane; t < s_cnt[j]; t += 32) {
+            const int o = cq[t] - (int)lo_id;
+            int below = __popcll(mask[o * TGW + (j >> 6)] & lowbits);
+            if (TGW > 1 && j >= 64) below += __popcll(mask[o * TGW]);
+            u.pair_pos[s_pb + pbl[o] + below] = s_base[j] + t;
         }
-        const int t = e - s_off[lo];
-        const int id = cand[(long long)s_q[lo] * stride + s_base[lo] + t];
-        const int o = id - (int)lo_id;
-        int below = __popcll(mask[o * TGW + (lo >> 6)] & ((1ull << (lo & 63)) - 1ull));
-        if (TGW > 1 && lo >= 64) below += __popcll(mask[o * TGW]);
-        const long long slot = s_pb + pbl[o] + below;
-        u.pair_pos[slot] = s_base[lo] + t;
     }
 }
 
@@ -355,7 +347,7 @@ struct TrArgs {
     const int *pair_pos;
     const int2 *items_arr;          // [ngroups][R]
     unsigned long long *counter;    // work-item counter
-    float2 *ulb;                    // [nq][stride] (upper, lower) bound of each pair's CR32 distance
+    float *ub, *lb;                 // [nq][stride] upper / lower bound of each pair's CR32 distance
     float c1, c2, c3, c4, gam;      // error-bound constants (file comment)
 };
 
@@ -711,7 +703,9 @@ __global__ void __launch_bounds__(TR_NT, 1) k_rerank_tc(const __grid_constant__ 
                         const float dt = ss - 2.0f * __uint_as_float(v[jj]);
                         const float E = mt.gn1[j] * c1rx + a.c2 * ss + (a.c3 * (rx + mt.gn1[j]) + a.c4);
                         const float E2 = E + a.gam * (fabsf(dt) + E);
-                        a.ulb[(long long)mt.gq[j] * a.stride + pos[jj]] = make_float2(fmaxf(dt + E2, 0.0f), dt - E2);
+                        const long long at = (long long)mt.gq[j] * a.stride + pos[jj];
+                        a.ub[at] = fmaxf(dt + E2, 0.0f);
+                        a.lb[at] = dt - E2;
                     }
                 }
             }
@@ -891,7 +885,8 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)ecap),
                  o_mask = take(sizeof(unsigned long long) * TGW * (size_t)ecap), o_pb = take(sizeof(int) * (size_t)ecap),
                  o_enx = take(sizeof(float) * (size_t)ecap),
-                 o_pp = take(sizeof(int) * (size_t)pcap), o_ulb = take(sizeof(float2) * (size_t)nq * stride),
+                 o_pp = take(sizeof(int) * (size_t)pcap), o_ub = take(sizeof(float) * (size_t)nq * stride),
+                 o_lb = take(sizeof(float) * (size_t)nq * stride),
                  o_rc = take(sizeof(int) * (size_t)nq * stride), o_nr = take(sizeof(int64_t) * nq);
     uint8_t *buf = nullptr;
     CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
@@ -899,7 +894,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     int *qord = (int *)(buf + o_qord), *pos = (int *)(buf + o_pos), *gq = (int *)(buf + o_gq);
     float *gn2 = (float *)(buf + o_gn2), *gn1 = (float *)(buf + o_gn1), *Qg = (float *)(buf + o_qg);
     uint16_t *Qgb = bf ? (uint16_t *)(buf + o_qgb) : nullptr;
-    float2 *ulb = (float2 *)(buf + o_ulb);
+    float *ub = (float *)(buf + o_ub), *lb = (float *)(buf + o_lb);
     int32_t *rc = (int32_t *)(buf + o_rc);
     int64_t *nr = (int64_t *)(buf + o_nr);
     TUnion u;
@@ -959,7 +954,8 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         ta.pair_pos = u.pair_pos;
         ta.items_arr = u.items;
         ta.counter = counts + 2;
-        ta.ulb = ulb;
+        ta.ub = ub;
+        ta.lb = lb;
         const int K = bf ? 16 : 8;
         const double eps_acc = (double)(Dp / K + 1) * (K + 1) * std::ldexp(1.0, -22);
         // coarse scores are of the BF16 rows themselves: only the query is rounded
@@ -1002,7 +998,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
             g_prof_recs.push_back(rec);
         }
         s = crisp_run_bound_select(nq, cand, stride, ncand, task.k, task.qp, task.coarse ? 1 : 0, task.S_per_query,
-                                   ulb, err_word, rc, nr, st);
+                                   ub, lb, err_word, rc, nr, st);
         if (s) break;
         if (task.coarse)   // the kept candidates' exact coarse scores (streaming) -> the S best
             s = crisp_run_shortlist(ix, Qr, nq, rc, stride, nr, 1, task.k, dbuf, task.out, task.out_stride, task.nout,
