@@ -260,7 +260,8 @@ typedef struct crisp_server crisp_server;
 typedef struct {
     int32_t streams;           /* concurrent batches (stream slots), 1..64 */
     int32_t max_batch;         /* requests per batch */
-    int64_t scratch_budget;    /* device bytes of search scratch in flight (0: 8 GiB) */
+    int64_t scratch_budget;    /* device bytes of search scratch in flight (0: half the device memory
+                                  free at creation, between 8 and 64 GiB) */
 } crisp_server_params;
 
 typedef struct {

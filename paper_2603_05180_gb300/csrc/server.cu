@@ -209,9 +209,17 @@ extern "C" crisp_status crisp_server_create(const crisp_index *ix, const crisp_s
     crisp_server *sv = new crisp_server();
     sv->ix = ix;
     sv->prm = *p;
-    if (sv->prm.scratch_budget == 0) sv->prm.scratch_budget = (int64_t)8 << 30;
     sv->device = ix->device;
     cudaSetDevice(sv->device);
+    if (sv->prm.scratch_budget == 0) {
+        // default: half the device memory free now, between 8 and 64 GiB
+        size_t free_b = 0, total_b = 0;
+        int64_t b = (int64_t)8 << 30;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            b = std::min<int64_t>(std::max<int64_t>(b, (int64_t)(free_b / 2)), (int64_t)64 << 30);
+        else cudaGetLastError();
+        sv->prm.scratch_budget = b;
+    }
     sv->slots.resize(p->streams);
     const size_t B = (size_t)p->max_batch, D = (size_t)ix->D, KO = CRISP_KOUT_MAX;
     for (Slot &s : sv->slots) {
