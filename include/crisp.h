@@ -430,15 +430,19 @@ crisp_status crisp_kmeans(const float *T, int64_t S, int32_t ldt, int32_t off, i
 crisp_status crisp_assign_cells(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
                                 int32_t H, const int32_t *sub, const float *cent, uint16_t *cells, void *stream);
 
-/* B3 on the tensor cores (tcgen05, TF32 pipe), same result as
- * crisp_assign_cells bit for bit: the tensor cores score every centroid
- * (|c|^2 - 2 x.c), and the centroids whose score is within its proven error
- * bound of the best are re-measured with the SEQ distance (ties to the lowest
- * index).  The build uses it for every row.  Xr must be 16-byte aligned with
- * Dp a multiple of 32 (rows are fetched by TMA); K <= 64.  Synchronous on the
- * stream: ECUDA if a pipeline wait of the kernel timed out. */
-crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                   int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
+/* B3 on the tensor cores (tcgen05), same result as crisp_assign_cells bit
+ * for bit: the tensor cores score every centroid (|c|^2 - 2 x.c), and the
+ * centroids whose score is within its proven error bound of the best are
+ * re-measured with the SEQ distance on the FP32 rows (ties to the lowest
+ * index).  Xb NULL: one TF32 pass over Xr; else Xb (device [N][Dp] BF16 bits,
+ * the round-to-nearest-even copy of Xr, as crisp_quantize_bf16 writes it) is
+ * scored in one BF16 pass against the centroids rounded to BF16 (half the
+ * bytes, a bound about twice as wide, so more centroids are re-measured).
+ * The build uses the TF32 form for every row.  Xr and Xb must be 16-byte
+ * aligned with Dp a multiple of 32 (rows are fetched by TMA); K <= 64.
+ * Synchronous on the stream: ECUDA if a pipeline wait of the kernel timed out. */
+crisp_status crisp_assign_cells_tc(const float *Xr, const uint16_t *Xb, int64_t N, int32_t D, int32_t Dp, int32_t M,
+                                   int32_t K, int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
                                    void *stream);
 
 /* B4 (§4.2 CSR): for one subspace, Offsets (device [K2+1] int32) and ids

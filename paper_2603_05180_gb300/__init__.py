@@ -103,7 +103,7 @@ _SIGS = {
     "crisp_rotate_rows_tc": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
     "crisp_kmeans": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P, _P],
     "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
-    "crisp_assign_cells_tc": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
+    "crisp_assign_cells_tc": [_P, _P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
     "crisp_column_variance": [_P, _I64, _I32, _I32, _P, _I64, _P, _P],
     "crisp_adaptive_bounds": [_P, _I32, _I32, _P],
     "crisp_csr_build": [_P, _I64, _I32, _P, _P, _P],
@@ -350,9 +350,11 @@ def crisp_assign_cells(Xr, N, D, Dp, M, K, H, cent, cells, stream=None, sub=None
     _call("crisp_assign_cells", _ptr(Xr), N, D, Dp, M, K, H, _ptr(sb), _ptr(cent), _ptr(cells), _stream(stream))
 
 
-def crisp_assign_cells_tc(Xr, N, D, Dp, M, K, H, cent, cells, stream=None, sub=None):
+def crisp_assign_cells_tc(Xr, N, D, Dp, M, K, H, cent, cells, stream=None, sub=None, Xb=None):
+    """``Xb``: the BF16 copy of ``Xr`` (device) for the BF16 pass; None: one TF32 pass."""
     sb = _host_i32(sub)
-    _call("crisp_assign_cells_tc", _ptr(Xr), N, D, Dp, M, K, H, _ptr(sb), _ptr(cent), _ptr(cells), _stream(stream))
+    _call("crisp_assign_cells_tc", _ptr(Xr), _ptr(Xb), N, D, Dp, M, K, H, _ptr(sb), _ptr(cent), _ptr(cells),
+          _stream(stream))
 
 
 def crisp_column_variance(X, N, D, ldx, rows, S, var, stream=None):

@@ -134,8 +134,10 @@ void crisp_scratch_free(void *p, cudaStream_t st);
 // Tensor-core cell assignment (tc.cu): cells [M][N], or per-half centroid
 // indices asg [2M][N] when asg is not null.  Synchronous on st.
 // sub: host [M+1] subspace boundaries.
+// Xb (optional): the BF16 copy of Xr; given, the scores come from one BF16 pass.
 crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
-                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st);
+                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st,
+                             const uint16_t *Xb = nullptr);
 // X' = X R on the tensor cores writing only Y[:, 0:ncols] (ncols <= D rounded up to 32).
 crisp_status crisp_rotate_rows_tc_cols(const float *X, int64_t N, int32_t D, int32_t ldx, const float *R, float *Y,
                                        int32_t ldy, int32_t ncols, cudaStream_t st);

@@ -22,6 +22,8 @@
 
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -379,7 +381,13 @@ struct AsgArgs {
 
 // TF32 score error bound (both operands truncated to 10 mantissa bits, FP32
 // accumulation) plus the FP32 rounding of the exact distances, generously.
+template <bool BF>
 __device__ __forceinline__ float asg_bound(float nx, float nx2, float c, float c2) {
+    // BF16 (both operands rounded to nearest, 2^-9 each): each product within
+    // (2^-8 + 2^-18) |x_i c_i|, the FP32 accumulation of h <= 128 dims in K = 16
+    // steps within 3.6e-5 |x| |c|: |score~ - score| <= 7.9e-3 |x| |c|; 1.2e-2
+    // with margin, plus the same rounding term as TF32
+    if (BF) return 1.2e-2f * nx * c + 1e-4f * (nx2 + c2) + 1e-30f;
     return 6e-3f * nx * c + 1e-4f * (nx2 + c2);
 }
 
@@ -390,8 +398,13 @@ __host__ __device__ inline size_t asg_smem_bytes(int K, int HS) {
     return 1024 + 2 * (size_t)asg_stage_bytes() + sizeof(float) * (2 * (size_t)K * HS + 4 * AS_KPAD) + 64;
 }
 
+// BF = false: one TF32 pass over the FP32 rows (k-blocks of 32 floats);
+// BF = true: one BF16 pass over the rows' BF16 copy against BF16 centroids
+// (k-blocks of 64 elements).  The exact re-measure reads the FP32 rows either way.
+template <bool BF>
 __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUtensorMap tmX,
                                                      const __grid_constant__ CUtensorMap tmB, AsgArgs a) {
+    constexpr int KE = BF ? 64 : TC_BK;                               // elements per 128-byte k-block
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
     uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);   // swizzled tiles need 1024-byte alignment
@@ -401,8 +414,8 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
     const long long row0 = (long long)(blockIdx.x / (unsigned)a.M) * TC_BM;
     const int lo = a.sub[m], hi_ = a.sub[m + 1];
     const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl, HS = hr;     // hr >= hl
-    const int base = lo & ~(TC_BK - 1);
-    const int nk = (hi_ - base + TC_BK - 1) / TC_BK;
+    const int base = lo & ~(KE - 1);
+    const int nk = (hi_ - base + KE - 1) / KE;
     float *sC = (float *)(sm + 2 * STAGE);                             // [2][K][HS]
     float *sN2 = sC + 2 * a.K * HS, *sN1 = sN2 + 2 * AS_KPAD;           // [2][64] each
     uint64_t *bars = (uint64_t *)(sN1 + 2 * AS_KPAD);                  // full[2], empty[2], done
@@ -433,9 +446,9 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
         const uint32_t fb = full0 + 8u * s;
         uint8_t *st = sm + s * STAGE;
         mbar_expect_tx(fb, STAGE);
-        tma_load_2d(smem_addr(st), &tmX, base + kb * TC_BK, (int)row0, fb);
-        tma_load_2d(smem_addr(st + A_BYTES), &tmB, kb * TC_BK, (m * 2 + 0) * AS_KPAD, fb);
-        tma_load_2d(smem_addr(st + A_BYTES + B_BYTES), &tmB, kb * TC_BK, (m * 2 + 1) * AS_KPAD, fb);
+        tma_load_2d(smem_addr(st), &tmX, base + kb * KE, (int)row0, fb);
+        tma_load_2d(smem_addr(st + A_BYTES), &tmB, kb * KE, (m * 2 + 0) * AS_KPAD, fb);
+        tma_load_2d(smem_addr(st + A_BYTES + B_BYTES), &tmB, kb * KE, (m * 2 + 1) * AS_KPAD, fb);
         last_use[s] = kb;
     };
     if (tid == 0) {
@@ -450,7 +463,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
             issue(issued);
         }
     } else if (tid == 32) {
-        const uint32_t idesc = tf32_idesc(AS_KPAD, TC_BM);
+        const uint32_t idesc = BF ? bf16_idesc(AS_KPAD, TC_BM) : tf32_idesc(AS_KPAD, TC_BM);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb & 1;
             if (!mbar_wait(full0 + 8u * s, (uint32_t)(kb >> 1) & 1u)) {
@@ -460,10 +473,15 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
             tc_fence_after();
             const uint32_t sa = smem_addr(sm + s * STAGE), sl = sa + A_BYTES, sr = sa + A_BYTES + B_BYTES;
 #pragma unroll
-            for (int j = 0; j < TC_BK / 8; ++j) {
+            for (int j = 0; j < 4; ++j) {   // four 32-byte K steps per 128-byte k-block
                 const uint32_t o = 32u * j, acc = (kb | j) != 0;
-                mma_tf32(tmem, sw128_desc(sa + o), sw128_desc(sl + o), idesc, acc);
-                mma_tf32(tmem + AS_KPAD, sw128_desc(sa + o), sw128_desc(sr + o), idesc, acc);
+                if (BF) {
+                    mma_bf16(tmem, sw128_desc(sa + o), sw128_desc(sl + o), idesc, acc);
+                    mma_bf16(tmem + AS_KPAD, sw128_desc(sa + o), sw128_desc(sr + o), idesc, acc);
+                } else {
+                    mma_tf32(tmem, sw128_desc(sa + o), sw128_desc(sl + o), idesc, acc);
+                    mma_tf32(tmem + AS_KPAD, sw128_desc(sa + o), sw128_desc(sr + o), idesc, acc);
+                }
             }
             mma_commit(empty0 + 8u * s);
         }
@@ -492,7 +510,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
         const bool live = r < a.N;
         // the row's subspace values: from the resident tiles when the subspace
         // spans at most the two stages, else from global memory
-        const bool resident = nk <= 2;
+        const bool resident = !BF && nk <= 2;            // BF16 tiles: the FP32 values come from global memory
         const float *xg = a.Xr + (live ? r : 0) * (long long)a.Dp + lo;
         auto xval = [&](int j) -> float {               // j: column relative to lo
             if (!resident) return xg[j];
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
                     const int c = c0 + q;
                     if (c < a.K) {
                         const float sc = c2[c] - 2.0f * __uint_as_float(v[q]);
-                        U = fminf(U, sc + asg_bound(nx, nx2, c1[c], c2[c]));
+                        U = fminf(U, sc + asg_bound<BF>(nx, nx2, c1[c], c2[c]));
                     }
                 }
             }
@@ -536,7 +554,7 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
                     const int c = c0 + q;
                     if (c >= a.K) continue;
                     const float sc = c2[c] - 2.0f * __uint_as_float(v[q]);
-                    if (!(sc - asg_bound(nx, nx2, c1[c], c2[c]) <= U)) continue;
+                    if (!(sc - asg_bound<BF>(nx, nx2, c1[c], c2[c]) <= U)) continue;
                     const float *cc = C + c * HS;
                     float acc = 0.0f;
                     for (int d = 0; d < h; ++d) {
@@ -571,12 +589,15 @@ __global__ void __launch_bounds__(TC_NT) k_assign_tc(const __grid_constant__ CUt
     }
 }
 
-// Bm [M][2][64][KB*32]: row c of half h holds centroid c at the Xr columns of
-// that half (relative to the subspace's 32-aligned base column), zeros
-// elsewhere; cn2 / cn: |c|^2 and |c| (zero rows past K).
+// Bm [M][2][64][KB*KE]: row c of half h holds centroid c at the Xr columns of
+// that half (relative to the subspace's KE-aligned base column), zeros
+// elsewhere, FP32 (KE = 32) or rounded to BF16 (KE = 64); cn2 / cn: |c|^2 and
+// |c| of the FP32 centroids (zero rows past K).
+template <bool BF>
 __global__ void k_asg_prep(const float *__restrict__ cent, const int32_t *__restrict__ sub, int M, int K, int H, int KB,
-                           float *__restrict__ Bm, float *__restrict__ cn2, float *__restrict__ cn) {
-    const int W = KB * TC_BK;
+                           void *__restrict__ Bm, float *__restrict__ cn2, float *__restrict__ cn) {
+    constexpr int KE = BF ? 64 : TC_BK;
+    const int W = KB * KE;
     const long long tot = (long long)M * 2 * AS_KPAD * W;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
@@ -585,10 +606,11 @@ __global__ void k_asg_prep(const float *__restrict__ cent, const int32_t *__rest
         const int c = (int)(rowi % AS_KPAD), half = (int)((rowi / AS_KPAD) % 2), m = (int)(rowi / (2 * AS_KPAD));
         const int lo = sub[m], hi_ = sub[m + 1];
         const int hl = (hi_ - lo) / 2, hr = (hi_ - lo) - hl;
-        const int start = lo + (half ? hl : 0) - (lo & ~(TC_BK - 1)), h = half ? hr : hl;
+        const int start = lo + (half ? hl : 0) - (lo & ~(KE - 1)), h = half ? hr : hl;
         float v = 0.0f;
         if (c < K && j >= start && j < start + h) v = cent[(((long long)m * 2 + half) * K + c) * H + (j - start)];
-        Bm[e] = v;
+        if (BF) reinterpret_cast<uint16_t *>(Bm)[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        else reinterpret_cast<float *>(Bm)[e] = v;
         if (j == 0) {
             float s = 0.0f;
             if (c < K)
@@ -605,44 +627,55 @@ __global__ void k_asg_prep(const float *__restrict__ cent, const int32_t *__rest
 }  // namespace
 
 crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K, int32_t H,
-                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st) {
+                             const int32_t *sub, const float *cent, uint16_t *cells, int32_t *asg, cudaStream_t st,
+                             const uint16_t *Xb) {
     CRISP_REQUIRE(Xr && sub && cent && (cells || asg), "crisp_assign_cells_tc: null pointer");
     CRISP_REQUIRE(K >= 2 && K <= AS_KPAD && M >= 1 && 2 * M <= D && Dp >= D && N >= 1 && H >= 1,
                   "crisp_assign_cells_tc: bad sizes");
-    CRISP_REQUIRE(Dp % TC_BK == 0 && ((uintptr_t)Xr % 16) == 0,
-                  "crisp_assign_cells_tc: Xr must be 16-byte aligned with Dp a multiple of 32");
+    CRISP_REQUIRE(Dp % TC_BK == 0 && ((uintptr_t)Xr % 16) == 0 && ((uintptr_t)Xb % 16) == 0,
+                  "crisp_assign_cells_tc: Xr (and Xb) must be 16-byte aligned with Dp a multiple of 32");
     CRISP_REQUIRE(crisp_bounds_valid(sub, D, M, "crisp_assign_cells_tc") && crisp_bounds_half_max(sub, M) <= H,
                   "crisp_assign_cells_tc: subspace boundaries do not fit H = %d", H);
+    const bool bf = Xb != nullptr;
+    const int KE = bf ? 64 : TC_BK;                 // elements per 128-byte k-block
     int KB = 1, HS = 1;
     for (int m = 0; m < M; ++m) {
         const int lo = sub[m], hi_ = sub[m + 1];
-        KB = std::max(KB, (hi_ - (lo & ~(TC_BK - 1)) + TC_BK - 1) / TC_BK);
+        KB = std::max(KB, (hi_ - (lo & ~(KE - 1)) + KE - 1) / KE);
         HS = std::max(HS, (hi_ - lo) - (hi_ - lo) / 2);
     }
-    const size_t bm_n = (size_t)M * 2 * AS_KPAD * KB * TC_BK, nn = (size_t)M * 2 * AS_KPAD;
-    float *buf = nullptr;
-    CRISP_CK(cudaMallocAsync((void **)&buf, sizeof(float) * (bm_n + 2 * nn) + sizeof(int32_t) * ((size_t)M + 1), st));
-    float *Bm = buf, *cn2 = buf + bm_n, *cn = cn2 + nn;
+    const size_t bm_n = (size_t)M * 2 * AS_KPAD * KB * KE, nn = (size_t)M * 2 * AS_KPAD;
+    const size_t bm_bytes = (bm_n * (bf ? 2 : 4) + 255) / 256 * 256;
+    uint8_t *buf = nullptr;
+    CRISP_CK(cudaMallocAsync((void **)&buf, bm_bytes + sizeof(float) * 2 * nn + sizeof(int32_t) * ((size_t)M + 1), st));
+    void *Bm = buf;
+    float *cn2 = (float *)(buf + bm_bytes), *cn = cn2 + nn;
     int32_t *dsub = (int32_t *)(cn + nn);
     const std::vector<int32_t> hsub(sub, sub + M + 1);   // pageable: the copy is staged before return
     crisp_status s = CRISP_OK;
     do {
         cudaError_t e = cudaMemcpyAsync(dsub, hsub.data(), sizeof(int32_t) * hsub.size(), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__); break; }
-        k_asg_prep<<<(unsigned)std::min<size_t>((bm_n + 255) / 256, 4096), 256, 0, st>>>(cent, dsub, M, K, H, KB, Bm,
-                                                                                         cn2, cn);
+        const unsigned pg = (unsigned)std::min<size_t>((bm_n + 255) / 256, 4096);
+        if (bf) k_asg_prep<true><<<pg, 256, 0, st>>>(cent, dsub, M, K, H, KB, Bm, cn2, cn);
+        else k_asg_prep<false><<<pg, 256, 0, st>>>(cent, dsub, M, K, H, KB, Bm, cn2, cn);
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_asg_prep", __FILE__, __LINE__); break; }
         CUtensorMap mx, mb;
-        if (!make_map(&mx, Xr, N, Dp, Dp, TC_BM) || !make_map(&mb, Bm, (long long)M * 2 * AS_KPAD, KB * TC_BK,
-                                                              KB * TC_BK, AS_KPAD)) {
+        const bool mapped =
+            bf ? crisp_make_map_bf16(&mx, Xb, N, Dp, Dp, TC_BM) &&
+                     crisp_make_map_bf16(&mb, (const uint16_t *)Bm, (long long)M * 2 * AS_KPAD, KB * KE, KB * KE, AS_KPAD)
+               : make_map(&mx, Xr, N, Dp, Dp, TC_BM) &&
+                     make_map(&mb, (const float *)Bm, (long long)M * 2 * AS_KPAD, KB * KE, KB * KE, AS_KPAD);
+        if (!mapped) {
             crisp_set_error("crisp_assign_cells_tc: tensor map encoding failed");
             s = CRISP_ECUDA;
             break;
         }
         const size_t smem = asg_smem_bytes(K, HS);
-        e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = bf ? cudaFuncSetAttribute(k_assign_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaFuncSetAttribute(k_assign_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
         unsigned int zero = 0;
         e = cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st);
@@ -654,7 +687,8 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
             break;
         }
         AsgArgs a{N, D, Dp, M, K, H, KB, Xr, dsub, cent, cn2, cn, cells, asg};
-        k_assign_tc<<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mb, a);
+        if (bf) k_assign_tc<true><<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mb, a);
+        else k_assign_tc<false><<<(unsigned)tiles, TC_NT, smem, st>>>(mx, mb, a);
         CRISP_COUNT_LAUNCH();
         e = cudaGetLastError();
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "k_assign_tc", __FILE__, __LINE__); break; }
@@ -671,10 +705,10 @@ crisp_status crisp_tc_assign(const float *Xr, int64_t N, int32_t D, int32_t Dp, 
     return s;
 }
 
-extern "C" crisp_status crisp_assign_cells_tc(const float *Xr, int64_t N, int32_t D, int32_t Dp, int32_t M, int32_t K,
-                                              int32_t H, const int32_t *sub, const float *cent, uint16_t *cells,
-                                              void *stream) {
+extern "C" crisp_status crisp_assign_cells_tc(const float *Xr, const uint16_t *Xb, int64_t N, int32_t D, int32_t Dp,
+                                              int32_t M, int32_t K, int32_t H, const int32_t *sub, const float *cent,
+                                              uint16_t *cells, void *stream) {
     CRISP_REQUIRE(cells && M >= 1, "crisp_assign_cells_tc: null pointer or M < 1");
     const std::vector<int32_t> eq = crisp_equal_bounds(D, M);
-    return crisp_tc_assign(Xr, N, D, Dp, M, K, H, sub ? sub : eq.data(), cent, cells, nullptr, as_stream(stream));
+    return crisp_tc_assign(Xr, N, D, Dp, M, K, H, sub ? sub : eq.data(), cent, cells, nullptr, as_stream(stream), Xb);
 }

@@ -70,13 +70,23 @@ def test_rotate_tc_rejects_unaligned_rows():
 
 # ------------------------------------------------------------ B3 cell assignment
 def _assign_both(Xr, N, D, Dp, M, K, H, cent):
+    """Cells from the tensor-core kernel with one TF32 pass and with one BF16
+    pass (its BF16 copy of the rows made by the oracle's rounding), both
+    checked against the SIMT kernel; returns (tensor cores, SIMT)."""
+    import oracle
+
     dX = torch.from_numpy(np.ascontiguousarray(Xr)).to(DEV)
+    dXb = torch.from_numpy(oracle.quantize_bf16(np.ascontiguousarray(Xr, np.float32)).view(np.int16)).to(DEV)
     dC = torch.from_numpy(np.ascontiguousarray(cent)).to(DEV)
     a = torch.empty((M, N), dtype=torch.int16, device=DEV)
     b = torch.empty((M, N), dtype=torch.int16, device=DEV)
+    c = torch.empty((M, N), dtype=torch.int16, device=DEV)
     crisp.crisp_assign_cells_tc(dX, N, D, Dp, M, K, H, dC, a)
     crisp.crisp_assign_cells(dX, N, D, Dp, M, K, H, dC, b)
-    return a.cpu().numpy().view(np.uint16), b.cpu().numpy().view(np.uint16)
+    crisp.crisp_assign_cells_tc(dX, N, D, Dp, M, K, H, dC, c, Xb=dXb)
+    a, b, c = (t.cpu().numpy().view(np.uint16) for t in (a, b, c))
+    assert np.array_equal(c, b), "BF16 pass"
+    return a, b
 
 
 def test_assign_tc_bitexact_with_the_oracle():

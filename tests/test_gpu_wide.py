@@ -208,12 +208,16 @@ def test_coarse_shortlists(wide):
             assert nout[i] == len(ro) and np.array_equal(out[i, :nout[i]], ro), (prec, i)
 
 
-def test_tensor_core_cells(wide):
-    """The tensor-core assignment (TF32 scores, exact re-measure near ties)
-    gives the oracle's cells over 192- and 256-dim subspaces."""
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tensor_core_cells(wide, bf16):
+    """The tensor-core assignment (one TF32 pass over the FP32 rows, or one
+    BF16 pass over the oracle's BF16 copy; exact re-measure near ties) gives
+    the oracle's cells over 192- and 256-dim subspaces."""
     name, X, Q, ix_o, ix = wide
     cells = torch.empty((ix_o.M, ix_o.N), dtype=torch.int16, device=DEV)
-    crisp.crisp_assign_cells_tc(dev(ix_o.Xr), ix_o.N, ix_o.D, ix_o.Dp, ix_o.M, ix_o.K, ix_o.H, dev(ix_o.cent), cells)
+    Xb = dev(ix_o.Xb.view(np.int16)) if bf16 else None
+    crisp.crisp_assign_cells_tc(dev(ix_o.Xr), ix_o.N, ix_o.D, ix_o.Dp, ix_o.M, ix_o.K, ix_o.H, dev(ix_o.cent), cells,
+                                Xb=Xb)
     assert np.array_equal(cells.cpu().numpy().view(np.uint16), ix_o.cells)
 
 
