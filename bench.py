@@ -526,6 +526,9 @@ def run_crisp(args):
                 "gpu_launches": launches, "clocks": clk,
                 "coarse_scoring": variants, "learned_bf16": learned, "modes": modes, "tf32_rows": tf32_rows,
                 "leg_seconds": leg_s, **big}
+        if tf32_rows:   # the low-precision forms against the plain path that reads only the FP32 rows
+            for v in list(variants.values()) + ([learned] if learned else []):
+                v["speedup_vs_fp32_rows_only"] = v["value"] / tf32_rows["value"]
         if serving:
             ok = [r for r in serving["rates"] if r["achieved_qps"] >= 0.95 * r["offered_qps"]] or serving["rates"][:1]
             top = max(ok, key=lambda r: r["offered_qps"])

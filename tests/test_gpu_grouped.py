@@ -116,3 +116,28 @@ def test_grouped_shortlist_bitexact(grouped_case, precision, S):
         qr, C = _oracle_cut(ix_o, Q, q, 0.05, 0.3, 10, c, n)
         ref = oracle.shortlist(ix_o, qr, C, S, "bf16" if precision == 1 else "fp8", quant)
         assert gn[q] == ref.size and np.array_equal(go[q, :gn[q]], ref), q
+
+
+def test_duplicate_rows_select_by_id():
+    """4,000 copies of one row among 2,000 others, 300 queries near it: every
+    copy is a candidate at the same distance, so the selection's 16-bit bin
+    holds more keys than its shared-memory buffer (the four-pass path), and
+    the top-k among equal distances must be the lowest ids, as in the oracle."""
+    r = np.random.default_rng(17)
+    N, D, nq, M = 6000, 64, 300, 4
+    X = r.standard_normal((N, D)).astype(np.float32)
+    v = r.standard_normal(D).astype(np.float32)
+    dup = np.sort(r.choice(N, 4000, replace=False))
+    X[dup] = v
+    Q = (v[None, :] + 0.01 * r.standard_normal((nq, D))).astype(np.float32)
+    ix_o = oracle.build_index(X, M=M, K=16, draws=synthetic.method_draws(N, D, M, 16, seed=17, kmeans_train=N))
+    ix = crisp.crisp_index_import(oracle.export_blob(ix_o))
+    crisp.crisp_index_add_copies(ix, 1)
+    for kw in (dict(k=10, mode=0, rho=0.5, alpha=0.5), dict(k=100, mode=0, rho=0.5, alpha=0.25)):
+        k = kw["k"]
+        ids = empty((nq, k), torch.int64)
+        d2 = empty((nq, k), torch.float32)
+        crisp.crisp_search(ix, dev(Q), nq, crisp.search_params(**kw), ids, d2)
+        oi, od, _, _ = oracle.search(ix_o, Q, oracle.SearchParams(**kw))
+        assert np.array_equal(ids.cpu().numpy(), oi) and np.array_equal(d2.cpu().numpy(), od)
+        assert np.all(np.isin(oi[:, 0], dup))
