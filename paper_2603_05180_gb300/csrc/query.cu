@@ -340,9 +340,15 @@ constexpr int CNT_U = CRISP_CNT_U;
 constexpr int CNT_MINB = CRISP_CNT_MINB;
 constexpr int CNT_EC = CRISP_CNT_ECACHE;
 
+// One flag bit per 32-bit counter word (four ids) of a tile.
+constexpr int CNT_FLAG_WORDS = CRISP_TILE / 128;
+
 struct CountShared {
     int base[129];
-    unsigned hist[256];
+    union {
+        unsigned hist[256];                // passes A and B (fallback / cap)
+        unsigned flag[CNT_FLAG_WORDS];     // pass 1: counter words holding an id that reached tau
+    };
     int w_gt[CNT_NT / 32], w_eq[CNT_NT / 32];
     long long w_eqbase[CNT_NT / 32], w_outbase[CNT_NT / 32];
     long long tile_sel, tile_eq;
@@ -357,18 +363,25 @@ struct CountShared {
 };
 
 // Count tile t of query q into the byte counters `cnt` (zeroed here): every id
-// of every activated cell that falls in the tile adds its cell's weight.  The
+// of every activated cell that falls in the tile adds its cell's weight.  With
+// FLAG, the counter's old value (returned by the shared atomic) tells whether
+// this addition took the id from below tau to tau or above; such an id sets
+// the flag bit of its counter word, so that the cut reads only flagged words
+// (counters only grow, so every id with V >= tau crosses exactly once).  The
 // cells are staged 512 at a time, keeping those with ids in the tile; the flat
 // id range is then cut into one contiguous piece per warp, lanes on consecutive
 // ids (coalesced loads).  A lane finds its cell from the cell starts inside its
 // warp's 32 ids: lane j marks bit (start of cell ecur+1+j) - first id, the OR of
 // the marks over the warp has one bit per start (starts are distinct), and a
 // lane's cell is ecur plus the marks at or below its own position.
+template <bool FLAG>
 __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, CountShared &S, int E, int t,
-                           uint32_t *cnt) {
+                           uint32_t *cnt, int tau = 0) {
     const int K2 = ix.K * ix.K, T = ix.T, M = ix.M;
     uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
     for (int i = threadIdx.x; i < CRISP_TILE / 16; i += CNT_NT) c4[i] = make_uint4(0, 0, 0, 0);
+    if (FLAG)
+        for (int i = threadIdx.x; i < CNT_FLAG_WORDS; i += CNT_NT) S.flag[i] = 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tbase = t << CRISP_TILE_LOG2;
     const unsigned upto = 0xFFFFFFFFu >> (31 - lane);    // bits 0..lane
@@ -436,8 +449,15 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
 #pragma unroll
                 for (int u = 0; u < CNT_U; ++u) {
                     if (ids_v[u] >= 0) {
-                        const int local = ids_v[u] - tbase;
-                        atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << ((local & 3) * 8));
+                        const int local = ids_v[u] - tbase, sh = (local & 3) * 8;
+                        if (FLAG) {
+                            // old byte ob crosses: tau - w <= ob < tau
+                            const int ob = (int)((atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << sh) >> sh) & 0xFFu);
+                            if ((unsigned)(ob + wv[u] - tau) < (unsigned)wv[u])
+                                atomicOr(&S.flag[local >> 7], 1u << ((local >> 2) & 31));
+                        } else {
+                            atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << sh);
+                        }
                     }
                 }
             }
@@ -580,6 +600,55 @@ __device__ long long emit_tile_gt(const IxView &ix, CountShared &S, const uint32
     if (S.w_gt[warp] > 0) {
         if (fast) emit_write<true>(wc, s_hi, addc, vlim, S.w_outbase[warp], id0, candq, scoreq, stride);
         else emit_write<false>(wc, s_hi, addc, vlim, S.w_outbase[warp], id0, candq, scoreq, stride);
+    }
+    __syncthreads();
+    return tot_sel;
+}
+
+// Emit, in ascending id, the ids of tile t whose counter v satisfies v >= tau
+// (tau >= 1), from the flags count_tile<true> set: lane l of warp w owns flag
+// word 32 w + l, i.e. counter words 32 (32 w + l) .. + 31 (128 ids), and reads
+// only the flagged ones.  Ids past N are never counted, so their counters stay
+// 0 and need no mask.  Same output as emit_tile_gt(s_hi = tau - 1).
+__device__ long long emit_tile_flag(CountShared &S, const uint32_t *cnt, int t, int tau, long long out_base,
+                                    int *candq, uint8_t *scoreq, long long stride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int fw = warp * 32 + lane;
+    const unsigned fl = S.flag[fw];
+    const uint32_t *cw = cnt + fw * 32;
+    const long long id0 = ((long long)t << CRISP_TILE_LOG2) + (long long)fw * 128;
+    int c = 0;
+    for (unsigned m = fl; m; m &= m - 1) c += __popc(gt_bits(cw[__ffs(m) - 1], tau - 1));
+    int c_in = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, c_in, o);
+        if (lane >= o) c_in += y;
+    }
+    if (lane == 31) S.w_gt[warp] = c_in;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long outb = out_base;
+        for (int w = 0; w < CNT_NT / 32; ++w) {
+            S.w_outbase[w] = outb;
+            outb += S.w_gt[w];
+        }
+        S.tile_sel = outb - out_base;
+    }
+    __syncthreads();
+    const long long tot_sel = S.tile_sel;
+    long long pos = S.w_outbase[warp] + (c_in - c);
+    for (unsigned m = fl; m; m &= m - 1) {
+        const int b = __ffs(m) - 1;
+        const unsigned v = cw[b];
+        for (unsigned g = gt_bits(v, tau - 1); g; g &= g - 1) {
+            const int bb = (__ffs(g) - 1) >> 3;
+            if (pos < stride) {
+                candq[pos] = (int)(id0 + 4 * b + bb);
+                if (scoreq) scoreq[pos] = (uint8_t)((v >> (8 * bb)) & 0xFFu);
+            }
+            ++pos;
+        }
     }
     __syncthreads();
     return tot_sel;
@@ -749,8 +818,13 @@ __global__ void __launch_bounds__(CNT_NT, CNT_MINB) k_count_cut(IxView ix, const
     // pass 1: C = {x : V[x] >= tau}
     long long total = 0, eq_seen = 0;
     for (int t = 0; t < T; ++t) {
-        count_tile(ix, actq, S, E, t, cnt);
-        total += emit_tile(ix, S, cnt, t, tau - 1, 0, &eq_seen, total, candq, scoreq, stride);
+        if (tau >= 1) {
+            count_tile<true>(ix, actq, S, E, t, cnt, tau);
+            total += emit_tile_flag(S, cnt, t, tau, total, candq, scoreq, stride);
+        } else {
+            count_tile<false>(ix, actq, S, E, t, cnt);
+            total += emit_tile(ix, S, cnt, t, tau - 1, 0, &eq_seen, total, candq, scoreq, stride);
+        }
     }
     int mode = 0;
     long long want = 0;
@@ -768,7 +842,7 @@ __global__ void __launch_bounds__(CNT_NT, CNT_MINB) k_count_cut(IxView ix, const
     for (int i = threadIdx.x; i < 256; i += CNT_NT) S.hist[i] = 0;
     __syncthreads();
     for (int t = 0; t < T; ++t) {
-        count_tile(ix, actq, S, E, t, cnt);
+        count_tile<false>(ix, actq, S, E, t, cnt);
         const long long id0 = ((long long)t << CRISP_TILE_LOG2);
         const uint8_t *cb = reinterpret_cast<const uint8_t *>(cnt);
         for (int i = threadIdx.x; i < CRISP_TILE; i += CNT_NT) {
@@ -799,7 +873,7 @@ __global__ void __launch_bounds__(CNT_NT, CNT_MINB) k_count_cut(IxView ix, const
     long long out = 0;
     eq_seen = 0;
     for (int t = 0; t < T; ++t) {
-        count_tile(ix, actq, S, E, t, cnt);
+        count_tile<false>(ix, actq, S, E, t, cnt);
         out += emit_tile(ix, S, cnt, t, s_star, need, &eq_seen, out, candq, scoreq, stride);
     }
     if (threadIdx.x == 0) {
