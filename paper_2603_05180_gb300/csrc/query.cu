@@ -2049,10 +2049,11 @@ __global__ void __launch_bounds__(RR_NT) k_select_rows(int nq, const int *__rest
     }
 }
 
-// Re-measure set of the tensor-core re-rank.  ulb holds, for every listed
-// candidate, an upper and a lower bound of its CR32 distance (x, y).  With U the kk-th
-// smallest upper bound, every candidate whose lower bound is <= U is written (in
-// list order, so ascending id) to rc, their number to nr.  A candidate left out
+// Re-measure set of the tensor-core re-rank.  ub / lb hold, for every listed
+// candidate, an upper and a lower bound of its CR32 distance.  With U a value
+// that has at least kk upper bounds at or below it (so U >= the kk-th smallest
+// upper bound), every candidate whose lower bound is <= U is written (in list
+// order, so ascending id) to rc, their number to nr.  A candidate left out
 // has CR32 distance >= its lower bound > U >= the kk-th smallest CR32 distance,
 // so it cannot be among the kk nearest by (distance, id); the exact re-rank of
 // rc alone therefore gives the top-kk of the whole list.
@@ -2081,7 +2082,36 @@ __global__ void __launch_bounds__(RR_NT) k_bound_select(int nq, const int *__res
         if (tid == 0) nr[q] = n;
         return;
     }
-    const float U = __uint_as_float(radix_kth_gather(ub + (long long)q * stride, n, kk, S, gbuf));
+    unsigned ukey;
+    if (kk <= RR_NT) {
+        // The cut from each thread's smallest upper bound over its strided share:
+        // V, the kk-th smallest of these minima, has at least kk upper bounds at
+        // or below it (each thread's minimum is one), so the kk-th smallest upper
+        // bound is <= V and V cuts exactly as well (it may keep a few more).
+        // One read of the bounds; V found bit by bit (keys are non-negative
+        // FP32, ordered like their bit patterns) with block-wide counts.
+        const float *uq = ub + (long long)q * stride;
+        unsigned mn = 0x7F800000u;              // +inf: a thread with no entry
+        for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {
+            unsigned key[SEL_U];
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u) {
+                const long long i = c00 + (long long)u * RR_NT + tid;
+                key[u] = i < n ? __float_as_uint(uq[i]) : 0x7F800000u;
+            }
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u) mn = key[u] < mn ? key[u] : mn;
+        }
+        unsigned p = 0;                          // smallest p with #{mn <= p} >= kk
+        for (int b = 30; b >= 0; --b) {
+            const unsigned c = p | ((1u << b) - 1u);
+            if (__syncthreads_count(mn <= c) < kk) p |= 1u << b;
+        }
+        ukey = p;
+    } else {
+        ukey = radix_kth_gather(ub + (long long)q * stride, n, kk, S, gbuf);
+    }
+    const float U = __uint_as_float(ukey);
     const float *lq = lb + (long long)q * stride;
     long long run = 0;
     for (long long c00 = 0; c00 < n; c00 += (long long)RR_NT * SEL_U) {

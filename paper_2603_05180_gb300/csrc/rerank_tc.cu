@@ -216,6 +216,46 @@ __device__ __forceinline__ long long tr_block_scan(long long v, long long *ws, l
 // the group needs, their member masks, and the slot of every (row, member)
 // pair.  Entry order inside a (group, range) is arbitrary: every pair has its
 // own slot, so nothing downstream depends on it.
+// The ids of a group's members j = warp, warp + 8, ... (one warp's share) in
+// the current range, visited as one flat list: lanes on consecutive entries
+// (coalesced), TU_U entries a lane loaded before any is used (independent
+// loads in flight), f(j, t, id) for entry t of member j.  A lane finds its
+// member from the members' cumulative counts, held in registers.
+constexpr int TU_NW = TU_NT / 32, TU_MPW = TG / TU_NW, TU_U = 4;
+static_assert(TG % TU_NW == 0 && TU_MPW <= 32, "k_union: members per warp");
+template <class F>
+__device__ __forceinline__ void warp_member_ids(const int *__restrict__ cand, long long stride, const int *s_q,
+                                                const int *s_base, const int *s_cnt, int warp, int lane, F f) {
+    int c = lane < TU_MPW ? s_cnt[warp + TU_NW * lane] : 0;
+#pragma unroll
+    for (int o = 1; o < TU_MPW; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, c, o);
+        if (lane >= o) c += y;
+    }
+    int ends[TU_MPW];                        // inclusive scan: end of member i's entries
+#pragma unroll
+    for (int i = 0; i < TU_MPW; ++i) ends[i] = __shfl_sync(0xffffffffu, c, i);
+    const int total = ends[TU_MPW - 1];
+    for (int f0 = 0; f0 < total; f0 += 32 * TU_U) {
+        int id[TU_U], jj[TU_U], tt[TU_U];
+#pragma unroll
+        for (int u = 0; u < TU_U; ++u) {
+            const int fi = f0 + 32 * u + lane;
+            int i = 0, start = 0;
+#pragma unroll
+            for (int k = 0; k < TU_MPW - 1; ++k)
+                if (fi >= ends[k]) { i = k + 1; start = ends[k]; }
+            const int j = warp + TU_NW * i;
+            jj[u] = j;
+            tt[u] = fi - start;
+            id[u] = fi < total ? __ldg(cand + (long long)s_q[j] * stride + s_base[j] + (fi - start)) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < TU_U; ++u)
+            if (id[u] >= 0) f(jj[u], tt[u], id[u]);
+    }
+}
+
 __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, long long stride, TUnion u) {
     extern __shared__ __align__(16) unsigned long long usm[];
     unsigned long long *mask = usm;                      // [TSPAN][TGW]
@@ -250,12 +290,10 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
     const int np = s_off[TG];
     const long long lo_id = (long long)r * TSPAN;
     const int warp = tid >> 5, lane = tid & 31;
-    // a warp per member, lanes over the member's ids in the range (coalesced)
-    for (int j = warp; j < TG; j += TU_NT / 32) {
-        const int *cq = cand + (long long)s_q[j] * stride + s_base[j];
-        const unsigned long long bit = 1ull << (j & 63);
-        for (int t = lane; t < s_cnt[j]; t += 32) atomicOr(&mask[(cq[t] - lo_id) * TGW + (j >> 6)], bit);
-    }
+    // member masks: every member's ids in the range set the member's bit
+    warp_member_ids(cand, stride, s_q, s_base, s_cnt, warp, lane, [&](int j, int, int id) {
+        atomicOr(&mask[(id - lo_id) * TGW + (j >> 6)], 1ull << (j & 63));
+    });
     __syncthreads();
     // thread t owns the ids t, t + TU_NT, ... (conflict-free reads); one packed
     // scan (pairs high, rows low) places every thread's rows and pairs
@@ -305,16 +343,12 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
     }
     __syncthreads();
     // pair slots: member j of row o goes to slot base(o) + (members of o below j)
-    for (int j = warp; j < TG; j += TU_NT / 32) {
-        const int *cq = cand + (long long)s_q[j] * stride + s_base[j];
-        const unsigned long long lowbits = (1ull << (j & 63)) - 1ull;
-        for (int t = lane; t < s_cnt[j]; t += 32) {
-            const int o = cq[t] - (int)lo_id;
-            int below = __popcll(mask[o * TGW + (j >> 6)] & lowbits);
-            if (TGW > 1 && j >= 64) below += __popcll(mask[o * TGW]);
-            u.pair_pos[s_pb + pbl[o] + below] = s_base[j] + t;
-        }
-    }
+    warp_member_ids(cand, stride, s_q, s_base, s_cnt, warp, lane, [&](int j, int t, int id) {
+        const int o = id - (int)lo_id;
+        int below = __popcll(mask[o * TGW + (j >> 6)] & ((1ull << (j & 63)) - 1ull));
+        if (TGW > 1 && j >= 64) below += __popcll(mask[o * TGW]);
+        u.pair_pos[s_pb + pbl[o] + below] = s_base[j] + t;
+    });
 }
 
 struct TileMeta {

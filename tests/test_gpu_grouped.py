@@ -101,7 +101,7 @@ def test_grouped_rerank_bitexact(grouped_case, k, scorer, monkeypatch):
         assert np.array_equal(gi[q], ri) and np.array_equal(gd[q], rd), q
 
 
-@pytest.mark.parametrize("precision,S", [(1, 40), (2, 60)])
+@pytest.mark.parametrize("precision,S", [(1, 40), (2, 60), (1, 300)])
 def test_grouped_shortlist_bitexact(grouped_case, precision, S):
     X, Q, ix_o, ix = grouped_case
     nq = Q.shape[0]
