@@ -1976,21 +1976,11 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
 
 }  // namespace
 
-// Query groups of a large batch for the tensor-core re-rank: the MinHash order
-// of the queries (qord), and pos[q][r], the first list position of query q with
-// id >= r GS_SPAN (r = 0..R).  key is scratch [nq].
-crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
-                                   unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st) {
+// pos[q][r] of a large batch for the tensor-core re-rank: the first list
+// position of query q with id >= r GS_SPAN (r = 0..R).
+crisp_status crisp_run_group_pos(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
+                                 int32_t *pos, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
-    CRISP_REQUIRE(nq <= SCH_MAXQ, "group order: at most %d queries", SCH_MAXQ);
-    k_minhash_key<<<nq, RR_NT, 0, st>>>(cand, (long long)stride, (const long long *)ncand, nq, key);
-    CRISP_COUNT_LAUNCH();
-    int n2 = 1;
-    while (n2 < nq) n2 <<= 1;
-    CRISP_CK(cudaFuncSetAttribute(k_sort_queries, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(unsigned long long) * n2)));
-    k_sort_queries<<<1, 1024, sizeof(unsigned long long) * n2, st>>>(key, nq, qord);
-    CRISP_COUNT_LAUNCH();
     const long long npos = (long long)nq * (R + 1);
     k_sched_pos<<<(unsigned)((npos + 255) / 256), 256, 0, st>>>(cand, (long long)stride, (const long long *)ncand,
                                                                 nq, R, pos);

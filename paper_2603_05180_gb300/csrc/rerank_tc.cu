@@ -2,9 +2,10 @@
 // the O(|C| D) verification the paper names as the dominant query cost, §4.4).
 //
 // The candidate lists of a large batch overlap: on the 1M-row workload a row is
-// a candidate of about 200 of 10,000 queries.  The queries are ordered by the
-// MinHash of their candidate sets and cut into groups of TG (64) queries; the id space
-// into ranges of TSPAN ids.  For every (group, range) k_union lists the rows
+// a candidate of about 200 of 10,000 queries.  The queries are ordered by a k-d
+// partition of their coordinates along the batch's top principal directions
+// (queries close in space share most candidates) and cut into groups of TG (64)
+// queries; the id space into ranges of TSPAN ids.  For every (group, range) k_union lists the rows
 // some member needs, with a 64-bit member mask and each (row, member) pair's
 // slot in that member's list.  Then:
 //
@@ -79,8 +80,8 @@
 
 bool crisp_make_map_bf16(CUtensorMap *m, const uint16_t *base, long long rows, int cols, int ld, int box_rows);
 bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows);
-crisp_status crisp_run_group_order(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
-                                   unsigned long long *key, int32_t *qord, int32_t *pos, cudaStream_t st);
+crisp_status crisp_run_group_pos(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
+                                 int32_t *pos, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
                                     const QParam *qp, int32_t qfield, const int64_t *kq, const float *ub,
                                     const float *lb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
@@ -104,7 +105,18 @@ constexpr int TGW = TG / 64;
 static_assert(TG == 64 || TG == 128, "query groups of 64 or 128");
 constexpr int TR_MINQ = 256;        // smaller batches re-rank query by query
 constexpr int TSPAN = 4096;         // ids per range (the ordering's range size)
-constexpr int TU_NT = 256;          // k_union threads
+// k_union tuning (compile time): threads a CTA, ids a lane loaded before use,
+// CTAs an SM the registers are budgeted for (512 x 4: a full SM of warps).
+#ifndef CRISP_TU_NT
+#define CRISP_TU_NT 512
+#endif
+#ifndef CRISP_TU_U
+#define CRISP_TU_U 4
+#endif
+#ifndef CRISP_TU_MINB
+#define CRISP_TU_MINB 4
+#endif
+constexpr int TU_NT = CRISP_TU_NT;  // k_union threads
 constexpr int TR_ROWS = 256;        // rows per tile: two M = 128 accumulators
 // Stage geometry (tunable at compile time): TR_NS stages of TR_KB 32-float
 // k-blocks of a tile each, TR_NB accumulator buffers, TR_RB id ranges per item.
@@ -221,7 +233,7 @@ __device__ __forceinline__ long long tr_block_scan(long long v, long long *ws, l
 // (coalesced), TU_U entries a lane loaded before any is used (independent
 // loads in flight), f(j, t, id) for entry t of member j.  A lane finds its
 // member from the members' cumulative counts, held in registers.
-constexpr int TU_NW = TU_NT / 32, TU_MPW = TG / TU_NW, TU_U = 4;
+constexpr int TU_NW = TU_NT / 32, TU_MPW = TG / TU_NW, TU_U = CRISP_TU_U;
 static_assert(TG % TU_NW == 0 && TU_MPW <= 32, "k_union: members per warp");
 template <class F>
 __device__ __forceinline__ void warp_member_ids(const int *__restrict__ cand, long long stride, const int *s_q,
@@ -256,11 +268,11 @@ __device__ __forceinline__ void warp_member_ids(const int *__restrict__ cand, lo
     }
 }
 
-__global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, long long stride, TUnion u) {
+__global__ void __launch_bounds__(TU_NT, CRISP_TU_MINB) k_union(const int *__restrict__ cand, long long stride, TUnion u) {
     extern __shared__ __align__(16) unsigned long long usm[];
     unsigned long long *mask = usm;                      // [TSPAN][TGW]
     int *pbl = reinterpret_cast<int *>(usm + TSPAN * TGW);   // [TSPAN] pair base of each row, within the block
-    __shared__ int s_q[TG], s_base[TG], s_cnt[TG], s_off[TG + 1];
+    __shared__ int s_q[TG], s_base[TG], s_cnt[TG], s_np[TG / 32];
     __shared__ long long scan_ws[TU_NT / 32 + 1];
     __shared__ long long s_eb, s_pb;
     const int r = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
@@ -275,24 +287,22 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
         s_q[tid] = q < 0 ? 0 : q;
         s_base[tid] = a;
         s_cnt[tid] = b - a;
+        const int w_np = __reduce_add_sync(0xffffffffu, b - a);
+        if ((tid & 31) == 0) s_np[tid >> 5] = w_np;
     }
     for (int o = tid; o < TSPAN * TGW; o += TU_NT) mask[o] = 0ull;
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int j = 0; j < TG; ++j) {
-            s_off[j] = acc;
-            acc += s_cnt[j];
-        }
-        s_off[TG] = acc;
-    }
-    __syncthreads();
-    const int np = s_off[TG];
+    int np = 0;
+#pragma unroll
+    for (int w = 0; w < TG / 32; ++w) np += s_np[w];
     const long long lo_id = (long long)r * TSPAN;
     const int warp = tid >> 5, lane = tid & 31;
     // member masks: every member's ids in the range set the member's bit
+    // (32-bit halves of the little-endian 64-bit words: bit j of row o is bit
+    // j & 31 of half 2 TGW o + (j >> 5))
+    unsigned *mask32 = reinterpret_cast<unsigned *>(mask);
     warp_member_ids(cand, stride, s_q, s_base, s_cnt, warp, lane, [&](int j, int, int id) {
-        atomicOr(&mask[(id - lo_id) * TGW + (j >> 6)], 1ull << (j & 63));
+        atomicOr(&mask32[(id - (int)lo_id) * 2 * TGW + (j >> 5)], 1u << (j & 31));
     });
     __syncthreads();
     // thread t owns the ids t, t + TU_NT, ... (conflict-free reads); one packed
@@ -349,6 +359,414 @@ __global__ void __launch_bounds__(TU_NT) k_union(const int *__restrict__ cand, l
         if (TGW > 1 && j >= 64) below += __popcll(mask[o * TGW]);
         u.pair_pos[s_pb + pbl[o] + below] = s_base[j] + t;
     });
+}
+
+// ------------------------------------ query order: k-d partition of the batch
+// Groups whose members have similar candidate sets list fewer rows (fewer row
+// fetches and MMAs for the same pairs).  Queries close in space share most of
+// their activated cells, hence most candidates, so the batch is ordered by a
+// k-d partition of the queries' coordinates along the batch's top PD_P
+// principal directions: every node larger than a group splits at a
+// group-aligned median of the coordinate with the widest range, so the leaves
+// are the groups.  The directions come from PD_IT subspace iterations on up to
+// PD_NS evenly spaced queries.  The order only decides which queries share a
+// group (speed); every result is the same for any order.
+#ifndef CRISP_PD_NS
+#define CRISP_PD_NS 2048
+#endif
+#ifndef CRISP_PD_IT
+#define CRISP_PD_IT 5
+#endif
+constexpr int PD_P = 4, PD_NS = CRISP_PD_NS, PD_IT = CRISP_PD_IT, PD_CH = 32, PD_NT = 128;
+constexpr int KD_NT = 1024, KD_MAXN = 256, KD_PER = CRISP_GROUP_MAXQ / KD_NT;
+
+// Sampled row r of n (r nq / n; every row when n = nq).
+__device__ __forceinline__ long long pd_row(int r, int nq, int n) { return (long long)r * nq / n; }
+
+// part[c][d] = sum over the sampled rows r of chunk c (blockIdx.y) of
+// (Qr[q_r][d] - mu[d]) Y[r]; with Y null, the plain column sums (in .x).
+__global__ void __launch_bounds__(PD_NT, 1) k_pd_back(const float *__restrict__ Qr, int nq, int Dp, int ns,
+                                                   const float *__restrict__ mu, const float4 *__restrict__ Y,
+                                                   float4 *__restrict__ part) {
+    const int d = blockIdx.x * PD_NT + threadIdx.x, c = blockIdx.y;
+    if (d >= Dp) return;
+    const int r0 = (int)((long long)ns * c / PD_CH), r1 = (int)((long long)ns * (c + 1) / PD_CH);
+    const float m = mu ? mu[d] : 0.0f;
+    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 8
+    for (int r = r0; r < r1; ++r) {
+        const float x = Qr[pd_row(r, nq, ns) * Dp + d] - m;
+        if (Y) {
+            const float4 y = Y[r];
+            a.x += x * y.x;
+            a.y += x * y.y;
+            a.z += x * y.z;
+            a.w += x * y.w;
+        } else {
+            a.x += x;
+        }
+    }
+    part[(long long)c * Dp + d] = a;
+}
+
+// Sum of v over the CTA (fixed order), returned to every thread.
+__device__ float pd_block_sum(float v, float *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        float t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    const float t = red[32];
+    __syncthreads();
+    return t;
+}
+
+// A fixed value in [-1, 1) for (d, j): the subspace iteration's start.
+__device__ __forceinline__ float pd_start(int d, int j) {
+    unsigned h = (unsigned)d * 0x9E3779B1u + (unsigned)j * 0x7F4A7C15u + 0x165667B1u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+// One CTA.  W = the chunks' sum of part; mode 0: mu = W.x / ns and V starts
+// from pd_start; mode 1: V = W.  V's PD_P columns are then orthonormalised
+// (modified Gram-Schmidt; a column that vanishes becomes a unit vector).
+__global__ void __launch_bounds__(1024) k_pd_finish(const float4 *__restrict__ part, int Dp, int ns, int mode,
+                                                    float *__restrict__ mu, float4 *__restrict__ V) {
+    __shared__ float red[33];
+    float *Vf = reinterpret_cast<float *>(V);
+    for (int d = threadIdx.x; d < Dp; d += blockDim.x) {
+        float4 w = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int c = 0; c < PD_CH; ++c) {
+            const float4 p = part[(long long)c * Dp + d];
+            w.x += p.x;
+            w.y += p.y;
+            w.z += p.z;
+            w.w += p.w;
+        }
+        if (mode == 0) {
+            mu[d] = w.x / (float)ns;
+            w = make_float4(pd_start(d, 0), pd_start(d, 1), pd_start(d, 2), pd_start(d, 3));
+        }
+        V[d] = w;
+    }
+    __syncthreads();
+    for (int j = 0; j < PD_P; ++j) {
+        for (int i = 0; i < j; ++i) {
+            float t = 0.0f;
+            for (int d = threadIdx.x; d < Dp; d += blockDim.x) t += Vf[4 * d + i] * Vf[4 * d + j];
+            const float dot = pd_block_sum(t, red);
+            for (int d = threadIdx.x; d < Dp; d += blockDim.x) Vf[4 * d + j] -= dot * Vf[4 * d + i];
+            __syncthreads();
+        }
+        float t = 0.0f;
+        for (int d = threadIdx.x; d < Dp; d += blockDim.x) t += Vf[4 * d + j] * Vf[4 * d + j];
+        const float nrm = sqrtf(pd_block_sum(t, red));
+        for (int d = threadIdx.x; d < Dp; d += blockDim.x)
+            Vf[4 * d + j] = nrm > 1e-30f ? Vf[4 * d + j] / nrm : (d == j ? 1.0f : 0.0f);
+        __syncthreads();
+    }
+}
+
+// Y[r] = (Qr[q_r] - mu) V for the rows r < n: one warp a row.
+__global__ void __launch_bounds__(256) k_pd_proj(const float *__restrict__ Qr, int nq, int Dp, int n,
+                                                 const float *__restrict__ mu, const float4 *__restrict__ V,
+                                                 float4 *__restrict__ Y) {
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *x = Qr + pd_row(r, nq, n) * Dp;
+    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int d = lane; d < Dp; d += 32) {
+        const float v = x[d] - mu[d];
+        const float4 w = V[d];
+        a.x += v * w.x;
+        a.y += v * w.y;
+        a.z += v * w.z;
+        a.w += v * w.w;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+        a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+        a.z += __shfl_xor_sync(0xffffffffu, a.z, o);
+        a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
+    }
+    if (lane == 0) Y[r] = a;
+}
+
+// FP32 bits mapped so that unsigned order is the value order.
+__device__ __forceinline__ unsigned pd_key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float pd_unkey(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ float pd_comp(const float4 &y, int j) {
+    return j == 0 ? y.x : j == 1 ? y.y : j == 2 ? y.z : y.w;
+}
+
+// One CTA: the k-d order qord of nq <= CRISP_GROUP_MAXQ queries with
+// coordinates Y, leaves of G (nodes hold positions [start, start + size) of
+// perm; a node larger than G splits into its h = G ceil(size / 2G) smallest
+// along the chosen coordinate, ties by position, and the rest).  Per level:
+// the coordinate ranges of every splitting node (shared atomics on ordered
+// keys), a 4-bit radix select of each node's h-th smallest key, and a stable
+// partition from one packed scan (keys below the pivot in the low half, equal
+// keys in the high half: both counts stay below 2^16).
+__global__ void __launch_bounds__(KD_NT, 1) k_kd_order(const float4 *__restrict__ Y, int nq, int G,
+                                                       int *__restrict__ qord) {
+    extern __shared__ __align__(16) uint8_t kd_sm[];
+    unsigned *keys = reinterpret_cast<unsigned *>(kd_sm);
+    uint16_t *perm = reinterpret_cast<uint16_t *>(keys + CRISP_GROUP_MAXQ);
+    uint16_t *perm2 = perm + CRISP_GROUP_MAXQ;
+    uint8_t *nid = reinterpret_cast<uint8_t *>(perm2 + CRISP_GROUP_MAXQ);
+    __shared__ int n_start[KD_MAXN], n_size[KD_MAXN], n_h[KD_MAXN], n_need[KD_MAXN], n_dim[KD_MAXN];
+    __shared__ int t_start[KD_MAXN], t_size[KD_MAXN];
+    __shared__ unsigned n_pref[KD_MAXN], n_base[KD_MAXN], n_mn[KD_MAXN][PD_P], n_mx[KD_MAXN][PD_P];
+    __shared__ unsigned hist[KD_MAXN * 16];
+    __shared__ long long scan_ws[KD_NT / 32 + 1];
+    __shared__ int s_nn, s_split;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nq; i += KD_NT) {
+        perm[i] = (uint16_t)i;
+        nid[i] = 0;
+    }
+    if (tid == 0) {
+        n_start[0] = 0;
+        n_size[0] = nq;
+        s_nn = 1;
+        s_split = nq > G;
+    }
+    __syncthreads();
+    const int per = (nq + KD_NT - 1) / KD_NT, p0 = tid * per;
+    while (s_split) {
+        const int nn = s_nn;
+        // coordinate ranges of the splitting nodes
+        for (int i = tid; i < nn * PD_P; i += KD_NT) {
+            n_mn[i / PD_P][i % PD_P] = 0xFFFFFFFFu;
+            n_mx[i / PD_P][i % PD_P] = 0u;
+        }
+        __syncthreads();
+        // (lanes hold consecutive positions, mostly of one node: reduced over the
+        // warp per node, then one atomic per node and coordinate)
+        for (int i0 = 0; i0 < nq; i0 += KD_NT) {
+            const int i = i0 + tid;
+            int n = 0;
+            bool act = false;
+            unsigned k[PD_P];
+            if (i < nq) {
+                n = nid[i];
+                act = n_size[n] > G;
+            }
+            if (act) {
+                const float4 y = Y[perm[i]];
+#pragma unroll
+                for (int j = 0; j < PD_P; ++j) k[j] = pd_key(pd_comp(y, j));
+            }
+            unsigned pending = __ballot_sync(0xffffffffu, act);
+            while (pending) {
+                const int src = __ffs(pending) - 1;
+                const int tn = __shfl_sync(0xffffffffu, n, src);
+                const bool mine = act && n == tn;
+#pragma unroll
+                for (int j = 0; j < PD_P; ++j) {
+                    const unsigned mn = __reduce_min_sync(0xffffffffu, mine ? k[j] : 0xFFFFFFFFu);
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, mine ? k[j] : 0u);
+                    if ((tid & 31) == src) {
+                        atomicMin(&n_mn[tn][j], mn);
+                        atomicMax(&n_mx[tn][j], mx);
+                    }
+                }
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+            }
+        }
+        __syncthreads();
+        for (int n = tid; n < nn; n += KD_NT) {
+            if (n_size[n] <= G) continue;
+            int best = 0;
+            float bw = -1.0f;
+            for (int j = 0; j < PD_P; ++j) {
+                const float w = pd_unkey(n_mx[n][j]) - pd_unkey(n_mn[n][j]);
+                if (w > bw) {
+                    bw = w;
+                    best = j;
+                }
+            }
+            n_dim[n] = best;
+            n_h[n] = (n_size[n] / 2 + G - 1) / G * G;
+            n_need[n] = n_h[n];
+            n_pref[n] = 0u;
+        }
+        __syncthreads();
+        for (int i = tid; i < nq; i += KD_NT) {
+            const int n = nid[i];
+            keys[i] = n_size[n] > G ? pd_key(pd_comp(Y[perm[i]], n_dim[n])) : 0u;
+        }
+        // radix select, 4 bits a pass: the n_h-th smallest key of each splitting node
+        unsigned mask = 0u;
+        for (int shift = 28; shift >= 0; shift -= 4) {
+            for (int i = tid; i < nn * 16; i += KD_NT) hist[i] = 0u;
+            __syncthreads();
+            // lanes with the same (node, digit) add once, by their lowest lane
+            for (int i0 = 0; i0 < nq; i0 += KD_NT) {
+                const int i = i0 + tid;
+                unsigned bin = 0xFFFFFFFFu;
+                if (i < nq) {
+                    const int n = nid[i];
+                    const unsigned k = keys[i];
+                    if (n_size[n] > G && (k & mask) == n_pref[n]) bin = (unsigned)n * 16u + ((k >> shift) & 15u);
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                if (bin != 0xFFFFFFFFu && __ffs(peers) - 1 == (tid & 31)) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+            }
+            __syncthreads();
+            for (int n = tid; n < nn; n += KD_NT) {
+                if (n_size[n] <= G) continue;
+                int cum = 0, b = 0;
+                for (; b < 15; ++b) {
+                    const int c = (int)hist[n * 16 + b];
+                    if (cum + c >= n_need[n]) break;
+                    cum += c;
+                }
+                n_pref[n] |= (unsigned)b << shift;
+                n_need[n] -= cum;
+            }
+            mask |= 15u << shift;
+            __syncthreads();
+        }
+        // stable partition: keys below the pivot, then the first n_need equal
+        // keys, go to [start, start + h); the rest to [start + h, start + size)
+        unsigned f[KD_PER];
+        unsigned tot = 0u;
+#pragma unroll
+        for (int u = 0; u < KD_PER; ++u) {
+            const int i = p0 + u;
+            unsigned v = 0u;
+            if (u < per && i < nq) {
+                const int n = nid[i];
+                if (n_size[n] > G) {
+                    const unsigned k = keys[i];
+                    v = (k < n_pref[n] ? 1u : 0u) | (k == n_pref[n] ? 0x10000u : 0u);
+                }
+            }
+            f[u] = v;
+            tot += v;
+        }
+        long long all;
+        const unsigned excl = (unsigned)tr_block_scan<KD_NT>((long long)tot, scan_ws, &all);
+        unsigned run = excl;
+#pragma unroll
+        for (int u = 0; u < KD_PER; ++u) {
+            const int i = p0 + u;
+            if (u < per && i < nq && (i == 0 || nid[i] != nid[i - 1])) n_base[nid[i]] = run;
+            run += f[u];
+        }
+        __syncthreads();
+        run = excl;
+#pragma unroll
+        for (int u = 0; u < KD_PER; ++u) {
+            const int i = p0 + u;
+            if (u < per && i < nq) {
+                const int n = nid[i];
+                if (n_size[n] > G) {
+                    const unsigned b = n_base[n];
+                    const int lt_b = (int)((run & 0xFFFFu) - (b & 0xFFFFu));
+                    const int eq_b = (int)((run >> 16) - (b >> 16));
+                    const int need = n_need[n];
+                    const bool left = (f[u] & 1u) || ((f[u] >> 16) && eq_b < need);
+                    const int lb = lt_b + (eq_b < need ? eq_b : need);
+                    const int dst = left ? n_start[n] + lb : n_start[n] + n_h[n] + (i - n_start[n] - lb);
+                    perm2[dst] = perm[i];
+                } else {
+                    perm2[i] = perm[i];
+                }
+            }
+            run += f[u];
+        }
+        __syncthreads();
+        uint16_t *tp = perm;
+        perm = perm2;
+        perm2 = tp;
+        // the children
+        if (tid == 0) {
+            int m = 0, more = 0;
+            for (int n = 0; n < nn; ++n) {
+                if (n_size[n] > G) {
+                    t_start[m] = n_start[n];
+                    t_size[m++] = n_h[n];
+                    t_start[m] = n_start[n] + n_h[n];
+                    t_size[m++] = n_size[n] - n_h[n];
+                    more |= n_h[n] > G || n_size[n] - n_h[n] > G;
+                } else {
+                    t_start[m] = n_start[n];
+                    t_size[m++] = n_size[n];
+                }
+            }
+            for (int n = 0; n < m; ++n) {
+                n_start[n] = t_start[n];
+                n_size[n] = t_size[n];
+            }
+            s_nn = m;
+            s_split = more;
+        }
+        __syncthreads();
+        const int nn2 = s_nn;
+        for (int i = tid; i < nq; i += KD_NT) {
+            int lo = 0, hi = nn2 - 1;          // last node with start <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (n_start[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            nid[i] = (uint8_t)lo;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nq; i += KD_NT) qord[i] = perm[i];
+}
+
+constexpr size_t kd_smem_bytes() { return (size_t)CRISP_GROUP_MAXQ * (4 + 2 + 2 + 1); }
+
+// The k-d order of the batch's queries (qord), from their rows Qr [nq][Dp].
+// Scratch: V [Dp] float4, mu [Dp], part [PD_CH][Dp] float4, Y [max(nq, PD_NS)] float4.
+crisp_status tc_query_order(const float *Qr, int nq, int Dp, float4 *V, float *mu, float4 *part, float4 *Y,
+                            int *qord, cudaStream_t st) {
+    if (nq <= 0) return CRISP_OK;
+    CRISP_REQUIRE(nq <= CRISP_GROUP_MAXQ && (nq + TG - 1) / TG <= KD_MAXN, "query order: at most %d queries",
+                  CRISP_GROUP_MAXQ);
+    const int ns = nq < PD_NS ? nq : PD_NS;
+    const dim3 gb((unsigned)((Dp + PD_NT - 1) / PD_NT), PD_CH);
+    k_pd_back<<<gb, PD_NT, 0, st>>>(Qr, nq, Dp, ns, nullptr, nullptr, part);
+    CRISP_COUNT_LAUNCH();
+    k_pd_finish<<<1, 1024, 0, st>>>(part, Dp, ns, 0, mu, V);
+    CRISP_COUNT_LAUNCH();
+    for (int it = 0; it < PD_IT; ++it) {
+        k_pd_proj<<<(unsigned)((ns + 7) / 8), 256, 0, st>>>(Qr, nq, Dp, ns, mu, V, Y);
+        CRISP_COUNT_LAUNCH();
+        k_pd_back<<<gb, PD_NT, 0, st>>>(Qr, nq, Dp, ns, mu, Y, part);
+        CRISP_COUNT_LAUNCH();
+        k_pd_finish<<<1, 1024, 0, st>>>(part, Dp, ns, 1, mu, V);
+        CRISP_COUNT_LAUNCH();
+    }
+    k_pd_proj<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(Qr, nq, Dp, nq, mu, V, Y);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK(cudaFuncSetAttribute(k_kd_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem_bytes()));
+    k_kd_order<<<1, KD_NT, kd_smem_bytes(), st>>>(Y, nq, TG, qord);
+    CRISP_COUNT_LAUNCH();
+    CRISP_CK_LAUNCH();
+    return CRISP_OK;
 }
 
 struct TileMeta {
@@ -911,8 +1329,10 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     const char *force_tf32 = getenv("CRISP_RERANK_TF32");
     const bool bf = task.coarse || (ix->Xb != nullptr && !(force_tf32 && atoi(force_tf32) != 0));
     const int Dp64 = (Dp + 63) / 64 * 64;
-    const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
-                 o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
+    const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
+                 o_pdv = take(sizeof(float4) * (size_t)Dp), o_pdmu = take(sizeof(float) * (size_t)Dp),
+                 o_pdpart = take(sizeof(float4) * (size_t)PD_CH * Dp),
+                 o_pdy = take(sizeof(float4) * (size_t)std::max(nq, PD_NS)),
                  o_gq = take(sizeof(int) * nslots), o_gn2 = take(sizeof(float) * nslots),
                  o_gn1 = take(sizeof(float) * nslots), o_qg = take(sizeof(float) * (size_t)nslots * Dp),
                  o_qgb = take(bf ? sizeof(uint16_t) * (size_t)nslots * Dp64 : 0),
@@ -953,7 +1373,10 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         e = cudaGetSymbolAddress((void **)&err_word, g_tr_error);
         if (e == cudaSuccess) e = cudaMemsetAsync(err_word, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "error word", __FILE__, __LINE__); break; }
-        s = crisp_run_group_order(cand, stride, ncand, nq, R, (unsigned long long *)(buf + o_key), qord, pos, st);
+        s = tc_query_order(Qr, nq, Dp, (float4 *)(buf + o_pdv), (float *)(buf + o_pdmu), (float4 *)(buf + o_pdpart),
+                           (float4 *)(buf + o_pdy), qord, st);
+        if (s) break;
+        s = crisp_run_group_pos(cand, stride, ncand, nq, R, pos, st);
         if (s) break;
         k_group_queries<<<(nslots + 7) / 8, 256, 0, st>>>(Qr, nq, Dp, qord, nslots, Qg, Qgb, Dp64, gq, gn2, gn1);
         CRISP_COUNT_LAUNCH();
