@@ -356,8 +356,8 @@ struct CountShared {
     // one batch of activated cells staged for one tile; only the cells with ids
     // in the tile are kept, so their flat starts strictly increase
     int c_pre[CNT_NT + 33];     // flat start of each kept cell; then the total, then INT_MAX
-    int c_gd[CNT_NT + 1];       // id-array position of the cell's flat id 0: m N + first - c_pre
-    int c_w[CNT_NT + 1];        // the cell's weight (entry CNT_NT: read by lanes past the end, unused)
+    int2 c_gw[CNT_NT + 1];      // per kept cell: id-array position of its flat id 0 (m N + first - c_pre)
+                                // and its weight (entry CNT_NT: read by lanes past the end, unused)
     long long scan_ws[CNT_NT / 32 + 1];
     int ecache[CNT_EC > 0 ? CNT_EC : 1];   // (m << 20) | (w << 16) | cell per activated cell, when E <= CNT_EC
 };
@@ -418,8 +418,7 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
         if (len > 0) {
             const int ci = (int)(ex & 0xFFFFFFFF), pre = (int)(ex >> 32);
             S.c_pre[ci] = pre;
-            S.c_gd[ci] = m * (int)ix.N + beg - pre;
-            S.c_w[ci] = w;
+            S.c_gw[ci] = make_int2(m * (int)ix.N + beg - pre, w);
         }
         if (i <= 32) S.c_pre[nne + i] = i == 0 ? total : INT_MAX;
         __syncthreads();
@@ -440,10 +439,13 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
                 for (int u = 0; u < CNT_U; ++u) {
                     const int f0 = fb + 32 * u, f = f0 + lane;
                     const int B = S.c_pre[ecur + 1 + lane] - f0;     // > 0: cell ecur holds f0
-                    const unsigned marks = __reduce_or_sync(0xffffffffu, (unsigned)B < 32u ? 1u << B : 0u);
+                    unsigned bit;                                     // 1 << B, 0 for B outside [0, 31]
+                    asm("shl.b32 %0, 1, %1;" : "=r"(bit) : "r"((unsigned)B));
+                    const unsigned marks = __reduce_or_sync(0xffffffffu, bit);
                     const int e = ecur + __popc(marks & upto);
-                    wv[u] = S.c_w[e];
-                    ids_v[u] = f < f_hi ? __ldg(ix.ids + (S.c_gd[e] + f)) : -1;
+                    const int2 gw = S.c_gw[e];
+                    wv[u] = gw.y;
+                    ids_v[u] = f < f_hi ? __ldg(ix.ids + (gw.x + f)) : -1;
                     ecur = __shfl_sync(0xffffffffu, e, 31);
                 }
 #pragma unroll
