@@ -1161,7 +1161,7 @@ def stage_pass(torch, crisp, ix, info, Q, point, k, steps, stream, flush):
     nb = torch.empty((nq,), dtype=torch.int64, device=dev)
     names = ["rotate", "activate", "count_cut", "rerank" if point["mode"] == 0 else "verify_opt"]
     # batches of >= 256 queries with candidate lists >= 2,048 wide re-rank on the
-    # tensor cores (MinHash-ordered query groups, bounded TF32 scores, exact re-measure
+    # tensor cores (k-d-ordered query groups, bounded TF32 scores, exact re-measure
     # of the candidates that can reach the top-k); smaller ones stream (k_dist_flat)
     grouped = nq >= 256 and stride >= 2048
     kernels = ["k_rotate", "k_activate", "k_count_cut",

@@ -523,7 +523,9 @@ crisp_status crisp_count_cut(const crisp_index *index, const int32_t *act, const
  * (distance, id).  cand/ncand as written by crisp_count_cut (ascending ids).
  * ids: device [nq][k] int64, sqdist: device [nq][k] float32, padded -1/+inf.
  * Batches of 256 to 16,384 queries with cand_stride >= 2,048 are ordered by
- * the MinHash of their candidate sets and scored in groups of 64 queries that
+ * a k-d partition of the query rows along the batch's top principal
+ * directions (queries close in space share most candidates) and scored in
+ * groups of 64 queries that
  * fetch each shared candidate row once: one TF32 pass on the tensor cores
  * gives every (query, candidate) pair an upper and a lower bound of its CR32
  * distance, and only the candidates whose lower bound reaches the k-th

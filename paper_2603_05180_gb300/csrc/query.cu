@@ -6,8 +6,8 @@
 //   k_dist_flat     Q6       exact CR32 distances of (query, candidate) pairs, persistent
 //                            (small batches, and the candidates the tensor-core re-rank of
 //                            rerank_tc.cu keeps for the exact measure)
-//   k_minhash_key, k_sort_queries, k_sched_pos
-//                   Q6 / F2  large batches: MinHash query order, list position of each id range
+//   k_sched_pos     Q6 / F2  large batches: list position of each id range (the k-d query
+//                   order of the groups is in rerank_tc.cu)
 //   k_bound_select  Q6       per query: the candidates whose distance bound can reach the top-k
 //   k_select_rows   Q6       per query: radix select + bitonic top-k of the exact distances
 //   k_gunion        F2       large batches: per (query group, id range) the rows some member needs
@@ -24,6 +24,9 @@
 
 #include "internal.cuh"
 #include "ptx.cuh"
+
+size_t crisp_query_order_scratch(int nq, int Dp);
+crisp_status crisp_run_query_order(const float *Qr, int nq, int Dp, int G, void *scratch, int *qord, cudaStream_t st);
 
 namespace {
 
@@ -1379,8 +1382,10 @@ __global__ void __launch_bounds__(RR_NT, 4) k_score_flat(IxView ix, const float 
 
 // ------------------------------------------- grouped scoring (row reuse)
 // The candidate sets of a large batch overlap: on the 1M-row workload a row is a
-// candidate of about 200 of 10,000 queries.  Queries are ordered by the MinHash
-// of their candidate sets and cut into groups (of GT_G, at most GS_G); the id
+// candidate of about 200 of 10,000 queries.  Queries are ordered by a k-d
+// partition of their coordinates along the batch's top principal directions
+// (crisp_run_query_order: queries close in space share most candidates) and
+// cut into groups (of GT_G, at most GS_G); the id
 // space into ranges of GS_SPAN ids.  k_gunion lists, for each (group, range),
 // the rows some member needs, with the member mask and where each (row, member)
 // distance goes in that member's list.  The coarse scorers (k_gscore)
@@ -1395,66 +1400,6 @@ constexpr int GS_MINSTRIDE = 2048;  // so do short candidate lists (shortlists)
 constexpr int GU_NT = 256;
 // scorer CTA: 24 warps, 80 registers a thread at most, no spills
 constexpr int GK_NT = 768;
-
-// key[q] = h1 << 34 | h2 << 14 | q, where h1 and h2 are the minima over the
-// candidates of two 24-bit multiplicative hashes of the id, clamped to 20 bits:
-// queries sorted by (h1, h2) put those that share their first and second
-// min-hash candidates next to each other.  One block per query.
-__global__ void __launch_bounds__(RR_NT) k_minhash_key(const int *__restrict__ cand, long long stride,
-                                                       const long long *__restrict__ ncand, int nq,
-                                                       unsigned long long *__restrict__ key) {
-    __shared__ unsigned wmin[2][RR_NT / 32];
-    const int q = blockIdx.x;
-    const long long n = ncand[q] < stride ? ncand[q] : stride;
-    const int *c = cand + (long long)q * stride;
-    unsigned m1 = 0xFFFFFFFFu, m2 = 0xFFFFFFFFu;
-    for (long long i = threadIdx.x; i < n; i += RR_NT) {
-        const unsigned h1 = ((unsigned)c[i] * 2654435761u) >> 8, h2 = ((unsigned)c[i] * 2246822519u) >> 8;
-        m1 = h1 < m1 ? h1 : m1;
-        m2 = h2 < m2 ? h2 : m2;
-    }
-    m1 = __reduce_min_sync(0xffffffffu, m1);
-    m2 = __reduce_min_sync(0xffffffffu, m2);
-    if ((threadIdx.x & 31) == 0) {
-        wmin[0][threadIdx.x >> 5] = m1;
-        wmin[1][threadIdx.x >> 5] = m2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned a = wmin[0][0], b = wmin[1][0];
-        for (int w = 1; w < RR_NT / 32; ++w) {
-            a = wmin[0][w] < a ? wmin[0][w] : a;
-            b = wmin[1][w] < b ? wmin[1][w] : b;
-        }
-        a = a > 0xFFFFFu ? 0xFFFFFu : a;
-        b = b > 0xFFFFFu ? 0xFFFFFu : b;
-        key[q] = ((unsigned long long)a << 34) | ((unsigned long long)b << 14) | (unsigned long long)q;
-    }
-}
-
-// One CTA: bitonic sort of the nq (<= SCH_MAXQ) keys; qord = their low 14 bits.
-__global__ void __launch_bounds__(1024) k_sort_queries(const unsigned long long *__restrict__ key, int nq,
-                                                       int *__restrict__ qord) {
-    extern __shared__ unsigned long long sk[];
-    int n2 = 1;
-    while (n2 < nq) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += 1024) sk[i] = i < nq ? key[i] : ~0ull;
-    __syncthreads();
-    for (int size = 2; size <= n2; size <<= 1) {
-        for (int st = size >> 1; st > 0; st >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += 1024) {
-                const int j = i ^ st;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const unsigned long long a = sk[i], b = sk[j];
-                    if ((a > b) == up) { sk[i] = b; sk[j] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < nq; i += 1024) qord[i] = (int)(sk[i] & 0x3FFFull);
-}
 
 // pos[q][r] = first list position with id >= r GS_SPAN (r = 0..R).
 __global__ void k_sched_pos(const int *__restrict__ cand, long long stride, const long long *__restrict__ ncand,
@@ -1919,7 +1864,7 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     if (cap > (1LL << 31) - 1) return CRISP_OK;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += (b + 255) / 256 * 256; return o; };
-    const size_t o_cnt = take(3 * sizeof(unsigned long long)), o_key = take(sizeof(unsigned long long) * nq),
+    const size_t o_cnt = take(3 * sizeof(unsigned long long)), o_ord = take(crisp_query_order_scratch(nq, ix->Dp)),
                  o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
                  o_items = take(sizeof(int2) * (size_t)ngroups * R), o_row = take(sizeof(int) * (size_t)cap),
                  o_mask = take(sizeof(unsigned) * (size_t)cap), o_pb = take(sizeof(int) * (size_t)cap),
@@ -1928,7 +1873,6 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     CRISP_CK(crisp_scratch_alloc((void **)&buf, off, st));
     GUnion u;
     u.counts = (unsigned long long *)(buf + o_cnt);
-    unsigned long long *key = (unsigned long long *)(buf + o_key);
     u.qord = (int *)(buf + o_qord);
     u.pos = (int *)(buf + o_pos);
     u.items = (int2 *)(buf + o_items);
@@ -1944,15 +1888,8 @@ static crisp_status run_grouped(const crisp_index *ix, const float *Qr, int32_t 
     do {
         cudaError_t e = cudaMemsetAsync(u.counts, 0, 3 * sizeof(unsigned long long), st);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__); break; }
-        k_minhash_key<<<nq, RR_NT, 0, st>>>(cand, (long long)stride, (const long long *)ncand, nq, key);
-        CRISP_COUNT_LAUNCH();
-        int n2 = 1;
-        while (n2 < nq) n2 <<= 1;
-        e = cudaFuncSetAttribute(k_sort_queries, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(unsigned long long) * n2));
-        if (e != cudaSuccess) { s = crisp_cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); break; }
-        k_sort_queries<<<1, 1024, sizeof(unsigned long long) * n2, st>>>(key, nq, (int *)u.qord);
-        CRISP_COUNT_LAUNCH();
+        s = crisp_run_query_order(Qr, nq, ix->Dp, G, buf + o_ord, (int *)u.qord, st);
+        if (s) break;
         const long long npos = (long long)nq * (R + 1);
         k_sched_pos<<<(unsigned)((npos + 255) / 256), 256, 0, st>>>(cand, (long long)stride,
                                                                     (const long long *)ncand, nq, R, (int *)u.pos);

@@ -82,6 +82,8 @@ bool crisp_make_map_bf16(CUtensorMap *m, const uint16_t *base, long long rows, i
 bool crisp_make_map_f32(CUtensorMap *m, const float *base, long long rows, int cols, int ld, int box_rows);
 crisp_status crisp_run_group_pos(const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t nq, int32_t R,
                                  int32_t *pos, cudaStream_t st);
+size_t crisp_query_order_scratch(int nq, int Dp);
+crisp_status crisp_run_query_order(const float *Qr, int nq, int Dp, int G, void *scratch, int *qord, cudaStream_t st);
 crisp_status crisp_run_bound_select(int32_t nq, const int32_t *cand, int64_t stride, const int64_t *ncand, int32_t k,
                                     const QParam *qp, int32_t qfield, const int64_t *kq, const float *ub,
                                     const float *lb, const unsigned *err, int32_t *rc, int64_t *nr, cudaStream_t st);
@@ -372,10 +374,10 @@ __global__ void __launch_bounds__(TU_NT, CRISP_TU_MINB) k_union(const int *__res
 // PD_NS evenly spaced queries.  The order only decides which queries share a
 // group (speed); every result is the same for any order.
 #ifndef CRISP_PD_NS
-#define CRISP_PD_NS 2048
+#define CRISP_PD_NS 1024
 #endif
 #ifndef CRISP_PD_IT
-#define CRISP_PD_IT 5
+#define CRISP_PD_IT 4
 #endif
 constexpr int PD_P = 4, PD_NS = CRISP_PD_NS, PD_IT = CRISP_PD_IT, PD_CH = 32, PD_NT = 128;
 constexpr int KD_NT = 1024, KD_MAXN = 256, KD_PER = CRISP_GROUP_MAXQ / KD_NT;
@@ -739,13 +741,92 @@ __global__ void __launch_bounds__(KD_NT, 1) k_kd_order(const float4 *__restrict_
 
 constexpr size_t kd_smem_bytes() { return (size_t)CRISP_GROUP_MAXQ * (4 + 2 + 2 + 1); }
 
-// The k-d order of the batch's queries (qord), from their rows Qr [nq][Dp].
-// Scratch: V [Dp] float4, mu [Dp], part [PD_CH][Dp] float4, Y [max(nq, PD_NS)] float4.
-crisp_status tc_query_order(const float *Qr, int nq, int Dp, float4 *V, float *mu, float4 *part, float4 *Y,
-                            int *qord, cudaStream_t st) {
+// Groups smaller than KD_LEAF: each k-d leaf of KD_LEAF positions (the last one
+// may be shorter) is split further, down to G, the same way (widest coordinate
+// range, group-aligned median, ties by position).  One thread per leaf.
+constexpr int KD_LEAF = 64;
+__global__ void k_kd_leaf(const float4 *__restrict__ Y, int nq, int G, int *__restrict__ qord) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s0 = l * KD_LEAF;
+    if (s0 >= nq) return;
+    const int n = nq - s0 < KD_LEAF ? nq - s0 : KD_LEAF;
+    int idx[KD_LEAF];
+    for (int i = 0; i < n; ++i) idx[i] = qord[s0 + i];
+    int ns_[KD_LEAF], nz_[KD_LEAF], nn = 1;     // nodes of the current level
+    ns_[0] = 0;
+    nz_[0] = n;
+    bool more = n > G;
+    while (more) {
+        int ts[KD_LEAF], tz[KD_LEAF], m = 0;
+        more = false;
+        for (int k = 0; k < nn; ++k) {
+            const int a = ns_[k], z = nz_[k];
+            if (z <= G) {
+                ts[m] = a;
+                tz[m++] = z;
+                continue;
+            }
+            float lo[PD_P], hi[PD_P];
+            for (int j = 0; j < PD_P; ++j) lo[j] = hi[j] = pd_comp(Y[idx[a]], j);
+            for (int i = a + 1; i < a + z; ++i) {
+                const float4 y = Y[idx[i]];
+                for (int j = 0; j < PD_P; ++j) {
+                    lo[j] = fminf(lo[j], pd_comp(y, j));
+                    hi[j] = fmaxf(hi[j], pd_comp(y, j));
+                }
+            }
+            int d = 0;
+            for (int j = 1; j < PD_P; ++j)
+                if (hi[j] - lo[j] > hi[d] - lo[d]) d = j;
+            for (int i = a + 1; i < a + z; ++i) {       // stable insertion sort by coordinate d
+                const int v = idx[i];
+                const unsigned kv = pd_key(pd_comp(Y[v], d));
+                int t = i - 1;
+                while (t >= a && pd_key(pd_comp(Y[idx[t]], d)) > kv) {
+                    idx[t + 1] = idx[t];
+                    --t;
+                }
+                idx[t + 1] = v;
+            }
+            const int h = (z / 2 + G - 1) / G * G;
+            ts[m] = a;
+            tz[m++] = h;
+            ts[m] = a + h;
+            tz[m++] = z - h;
+            more |= h > G || z - h > G;
+        }
+        for (int k = 0; k < m; ++k) {
+            ns_[k] = ts[k];
+            nz_[k] = tz[k];
+        }
+        nn = m;
+    }
+    for (int i = 0; i < n; ++i) qord[s0 + i] = idx[i];
+}
+
+}  // namespace
+
+// The k-d order of a batch's queries for groups of G (qord), from their rows
+// Qr [nq][Dp] (see the k-d partition above).  Scratch: V [Dp] float4,
+// mu [Dp], part [PD_CH][Dp] float4, Y [max(nq, PD_NS)] float4 (the sizes
+// crisp_query_order_scratch gives).
+size_t crisp_query_order_scratch(int nq, int Dp) {
+    auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+    return r(sizeof(float4) * (size_t)Dp) + r(sizeof(float) * (size_t)Dp) + r(sizeof(float4) * (size_t)PD_CH * Dp) +
+           r(sizeof(float4) * (size_t)std::max(nq, PD_NS));
+}
+
+crisp_status crisp_run_query_order(const float *Qr, int nq, int Dp, int G, void *scratch, int *qord, cudaStream_t st) {
     if (nq <= 0) return CRISP_OK;
-    CRISP_REQUIRE(nq <= CRISP_GROUP_MAXQ && (nq + TG - 1) / TG <= KD_MAXN, "query order: at most %d queries",
-                  CRISP_GROUP_MAXQ);
+    const int Gt = G < KD_LEAF ? KD_LEAF : G;          // the tree's leaves
+    CRISP_REQUIRE(G >= 1 && nq <= CRISP_GROUP_MAXQ && (nq + Gt - 1) / Gt <= KD_MAXN,
+                  "query order: at most %d queries", CRISP_GROUP_MAXQ);
+    auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+    uint8_t *sp = (uint8_t *)scratch;
+    float4 *V = (float4 *)sp;
+    float *mu = (float *)(sp + r(sizeof(float4) * (size_t)Dp));
+    float4 *part = (float4 *)((uint8_t *)mu + r(sizeof(float) * (size_t)Dp));
+    float4 *Y = (float4 *)((uint8_t *)part + r(sizeof(float4) * (size_t)PD_CH * Dp));
     const int ns = nq < PD_NS ? nq : PD_NS;
     const dim3 gb((unsigned)((Dp + PD_NT - 1) / PD_NT), PD_CH);
     k_pd_back<<<gb, PD_NT, 0, st>>>(Qr, nq, Dp, ns, nullptr, nullptr, part);
@@ -763,11 +844,18 @@ crisp_status tc_query_order(const float *Qr, int nq, int Dp, float4 *V, float *m
     k_pd_proj<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(Qr, nq, Dp, nq, mu, V, Y);
     CRISP_COUNT_LAUNCH();
     CRISP_CK(cudaFuncSetAttribute(k_kd_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem_bytes()));
-    k_kd_order<<<1, KD_NT, kd_smem_bytes(), st>>>(Y, nq, TG, qord);
+    k_kd_order<<<1, KD_NT, kd_smem_bytes(), st>>>(Y, nq, Gt, qord);
     CRISP_COUNT_LAUNCH();
+    if (G < KD_LEAF) {
+        const int nl = (nq + KD_LEAF - 1) / KD_LEAF;
+        k_kd_leaf<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(Y, nq, G, qord);
+        CRISP_COUNT_LAUNCH();
+    }
     CRISP_CK_LAUNCH();
     return CRISP_OK;
 }
+
+namespace {
 
 struct TileMeta {
     int g;                          // query group of the tile
@@ -1330,9 +1418,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
     const bool bf = task.coarse || (ix->Xb != nullptr && !(force_tf32 && atoi(force_tf32) != 0));
     const int Dp64 = (Dp + 63) / 64 * 64;
     const size_t o_cnt = take(4 * sizeof(unsigned long long)), o_qord = take(sizeof(int) * nq), o_pos = take(sizeof(int) * (size_t)nq * (R + 1)),
-                 o_pdv = take(sizeof(float4) * (size_t)Dp), o_pdmu = take(sizeof(float) * (size_t)Dp),
-                 o_pdpart = take(sizeof(float4) * (size_t)PD_CH * Dp),
-                 o_pdy = take(sizeof(float4) * (size_t)std::max(nq, PD_NS)),
+                 o_ord = take(crisp_query_order_scratch(nq, Dp)),
                  o_gq = take(sizeof(int) * nslots), o_gn2 = take(sizeof(float) * nslots),
                  o_gn1 = take(sizeof(float) * nslots), o_qg = take(sizeof(float) * (size_t)nslots * Dp),
                  o_qgb = take(bf ? sizeof(uint16_t) * (size_t)nslots * Dp64 : 0),
@@ -1373,8 +1459,7 @@ static crisp_status rerank_tc_batch(const crisp_index *ix, const float *Qr, int3
         e = cudaGetSymbolAddress((void **)&err_word, g_tr_error);
         if (e == cudaSuccess) e = cudaMemsetAsync(err_word, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) { s = crisp_cuda_fail(e, "error word", __FILE__, __LINE__); break; }
-        s = tc_query_order(Qr, nq, Dp, (float4 *)(buf + o_pdv), (float *)(buf + o_pdmu), (float4 *)(buf + o_pdpart),
-                           (float4 *)(buf + o_pdy), qord, st);
+        s = crisp_run_query_order(Qr, nq, Dp, TG, buf + o_ord, qord, st);
         if (s) break;
         s = crisp_run_group_pos(cand, stride, ncand, nq, R, pos, st);
         if (s) break;
