@@ -581,6 +581,21 @@ typedef struct {
 crisp_status crisp_rerank_profile_enable(int32_t on);
 crisp_status crisp_rerank_profile_read(crisp_rerank_profile *out);
 
+/* The query order of a large batch's row-sharing groups (an engineering step
+ * of the grouped re-rank and coarse scorers; the paper's engine scores one
+ * query at a time, §4.3.2): qord (device [nq] int32) receives a permutation of
+ * 0..nq-1 such that each run of G consecutive entries (the last one shorter)
+ * is one group.  Queries are ordered by a k-d partition of their coordinates
+ * along the batch's top four principal directions (from subspace iteration
+ * on up to 1,024 evenly spaced rows): every node larger than max(G, 64)
+ * splits at a group-aligned median of its coordinate with the widest range,
+ * ties by position, and for G < 64 each leaf of 64 splits on down to G the
+ * same way.  Qr: device [nq][Dp] float32 (the rotated queries).  The order
+ * decides only which queries share a group, never a search result.
+ * Deterministic.  EINVAL: nq > 16,384, G < 1, Dp < 1, or more than 256 leaves
+ * of max(G, 64). */
+crisp_status crisp_query_order(const float *Qr, int32_t nq, int32_t Dp, int32_t G, int32_t *qord, void *stream);
+
 /* Q7 (§4.3.2 Stages 2-3, phi = 1; Eq. 2): candidates ordered by (Hamming
  * distance of sign codes, id); each is pruned by ADSampling checks at t = 32,
  * 64, ... < D when the running top-k is full (d_t > fl(r_k^2 * f_t), f_t =

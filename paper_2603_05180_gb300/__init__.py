@@ -101,6 +101,7 @@ _SIGS = {
     "crisp_rotation_from_gaussian": [_P, _I32, _P, _P],
     "crisp_rotate_rows": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
     "crisp_rotate_rows_tc": [_P, _I64, _I32, _I32, _P, _P, _I32, _P],
+    "crisp_query_order": [_P, _I32, _I32, _I32, _P, _P],
     "crisp_kmeans": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _P, _P],
     "crisp_assign_cells": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
     "crisp_assign_cells_tc": [_P, _P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _P],
@@ -334,6 +335,10 @@ def crisp_rotate_rows(X, N, D, ldx, R, Y, ldy, stream=None):
 
 def crisp_rotate_rows_tc(X, N, D, ldx, R, Y, ldy, stream=None):
     _call("crisp_rotate_rows_tc", _ptr(X), N, D, ldx, _ptr(R), _ptr(Y), ldy, _stream(stream))
+
+
+def crisp_query_order(Qr, nq, Dp, G, qord, stream=None):
+    _call("crisp_query_order", _ptr(Qr), nq, Dp, G, _ptr(qord), _stream(stream))
 
 
 def crisp_kmeans(T, S, ldt, off, h, K, H, init, iters, Cout, stream=None):

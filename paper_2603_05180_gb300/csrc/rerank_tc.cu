@@ -1289,6 +1289,22 @@ std::vector<ProfRec> g_prof_recs;
 
 }  // namespace
 
+extern "C" crisp_status crisp_query_order(const float *Qr, int32_t nq, int32_t Dp, int32_t G, int32_t *qord,
+                                          void *stream) {
+    CRISP_REQUIRE(nq >= 0 && Dp >= 1 && G >= 1, "crisp_query_order: nq = %d, Dp = %d, G = %d", nq, Dp, G);
+    if (nq == 0) return CRISP_OK;
+    CRISP_REQUIRE(Qr && qord, "crisp_query_order: null pointer");
+    const int Gt = G < KD_LEAF ? KD_LEAF : G;
+    CRISP_REQUIRE(nq <= CRISP_GROUP_MAXQ && (nq + Gt - 1) / Gt <= KD_MAXN,
+                  "crisp_query_order: at most %d queries and %d groups of max(G, 64)", CRISP_GROUP_MAXQ, KD_MAXN);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *buf = nullptr;
+    CRISP_CK(crisp_scratch_alloc(&buf, crisp_query_order_scratch(nq, Dp), st));
+    const crisp_status s = crisp_run_query_order(Qr, nq, Dp, G, buf, qord, st);
+    crisp_scratch_free(buf, st);
+    return s;
+}
+
 extern "C" crisp_status crisp_rerank_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;

@@ -53,6 +53,10 @@ def test_argument_errors_without_gpu(libc):
         crisp.crisp_search_scratch_bytes(crisp.Index(0), 10, crisp.search_params())
     assert e.value.status == crisp.CRISP_EINVAL
     assert libc.crisp_last_error() != b""
+    for nq, G in ((16385, 64), (100, 0)):     # refused before any launch
+        with pytest.raises(crisp.CrispError) as e:
+            crisp.crisp_query_order(None, nq, 8, G, None)
+        assert e.value.status == crisp.CRISP_EINVAL
     libc.crisp_free(None)   # NULL is a no-op
 
 
