@@ -436,32 +436,40 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
                 else hi = mid - 1;
             }
             int ecur = lo;
+            // counters and flags indexed by the global id (tbase is a multiple of 128)
+            uint32_t *cnt_t = cnt - (tbase >> 2);
+            unsigned *flag_t = S.flag - (tbase >> 7);
             for (int fb = f_lo; fb < f_hi; fb += 32 * CNT_U) {
                 int ids_v[CNT_U], wv[CNT_U];
 #pragma unroll
                 for (int u = 0; u < CNT_U; ++u) {
                     const int f0 = fb + 32 * u, f = f0 + lane;
-                    const int B = S.c_pre[ecur + 1 + lane] - f0;     // > 0: cell ecur holds f0
-                    unsigned bit;                                     // 1 << B, 0 for B outside [0, 31]
-                    asm("shl.b32 %0, 1, %1;" : "=r"(bit) : "r"((unsigned)B));
-                    const unsigned marks = __reduce_or_sync(0xffffffffu, bit);
-                    const int e = ecur + __popc(marks & upto);
+                    int e = ecur;
+                    // most 32-id windows lie inside one cell: one broadcast read decides
+                    if (S.c_pre[ecur + 1] < f0 + 32) {
+                        const int B = S.c_pre[ecur + 1 + lane] - f0;     // > 0: cell ecur holds f0
+                        unsigned bit;                                     // 1 << B, 0 for B outside [0, 31]
+                        asm("shl.b32 %0, 1, %1;" : "=r"(bit) : "r"((unsigned)B));
+                        const unsigned marks = __reduce_or_sync(0xffffffffu, bit);
+                        e = ecur + __popc(marks & upto);
+                        ecur = __shfl_sync(0xffffffffu, e, 31);
+                    }
                     const int2 gw = S.c_gw[e];
                     wv[u] = gw.y;
                     ids_v[u] = f < f_hi ? __ldg(ix.ids + (gw.x + f)) : -1;
-                    ecur = __shfl_sync(0xffffffffu, e, 31);
                 }
 #pragma unroll
                 for (int u = 0; u < CNT_U; ++u) {
-                    if (ids_v[u] >= 0) {
-                        const int local = ids_v[u] - tbase, sh = (local & 3) * 8;
+                    const int id = ids_v[u];
+                    if (id >= 0) {
+                        const int sh = (id & 3) * 8;
                         if (FLAG) {
                             // old byte ob crosses: tau - w <= ob < tau
-                            const int ob = (int)((atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << sh) >> sh) & 0xFFu);
+                            const int ob = (int)((atomicAdd(&cnt_t[id >> 2], (uint32_t)wv[u] << sh) >> sh) & 0xFFu);
                             if ((unsigned)(ob + wv[u] - tau) < (unsigned)wv[u])
-                                atomicOr(&S.flag[local >> 7], 1u << ((local >> 2) & 31));
+                                atomicOr(&flag_t[id >> 7], 1u << ((id >> 2) & 31));
                         } else {
-                            atomicAdd(&cnt[local >> 2], (uint32_t)wv[u] << sh);
+                            atomicAdd(&cnt_t[id >> 2], (uint32_t)wv[u] << sh);
                         }
                     }
                 }
