@@ -224,7 +224,9 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
     struct A { void **p; size_t n; } arrs[] = {
         {(void **)&ix->cent, sizeof(float) * (size_t)ix->M * 2 * ix->K * ix->H},   // 0 while H = 0
         {(void **)&ix->offsets, sizeof(int32_t) * (size_t)ix->M * (K2 + 1)},
-        {(void **)&ix->ids, sizeof(int32_t) * (size_t)ix->M * ix->N},
+        // + 4 entries: the count kernel reads the ids as aligned 16-byte quads,
+        // the last of which may reach 3 entries past the end (masked out)
+        {(void **)&ix->ids, sizeof(int32_t) * ((size_t)ix->M * ix->N + 4)},
         {(void **)&ix->tile_off, sizeof(int32_t) * (size_t)ix->M * K2 * (ix->T + 1)},
         {(void **)&ix->Xr, sizeof(float) * (size_t)ix->N * ix->Dp},
         {(void **)&ix->codes, sizeof(uint32_t) * (size_t)ix->N * (ix->Dp / 32)},
@@ -238,6 +240,7 @@ crisp_status crisp_alloc_index(crisp_index *ix) {
         CRISP_CK(cudaMalloc(a.p, a.n));
         ix->bytes += (int64_t)a.n;
     }
+    CRISP_CK(cudaMemset(ix->ids + (size_t)ix->M * ix->N, 0, 4 * sizeof(int32_t)));
     return CRISP_OK;
 }
 

@@ -28,7 +28,7 @@ struct crisp_index {
     float *R32 = nullptr;          // [D][D]
     float *cent = nullptr;         // [M][2][K][H]
     int32_t *offsets = nullptr;    // [M][K*K+1]
-    int32_t *ids = nullptr;        // [M][N]
+    int32_t *ids = nullptr;        // [M][N] (+ 4 zero entries: 16-byte quad reads)
     int32_t *tile_off = nullptr;   // [M][K*K][T+1]
     float *Xr = nullptr;           // [N][Dp]
     uint32_t *codes = nullptr;     // [N][Dp/32]

@@ -339,9 +339,19 @@ constexpr int CNT_NT = 512;
 #ifndef CRISP_CNT_ECACHE
 #define CRISP_CNT_ECACHE 0
 #endif
+// CRISP_CNT_QUAD: lanes take aligned 16-byte quads of the id array (four ids,
+// those outside the cell's segment masked) instead of single ids; CNT_QU
+// quads a lane in flight.
+#ifndef CRISP_CNT_QUAD
+#define CRISP_CNT_QUAD 1
+#endif
+#ifndef CRISP_CNT_QU
+#define CRISP_CNT_QU 2
+#endif
 constexpr int CNT_U = CRISP_CNT_U;
 constexpr int CNT_MINB = CRISP_CNT_MINB;
 constexpr int CNT_EC = CRISP_CNT_ECACHE;
+constexpr int CNT_QU = CRISP_CNT_QU;
 
 // One flag bit per 32-bit counter word (four ids) of a tile.
 constexpr int CNT_FLAG_WORDS = CRISP_TILE / 128;
@@ -414,6 +424,23 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
             len = to[1] - beg;
             w = ent >> 16;
         }
+#if CRISP_CNT_QUAD
+        // flat units are the aligned quads of the id array that overlap a cell's
+        // segment [gs, ge): one scan, quad counts in the high word, kept-cell
+        // flags in the low word; per cell its first quad minus its flat start,
+        // and the weight with the first quad's leading and the last quad's final
+        // valid entry (gs & 3, (ge - 1) & 3)
+        const int gs = m * (int)ix.N + beg, ge = gs + len;
+        const int nqd = len > 0 ? ((ge + 3) >> 2) - (gs >> 2) : 0;
+        long long tot;
+        const long long ex = block_excl_scan<CNT_NT>(((long long)nqd << 32) | (len > 0 ? 1 : 0), S.scan_ws, &tot);
+        const int total = (int)(tot >> 32), nne = (int)(tot & 0xFFFFFFFF);
+        if (len > 0) {
+            const int ci = (int)(ex & 0xFFFFFFFF), pre = (int)(ex >> 32);
+            S.c_pre[ci] = pre;
+            S.c_gw[ci] = make_int2((gs >> 2) - pre, (w & 0xFFFF) | ((gs & 3) << 16) | (((ge - 1) & 3) << 18));
+        }
+#else
         // one scan: id counts in the high word, kept-cell flags in the low word
         long long tot;
         const long long ex = block_excl_scan<CNT_NT>(((long long)len << 32) | (len > 0 ? 1 : 0), S.scan_ws, &tot);
@@ -423,6 +450,7 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
             S.c_pre[ci] = pre;
             S.c_gw[ci] = make_int2(m * (int)ix.N + beg - pre, w);
         }
+#endif
         if (i <= 32) S.c_pre[nne + i] = i == 0 ? total : INT_MAX;
         __syncthreads();
         const int per = (total + CNT_NT / 32 - 1) / (CNT_NT / 32);
@@ -439,6 +467,54 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
             // counters and flags indexed by the global id (tbase is a multiple of 128)
             uint32_t *cnt_t = cnt - (tbase >> 2);
             unsigned *flag_t = S.flag - (tbase >> 7);
+#if CRISP_CNT_QUAD
+            const int4 *ids4 = reinterpret_cast<const int4 *>(ix.ids);
+            for (int fb = f_lo; fb < f_hi; fb += 32 * CNT_QU) {
+                int4 q4[CNT_QU];
+                int wv[CNT_QU];
+                unsigned vm[CNT_QU];
+#pragma unroll
+                for (int u = 0; u < CNT_QU; ++u) {
+                    const int f0 = fb + 32 * u, f = f0 + lane;
+                    int e = ecur;
+                    // most 32-quad windows lie inside one cell: one broadcast read decides
+                    if (S.c_pre[ecur + 1] < f0 + 32) {
+                        const int B = S.c_pre[ecur + 1 + lane] - f0;     // > 0: cell ecur holds f0
+                        unsigned bit;                                     // 1 << B, 0 for B outside [0, 31]
+                        asm("shl.b32 %0, 1, %1;" : "=r"(bit) : "r"((unsigned)B));
+                        const unsigned marks = __reduce_or_sync(0xffffffffu, bit);
+                        e = ecur + __popc(marks & upto);
+                        ecur = __shfl_sync(0xffffffffu, e, 31);
+                    }
+                    const int2 gw = S.c_gw[e];
+                    // entries of the quad inside the cell's segment: from the first
+                    // valid one of its first quad to the last valid one of its last
+                    const int lo_j = f == S.c_pre[e] ? (gw.y >> 16) & 3 : 0;
+                    const int hi_j = f == S.c_pre[e + 1] - 1 ? (gw.y >> 18) & 3 : 3;
+                    vm[u] = f < f_hi ? (0xFu << lo_j) & (0xFu >> (3 - hi_j)) : 0u;
+                    wv[u] = gw.y & 0xFFFF;
+                    q4[u] = vm[u] ? __ldg(ids4 + (gw.x + f)) : make_int4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < CNT_QU; ++u) {
+                    const int idv[4] = {q4[u].x, q4[u].y, q4[u].z, q4[u].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if ((vm[u] >> j) & 1u) {
+                            const int id = idv[j], sh = (id & 3) * 8;
+                            if (FLAG) {
+                                const int ob =
+                                    (int)((atomicAdd(&cnt_t[id >> 2], (uint32_t)wv[u] << sh) >> sh) & 0xFFu);
+                                if ((unsigned)(ob + wv[u] - tau) < (unsigned)wv[u])
+                                    atomicOr(&flag_t[id >> 7], 1u << ((id >> 2) & 31));
+                            } else {
+                                atomicAdd(&cnt_t[id >> 2], (uint32_t)wv[u] << sh);
+                            }
+                        }
+                    }
+                }
+            }
+#else
             for (int fb = f_lo; fb < f_hi; fb += 32 * CNT_U) {
                 int ids_v[CNT_U], wv[CNT_U];
 #pragma unroll
@@ -474,6 +550,7 @@ __device__ void count_tile(const IxView &ix, const int *__restrict__ actq, Count
                     }
                 }
             }
+#endif
         }
         __syncthreads();
     }
